@@ -1,0 +1,114 @@
+/*
+ * TensCol reference oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 restatement of one iteration of the
+ * population-based gradient-descent weight learning for graph coloring
+ * (Goudet, Duval, Hao, "Population-based gradient descent weight learning
+ * for graph coloring problems", Section 3 and Algorithm 1), over adjacency
+ * lists.  Only the test suite, the package smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper
+ * with the CUDA library, and the CUDA library never calls it.
+ *
+ * Conventions (all buffers are caller-owned host memory):
+ *   graph   : n vertices, adjacency lists adj_off[n+1] / adj[adj_off[n]]
+ *             (symmetric, no self loops, neighbour ids in [0, n)).
+ *   W       : D*n*k doubles, index (d*n + i)*k + j  (w_{d,i,j}, Section 3.2)
+ *   colors  : D*n ints, c_d(i) in [0, k)
+ *   Mt      : n*n ints, \tilde m_{i,m} (eq. 4)
+ * Every function returns 0 on success and a negative value on bad input.
+ */
+#ifndef TENSCOL_ORACLE_H
+#define TENSCOL_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int problem;        /* 0 = k-COL (GCP), 1 = ECP                         */
+    double sigma0;      /* std of the N(0, sigma0) initial weights (Table 2) */
+    double eta;         /* learning rate                                      */
+    double alpha;       /* penalisation exponent  (eq. 5)                     */
+    double lambda_;     /* penalisation weight    (eq. 7)                     */
+    double beta;        /* bonus exponent         (eq. 6)                     */
+    double mu;          /* bonus weight           (eq. 7)                     */
+    double nu;          /* equity weight          (eq. 7)                     */
+    double rho;         /* smoothing divisor      (eq. 8)                     */
+    int nb_iter;        /* smoothing period       (Step 4-iv)                 */
+    int bonus_diag;     /* 1: \bar A = J - A keeps its diagonal (Section 3.5.2)*/
+} orc_params;
+
+/* Structural check of the adjacency lists: ids in range, no self loop,
+ * every edge listed in both directions, no duplicates. 0 if valid. */
+int orc_validate_graph(int n, const int *adj_off, const int *adj);
+
+/* Step 1: c_d(i) = lowest j with w_{d,i,j} maximal (Section 3.4). */
+int orc_assign(int D, int n, int k, const double *W, int *colors);
+
+/* Gamma = A . S_d  (footnote to eq. 13): Gamma[(d*n+i)*k+j] = number of
+ * neighbours of i with colour j in individual d. */
+int orc_gamma(int D, int n, int k, const int *adj_off, const int *adj,
+              const int *colors, int *Gamma);
+
+/* Step 2 (eq. 1): gamma_own[d*n+i] = conflicting neighbours of i,
+ * f_color[d] = half their sum = monochromatic edges of individual d. */
+int orc_fitness(int D, int n, int k, const int *adj_off, const int *adj,
+                const int *colors, int *gamma_own, long long *f_color);
+
+/* Equity (eq. 3, eq. 14): sizes[d*k+j] = #V_{d,j}; f_eq[d]; E[d*k+j] in
+ * {-1,0,+1} = d f_eq / d s_{d,i,j}.  c1 = floor(n/k), c2 = ceil(n/k). */
+int orc_equity(int D, int n, int k, const int *colors,
+               int *sizes, long long *f_eq, int *E);
+
+/* Step 3-i (eq. 4): Mt[i*n+m] = #{d : c_d(i) == c_d(m)}; Mt[i*n+i] = D. */
+int orc_mtilde(int D, int n, const int *colors, int *Mt);
+
+/* eq. 5 and eq. 6 over ordered pairs (i, m):
+ * kappa = sum a_im Mt^alpha, varpi = sum (1 - a_im) Mt^beta
+ * (diagonal of \bar A included iff bonus_diag). */
+int orc_penalty_bonus(int n, const int *adj_off, const int *adj, const int *Mt,
+                      double alpha, double beta, int bonus_diag,
+                      double *kappa, double *varpi);
+
+/* eq. 13: grad_S L for the one-hot population at iteration t, D*n*k. */
+int orc_grad_S(int D, int n, int k, const int *adj_off, const int *adj,
+               const int *colors, const int *Mt, const int *E,
+               const orc_params *p, long long t, double *G);
+
+/* Step 4 (eq. 10-12, eq. 8): softmax straight-through gradient
+ * gW = S^ (.) (G - (S^ (.) G) J), W <- W - eta gW, then W <- W / rho when
+ * (t + 1) is a multiple of nb_iter.  gW may be NULL. */
+int orc_update(int D, int n, int k, const orc_params *p, long long t,
+               const double *G, double *W, double *gW);
+
+/* One full iteration at counter t on W (in/out).  Every output may be NULL.
+ * loss = f_color(S) + nu t f_eq(S) + lambda t kappa - mu t varpi  (eq. 7).
+ * f[d] = f_color + (problem == ECP ? f_eq : 0); *f_min, *d_star = lowest
+ * d attaining it.  If stop_on_legal and f_min == 0 the weights are left
+ * untouched and *updated = 0 (Algorithm 1 stop rule), else *updated = 1. */
+int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
+             const orc_params *p, long long t, int stop_on_legal,
+             double *W,
+             int *colors, int *gamma_own, long long *f_color, long long *f_eq,
+             int *Mt, double *G, double *gW,
+             double *loss, double *kappa, double *varpi,
+             long long *f_min, int *d_star, int *updated);
+
+/* Algorithm 1 loop: up to max_iter iterations from counter *t (in/out).
+ * Keeps the best-so-far individual (strictly improving f_min, lowest d on
+ * ties) in best_colors[n]; stops early on a legal population when
+ * stop_on_legal.  Returns iterations performed (updates) or < 0. */
+long long orc_run(int D, int n, int k, const int *adj_off, const int *adj,
+                  const orc_params *p, long long *t, long long max_iter,
+                  int stop_on_legal, double *W,
+                  int *best_colors, long long *best_f, long long *best_t);
+
+/* Checker: recount conflicts edge by edge from an edge list (u[e], v[e]),
+ * and the equity deviation of a single colouring. */
+long long orc_check_conflicts(long long n_edges, const int *u, const int *v,
+                              const int *coloring);
+long long orc_check_equity(int n, int k, const int *coloring);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
