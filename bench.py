@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput of the TensCol population step on GB300.
+
+Metric: individual-steps/s = (individuals advanced by one iteration of
+Algorithm 1) per second, on the synthetic stand-in for the paper's random
+DIMACS graphs: G(n=1000, p=0.5) (seed 2), k = 90 colours, D = 200
+individuals, Table 2 GCP parameters with rho = 100, stop-on-legal off.
+
+One "step" = one full iteration over the population (pair compare, colour
+classes / population reduction, fused gradient + update + argmax).  The
+weights stay resident in HBM; between timed steps a 256 MB buffer is written
+to flush the 129 MB L2 (the step's own working set, 77 MB, would otherwise
+stay cached).  Each step is bracketed by CUDA events on the stream the
+library launches on; the sum over K steps is the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): N independent replicas (one population per GPU, own
+seed), weak scaling; the only collective is the timing max-reduce.
+--impl reference times the CPU oracle (single thread) on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "gnp1000_k90_D200"
+METRIC = "individual-steps/s, G(1000,0.5) k=90 D=200, tensor-core vs plain FP32 GPU"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-baseline-iters", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1909_02261_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    rp, ci = inputs.gnp(w["n"], w["p"], w["graph_seed"])
+    return w, rp, ci
+
+
+def algorithmic_update_bytes(n, k, D):
+    """Bytes the fused update kernel must move per launch: W read + write
+    (2 n k 4 per individual), the colour-class permutation (2 n) and offsets
+    (4 (k+1)), the equity signs (k), the new colours in both layouts (2 x 2 n),
+    plus the n x n pair-coefficient matrix read once (4 n^2)."""
+    per_ind = 2 * n * k * 4 + 2 * n + 4 * (k + 1) + k + 4 * n
+    return D * per_ind + 4 * n * n
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull if False else f"/tmp/tc_clocks_{os.getpid()}.csv", "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def traffic_record(kernel, src_files):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[f"{kernel}@{WORKLOAD}"]
+    except (OSError, ValueError, KeyError):
+        return None
+    h = hashlib.sha256()
+    for f in src_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == h.hexdigest() else None
+
+
+def cpu_oracle_rate(rp, ci, w, iters):
+    """The oracle as it stands: `iters` full iterations, single thread."""
+    from oracle import oracle as O
+    from paper_1909_02261_gb300 import inputs
+    W = inputs.init_weights(w["D"], w["n"], w["k"], 0.01, seed=w["w_seed"])
+    po = O.make_params(rho=100.0)
+    O.run(rp, ci, W[:1, :50], po, 0, 1, stop_on_legal=False)  # load/compile outside timing
+    t0 = time.perf_counter()
+    r = O.run(rp, ci, W, po, 0, iters, stop_on_legal=False)
+    dt = time.perf_counter() - t0
+    assert r["iters"] == iters
+    return w["D"] * iters / dt, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, single-threaded, on the same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, rp, ci = workload()
+    from oracle import oracle as O
+    from paper_1909_02261_gb300 import inputs
+    # each step is one oracle iteration over a sub-population sized so the
+    # whole warmup + K run stays within ~3 minutes (~3 s per full iteration)
+    total = max(1, args.steps + args.warmup)
+    Ds = max(2, min(w["D"], int(w["D"] * 60 / total)))
+    W = inputs.init_weights(Ds, w["n"], w["k"], 0.01, seed=w["w_seed"])
+    po = O.make_params(rho=100.0)
+    t = 0
+    for _ in range(args.warmup):
+        r = O.run(rp, ci, W, po, t, 1, stop_on_legal=False)
+        W, t = r["W"], r["t"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = O.run(rp, ci, W, po, t, 1, stop_on_legal=False)
+        W, t = r["W"], r["t"]
+    dt = time.perf_counter() - t0
+    value = Ds * args.steps / dt
+    sample = f"{args.steps} oracle iterations over a {Ds}-individual sub-population of {WORKLOAD}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "individual-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "G(1000,0.5) seed 2", "k": w["k"], "D": Ds,
+                   "params": "Table 2 GCP, rho=100"},
+        "cpu_baseline": {"value": value, "unit": "individual-steps/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "individual-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1909_02261_gb300 import tenscol as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w, rp, ci = workload()
+    n, k, D = w["n"], w["k"], w["D"]
+    ctx = T.TensCol(local)
+    ctx.tc_init_graph(n, rp, ci)
+    p = T.params(T.TC_KCOL, stop_on_legal=0)
+    ctx.tc_init_population(w["w_seed"] + 1000 * rank, D, k, p)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.tc_set_stream(stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.tc_step_async(1)
+            flush.zero_()
+        stream.synchronize()
+        ctx.tc_set_timing(True)
+        launches0 = ctx.tc_launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)  # first samples before load
+        barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for a, b in evs:
+            a.record(stream)
+            ctx.tc_step_async(1)
+            b.record(stream)
+            flush.zero_()
+        stream.synchronize()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        barrier()
+        clocks = sampler.stop()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        launches = ctx.tc_launch_count() - launches0
+        kms, kcnt = ctx.tc_kernel_times()
+        ctx.tc_set_timing(False)
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    W_, t_now = ctx.tc_get_state()
+    assert t_now == args.warmup + args.steps, (t_now, args.warmup, args.steps)
+    value = world * D * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: per step the weights go
+    # host -> device, one iteration runs, the weights and the best colouring
+    # come back (pinned host memory)
+    Wh = torch.empty((D, n, k), dtype=torch.float32, pin_memory=True).numpy()
+    ctx.tc_get_state(Wh)
+    e2e_times = []
+    for s in range(args.e2e_steps + 2):
+        t0 = time.perf_counter()
+        ctx.tc_set_state(Wh)
+        ctx.tc_step(1)
+        ctx.tc_get_state(Wh)
+        best = ctx.tc_best()
+        if s >= 2:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_total = float(sum(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * D * len(e2e_times) / e2e_total
+    h2d = Wh.nbytes
+    d2h = Wh.nbytes + 4 * n + 64
+
+    # roofline of the dominant kernel
+    kid = int(np.argmax(kms))
+    name = T.KERNEL_NAMES.get(kid, f"kid{kid}")
+    avg_ms = kms[kid] / max(1, kcnt[kid])
+    peaks = measured_peaks()
+    if kid == T.TC_KID_UPDATE:
+        alg = algorithmic_update_bytes(n, k, D)
+        achieved = alg / (avg_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": traffic_record("k_update",
+                                          ["paper_1909_02261_gb300/csrc/tc_onehot.cu"]),
+                "kernel": name, "algorithmic_bytes_per_launch": alg,
+                "avg_launch_ms": avg_ms,
+                "peak_source": "measured" if peaks else "fallback"}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                "traffic": None, "kernel": name, "avg_launch_ms": avg_ms}
+    kernels = {T.KERNEL_NAMES.get(q, f"kid{q}"): {"launches": int(kcnt[q]),
+                                                   "avg_us": 1e3 * kms[q] / max(1, kcnt[q])}
+               for q in range(len(kms)) if kcnt[q] > 0}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "individual-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "G(1000,0.5) seed 2", "n": n, "k": k, "D": D,
+                   "params": "Table 2 GCP, rho=100, stop_on_legal=0", "form": "onehot",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "individual-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": len(e2e_times)},
+        "wall_s_timed_region": wall,
+        "best_conflicts_seen": best["conflicts"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(rp, ci, w, args.cpu_baseline_iters)
+        line["cpu_baseline"] = {"value": rate, "unit": "individual-steps/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_baseline_iters} full oracle iterations of "
+                                          f"{WORKLOAD} ({dt:.1f} s, single thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

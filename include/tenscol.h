@@ -1,0 +1,196 @@
+/*
+ * tenscol.h -- C ABI of the GB300 (sm_103a) TensCol population step.
+ *
+ * TensCol (Goudet, Duval, Hao, "Population-based gradient descent weight
+ * learning for graph coloring problems") keeps D candidate k-colourings of a
+ * graph G = (V, E), |V| = n, as a real weight tensor W (D x n x k,
+ * Section 3.2) and advances all of them at once with one iteration of
+ * Algorithm 1 (Section 3.3):
+ *   Step 1  S = one_hot(argmax W)                           (Section 3.4)
+ *   Step 2  conflicts / fitness f(S_d), equity f_eq (ECP)    (eq. 1-3)
+ *   Step 3  group concentration M~ = sum_d S_d S_d^T, penalty kappa and
+ *           bonus varpi, loss L, gradient grad_S L           (eq. 4-7, 13-14)
+ *   Step 4  softmax straight-through gradient, W <- W - eta grad_W L,
+ *           smoothing W <- W / rho every nb_iter iterations  (eq. 8, 10-12)
+ * until some individual is legal (f = 0) or the iteration budget ends.
+ *
+ * Conventions for every entry point:
+ *   - Return TC_OK (0) or a negative TC_ERR_* code; tc_strerror() names it.
+ *     No call throws across the ABI.  A failed call leaves the context in
+ *     the state it had before the call, unless stated otherwise.
+ *   - Pointer arguments are HOST memory unless the name ends in _dev.  All
+ *     host buffers are caller-owned; the library copies in or out during
+ *     the call and keeps no caller pointer.
+ *   - A context is bound to one CUDA device and is not thread-safe: callers
+ *     serialise calls on one context.  Contexts are independent.
+ *   - Integer tensors are row-major: W index (d * n + i) * k + j,
+ *     colours index d * n + i, M~ index i * n + m.
+ */
+#ifndef TENSCOL_H
+#define TENSCOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define TC_OK 0
+#define TC_ERR_ARG (-1)            /* invalid argument or size              */
+#define TC_ERR_GRAPH_ASYM (-2)     /* adjacency not symmetric / duplicated   */
+#define TC_ERR_GRAPH_SELFLOOP (-3) /* a vertex adjacent to itself            */
+#define TC_ERR_OOM (-4)            /* device or host allocation failed       */
+#define TC_ERR_CUDA (-5)           /* a CUDA runtime call failed             */
+#define TC_ERR_TIMEOUT (-6)        /* a bounded device wait expired          */
+#define TC_ERR_DEVICE_BOUNDS (-7)  /* a device-side index check failed       */
+#define TC_ERR_STATE (-8)          /* call out of order (no graph / no population) */
+#define TC_ERR_UNSUPPORTED (-9)    /* size or form outside the built limits  */
+#define TC_ERR_INJECTED (-10)      /* host-side fault injection (TC_FAULT)   */
+
+/* ---- problems and step forms -------------------------------------------- */
+#define TC_KCOL 0 /* k-colouring, GCP by k-descent (Section 3.5: f = f_color) */
+#define TC_ECP 1  /* equitable colouring (eq. 3: f = f_color + f_eq)          */
+
+/* How steps 2-3 and the products of eq. 13 are computed.  All forms give
+ * identical colours, conflicts and fitness and the same W step to FP32
+ * rounding. */
+#define TC_FORM_ONEHOT 0     /* gather/compare form: O(D n^2) CUDA-core work  */
+#define TC_FORM_DENSE_FP8 1  /* A.S and S S^T as FP8 tcgen05 tensor-core GEMMs */
+#define TC_FORM_DENSE_FP32 2 /* A.S and S S^T as FP32 CUDA-core GEMMs         */
+
+/* Limits of this build. */
+#define TC_MAX_N 32768
+#define TC_MAX_K 1024
+#define TC_MAX_D 65535
+
+/* Parameters of Table 2 of the paper plus the run policy. */
+typedef struct {
+    int problem;     /* TC_KCOL or TC_ECP                                    */
+    float sigma0;    /* std of the N(0, sigma0) initial weights (Section 3.2)*/
+    float eta;       /* learning rate (Section 3.6)                          */
+    float alpha;     /* penalisation exponent, > 1 (eq. 5)                   */
+    float lambda_;   /* penalisation weight (eq. 7)                          */
+    float beta;      /* bonus exponent, > 1 (eq. 6)                          */
+    float mu;        /* bonus weight (eq. 7)                                 */
+    float nu;        /* equity weight (eq. 7), 0 for the GCP                 */
+    float rho;       /* smoothing divisor >= 1 (eq. 8); 1 disables smoothing */
+    int nb_iter;     /* smoothing period in iterations (Step 4-iv)           */
+    int stop_on_legal; /* 1: stop once min_d f(S_d) == 0 (Algorithm 1)       */
+    int bonus_diag;  /* 1: bar A = J - A keeps its diagonal (Section 3.5.2)  */
+    int form;        /* TC_FORM_*                                            */
+} tc_params;
+
+typedef struct tc_ctx tc_ctx; /* opaque: one graph + one population */
+
+/* Fills *p with Table 2's column for `problem` (GCP: mu = 1e-6, nu = 0;
+ * ECP: mu = 0, nu = 1e-5), rho = 100, stop_on_legal = 1, bonus_diag = 1,
+ * form = TC_FORM_ONEHOT.  Returns TC_ERR_ARG for a NULL p or bad problem. */
+int tc_params_default(tc_params *p, int problem);
+
+/* Creates a context on CUDA device `device` with its own stream.
+ * *out receives the context; on error *out is set to NULL. */
+int tc_create(tc_ctx **out, int device);
+
+/* Frees every device and host resource of the context (NULL is accepted). */
+int tc_destroy(tc_ctx *ctx);
+
+/* Runs later work on `stream` (a cudaStream_t of the context's device,
+ * borrowed, never destroyed by the library); NULL restores the context's own
+ * stream.  Captured CUDA graphs are dropped. */
+int tc_set_stream(tc_ctx *ctx, void *stream);
+
+/* Step "Input" of Algorithm 1: the graph.  Either CSR (rowptr[n+1],
+ * colidx[rowptr[n]], each undirected edge listed from both ends, rows in any
+ * order) or, when rowptr == NULL, a dense n*n row-major 0/1 matrix `dense`
+ * (A of Section 3.5).  The graph is validated (symmetry, no self loop, ids
+ * in range) and copied to the device.  Replaces any previous graph and
+ * drops the population. */
+int tc_init_graph(tc_ctx *ctx, int n, const int32_t *rowptr, const int32_t *colidx,
+                  const uint8_t *dense);
+
+/* Allocates a population of D individuals over k colours and draws
+ * W ~ N(0, sigma0) on the device (Philox4x32-10 counter (d, i, j) keyed by
+ * `seed`, Box-Muller), sets t = 0 and the best-so-far to "none".  *p is
+ * copied; NULL means tc_params_default(TC_KCOL).  Parameters are checked
+ * before anything changes; after that, any previous population is dropped
+ * first, so a failed allocation leaves the context without a population. */
+int tc_init_population(tc_ctx *ctx, uint64_t seed, int D, int k, const tc_params *p);
+
+/* Replaces the parameters of the live population (same D, k). */
+int tc_set_params(tc_ctx *ctx, const tc_params *p);
+
+/* Runs up to n_iters iterations of Algorithm 1 (Steps 1-4 each).  Stops
+ * early, without updating W, at the first iteration whose population holds a
+ * legal individual when stop_on_legal is set.  *iters_done (may be NULL)
+ * receives the number of weight updates performed.  The best-so-far
+ * individual is tracked on the device at every evaluated iteration. */
+int tc_step(tc_ctx *ctx, int64_t n_iters, int64_t *iters_done);
+
+/* Best-so-far individual over all evaluated iterations (lowest d among
+ * ties, first iteration reaching the value): coloring[n] (caller-owned),
+ * its f_color and f_eq, the individual index and the iteration t at which it
+ * was seen.  Any output pointer may be NULL.  TC_ERR_STATE if no iteration
+ * has been evaluated yet. */
+int tc_best(tc_ctx *ctx, int32_t *coloring, int64_t *conflicts, int64_t *equity,
+            int32_t *individual, int64_t *iteration);
+
+/* Copies W (D*n*k floats) and the iteration counter t out / in.  Setting
+ * the state also recomputes the assignment S (Step 1) and clears the stop
+ * flag; the best-so-far is kept.  Either pointer may be NULL to skip it. */
+int tc_get_state(tc_ctx *ctx, float *W, int64_t *t);
+int tc_set_state(tc_ctx *ctx, const float *W, const int64_t *t);
+
+/* Device-resident variants: W_dev is a device pointer on the context's
+ * device (D*n*k floats), copied on the context's stream. */
+int tc_get_state_dev(tc_ctx *ctx, float *W_dev);
+int tc_set_state_dev(tc_ctx *ctx, const float *W_dev);
+
+/* Steps 1-3 for the current W at the current t, without updating W, the
+ * counter or the best-so-far.  Outputs (each may be NULL):
+ *   colors[D*n]    c_d(i) = argmax_j w_{d,i,j}, lowest j on ties (Section 3.4)
+ *   gamma_own[D*n] conflicting neighbours of i in individual d (eq. 1)
+ *   f_color[D]     monochromatic edges of individual d (eq. 1)
+ *   f_eq[D]        equity fitness (eq. 3)
+ *   Mtilde[n*n]    group concentration matrix (eq. 4)
+ *   G[D*n*k]       grad_S L at iteration t (eq. 13)
+ *   loss[4]        L (eq. 7), kappa (eq. 5), varpi (eq. 6), sum_d f_color */
+int tc_evaluate(tc_ctx *ctx, int32_t *colors, int32_t *gamma_own, int32_t *f_color,
+                int32_t *f_eq, int32_t *Mtilde, float *G, float *loss);
+
+/* Enqueues n_iters iterations on the context's stream and returns without
+ * waiting (no host synchronisation, no stop polling).  Once the device stop
+ * flag is raised the remaining enqueued iterations do nothing.  Read the
+ * outcome later with tc_get_state / tc_best (which synchronise). */
+int tc_step_async(tc_ctx *ctx, int64_t n_iters);
+
+/* Kernel identifiers for tc_kernel_times. */
+#define TC_KID_PAIRS 0   /* pair compare: M~, fitness, pair coefficients    */
+#define TC_KID_CLASSES 1 /* colour classes, equity, population reduction    */
+#define TC_KID_UPDATE 2  /* fused gradient gather + softmax-ST update        */
+#define TC_NUM_KID 8
+
+/* Per-kernel device timing with CUDA events recorded around every launch
+ * of tc_step / tc_step_async (on=1) or off (on=0; the default).  Graph
+ * replay is not timed per kernel.  tc_kernel_times synchronises the stream,
+ * adds the elapsed times of all completed launches to ms[TC_NUM_KID] and
+ * count[TC_NUM_KID] (totals since timing was switched on) and returns them. */
+int tc_set_timing(tc_ctx *ctx, int on);
+int tc_kernel_times(tc_ctx *ctx, double *ms, int64_t *count);
+
+/* Number of device kernel launches issued by this context since creation
+ * (for launch accounting in benchmarks). */
+int tc_launch_count(tc_ctx *ctx, int64_t *count);
+
+/* Enables (chunk > 0) or disables (chunk = 0) CUDA-graph replay of tc_step:
+ * `chunk` iterations are captured once into one graph and replayed. */
+int tc_set_graph_chunk(tc_ctx *ctx, int chunk);
+
+/* Name of a status code (static storage). */
+const char *tc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENSCOL_H */

@@ -1,0 +1,72 @@
+// Internal declarations shared by the CUDA translation units of libtenscol.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tenscol.h"
+
+// Device-resident iteration state.  Every field is written only by device
+// code during an iteration; the host reads it after synchronising.
+struct tc_dev_state {
+    long long t;          // iteration counter of Algorithm 1
+    long long evaluated;  // iterations whose Steps 1-2 ran (best-so-far checks)
+    long long best_t;     // iteration at which the best-so-far was seen
+    long long fcolor_sum; // sum_d f_color of the last evaluated iteration
+    int stop;             // 1 once a legal individual is seen (stop_on_legal)
+    int err;              // device error word (TC_ERR_* or 0)
+    int best_f;           // best-so-far f (-1: none yet)
+    int best_fcolor;
+    int best_feq;
+    int best_d;
+    int last_fmin;
+    int last_dstar;
+    unsigned int done_classes;  // completion tickets (last-block patterns)
+    unsigned int done_update;
+    float loss, kappa, varpi;
+    int pad;
+};
+
+// Everything a kernel of the step needs, passed by value.
+struct tc_kparams {
+    int n, D, k;
+    int Dp;           // colours per row of cT (D rounded up to even)
+    int adj_words;    // 32-bit words per adjacency-bitmask row
+    int problem, nb_iter, bonus_diag, stop_on_legal, commit;
+    float eta, rho, lambda_, mu, nu;
+    float* W;                 // D x n x k
+    uint16_t* c;              // D x n colours
+    uint16_t* cT;             // n x Dp colours (vertex-major), pads = 0xFFFF
+    const uint32_t* adj;      // n x adj_words adjacency bitmask
+    const int* rowptr;        // CSR
+    const int* colidx;
+    float* B;                 // n x n pair coefficients of eq. 13 (symmetric)
+    uint16_t* perm;           // D x n vertices sorted by colour (stable)
+    int* off;                 // D x (k + 1) colour-class offsets into perm
+    int8_t* E;                // D x k equity gradient signs (eq. 14)
+    int* fcolor;              // D conflicts (eq. 1)
+    int* feq;                 // D equity fitness (eq. 3)
+    float* loss_part;         // 2 x n_pair_blocks partial kappa / varpi
+    int n_pair_blocks;
+    const int2* pair_tiles;   // upper-triangular 32x32 tile list
+    const float* lutA;        // [0..D]: 2 alpha v^(alpha-1)
+    const float* lutB;        // [0..D]: 2 beta v^(beta-1)
+    const float* powA;        // [0..D]: v^alpha
+    const float* powB;        // [0..D]: v^beta
+    tc_dev_state* st;
+    uint16_t* best;           // n best-so-far colours
+    int* dbg_Mt;              // optional n x n group concentration output
+    float* dbg_G;             // optional D x n x k grad_S L output
+    int* dbg_gamma;           // optional D x n conflicting-neighbour counts
+};
+
+// Launchers (tc_onehot.cu).  All return cudaGetLastError() of the launch.
+cudaError_t tc_launch_init_weights(float* W, long long count, unsigned long long seed,
+                                   float sigma0, cudaStream_t s);
+cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s);
+cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s);
+cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s);
+cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only);
+cudaError_t tc_launch_debug_gamma(const tc_kparams& P, cudaStream_t s);
+int tc_pair_tile_count(int n);
+int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem);

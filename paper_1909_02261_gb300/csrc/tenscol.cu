@@ -1,0 +1,828 @@
+// Host engine of libtenscol: the C ABI of include/tenscol.h.
+//
+// One context = one graph + one population on one device.  Per iteration of
+// Algorithm 1 the engine issues, on the context's stream,
+//   memset(f_color) -> k_pairs -> k_classes -> k_update
+// (see tc_onehot.cu).  The iteration counter, stop flag and best-so-far live
+// in device memory, so any number of iterations can be queued (or captured
+// in one CUDA graph) without a host round trip; the host polls the stop flag
+// between chunks.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tc_internal.cuh"
+
+struct tc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    long long launches = 0;
+    // graph
+    int n = 0;
+    long long nnz = 0;
+    int* d_rowptr = nullptr;
+    int* d_colidx = nullptr;
+    uint32_t* d_adj = nullptr;
+    int adj_words = 0;
+    int2* d_tiles = nullptr;
+    int n_tiles = 0;
+    // population
+    bool pop = false;
+    int D = 0, k = 0, Dp = 0;
+    tc_params p{};
+    float* d_W = nullptr;
+    uint16_t* d_c = nullptr;
+    uint16_t* d_cT = nullptr;
+    float* d_B = nullptr;
+    uint16_t* d_perm = nullptr;
+    int* d_off = nullptr;
+    int8_t* d_E = nullptr;
+    int* d_fcolor = nullptr;
+    int* d_feq = nullptr;
+    float* d_loss_part = nullptr;
+    float* d_lut = nullptr;  // 4 x (D + 1): lutA, lutB, powA, powB
+    tc_dev_state* d_st = nullptr;
+    uint16_t* d_best = nullptr;
+    // CUDA graph of graph_chunk iterations
+    int graph_chunk = 0;
+    cudaGraphExec_t gexec = nullptr;
+    // per-kernel event timing
+    int timing = 0;
+    bool capturing = false;
+    struct Timed {
+        int kid;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> spare;
+    double kms[TC_NUM_KID] = {0};
+    long long kcount[TC_NUM_KID] = {0};
+};
+
+namespace {
+
+bool fault(const char* where) {
+    const char* f = getenv("TC_FAULT");
+    return f && strcmp(f, where) == 0;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return TC_OK;
+    if (e == cudaErrorMemoryAllocation) return TC_ERR_OOM;
+    return TC_ERR_CUDA;
+}
+
+#define TC_CHECK(expr)                          \
+    do {                                        \
+        cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) {                \
+            (void)cudaGetLastError();           \
+            return cuda_status(_e);             \
+        }                                       \
+    } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (fault("alloc")) return TC_ERR_INJECTED;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return TC_ERR_OOM;
+    }
+    return TC_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+void drop_graph_exec(tc_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
+void free_population(tc_ctx* c) {
+    drop_graph_exec(c);
+    dfree(c->d_W);
+    dfree(c->d_c);
+    dfree(c->d_cT);
+    dfree(c->d_B);
+    dfree(c->d_perm);
+    dfree(c->d_off);
+    dfree(c->d_E);
+    dfree(c->d_fcolor);
+    dfree(c->d_feq);
+    dfree(c->d_loss_part);
+    dfree(c->d_lut);
+    dfree(c->d_st);
+    dfree(c->d_best);
+    c->pop = false;
+    c->D = c->k = c->Dp = 0;
+}
+
+void free_graph(tc_ctx* c) {
+    free_population(c);
+    dfree(c->d_rowptr);
+    dfree(c->d_colidx);
+    dfree(c->d_adj);
+    dfree(c->d_tiles);
+    c->n = 0;
+    c->nnz = 0;
+}
+
+int check_params(const tc_params* p) {
+    if (p->problem != TC_KCOL && p->problem != TC_ECP) return TC_ERR_ARG;
+    if (!(p->eta >= 0.f) || !(p->rho >= 1.f) || p->nb_iter < 1) return TC_ERR_ARG;
+    if (!(p->alpha > 1.f) || !(p->beta > 1.f)) return TC_ERR_ARG;
+    if (!(p->lambda_ >= 0.f) || !(p->mu >= 0.f) || !(p->nu >= 0.f) || !(p->sigma0 >= 0.f))
+        return TC_ERR_ARG;
+    if (p->form != TC_FORM_ONEHOT) return TC_ERR_UNSUPPORTED;
+    return TC_OK;
+}
+
+tc_kparams make_kparams(tc_ctx* c, int commit) {
+    tc_kparams P;
+    memset(&P, 0, sizeof(P));
+    P.n = c->n;
+    P.D = c->D;
+    P.k = c->k;
+    P.Dp = c->Dp;
+    P.adj_words = c->adj_words;
+    P.problem = c->p.problem;
+    P.nb_iter = c->p.nb_iter;
+    P.bonus_diag = c->p.bonus_diag;
+    P.stop_on_legal = c->p.stop_on_legal;
+    P.commit = commit;
+    P.eta = c->p.eta;
+    P.rho = c->p.rho;
+    P.lambda_ = c->p.lambda_;
+    P.mu = c->p.mu;
+    P.nu = c->p.nu;
+    P.W = c->d_W;
+    P.c = c->d_c;
+    P.cT = c->d_cT;
+    P.adj = c->d_adj;
+    P.rowptr = c->d_rowptr;
+    P.colidx = c->d_colidx;
+    P.B = c->d_B;
+    P.perm = c->d_perm;
+    P.off = c->d_off;
+    P.E = c->d_E;
+    P.fcolor = c->d_fcolor;
+    P.feq = c->d_feq;
+    P.loss_part = c->d_loss_part;
+    P.n_pair_blocks = c->n_tiles;
+    P.pair_tiles = c->d_tiles;
+    const int D1 = c->D + 1;
+    P.lutA = c->d_lut;
+    P.lutB = c->d_lut + D1;
+    P.powA = c->d_lut + 2 * D1;
+    P.powB = c->d_lut + 3 * D1;
+    P.st = c->d_st;
+    P.best = c->d_best;
+    return P;
+}
+
+// The LUTs of the pair terms over the integer values v = 0..D of m~ (eq. 5,
+// 6, 13), computed once in double precision on the host.
+int upload_luts(tc_ctx* c) {
+    const int D1 = c->D + 1;
+    std::vector<float> h(4 * (size_t)D1);
+    const double a = c->p.alpha, b = c->p.beta;
+    for (int v = 0; v < D1; ++v) {
+        const double x = (double)v;
+        h[v] = (float)(2.0 * a * pow(x, a - 1.0));
+        h[D1 + v] = (float)(2.0 * b * pow(x, b - 1.0));
+        h[2 * D1 + v] = (float)pow(x, a);
+        h[3 * D1 + v] = (float)pow(x, b);
+    }
+    if (fault("copy")) return TC_ERR_INJECTED;
+    TC_CHECK(cudaMemcpyAsync(c->d_lut, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice,
+                             c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+cudaEvent_t take_event(tc_ctx* c) {
+    if (!c->spare.empty()) {
+        cudaEvent_t e = c->spare.back();
+        c->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Launches one kernel through `fn`, bracketed by timing events when enabled.
+template <typename F>
+cudaError_t timed(tc_ctx* c, int kid, F fn) {
+    const bool on = c->timing && !c->capturing;
+    cudaEvent_t a = on ? take_event(c) : nullptr;
+    cudaEvent_t b = on ? take_event(c) : nullptr;
+    if (a && b) cudaEventRecord(a, c->stream);
+    cudaError_t e = fn();
+    if (a && b) {
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back({kid, a, b});
+    } else {
+        if (a) c->spare.push_back(a);
+        if (b) c->spare.push_back(b);
+    }
+    c->launches += 1;
+    return e;
+}
+
+int collect_timing(tc_ctx* c) {
+    if (c->pending.empty()) return TC_OK;
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    for (auto& t : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            c->kms[t.kid] += ms;
+            c->kcount[t.kid] += 1;
+        } else {
+            (void)cudaGetLastError();
+        }
+        c->spare.push_back(t.a);
+        c->spare.push_back(t.b);
+    }
+    c->pending.clear();
+    return TC_OK;
+}
+
+void free_events(tc_ctx* c) {
+    for (auto& t : c->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->pending.clear();
+    for (auto e : c->spare) cudaEventDestroy(e);
+    c->spare.clear();
+}
+
+int launch_iteration(tc_ctx* c) {
+    if (fault("launch")) return TC_ERR_INJECTED;
+    tc_kparams P = make_kparams(c, 1);
+    TC_CHECK(cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * c->D, c->stream));
+    TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
+    TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
+    TC_CHECK(timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->num_sms, c->stream, 0); }));
+    return TC_OK;
+}
+
+int read_state(tc_ctx* c, tc_dev_state* h) {
+    TC_CHECK(cudaMemcpyAsync(h, c->d_st, sizeof(*h), cudaMemcpyDeviceToHost, c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+int build_graph_exec(tc_ctx* c) {
+    drop_graph_exec(c);
+    cudaGraph_t g = nullptr;
+    TC_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = TC_OK;
+    long long before = c->launches;
+    c->capturing = true;
+    for (int it = 0; it < c->graph_chunk && rc == TC_OK; ++it) rc = launch_iteration(c);
+    c->capturing = false;
+    c->launches = before;  // counted at replay
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc != TC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    TC_CHECK(e);
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    TC_CHECK(e);
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tc_strerror(int code) {
+    switch (code) {
+        case TC_OK: return "ok";
+        case TC_ERR_ARG: return "invalid argument";
+        case TC_ERR_GRAPH_ASYM: return "adjacency is not symmetric or has duplicate/out-of-range entries";
+        case TC_ERR_GRAPH_SELFLOOP: return "adjacency has a self loop";
+        case TC_ERR_OOM: return "out of memory";
+        case TC_ERR_CUDA: return "CUDA runtime error";
+        case TC_ERR_TIMEOUT: return "bounded device wait expired";
+        case TC_ERR_DEVICE_BOUNDS: return "device-side index check failed";
+        case TC_ERR_STATE: return "call out of order (no graph or no population)";
+        case TC_ERR_UNSUPPORTED: return "size or form not supported by this build";
+        case TC_ERR_INJECTED: return "injected fault (TC_FAULT)";
+        default: return "unknown status";
+    }
+}
+
+int tc_params_default(tc_params* p, int problem) {
+    if (!p || (problem != TC_KCOL && problem != TC_ECP)) return TC_ERR_ARG;
+    memset(p, 0, sizeof(*p));
+    p->problem = problem;
+    p->sigma0 = 0.01f;
+    p->eta = 1e-3f;
+    p->alpha = 2.5f;
+    p->lambda_ = 1e-5f;
+    p->beta = 1.2f;
+    p->mu = problem == TC_ECP ? 0.0f : 1e-6f;
+    p->nu = problem == TC_ECP ? 1e-5f : 0.0f;
+    p->rho = 100.0f;
+    p->nb_iter = 5;
+    p->stop_on_legal = 1;
+    p->bonus_diag = 1;
+    p->form = TC_FORM_ONEHOT;
+    return TC_OK;
+}
+
+int tc_create(tc_ctx** out, int device) {
+    if (!out) return TC_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        (void)cudaGetLastError();
+        return TC_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return TC_ERR_ARG;
+    DeviceGuard g(device);
+    tc_ctx* c = new (std::nothrow) tc_ctx();
+    if (!c) return TC_ERR_OOM;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return TC_ERR_CUDA;
+    }
+    c->stream = c->own;
+    *out = c;
+    return TC_OK;
+}
+
+int tc_destroy(tc_ctx* c) {
+    if (!c) return TC_OK;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_graph(c);
+    free_events(c);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+    return TC_OK;
+}
+
+int tc_set_stream(tc_ctx* c, void* stream) {
+    if (!c) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    drop_graph_exec(c);
+    c->stream = stream ? (cudaStream_t)stream : c->own;
+    return TC_OK;
+}
+
+int tc_init_graph(tc_ctx* c, int n, const int32_t* rowptr, const int32_t* colidx,
+                  const uint8_t* dense) {
+    if (!c || n < 1 || n > TC_MAX_N) return TC_ERR_ARG;
+    if (!rowptr && !dense) return TC_ERR_ARG;
+    if (rowptr && !colidx && rowptr[n] > 0) return TC_ERR_ARG;
+    // host-side CSR + bitmask, validated
+    const int aw = (n + 31) / 32;
+    std::vector<uint32_t> bits((size_t)n * aw, 0u);
+    std::vector<int> rp(n + 1, 0), ci;
+    if (rowptr) {
+        if (rowptr[0] != 0) return TC_ERR_ARG;
+        for (int i = 0; i < n; ++i)
+            if (rowptr[i + 1] < rowptr[i]) return TC_ERR_ARG;
+        for (int i = 0; i < n; ++i)
+            for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                const int m = colidx[e];
+                if (m < 0 || m >= n) return TC_ERR_GRAPH_ASYM;
+                if (m == i) return TC_ERR_GRAPH_SELFLOOP;
+                uint32_t& w = bits[(size_t)i * aw + (m >> 5)];
+                if (w & (1u << (m & 31))) return TC_ERR_GRAPH_ASYM;  // duplicate
+                w |= 1u << (m & 31);
+            }
+    } else {
+        for (int i = 0; i < n; ++i)
+            for (int m = 0; m < n; ++m)
+                if (dense[(size_t)i * n + m]) {
+                    if (dense[(size_t)i * n + m] != 1) return TC_ERR_ARG;
+                    if (m == i) return TC_ERR_GRAPH_SELFLOOP;
+                    bits[(size_t)i * aw + (m >> 5)] |= 1u << (m & 31);
+                }
+    }
+    for (int i = 0; i < n; ++i)  // symmetry
+        for (int w = 0; w < aw; ++w) {
+            uint32_t x = bits[(size_t)i * aw + w];
+            while (x) {
+                const int b = __builtin_ctz(x);
+                x &= x - 1;
+                const int m = w * 32 + b;
+                if (!((bits[(size_t)m * aw + (i >> 5)] >> (i & 31)) & 1u)) return TC_ERR_GRAPH_ASYM;
+            }
+        }
+    for (int i = 0; i < n; ++i) {  // canonical CSR: sorted neighbour lists
+        for (int w = 0; w < aw; ++w) {
+            uint32_t x = bits[(size_t)i * aw + w];
+            while (x) {
+                const int b = __builtin_ctz(x);
+                x &= x - 1;
+                ci.push_back(w * 32 + b);
+            }
+        }
+        rp[i + 1] = (int)ci.size();
+    }
+    // tile list of the upper triangle for k_pairs
+    const int T = (n + 31) / 32;
+    std::vector<int2> tiles;
+    tiles.reserve((size_t)T * (T + 1) / 2);
+    for (int I = 0; I < T; ++I)
+        for (int M = I; M < T; ++M) tiles.push_back(make_int2(I, M));
+
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    free_graph(c);
+    int rc;
+    if ((rc = dalloc(&c->d_rowptr, n + 1)) || (rc = dalloc(&c->d_colidx, ci.size())) ||
+        (rc = dalloc(&c->d_adj, bits.size())) || (rc = dalloc(&c->d_tiles, tiles.size()))) {
+        free_graph(c);
+        return rc;
+    }
+    if (fault("copy")) {
+        free_graph(c);
+        return TC_ERR_INJECTED;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_rowptr, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !ci.empty())
+        e = cudaMemcpyAsync(c->d_colidx, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_adj, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_graph(c);
+        return cuda_status(e);
+    }
+    c->n = n;
+    c->nnz = (long long)ci.size();
+    c->adj_words = aw;
+    c->n_tiles = (int)tiles.size();
+    return TC_OK;
+}
+
+int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* p_in) {
+    if (!c) return TC_ERR_ARG;
+    if (c->n < 1) return TC_ERR_STATE;
+    if (D < 1 || D > TC_MAX_D || k < 1 || k > TC_MAX_K) return TC_ERR_ARG;
+    tc_params p;
+    if (p_in) p = *p_in;
+    else tc_params_default(&p, TC_KCOL);
+    int rc = check_params(&p);
+    if (rc) return rc;
+    int w, sm, bts;
+    if (tc_update_config(c->n, k, &w, &sm, &bts) != TC_OK) return TC_ERR_UNSUPPORTED;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    free_population(c);
+    const int n = c->n;
+    const int Dp = (D + 1) & ~1;
+    const size_t Dnk = (size_t)D * n * k;
+    if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) ||
+        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)n * n)) ||
+        (rc = dalloc(&c->d_perm, (size_t)D * n)) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
+        (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_fcolor, D)) ||
+        (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
+        (rc = dalloc(&c->d_lut, 4 * (size_t)(D + 1))) || (rc = dalloc(&c->d_st, 1)) ||
+        (rc = dalloc(&c->d_best, n))) {
+        free_population(c);
+        return rc;
+    }
+    c->D = D;
+    c->k = k;
+    c->Dp = Dp;
+    c->p = p;
+    c->pop = true;
+    tc_dev_state st;
+    memset(&st, 0, sizeof(st));
+    st.best_f = -1;
+    st.best_d = -1;
+    st.best_t = -1;
+    cudaError_t e = cudaMemsetAsync(c->d_cT, 0xFF, sizeof(uint16_t) * (size_t)n * Dp, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * D, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_best, 0, sizeof(uint16_t) * n, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = tc_launch_init_weights(c->d_W, (long long)Dnk, seed, p.sigma0, c->stream);
+    if (e == cudaSuccess) e = tc_launch_assign(make_kparams(c, 0), c->stream);
+    c->launches += 2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_population(c);
+        return cuda_status(e);
+    }
+    rc = upload_luts(c);
+    if (rc) {
+        free_population(c);
+        return rc;
+    }
+    return TC_OK;
+}
+
+int tc_set_params(tc_ctx* c, const tc_params* p) {
+    if (!c || !p) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    int rc = check_params(p);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    tc_params old = c->p;
+    c->p = *p;
+    rc = upload_luts(c);
+    if (rc) {
+        c->p = old;
+        upload_luts(c);
+        return rc;
+    }
+    drop_graph_exec(c);
+    return TC_OK;
+}
+
+int tc_step(tc_ctx* c, int64_t n_iters, int64_t* iters_done) {
+    if (iters_done) *iters_done = 0;
+    if (!c || n_iters < 0) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    tc_dev_state h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    const long long t0 = h.t;
+    TC_CHECK(cudaMemsetAsync(&c->d_st->stop, 0, sizeof(int), c->stream));
+    long long left = n_iters;
+    // poll the device stop flag between chunks only when it can be raised
+    const long long poll = c->p.stop_on_legal ? 64 : (long long)1 << 62;
+    long long since_poll = 0;
+    while (left > 0) {
+        if (c->graph_chunk > 0 && left >= c->graph_chunk) {
+            if (!c->gexec) {
+                rc = build_graph_exec(c);
+                if (rc) return rc;
+            }
+            TC_CHECK(cudaGraphLaunch(c->gexec, c->stream));
+            c->launches += 3ll * c->graph_chunk;
+            left -= c->graph_chunk;
+            since_poll += c->graph_chunk;
+        } else {
+            rc = launch_iteration(c);
+            if (rc) return rc;
+            left -= 1;
+            since_poll += 1;
+        }
+        if (since_poll >= poll && left > 0) {
+            since_poll = 0;
+            rc = read_state(c, &h);
+            if (rc) return rc;
+            if (h.stop) break;
+        }
+    }
+    rc = read_state(c, &h);
+    if (rc) return rc;
+    if (h.err) return h.err;
+    if (iters_done) *iters_done = h.t - t0;
+    return TC_OK;
+}
+
+int tc_best(tc_ctx* c, int32_t* coloring, int64_t* conflicts, int64_t* equity, int32_t* individual,
+            int64_t* iteration) {
+    if (!c) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    tc_dev_state h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    if (h.best_f < 0) return TC_ERR_STATE;
+    if (coloring) {
+        std::vector<uint16_t> b(c->n);
+        TC_CHECK(cudaMemcpyAsync(b.data(), c->d_best, sizeof(uint16_t) * c->n, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        TC_CHECK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < c->n; ++i) coloring[i] = b[i];
+    }
+    if (conflicts) *conflicts = h.best_fcolor;
+    if (equity) *equity = h.best_feq;
+    if (individual) *individual = h.best_d;
+    if (iteration) *iteration = h.best_t;
+    return TC_OK;
+}
+
+int tc_get_state(tc_ctx* c, float* W, int64_t* t) {
+    if (!c) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    if (W) {
+        if (fault("copy")) return TC_ERR_INJECTED;
+        TC_CHECK(cudaMemcpyAsync(W, c->d_W, sizeof(float) * (size_t)c->D * c->n * c->k,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (t) {
+        long long tv = 0;
+        TC_CHECK(cudaMemcpyAsync(&tv, &c->d_st->t, sizeof(tv), cudaMemcpyDeviceToHost, c->stream));
+        TC_CHECK(cudaStreamSynchronize(c->stream));
+        *t = tv;
+    }
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+static int set_state_common(tc_ctx* c, const float* W, const int64_t* t, cudaMemcpyKind kind) {
+    if (!c) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    if (t && *t < 0) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (W) {
+        if (fault("copy")) return TC_ERR_INJECTED;
+        TC_CHECK(cudaMemcpyAsync(c->d_W, W, sizeof(float) * (size_t)c->D * c->n * c->k, kind, c->stream));
+    }
+    if (t) {
+        const long long tv = *t;
+        TC_CHECK(cudaMemcpyAsync(&c->d_st->t, &tv, sizeof(tv), cudaMemcpyHostToDevice, c->stream));
+    }
+    TC_CHECK(cudaMemsetAsync(&c->d_st->stop, 0, sizeof(int), c->stream));
+    TC_CHECK(tc_launch_assign(make_kparams(c, 0), c->stream));
+    c->launches += 1;
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+int tc_set_state(tc_ctx* c, const float* W, const int64_t* t) {
+    return set_state_common(c, W, t, cudaMemcpyHostToDevice);
+}
+
+int tc_get_state_dev(tc_ctx* c, float* W_dev) {
+    if (!c || !W_dev) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaMemcpyAsync(W_dev, c->d_W, sizeof(float) * (size_t)c->D * c->n * c->k,
+                             cudaMemcpyDeviceToDevice, c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+int tc_set_state_dev(tc_ctx* c, const float* W_dev) {
+    if (!W_dev) return TC_ERR_ARG;
+    return set_state_common(c, W_dev, nullptr, cudaMemcpyDeviceToDevice);
+}
+
+int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color, int32_t* f_eq,
+                int32_t* Mtilde, float* G, float* loss) {
+    if (!c) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    const int n = c->n, D = c->D, k = c->k;
+    int* d_mt = nullptr;
+    float* d_G = nullptr;
+    int* d_gam = nullptr;
+    int rc = TC_OK;
+    if (Mtilde && (rc = dalloc(&d_mt, (size_t)n * n))) return rc;
+    if (G && (rc = dalloc(&d_G, (size_t)D * n * k))) {
+        dfree(d_mt);
+        return rc;
+    }
+    if (gamma_own && (rc = dalloc(&d_gam, (size_t)D * n))) {
+        dfree(d_mt);
+        dfree(d_G);
+        return rc;
+    }
+    tc_kparams P = make_kparams(c, 0);
+    P.dbg_Mt = d_mt;
+    P.dbg_G = d_G;
+    P.dbg_gamma = d_gam;
+    cudaError_t e = cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * D, c->stream);
+    if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
+    if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
+    if (e == cudaSuccess && G) e = tc_launch_update(P, c->num_sms, c->stream, 1);
+    if (e == cudaSuccess && gamma_own) e = tc_launch_debug_gamma(P, c->stream);
+    c->launches += 2 + (G ? 1 : 0) + (gamma_own ? 1 : 0);
+    std::vector<uint16_t> hc;
+    tc_dev_state h;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && colors) {
+        hc.resize((size_t)D * n);
+        e = cudaMemcpy(hc.data(), c->d_c, hc.size() * 2, cudaMemcpyDeviceToHost);
+        for (size_t q = 0; q < hc.size(); ++q) colors[q] = hc[q];
+    }
+    if (e == cudaSuccess && gamma_own)
+        e = cudaMemcpy(gamma_own, d_gam, sizeof(int) * (size_t)D * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && f_color) e = cudaMemcpy(f_color, c->d_fcolor, sizeof(int) * D, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && f_eq) e = cudaMemcpy(f_eq, c->d_feq, sizeof(int) * D, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && Mtilde)
+        e = cudaMemcpy(Mtilde, d_mt, sizeof(int) * (size_t)n * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && G) e = cudaMemcpy(G, d_G, sizeof(float) * (size_t)D * n * k, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && loss) {
+        e = cudaMemcpy(&h, c->d_st, sizeof(h), cudaMemcpyDeviceToHost);
+        loss[0] = h.loss;
+        loss[1] = h.kappa;
+        loss[2] = h.varpi;
+        loss[3] = (float)h.fcolor_sum;
+    }
+    dfree(d_mt);
+    dfree(d_G);
+    dfree(d_gam);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return cuda_status(e);
+    }
+    return TC_OK;
+}
+
+int tc_step_async(tc_ctx* c, int64_t n_iters) {
+    if (!c || n_iters < 0) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    for (long long it = 0; it < n_iters;) {
+        int rc;
+        if (c->graph_chunk > 0 && n_iters - it >= c->graph_chunk) {
+            if (!c->gexec && (rc = build_graph_exec(c))) return rc;
+            TC_CHECK(cudaGraphLaunch(c->gexec, c->stream));
+            c->launches += 3ll * c->graph_chunk;
+            it += c->graph_chunk;
+        } else {
+            if ((rc = launch_iteration(c))) return rc;
+            it += 1;
+        }
+    }
+    return TC_OK;
+}
+
+int tc_set_timing(tc_ctx* c, int on) {
+    if (!c) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    int rc = collect_timing(c);
+    if (rc) return rc;
+    c->timing = on ? 1 : 0;
+    for (int q = 0; q < TC_NUM_KID; ++q) {
+        c->kms[q] = 0.0;
+        c->kcount[q] = 0;
+    }
+    return TC_OK;
+}
+
+int tc_kernel_times(tc_ctx* c, double* ms, int64_t* count) {
+    if (!c) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    int rc = collect_timing(c);
+    if (rc) return rc;
+    for (int q = 0; q < TC_NUM_KID; ++q) {
+        if (ms) ms[q] = c->kms[q];
+        if (count) count[q] = c->kcount[q];
+    }
+    return TC_OK;
+}
+
+int tc_launch_count(tc_ctx* c, int64_t* count) {
+    if (!c || !count) return TC_ERR_ARG;
+    *count = c->launches;
+    return TC_OK;
+}
+
+int tc_set_graph_chunk(tc_ctx* c, int chunk) {
+    if (!c || chunk < 0 || chunk > 100000) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    drop_graph_exec(c);
+    c->graph_chunk = chunk;
+    return TC_OK;
+}
+
+}  // extern "C"

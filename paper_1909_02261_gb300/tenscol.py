@@ -1,0 +1,239 @@
+"""Thin Python binding of libtenscol (include/tenscol.h) through ctypes.
+
+Argument marshalling only: every step of the TensCol iteration runs in the
+library's CUDA kernels.  Functions keep the C names (``tc_step`` ...); the
+``TensCol`` class wraps one context.  There is no CPU fallback: if the
+library cannot be loaded the import-time helpers raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+TC_OK = 0
+TC_KCOL, TC_ECP = 0, 1
+TC_FORM_ONEHOT, TC_FORM_DENSE_FP8, TC_FORM_DENSE_FP32 = 0, 1, 2
+TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE = 0, 1, 2
+KERNEL_NAMES = {TC_KID_PAIRS: "k_pairs", TC_KID_CLASSES: "k_classes", TC_KID_UPDATE: "k_update"}
+HEADER = os.path.join(_build.INCLUDE, "tenscol.h")
+
+
+class tc_params(C.Structure):
+    _fields_ = [
+        ("problem", C.c_int),
+        ("sigma0", C.c_float),
+        ("eta", C.c_float),
+        ("alpha", C.c_float),
+        ("lambda_", C.c_float),
+        ("beta", C.c_float),
+        ("mu", C.c_float),
+        ("nu", C.c_float),
+        ("rho", C.c_float),
+        ("nb_iter", C.c_int),
+        ("stop_on_legal", C.c_int),
+        ("bonus_diag", C.c_int),
+        ("form", C.c_int),
+    ]
+
+
+class TensColError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {tc_strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the entry points declared in include/tenscol.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tc_[a-z0-9_]+)\s*\(", src)))
+
+
+def load(build_if_missing: bool = True):
+    """Load (building if needed) the shared library and declare signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    L = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    P = C.POINTER
+    sig = {
+        "tc_strerror": (C.c_char_p, [C.c_int]),
+        "tc_params_default": (C.c_int, [P(tc_params), C.c_int]),
+        "tc_create": (C.c_int, [P(vp), C.c_int]),
+        "tc_destroy": (C.c_int, [vp]),
+        "tc_set_stream": (C.c_int, [vp, vp]),
+        "tc_init_graph": (C.c_int, [vp, C.c_int, vp, vp, vp]),
+        "tc_init_population": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, P(tc_params)]),
+        "tc_set_params": (C.c_int, [vp, P(tc_params)]),
+        "tc_step": (C.c_int, [vp, i64, P(i64)]),
+        "tc_best": (C.c_int, [vp, vp, P(i64), P(i64), P(i32), P(i64)]),
+        "tc_get_state": (C.c_int, [vp, vp, P(i64)]),
+        "tc_set_state": (C.c_int, [vp, vp, P(i64)]),
+        "tc_get_state_dev": (C.c_int, [vp, vp]),
+        "tc_set_state_dev": (C.c_int, [vp, vp]),
+        "tc_evaluate": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "tc_launch_count": (C.c_int, [vp, P(i64)]),
+        "tc_set_graph_chunk": (C.c_int, [vp, C.c_int]),
+        "tc_step_async": (C.c_int, [vp, i64]),
+        "tc_set_timing": (C.c_int, [vp, C.c_int]),
+        "tc_kernel_times": (C.c_int, [vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+    _lib = L
+    return L
+
+
+def tc_strerror(code: int) -> str:
+    try:
+        return load().tc_strerror(code).decode()
+    except OSError:
+        return f"status {code}"
+
+
+def _ck(rc: int, what: str):
+    if rc != TC_OK:
+        raise TensColError(rc, what)
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def params(problem: int = TC_KCOL, **kw) -> tc_params:
+    """Table 2 defaults for `problem`, overridden by keyword arguments."""
+    p = tc_params()
+    _ck(load().tc_params_default(C.byref(p), problem), "tc_params_default")
+    if "lambda" in kw:
+        kw["lambda_"] = kw.pop("lambda")
+    for key, val in kw.items():
+        if not hasattr(p, key):
+            raise KeyError(key)
+        setattr(p, key, val)
+    return p
+
+
+class TensCol:
+    """One context: a graph and a population on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._L = load()
+        h = C.c_void_p()
+        _ck(self._L.tc_create(C.byref(h), device), "tc_create")
+        self.h = h
+        self.n = self.D = self.k = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.tc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- setup ------------------------------------------------------------
+    def tc_init_graph(self, n, rowptr=None, colidx=None, dense=None):
+        rp = None if rowptr is None else np.ascontiguousarray(rowptr, np.int32)
+        ci = None if colidx is None else np.ascontiguousarray(colidx, np.int32)
+        de = None if dense is None else np.ascontiguousarray(dense, np.uint8)
+        _ck(self._L.tc_init_graph(self.h, int(n), _ptr(rp), _ptr(ci), _ptr(de)), "tc_init_graph")
+        self.n = int(n)
+
+    def tc_init_population(self, seed: int, D: int, k: int, p: tc_params | None = None):
+        _ck(self._L.tc_init_population(self.h, seed, D, k, None if p is None else C.byref(p)),
+            "tc_init_population")
+        self.D, self.k = D, k
+
+    def tc_set_params(self, p: tc_params):
+        _ck(self._L.tc_set_params(self.h, C.byref(p)), "tc_set_params")
+
+    def tc_set_stream(self, stream_handle: int | None):
+        _ck(self._L.tc_set_stream(self.h, stream_handle), "tc_set_stream")
+
+    def tc_set_graph_chunk(self, chunk: int):
+        _ck(self._L.tc_set_graph_chunk(self.h, chunk), "tc_set_graph_chunk")
+
+    # --- iterate ------------------------------------------------------------
+    def tc_step(self, n_iters: int) -> int:
+        done = C.c_int64()
+        _ck(self._L.tc_step(self.h, n_iters, C.byref(done)), "tc_step")
+        return done.value
+
+    def tc_best(self):
+        col = np.empty(self.n, np.int32)
+        fc, fe, t = C.c_int64(), C.c_int64(), C.c_int64()
+        d = C.c_int32()
+        _ck(self._L.tc_best(self.h, _ptr(col), C.byref(fc), C.byref(fe), C.byref(d), C.byref(t)),
+            "tc_best")
+        return dict(coloring=col, conflicts=fc.value, equity=fe.value, individual=d.value,
+                    iteration=t.value)
+
+    def tc_get_state(self, W_out=None):
+        W = W_out if W_out is not None else np.empty((self.D, self.n, self.k), np.float32)
+        t = C.c_int64()
+        _ck(self._L.tc_get_state(self.h, _ptr(W), C.byref(t)), "tc_get_state")
+        return W, t.value
+
+    def tc_set_state(self, W=None, t: int | None = None):
+        Wc = None if W is None else np.ascontiguousarray(W, np.float32)
+        if Wc is not None and Wc.size != self.D * self.n * self.k:
+            raise ValueError("W has the wrong size")
+        tt = None if t is None else C.byref(C.c_int64(t))
+        _ck(self._L.tc_set_state(self.h, _ptr(Wc), tt), "tc_set_state")
+
+    def tc_get_state_dev(self, ptr: int):
+        _ck(self._L.tc_get_state_dev(self.h, C.c_void_p(ptr)), "tc_get_state_dev")
+
+    def tc_set_state_dev(self, ptr: int):
+        _ck(self._L.tc_set_state_dev(self.h, C.c_void_p(ptr)), "tc_set_state_dev")
+
+    def tc_evaluate(self, want_G: bool = True, want_M: bool = True):
+        D, n, k = self.D, self.n, self.k
+        out = dict(colors=np.empty((D, n), np.int32), gamma_own=np.empty((D, n), np.int32),
+                   f_color=np.empty(D, np.int32), f_eq=np.empty(D, np.int32),
+                   Mt=np.empty((n, n), np.int32) if want_M else None,
+                   G=np.empty((D, n, k), np.float32) if want_G else None,
+                   loss=np.empty(4, np.float32))
+        _ck(self._L.tc_evaluate(self.h, _ptr(out["colors"]), _ptr(out["gamma_own"]),
+                                _ptr(out["f_color"]), _ptr(out["f_eq"]), _ptr(out["Mt"]),
+                                _ptr(out["G"]), _ptr(out["loss"])), "tc_evaluate")
+        return out
+
+    def tc_step_async(self, n_iters: int):
+        _ck(self._L.tc_step_async(self.h, n_iters), "tc_step_async")
+
+    def tc_set_timing(self, on: bool):
+        _ck(self._L.tc_set_timing(self.h, int(on)), "tc_set_timing")
+
+    def tc_kernel_times(self):
+        ms = np.zeros(8, np.float64)
+        cnt = np.zeros(8, np.int64)
+        _ck(self._L.tc_kernel_times(self.h, _ptr(ms), _ptr(cnt)), "tc_kernel_times")
+        return ms, cnt
+
+    def tc_launch_count(self) -> int:
+        c = C.c_int64()
+        _ck(self._L.tc_launch_count(self.h, C.byref(c)), "tc_launch_count")
+        return c.value
