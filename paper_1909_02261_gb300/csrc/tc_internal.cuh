@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtenscol.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,18 +31,21 @@ struct tc_dev_state {
 // Everything a kernel of the step needs, passed by value.
 struct tc_kparams {
     int n, D, k;
-    int Dp;           // colours per row of cT (D rounded up to even)
+    int Dp;           // colours per row of cT (D rounded up to a multiple of 4)
+    int ct_bytes;     // bytes per colour in cT: 1 when k <= 255, else 2
     int adj_words;    // 32-bit words per adjacency-bitmask row
     int problem, nb_iter, bonus_diag, stop_on_legal, commit;
     float eta, rho, lambda_, mu, nu;
     float* W;                 // D x n x k
     uint16_t* c;              // D x n colours
-    uint16_t* cT;             // n x Dp colours (vertex-major), pads = 0xFFFF
+    uint16_t* cT;             // n x Dp colours (vertex-major, ct_bytes each), pads all-ones
     const uint32_t* adj;      // n x adj_words adjacency bitmask
     const int* rowptr;        // CSR
     const int* colidx;
-    float* B;                 // n x n pair coefficients of eq. 13 (symmetric)
-    uint16_t* perm;           // D x n vertices sorted by colour (stable)
+    float* B;                 // n x ldb pair coefficients of eq. 13 (symmetric)
+    int ldb;                  // row stride of B: n rounded up to a multiple of 4
+    uint16_t* perm;           // D x perm_stride vertices sorted by colour (stable)
+    int perm_stride;          // n rounded up to a multiple of 8 (16-byte rows)
     int* off;                 // D x (k + 1) colour-class offsets into perm
     int8_t* E;                // D x k equity gradient signs (eq. 14)
     int* fcolor;              // D conflicts (eq. 1)
@@ -66,7 +70,14 @@ cudaError_t tc_launch_init_weights(float* W, long long count, unsigned long long
 cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s);
-cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only);
-cudaError_t tc_launch_debug_gamma(const tc_kparams& P, cudaStream_t s);
+cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int num_sms,
+                             cudaStream_t s, int debug_only);
+// Tiled 2-D tensor map (TMA) over a row-major matrix: `inner` elements per
+// row (contiguous), `outer` rows, `row_bytes` between rows (multiple of 16).
+int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint64_t inner,
+                      uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                      CUtensorMapSwizzle swizzle);
+constexpr int TC_BT_BOX_ROWS = 128;  // rows per TMA box of the B column panel
+int tc_pair_tile_edge();
 int tc_pair_tile_count(int n);
 int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem);

@@ -27,9 +27,9 @@
 
 namespace {
 
-constexpr int PT = 32;              // pair tile edge
-constexpr int PAIR_THREADS = 256;   // 8 warps x 4 rows each
-constexpr int PAIR_CW = 128;        // colour words (2 individuals each) per chunk
+constexpr int PT = 64;              // pair tile edge
+constexpr int PAIR_THREADS = 256;   // 16 x 16 threads, 4 x 4 pairs each
+constexpr int PAIR_CW = 64;         // colour words per chunk (< 256: lane counters)
 constexpr int CLS_THREADS = 256;
 constexpr int UPD_MAX_WARPS = 8;
 
@@ -88,9 +88,16 @@ __global__ void k_init_weights(float* W, long long count, unsigned long long see
         if (g * 4 + q < count) W[g * 4 + q] = z[q] * sigma0;
 }
 
-// ---------------------------------------------------------------------------
 // Step 1 (Section 3.4) for a fresh W: c_d(i) = lowest j with maximal w.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_colour(const tc_kparams& P, int d, int i, int c) {
+    P.c[(size_t)d * P.n + i] = (uint16_t)c;
+    if (P.ct_bytes == 1)
+        reinterpret_cast<uint8_t*>(P.cT)[(size_t)i * P.Dp + d] = (uint8_t)c;
+    else
+        P.cT[(size_t)i * P.Dp + d] = (uint16_t)c;
+}
+
 __global__ void k_assign(tc_kparams P) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (long long)P.D * P.n) return;
@@ -104,71 +111,76 @@ __global__ void k_assign(tc_kparams P) {
             best = j;
         }
     }
-    const int d = (int)(r / P.n), i = (int)(r % P.n);
-    P.c[r] = (uint16_t)best;
-    P.cT[(size_t)i * P.Dp + d] = (uint16_t)best;
+    store_colour(P, (int)(r / P.n), (int)(r % P.n), best);
 }
 
 // ---------------------------------------------------------------------------
-// k_pairs: one 32x32 tile (I <= M) of vertex pairs per block.
+// k_pairs: one 64x64 tile (I <= M) of vertex pairs per block, 4x4 pairs per
+// thread.  Colours are packed 4 (8-bit, k <= 255) or 2 (16-bit) to a word of
+// cT; equal colours are counted without branches: x = a ^ b has a zero lane
+// exactly where the colours agree, and ~(((x & 0x7f..) + 0x7f..) | x) sets
+// the top bit of precisely those lanes (no carry crosses a lane).
 // ---------------------------------------------------------------------------
+template <int CB>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     if (P.commit && P.st->stop) return;
-    __shared__ uint32_t s_ci[PT][PAIR_CW + 1];
-    __shared__ uint32_t s_cm[PT][PAIR_CW + 1];
-    __shared__ int s_conf[2 * PAIR_CW];
-    __shared__ float s_bt[PT][PT + 1];
-    __shared__ int s_mt[PT][PT + 1];
+    __shared__ uint32_t s_a[PT][PAIR_CW + 1];
+    __shared__ uint32_t s_b[PT][PAIR_CW + 1];
     __shared__ float s_red[2][PAIR_THREADS / 32];
+    constexpr uint32_t LOW = CB == 1 ? 0x7F7F7F7Fu : 0x7FFF7FFFu;
+    constexpr uint32_t HIGH = CB == 1 ? 0x80808080u : 0x80008000u;
+    constexpr int SH = CB == 1 ? 7 : 15;
 
     const int n = P.n, D = P.D;
     const int2 tile = P.pair_tiles[blockIdx.x];
     const int I = tile.x, M = tile.y;
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const int m = M * PT + tx;
-    const int Dw = P.Dp >> 1;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int Dw = P.Dp * CB / 4;
     const uint32_t* cTw = reinterpret_cast<const uint32_t*>(P.cT);
 
-    // which of my 4 pairs are edges / count towards the fitness (strict upper)
-    bool edge[4], upper[4];
+    uint32_t wide[4][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = I * PT + ty + 8 * r;
-        const bool ok = (i < n) && (m < n);
-        edge[r] = ok && ((P.adj[(size_t)i * P.adj_words + (m >> 5)] >> (m & 31)) & 1u);
-        upper[r] = ok && (I < M || tx > ty + 8 * r);
-    }
-
-    int cnt[4] = {0, 0, 0, 0};
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) wide[a][b] = 0u;
     for (int w0 = 0; w0 < Dw; w0 += PAIR_CW) {
         const int cw = min(PAIR_CW, Dw - w0);
         __syncthreads();
         for (int e = tid; e < PT * cw; e += PAIR_THREADS) {
             const int r = e / cw, w = e - r * cw;
             const int ii = I * PT + r, mm = M * PT + r;
-            s_ci[r][w] = ii < n ? cTw[(size_t)ii * Dw + w0 + w] : 0xFFFFFFFFu;
-            s_cm[r][w] = mm < n ? cTw[(size_t)mm * Dw + w0 + w] : 0xFFFFFFFFu;
+            s_a[r][w] = ii < n ? cTw[(size_t)ii * Dw + w0 + w] : 0u;
+            s_b[r][w] = mm < n ? cTw[(size_t)mm * Dw + w0 + w] : 0u;
         }
-        for (int e = tid; e < 2 * PAIR_CW; e += PAIR_THREADS) s_conf[e] = 0;
         __syncthreads();
+        uint32_t acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0u;
         for (int w = 0; w < cw; ++w) {
-            const uint32_t b = s_cm[tx][w];
+            uint32_t av[4], bv[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const uint32_t eq = __vcmpeq2(s_ci[ty + 8 * r][w], b);
-                cnt[r] += __popc(eq);
-                if (eq && edge[r] && upper[r]) {  // conflicts on this edge
-                    if (eq & 1u) atomicAdd(&s_conf[2 * w], 1);
-                    if (eq & 0x10000u) atomicAdd(&s_conf[2 * w + 1], 1);
-                }
+                av[r] = s_a[ty + 16 * r][w];
+                bv[r] = s_b[tx + 16 * r][w];
             }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t x = av[a] ^ bv[b];
+                    const uint32_t y = (x & LOW) + LOW;
+                    acc[a][b] += (~(y | x) & HIGH) >> SH;
+                }
         }
-        __syncthreads();
-        for (int e = tid; e < 2 * cw; e += PAIR_THREADS) {
-            const int d = 2 * w0 + e;
-            const int v = s_conf[e];
-            if (v && d < D) atomicAdd(&P.fcolor[d], v);
-        }
+        // fold the per-lane chunk counters (< 256) into two 16-bit lanes
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                wide[a][b] += CB == 1 ? (acc[a][b] & 0x00FF00FFu) + ((acc[a][b] >> 8) & 0x00FF00FFu)
+                                      : acc[a][b];
     }
 
     // pair coefficient of eq. 13 and loss terms of eq. 5-6
@@ -177,64 +189,70 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     const float cB = (float)((double)P.mu * (double)t);
     const int pad = P.Dp - D;  // padded colour slots always compare equal
     float kap = 0.f, var = 0.f;
+    __syncthreads();  // s_a / s_b are reused as transpose tiles
+    float(*s_t)[PT + 1] = reinterpret_cast<float(*)[PT + 1]>(&s_a[0][0]);
+    int(*s_m)[PT + 1] = reinterpret_cast<int(*)[PT + 1]>(&s_b[0][0]);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int il = ty + 8 * r;
-        const int i = I * PT + il;
-        float b = 0.f;
-        int mt = 0;
-        if (i < n && m < n && (I < M || tx >= il)) {
-            mt = (cnt[r] >> 4) - pad;
-            if (m == i) {
-                mt = D;
-                if (P.bonus_diag) {
-                    b = -cB * P.lutB[D];
-                    var += P.powB[D];
+    for (int a = 0; a < 4; ++a) {
+        const int il = ty + 16 * a, i = I * PT + il;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int ml = tx + 16 * b, m = M * PT + ml;
+            float bb = 0.f;
+            int mt = 0;
+            if (i < n && m < n && (I < M || ml >= il)) {
+                mt = (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
+                const bool edge = (P.adj[(size_t)i * P.adj_words + (m >> 5)] >> (m & 31)) & 1u;
+                if (m == i) {
+                    mt = D;
+                    if (P.bonus_diag) {
+                        bb = -cB * P.lutB[D];
+                        var += P.powB[D];
+                    }
+                } else if (edge) {
+                    bb = fmaf(cA, P.lutA[mt], 1.0f);
+                    kap += 2.0f * P.powA[mt];
+                } else {
+                    bb = -cB * P.lutB[mt];
+                    var += 2.0f * P.powB[mt];
                 }
-            } else if (edge[r]) {
-                b = fmaf(cA, P.lutA[mt], 1.0f);
-                kap += 2.0f * P.powA[mt];
-            } else {
-                b = -cB * P.lutB[mt];
-                var += 2.0f * P.powB[mt];
+                P.B[(size_t)i * P.ldb + m] = bb;
+                if (P.dbg_Mt) P.dbg_Mt[(size_t)i * n + m] = mt;
             }
-            P.B[(size_t)i * n + m] = b;
-            if (P.dbg_Mt) P.dbg_Mt[(size_t)i * n + m] = mt;
+            s_t[ml][il] = bb;
+            s_m[ml][il] = mt;
         }
-        s_bt[tx][il] = b;
-        s_mt[tx][il] = mt;
     }
     __syncthreads();
-    // transposed write of the strictly-lower counterpart: B[m][i] = B[i][m]
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int ml = ty + 8 * r;    // row of the transposed tile
-        const int mm = M * PT + ml;
-        const int ii = I * PT + tx;
-        if (mm < n && ii < n && (I < M || tx < ml)) {
-            P.B[(size_t)mm * n + ii] = s_bt[ml][tx];
-            if (P.dbg_Mt) P.dbg_Mt[(size_t)mm * n + ii] = s_mt[ml][tx];
+    // transposed counterpart B[m][i] = B[i][m] for the strictly-lower half
+    for (int e = tid; e < PT * PT; e += PAIR_THREADS) {
+        const int ml = e >> 6, il = e & 63;
+        const int mm = M * PT + ml, ii = I * PT + il;
+        if (mm < n && ii < n && (I < M || il < ml)) {
+            P.B[(size_t)mm * P.ldb + ii] = s_t[ml][il];
+            if (P.dbg_Mt) P.dbg_Mt[(size_t)mm * n + ii] = s_m[ml][il];
         }
     }
     // block partial sums (fixed order -> deterministic)
     kap = warp_sum(kap);
     var = warp_sum(var);
-    if (tx == 0) {
-        s_red[0][ty] = kap;
-        s_red[1][ty] = var;
+    if ((tid & 31) == 0) {
+        s_red[0][tid >> 5] = kap;
+        s_red[1][tid >> 5] = var;
     }
     __syncthreads();
     if (tid == 0) {
-        float a = 0.f, v = 0.f;
+        float ka = 0.f, va = 0.f;
         for (int q = 0; q < PAIR_THREADS / 32; ++q) {
-            a += s_red[0][q];
-            v += s_red[1][q];
+            ka += s_red[0][q];
+            va += s_red[1][q];
         }
-        P.loss_part[2 * blockIdx.x] = a;
-        P.loss_part[2 * blockIdx.x + 1] = v;
+        P.loss_part[2 * blockIdx.x] = ka;
+        P.loss_part[2 * blockIdx.x + 1] = va;
     }
 }
 
+// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // block-wide helpers for k_classes (CLS_THREADS threads)
 // ---------------------------------------------------------------------------
@@ -330,17 +348,21 @@ __device__ void finalize_population(const tc_kparams& P) {
     if (threadIdx.x == 0) st->done_classes = 0u;
 }
 
+// k_classes: one individual per block.  Class sizes and offsets, equity
+// (eq. 3, eq. 14), the stable counting sort, and the exact conflicts of
+// eq. 1: with X_j the bitmap of the vertices coloured j, vertex i has
+// gamma_d(i) = popcount(A_i & X_{c_d(i)}) conflicting neighbours.
+// Dynamic shared memory holds the bitmaps of `cls_colours` colours at a time.
 // ---------------------------------------------------------------------------
-// k_classes: one individual per block.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
+__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_colours) {
     if (P.commit && P.st->stop) return;
     __shared__ int s_hist[TC_MAX_K];
     __shared__ int s_cur[TC_MAX_K];
     __shared__ int s_scan[CLS_THREADS];
     __shared__ long long sh_ll[CLS_THREADS / 32];
     __shared__ int s_last;
-    const int n = P.n, k = P.k, d = blockIdx.x;
+    extern __shared__ uint32_t s_bits[];  // cls_colours x adj_words
+    const int n = P.n, k = P.k, d = blockIdx.x, aw = P.adj_words;
     const uint16_t* cd = P.c + (size_t)d * n;
     for (int j = threadIdx.x; j < k; j += blockDim.x) s_hist[j] = 0;
     __syncthreads();
@@ -381,7 +403,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     // stable counting sort of the vertices by colour (warp 0, 32 at a time)
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        uint16_t* pd = P.perm + (size_t)d * n;
+        uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
         for (int base = 0; base < n; base += 32) {
             const int i = base + lane;
             const unsigned valid = __ballot_sync(0xffffffffu, i < n);
@@ -396,6 +418,31 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
             __syncwarp();
         }
     }
+    // conflicts (eq. 1) by colour bitmaps, cls_colours colours per pass
+    long long twice = 0;
+    for (int cb = 0; cb < k; cb += cls_colours) {
+        const int ce = min(k, cb + cls_colours);
+        __syncthreads();
+        for (int e = threadIdx.x; e < (ce - cb) * aw; e += blockDim.x) s_bits[e] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int col = cd[i];
+            if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * aw + (i >> 5)], 1u << (i & 31));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int col = cd[i];
+            if (col < cb || col >= ce) continue;
+            const uint32_t* ar = P.adj + (size_t)i * aw;
+            const uint32_t* xr = s_bits + (col - cb) * aw;
+            int g = 0;
+            for (int w = 0; w < aw; ++w) g += __popc(__ldg(ar + w) & xr[w]);
+            twice += g;
+            if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
+        }
+    }
+    twice = block_sum<long long>(twice, sh_ll);
+    if (threadIdx.x == 0) P.fcolor[d] = (int)(twice / 2);
     // completion ticket: the last block reduces the population
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -411,151 +458,240 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
 }
 
 // ---------------------------------------------------------------------------
+
 // k_update: Step 3-ii + Step 4 for (32-vertex tile, individual) items.
-// KREG > 0 keeps the tile's grad_S rows in registers (k <= KREG), else in
-// shared memory.  BTS stages the tile's columns of B in shared memory.
+//
+// A block owns a contiguous range of items (tile-major), keeps the tile's 32
+// columns of B in shared memory (BTS) and gives one item at a time to each
+// warp.  Per item the warp
+//   1. starts a bulk async copy (TMA, cp.async.bulk) of the item's 32 x k
+//      weight rows (contiguous in W) into its shared tile Ws;
+//   2. walks the individual's vertices in colour order (8 per 16-byte load)
+//      summing B_im per class into Gs[j][lane] (grad_S L, lane = vertex);
+//   3. waits for the copy, then each lane updates its own row: softmax,
+//      straight-through gradient, descent step, smoothing, argmax;
+//   4. writes the row tile back with a bulk async store.
+// Rows are read at a lane-dependent rotation of the colour index so that the
+// 32 lanes hit 32 different banks for any k.
 // ---------------------------------------------------------------------------
-template <int KREG, bool BTS>
-__device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt, float* Ws,
-                                            float* Gs, int T, int d, float nut, bool smooth,
-                                            int debug_only) {
-    const int n = P.n, k = P.k, k1 = k + 1;
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^28 polls and reports TC_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+    for (unsigned it = 0; it < (1u << 28); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicCAS(err, 0, TC_ERR_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, unsigned bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(smem_dst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* gdst, const void* smem_src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(smem_src)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <bool BTS, bool BULK>
+__device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt, float* Gs, float* Ws,
+                                            uint64_t* bar, unsigned& phase, int T, int d, float nut,
+                                            bool smooth, int debug_only) {
+    const int n = P.n, k = P.k;
     const int lane = threadIdx.x & 31;
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
-    const uint16_t* pm = P.perm + (size_t)d * n;
+    const size_t wbase = ((size_t)d * n + i0) * k;
+    const unsigned wbytes = (unsigned)(rows * k * 4);
+
+    // 1. weight tile -> Ws
+    if (!debug_only) {
+        if (BULK) {
+            if (lane == 0) {
+                bulk_wait_read();  // the previous item's store has read Ws
+                mbar_expect_tx(bar, wbytes);
+                bulk_load(Ws, P.W + wbase, wbytes, bar);
+            }
+        } else {
+            for (int e = lane; e < rows * k; e += 32) Ws[e] = P.W[wbase + e];
+        }
+    }
+
+    // 2. grad_S L rows by colour-class segment sums
+    const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
     const int* of = P.off + (size_t)d * (k + 1);
     const int8_t* Ed = P.E + (size_t)d * k;
-    const float* Bcol;
-    int bstride;
-    if (BTS) {
-        Bcol = Bt + lane;
-        bstride = 32;
-    } else {
-        Bcol = P.B + min(i0 + lane, n - 1);
-        bstride = n;
+    const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
+    const int bstride = BTS ? 32 : P.ldb;
+    int j = 0;
+    int next_end = __ldg(of + 1);
+    while (j < k && next_end == 0) {  // leading empty classes
+        Gs[j * 32 + lane] = nut * (float)__ldg(Ed + j);
+        ++j;
+        next_end = j < k ? __ldg(of + j + 1) : n;
     }
-    float Gr[KREG > 0 ? KREG : 1];
-
-    // Phase A: grad_S L row of vertex i0 + lane, one colour class at a time
-    auto class_sum = [&](int j) -> float {
-        const int s = __ldg(of + j), e = __ldg(of + j + 1);
-        float a0 = 0.f, a1 = 0.f;
-        int p = s;
-        for (; p + 1 < e; p += 2) {
-            const int m0 = __ldg(pm + p), m1 = __ldg(pm + p + 1);
-            a0 += Bcol[m0 * bstride];
-            a1 += Bcol[m1 * bstride];
-        }
-        if (p < e) a0 += Bcol[__ldg(pm + p) * bstride];
-        return (a0 + a1) + nut * (float)__ldg(Ed + j);
-    };
-    if (KREG > 0) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int p0 = 0; p0 < n; p0 += 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(pm + p0));
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+        float b[8];
 #pragma unroll
-        for (int j = 0; j < (KREG > 0 ? KREG : 1); ++j)
-            if (j < k) Gr[j] = class_sum(j);
-    } else {
-        for (int j = 0; j < k; ++j) Gs[j * 33 + lane] = class_sum(j);
+        for (int q = 0; q < 8; ++q) {
+            const int m = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFF;
+            b[q] = (p0 + q < n) ? Bl[m * bstride] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q & 3] += b[q];
+            if (p0 + q + 1 == next_end) {  // class j ends here (uniform branch)
+                Gs[j * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + nut * (float)__ldg(Ed + j);
+                acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+                ++j;
+                next_end = j < k ? __ldg(of + j + 1) : n + 1;
+                while (j < k && next_end == p0 + q + 1) {  // empty classes
+                    Gs[j * 32 + lane] = nut * (float)__ldg(Ed + j);
+                    ++j;
+                    next_end = j < k ? __ldg(of + j + 1) : n + 1;
+                }
+            }
+        }
     }
+    __syncwarp();
     if (debug_only) {
         if (lane < rows) {
             float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
-            if (KREG > 0) {
-#pragma unroll
-                for (int j = 0; j < (KREG > 0 ? KREG : 1); ++j)
-                    if (j < k) g[j] = Gr[j];
-            } else {
-                for (int j = 0; j < k; ++j) g[j] = Gs[j * 33 + lane];
-            }
+            for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
         }
         __syncwarp();
         return;
     }
-    auto Gget = [&](int j) -> float { return KREG > 0 ? Gr[j] : Gs[j * 33 + lane]; };
 
-    // Phase B: the 32 x k weight tile through shared memory (coalesced)
-    const size_t wbase = ((size_t)d * n + i0) * k;
-    const int cnt = rows * k;
-    {
-        int r = 0, j = lane;
-        while (j >= k) { j -= k; ++r; }
-        for (int e = lane; e < cnt; e += 32) {
-            Ws[r * k1 + j] = P.W[wbase + e];
-            j += 32;
-            while (j >= k) { j -= k; ++r; }
-        }
+    // 3. per-row softmax straight-through step (lane = row)
+    if (BULK) {
+        mbar_wait_bounded(bar, phase, &P.st->err);
+        phase ^= 1u;
+    } else {
+        __syncwarp();
     }
-    __syncwarp();
     int newc = 0;
     if (lane < rows) {
-        float* w = Ws + lane * k1;
-        float mx = w[0];
-        for (int j = 1; j < k; ++j) mx = fmaxf(mx, w[j]);
+        float* wr = Ws + lane * k;
+        const float* gr = Gs + lane;
+        const int j0 = lane % k;
+        float mx = -INFINITY;
+        int jj = j0;
+#pragma unroll 4
+        for (int q = 0; q < k; ++q) {
+            mx = fmaxf(mx, wr[jj]);
+            jj = (jj + 1 == k) ? 0 : jj + 1;
+        }
         float Z = 0.f, num = 0.f;
-        if (KREG > 0) {
-#pragma unroll
-            for (int j = 0; j < (KREG > 0 ? KREG : 1); ++j)
-                if (j < k) {
-                    const float e = __expf(w[j] - mx);
-                    Z += e;
-                    num = fmaf(e, Gget(j), num);
-                }
-        } else {
-            for (int j = 0; j < k; ++j) {
-                const float e = __expf(w[j] - mx);
-                Z += e;
-                num = fmaf(e, Gget(j), num);
-            }
+        jj = j0;
+#pragma unroll 4
+        for (int q = 0; q < k; ++q) {
+            const float e = __expf(wr[jj] - mx);
+            Z += e;
+            num = fmaf(e, gr[jj * 32], num);
+            jj = (jj + 1 == k) ? 0 : jj + 1;
         }
         const float invZ = 1.0f / Z;
         const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
         float bestv = -INFINITY;
-        auto upd = [&](int j) {
-            const float s = __expf(w[j] - mx) * invZ;
-            float wn = w[j] - P.eta * (s * (Gget(j) - dot));
+        newc = k;
+        jj = j0;
+#pragma unroll 4
+        for (int q = 0; q < k; ++q) {
+            const float w = wr[jj];
+            const float s = __expf(w - mx) * invZ;
+            float wn = w - P.eta * (s * (gr[jj * 32] - dot));
             if (smooth) wn = wn / P.rho;
-            w[j] = wn;
-            if (wn > bestv) {
+            wr[jj] = wn;
+            if (wn > bestv || (wn == bestv && jj < newc)) {
                 bestv = wn;
-                newc = j;
+                newc = jj;
             }
-        };
-        if (KREG > 0) {
-#pragma unroll
-            for (int j = 0; j < (KREG > 0 ? KREG : 1); ++j)
-                if (j < k) upd(j);
-        } else {
-            for (int j = 0; j < k; ++j) upd(j);
+            jj = (jj + 1 == k) ? 0 : jj + 1;
         }
+        if (newc >= k) newc = 0;
     }
     __syncwarp();
-    {
-        int r = 0, j = lane;
-        while (j >= k) { j -= k; ++r; }
-        for (int e = lane; e < cnt; e += 32) {
-            P.W[wbase + e] = Ws[r * k1 + j];
-            j += 32;
-            while (j >= k) { j -= k; ++r; }
-        }
+
+    // 4. write back
+    if (BULK) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) bulk_store(P.W + wbase, Ws, wbytes);
+    } else {
+        for (int e = lane; e < rows * k; e += 32) P.W[wbase + e] = Ws[e];
     }
-    if (lane < rows) {
-        P.c[(size_t)d * n + i0 + lane] = (uint16_t)newc;
-        P.cT[(size_t)(i0 + lane) * P.Dp + d] = (uint16_t)newc;
-    }
+    if (lane < rows) store_colour(P, d, i0 + lane, newc);
     __syncwarp();
 }
 
-template <int KREG, bool BTS>
-__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, int items_per_block,
-                                                               int debug_only) {
+template <bool BTS, bool BULK>
+__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
+    k_update(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block, int debug_only) {
     tc_dev_state* st = P.st;
     if (!debug_only && st->stop) return;
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ __align__(8) uint64_t s_bbar;  // completion of the B panel copy
     const int n = P.n, D = P.D, k = P.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nbox = (n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS;
     float* Bt = sm;
-    float* Ws = sm + (BTS ? (size_t)n * 32 : 0) + (size_t)warp * (32 * (k + 1) + (KREG > 0 ? 0 : k * 33));
-    float* Gs = Ws + 32 * (k + 1);
+    float* Gs = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * (64 * k + 4);
+    float* Ws = Gs + 32 * k;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + 32 * k);
+    unsigned phase = 0, bphase = 0;
+    if (BULK && lane == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (BTS && threadIdx.x == 0) {
+        mbar_init(&s_bbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
     const long long t = st->t;
     const float nut = (float)((double)P.nu * (double)t);
     const bool smooth = ((t + 1) % P.nb_iter) == 0;
@@ -567,17 +703,29 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, 
         const int T = (int)(q / D);
         const long long seg_end = min(qend, (long long)(T + 1) * D);
         if (BTS) {
-            const int i0 = T * 32;
+            // B[0..n) x [32 T, 32 T + 32) -> Bt by 2-D TMA boxes (zero filled
+            // past the matrix edge); the panel is symmetric-transposed B
             __syncthreads();
-            for (int m = warp; m < n; m += nw)
-                Bt[m * 32 + lane] = (i0 + lane < n) ? P.B[(size_t)m * n + i0 + lane] : 0.f;
-            __syncthreads();
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
+                for (int b = 0; b < nbox; ++b)
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS),
+                        "r"(smem_u32(&s_bbar))
+                        : "memory");
+            }
+            mbar_wait_bounded(&s_bbar, bphase, &st->err);
+            bphase ^= 1u;
         }
         for (long long qq = q + warp; qq < seg_end; qq += nw)
-            update_item<KREG, BTS>(P, Bt, Ws, Gs, T, (int)(qq - (long long)T * D), nut, smooth,
-                                   debug_only);
+            update_item<BTS, BULK>(P, Bt, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), nut,
+                                   smooth, debug_only);
         q = seg_end;
     }
+    if (BULK && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores done
     if (!debug_only) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -592,23 +740,11 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, 
     }
 }
 
-// gamma_own[d, i] = conflicting neighbours (eq. 1), for tc_evaluate only.
-__global__ void k_debug_gamma(tc_kparams P) {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= (long long)P.D * P.n) return;
-    const int d = (int)(r / P.n), i = (int)(r % P.n);
-    const uint16_t* cd = P.c + (size_t)d * P.n;
-    const int ci = cd[i];
-    int g = 0;
-    for (int e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) g += (cd[P.colidx[e]] == ci);
-    P.dbg_gamma[r] = g;
-}
-
 constexpr int kSmemOptin = 232448;  // 227 KB per block on sm_100 / sm_103
 
-int pick_kreg(int k) { return k <= 32 ? 32 : (k <= 64 ? 64 : (k <= 96 ? 96 : 0)); }
-
 }  // namespace
+
+int tc_pair_tile_edge() { return PT; }
 
 int tc_pair_tile_count(int n) {
     const int T = (n + PT - 1) / PT;
@@ -616,9 +752,10 @@ int tc_pair_tile_count(int n) {
 }
 
 int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem) {
-    const int kreg = pick_kreg(k);
-    const long long per_warp = 4ll * (32ll * (k + 1) + (kreg > 0 ? 0 : 33ll * k));
-    const long long bt = 4ll * 32 * n;
+    // per warp: Gs (32 x k) + Ws (32 x k) floats + one mbarrier (16 B);
+    // the B panel: whole TMA boxes of TC_BT_BOX_ROWS x 32 floats
+    const long long per_warp = 4ll * (64ll * k + 4);
+    const long long bt = 4ll * 32 * ((n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
     int w = 0, bts = 0;
     if (bt + per_warp <= kSmemOptin) {
         bts = 1;
@@ -649,26 +786,38 @@ cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s) {
 }
 
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
-    k_pairs<<<P.n_pair_blocks, PAIR_THREADS, 0, s>>>(P);
+    if (P.ct_bytes == 1)
+        k_pairs<1><<<P.n_pair_blocks, PAIR_THREADS, 0, s>>>(P);
+    else
+        k_pairs<2><<<P.n_pair_blocks, PAIR_THREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
-    k_classes<<<P.D, CLS_THREADS, 0, s>>>(P);
+    // colour bitmaps in dynamic shared memory, at most ~160 KB per pass
+    const long long row = 4ll * P.adj_words;
+    int colours = (int)((160ll << 10) / row);
+    if (colours > P.k) colours = P.k;
+    if (colours < 1) colours = 1;
+    const int smem = (int)(colours * row);
+    cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_classes<<<P.D, CLS_THREADS, smem, s>>>(P, colours);
     return cudaGetLastError();
 }
 
-template <int KREG, bool BTS>
-static cudaError_t launch_update_t(const tc_kparams& P, int blocks, int warps, int smem,
-                                   int per_block, cudaStream_t s, int debug_only) {
-    auto fn = k_update<KREG, BTS>;
+template <bool BTS, bool BULK>
+static cudaError_t launch_update_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps,
+                                   int smem, int per_block, cudaStream_t s, int debug_only) {
+    auto fn = k_update<BTS, BULK>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    fn<<<blocks, warps * 32, smem, s>>>(P, per_block, debug_only);
+    fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
     return cudaGetLastError();
 }
 
-cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only) {
+cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,
+                             int debug_only) {
     int warps = 0, smem = 0, bts = 0;
     if (tc_update_config(P.n, P.k, &warps, &smem, &bts) != TC_OK) return cudaErrorInvalidValue;
     const long long items = (long long)((P.n + 31) / 32) * P.D;
@@ -676,21 +825,13 @@ cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, i
     if (blocks > items) blocks = items;
     if (blocks < 1) blocks = 1;
     const int per_block = (int)((items + blocks - 1) / blocks);
-    const int kreg = pick_kreg(P.k);
-#define TC_UPD(KR)                                                                                \
-    return bts ? launch_update_t<KR, true>(P, (int)blocks, warps, smem, per_block, s, debug_only)  \
-               : launch_update_t<KR, false>(P, (int)blocks, warps, smem, per_block, s, debug_only)
-    switch (kreg) {
-        case 32: TC_UPD(32);
-        case 64: TC_UPD(64);
-        case 96: TC_UPD(96);
-        default: TC_UPD(0);
-    }
-#undef TC_UPD
+    // bulk copies need 16-byte aligned, 16-byte multiple tiles: n k % 4 == 0
+    // (tile starts are (d n + 32 T) k floats, tile sizes rows k floats)
+    const bool bulk = ((long long)P.n * P.k) % 4 == 0 && (((uintptr_t)P.W) & 15) == 0;
+    if (bts)
+        return bulk ? launch_update_t<true, true>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
+                    : launch_update_t<true, false>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only);
+    return bulk ? launch_update_t<false, true>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
+                : launch_update_t<false, false>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only);
 }
 
-cudaError_t tc_launch_debug_gamma(const tc_kparams& P, cudaStream_t s) {
-    const long long rows = (long long)P.D * P.n;
-    k_debug_gamma<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(P);
-    return cudaGetLastError();
-}

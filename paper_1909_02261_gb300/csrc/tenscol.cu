@@ -49,6 +49,8 @@ struct tc_ctx {
     float* d_lut = nullptr;  // 4 x (D + 1): lutA, lutB, powA, powB
     tc_dev_state* d_st = nullptr;
     uint16_t* d_best = nullptr;
+    int ldb = 0;
+    alignas(64) CUtensorMap tmB;  // B column panels for k_update
     // CUDA graph of graph_chunk iterations
     int graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -169,6 +171,7 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.D = c->D;
     P.k = c->k;
     P.Dp = c->Dp;
+    P.ct_bytes = c->k <= 255 ? 1 : 2;
     P.adj_words = c->adj_words;
     P.problem = c->p.problem;
     P.nb_iter = c->p.nb_iter;
@@ -187,7 +190,9 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.rowptr = c->d_rowptr;
     P.colidx = c->d_colidx;
     P.B = c->d_B;
+    P.ldb = c->ldb;
     P.perm = c->d_perm;
+    P.perm_stride = (c->n + 7) & ~7;
     P.off = c->d_off;
     P.E = c->d_E;
     P.fcolor = c->d_fcolor;
@@ -289,10 +294,9 @@ void free_events(tc_ctx* c) {
 int launch_iteration(tc_ctx* c) {
     if (fault("launch")) return TC_ERR_INJECTED;
     tc_kparams P = make_kparams(c, 1);
-    TC_CHECK(cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * c->D, c->stream));
     TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
     TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
-    TC_CHECK(timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->num_sms, c->stream, 0); }));
+    TC_CHECK(timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->tmB, c->num_sms, c->stream, 0); }));
     return TC_OK;
 }
 
@@ -325,6 +329,34 @@ int build_graph_exec(tc_ctx* c) {
 }
 
 }  // namespace
+
+int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint64_t inner,
+                      uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+                      CUtensorMapSwizzle swizzle) {
+    typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+    static encode_fn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            (void)cudaGetLastError();
+            return TC_ERR_CUDA;
+        }
+        fn = (encode_fn)p;
+    }
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(out, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? TC_OK : TC_ERR_CUDA;
+}
 
 extern "C" {
 
@@ -462,7 +494,7 @@ int tc_init_graph(tc_ctx* c, int n, const int32_t* rowptr, const int32_t* colidx
         rp[i + 1] = (int)ci.size();
     }
     // tile list of the upper triangle for k_pairs
-    const int T = (n + 31) / 32;
+    const int T = (n + tc_pair_tile_edge() - 1) / tc_pair_tile_edge();
     std::vector<int2> tiles;
     tiles.reserve((size_t)T * (T + 1) / 2);
     for (int I = 0; I < T; ++I)
@@ -517,11 +549,11 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     TC_CHECK(cudaStreamSynchronize(c->stream));
     free_population(c);
     const int n = c->n;
-    const int Dp = (D + 1) & ~1;
+    const int Dp = (D + 3) & ~3;
     const size_t Dnk = (size_t)D * n * k;
     if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) ||
-        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)n * n)) ||
-        (rc = dalloc(&c->d_perm, (size_t)D * n)) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
+        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)n * ((n + 3) & ~3))) ||
+        (rc = dalloc(&c->d_perm, (size_t)D * ((n + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
         (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
         (rc = dalloc(&c->d_lut, 4 * (size_t)(D + 1))) || (rc = dalloc(&c->d_st, 1)) ||
@@ -533,7 +565,14 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     c->k = k;
     c->Dp = Dp;
     c->p = p;
+    c->ldb = (n + 3) & ~3;
     c->pop = true;
+    rc = tc_encode_tmap_2d(&c->tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->d_B, (uint64_t)n, (uint64_t)n,
+                           4ull * c->ldb, 32, TC_BT_BOX_ROWS, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (rc) {
+        free_population(c);
+        return rc;
+    }
     tc_dev_state st;
     memset(&st, 0, sizeof(st));
     st.best_f = -1;
@@ -729,12 +768,10 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
     P.dbg_Mt = d_mt;
     P.dbg_G = d_G;
     P.dbg_gamma = d_gam;
-    cudaError_t e = cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * D, c->stream);
-    if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
+    cudaError_t e = tc_launch_pairs(P, c->stream);
     if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
-    if (e == cudaSuccess && G) e = tc_launch_update(P, c->num_sms, c->stream, 1);
-    if (e == cudaSuccess && gamma_own) e = tc_launch_debug_gamma(P, c->stream);
-    c->launches += 2 + (G ? 1 : 0) + (gamma_own ? 1 : 0);
+    if (e == cudaSuccess && G) e = tc_launch_update(P, c->tmB, c->num_sms, c->stream, 1);
+    c->launches += 2 + (G ? 1 : 0);
     std::vector<uint16_t> hc;
     tc_dev_state h;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

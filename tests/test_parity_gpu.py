@@ -78,7 +78,8 @@ def test_trajectory_with_reinjection_gnp125():
 
 @pytest.mark.parametrize("n,p_edge,D,k", [
     (1, 0.0, 1, 1), (2, 1.0, 3, 2), (33, 0.5, 3, 5), (97, 0.3, 7, 33), (70, 0.5, 5, 97),
-    (64, 0.0, 4, 3), (40, 1.0, 2, 40), (161, 0.2, 9, 64), (250, 0.5, 31, 130)])
+    (64, 0.0, 4, 3), (40, 1.0, 2, 40), (161, 0.2, 9, 64), (250, 0.5, 31, 130),
+    (60, 0.5, 6, 300), (129, 0.7, 5, 256), (200, 0.5, 3, 11)])
 def test_ragged_and_degenerate_shapes(n, p_edge, D, k):
     rp, ci = inputs.gnp(n, p_edge, seed=n + D + k)
     W = inputs.init_weights(D, n, k, 0.05, seed=3)
