@@ -20,6 +20,7 @@
 //              step of eq. 10-12, W -= eta grad, smoothing (eq. 8) and the
 //              next Step 1 argmax, one 32-vertex tile of one individual per
 //              warp, W streamed through shared memory once.
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -499,10 +500,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^28 polls and reports TC_ERR_TIMEOUT.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up after one second and reports TC_ERR_TIMEOUT.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
-    for (unsigned it = 0; it < (1u << 28); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023u) == 0 && global_ns() - t0 > 1000000000ull) break;
+    }
     atomicCAS(err, 0, TC_ERR_TIMEOUT);
     return false;
 }
@@ -566,7 +577,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     while (j < k && next_end == 0) {  // leading empty classes
         Gs[j * 32 + lane] = nut * (float)__ldg(Ed + j);
         ++j;
-        next_end = j < k ? __ldg(of + j + 1) : n;
+        next_end = j < k ? __ldg(of + j + 1) : INT_MAX;
     }
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int p0 = 0; p0 < n; p0 += 8) {
@@ -585,11 +596,11 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
                 Gs[j * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + nut * (float)__ldg(Ed + j);
                 acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
                 ++j;
-                next_end = j < k ? __ldg(of + j + 1) : n + 1;
+                next_end = j < k ? __ldg(of + j + 1) : INT_MAX;  // no class left
                 while (j < k && next_end == p0 + q + 1) {  // empty classes
                     Gs[j * 32 + lane] = nut * (float)__ldg(Ed + j);
                     ++j;
-                    next_end = j < k ? __ldg(of + j + 1) : n + 1;
+                    next_end = j < k ? __ldg(of + j + 1) : INT_MAX;
                 }
             }
         }
@@ -740,7 +751,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     }
 }
 
-constexpr int kSmemOptin = 232448;  // 227 KB per block on sm_100 / sm_103
+constexpr int kSmemOptin = 232448 - 1024;  // 227 KB per block on sm_103, less static slack
 
 }  // namespace
 
