@@ -169,6 +169,8 @@ int tc_step_async(tc_ctx *ctx, int64_t n_iters);
 #define TC_KID_PAIRS 0   /* pair compare: M~, fitness, pair coefficients    */
 #define TC_KID_CLASSES 1 /* colour classes, equity, population reduction    */
 #define TC_KID_UPDATE 2  /* fused gradient gather + softmax-ST update        */
+#define TC_KID_GEMM_M 3  /* dense forms: M~ = S S^T GEMM                     */
+#define TC_KID_GEMM_G 4  /* dense forms: Gamma = A S GEMM                    */
 #define TC_NUM_KID 8
 
 /* Per-kernel device timing with CUDA events recorded around every launch

@@ -1,0 +1,424 @@
+// Dense forms of the two contractions of the TensCol iteration (Goudet,
+// Duval, Hao, Algorithm 1):
+//   Gamma = A . S_cat        Step 2 / first term of eq. 13 (the gamma matrix)
+//   M~    = S_cat . S_cat^T  Step 3-i, eq. 4
+// with S_cat (n x D k) the one-hot population side by side.  Both are
+// C[M x N] = X[M x K] . Y[N x K]^T with X and Y holding only 0 and 1, which
+// FP8 E4M3 represents exactly; FP32 accumulation is exact below 2^24, so the
+// results are the exact integer counts.
+//
+//   k_gemm_tc    tcgen05.mma (kind::f8f6f4, M = 128, N = 256, K = 32) on the
+//                5th-generation tensor cores: persistent CTA per SM, warp 0
+//                streams 128B-swizzled K-major tiles with TMA into a 4-stage
+//                shared-memory ring, warp 1 issues the MMAs into one of two
+//                TMEM accumulators (2 x 256 columns), warps 2-5 drain the other
+//                accumulator (tcgen05.ld) and store it.
+//   k_gemm_simt  the same contraction with FP32 FFMA on the CUDA cores (the
+//                plain FP32 comparator), same work units and epilogues.
+//
+// Work is a host-built list of units (tile row, tile column, first and last
+// K block); the M~ units cover only tiles touching the upper triangle and may
+// split K, their partial sums being added with FP32 atomics (exact: integer
+// values).  Every mbarrier wait is bounded by one second of wall time; on
+// expiry the kernel records TC_ERR_TIMEOUT, drains its MMAs, frees TMEM and
+// returns.
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "tc_internal.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 128;  // BK in bytes = FP8 elements
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TC_THREADS = 192;
+constexpr int TMEM_COLS = 512;  // two BN-column FP32 accumulators
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after one second or once another role aborted.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
+                                         int* err) {
+    if (bar_try(b, parity)) return true;
+    const unsigned long long t0 = gns();
+    for (unsigned it = 1;; ++it) {
+        if (bar_try(b, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (gns() - t0 > 1000000000ull) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, TC_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(b))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with 128-byte swizzling: rows of 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1u << 16;                  // leading byte offset (unused here)
+    d |= (uint64_t)(1024u >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1u << 46;                  // descriptor version of sm_100 family
+    d |= (uint64_t)2u << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = E4M3, both K-major, M = BM, N = BN.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, int accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     su32(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+          "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+          "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Epilogue of one row segment of 32 columns (values are exact integers).
+// Tiles never cross the padded allocation (n_pad rows, ldc columns).
+__device__ __forceinline__ void store_chunk(const tc_gemm_args& g, int row, int col0, const uint32_t (&v)[32]) {
+    if (row >= g.rows_alloc || col0 + 32 > g.cols_alloc) return;
+    if (g.mode == TC_GEMM_GAMMA) {
+        uint4* d4 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(g.C) + (size_t)row * g.ldc + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                pk[e] = __float2uint_rn(__uint_as_float(v[8 * q + 2 * e])) |
+                        (__float2uint_rn(__uint_as_float(v[8 * q + 2 * e + 1])) << 16);
+            d4[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    } else {
+        float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + (size_t)row * g.ldc + col0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            atomicAdd(d4 + q, make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])));
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+              tc_gemm_args g) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 128-byte swizzled tiles need 1024-byte aligned bases
+    uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bar_init(&tfull[a], 1);
+            bar_init(&tempty[a], 4);
+        }
+        bar_init(&drain, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            unsigned gk = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < g.n_units && ok; u += gridDim.x) {
+                const int4 w = g.units[u];
+                for (int kb = w.z; kb < w.w; ++kb, ++gk) {
+                    const int s = gk % STAGES;
+                    const unsigned r = gk / STAGES;
+                    if (!(ok = bar_wait(&empty[s], (r & 1u) ^ 1u, &abort_flag, g.err))) break;
+                    uint8_t* sa = smem + s * STAGE_BYTES;
+                    bar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(sa, &tmX, kb * BK, w.x * BM, &full[s]);
+                    tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN, &full[s]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            unsigned gk = 0, ui = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < g.n_units && ok; u += gridDim.x, ++ui) {
+                const int4 w = g.units[u];
+                const int a = ui & 1;
+                const unsigned ua = ui >> 1;
+                if (!(ok = bar_wait(&tempty[a], (ua & 1u) ^ 1u, &abort_flag, g.err))) break;
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(a * BN);
+                for (int kb = w.z; kb < w.w; ++kb, ++gk) {
+                    const int s = gk % STAGES;
+                    const unsigned r = gk / STAGES;
+                    if (!(ok = bar_wait(&full[s], r & 1u, &abort_flag, g.err))) break;
+                    tc_fence_after();
+                    const uint32_t sa = su32(smem + s * STAGE_BYTES);
+                    const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 32; ++kk)  // +32 bytes = +2 in the address field
+                        mma_f8(dt, ad + 2 * kk, bd + 2 * kk, (kb > w.z || kk > 0) ? 1 : 0);
+                    mma_commit(&empty[s]);  // stage s is free once these MMAs finish
+                }
+                if (ok) mma_commit(&tfull[a]);
+            }
+            // drain: every issued MMA completes before TMEM is released
+            mma_commit(&drain);
+            const unsigned long long t0 = gns();
+            while (!bar_try(&drain, 0)) {
+                if (gns() - t0 > 1000000000ull) {
+                    atomicCAS(g.err, 0, TC_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    } else {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ...
+        const int q = warp & 3;
+        const int row_in_tile = 32 * q + lane;
+        unsigned ui = 0;
+        for (int u = blockIdx.x; u < g.n_units; u += gridDim.x, ++ui) {
+            const int4 w = g.units[u];
+            const int a = ui & 1;
+            const unsigned ua = ui >> 1;
+            if (!bar_wait(&tfull[a], ua & 1u, &abort_flag, g.err)) break;
+            tc_fence_after();
+            const int row = w.x * BM + row_in_tile;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN + 32 * c), v);
+                store_chunk(g, row, w.y * BN + 32 * c, v);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&tempty[a]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 CUDA-core GEMM over the same operands (FP8 bytes decoded to FP32) and
+// the same work units: 128 x 256 tile, 256 threads, 8 x 16 outputs each.
+// ---------------------------------------------------------------------------
+constexpr int SK = 32;  // K elements per shared-memory stage
+
+__global__ void __launch_bounds__(256, 1) k_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk,
+                                                    tc_gemm_args g) {
+    __shared__ __align__(16) float As[SK][BM];
+    __shared__ __align__(16) float Bs[SK][BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int u = blockIdx.x; u < g.n_units; u += gridDim.x) {
+        const int4 w = g.units[u];
+        float acc[8][16];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 16; ++b) acc[a][b] = 0.f;
+        for (int kb = w.z * (BK / SK); kb < w.w * (BK / SK); ++kb) {
+            const int k0 = kb * SK;
+            __syncthreads();
+            {  // X tile: 128 rows x 32 bytes, one 16-byte vector per thread
+                const int r = tid >> 1, h = tid & 1;
+                const uint4 v = *reinterpret_cast<const uint4*>(X + (size_t)(w.x * BM + r) * ldk + k0 + 16 * h);
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(
+                        (__nv_fp8x2_storage_t)((wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu), __NV_E4M3);
+                    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&h2));
+                    As[16 * h + 2 * q][r] = f.x;
+                    As[16 * h + 2 * q + 1][r] = f.y;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {  // Y tile: 256 rows x 32 bytes
+                const int e = tid + 256 * p;
+                const int r = e >> 1, h = e & 1;
+                const uint4 v = *reinterpret_cast<const uint4*>(Y + (size_t)(w.y * BN + r) * ldk + k0 + 16 * h);
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2(
+                        (__nv_fp8x2_storage_t)((wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu), __NV_E4M3);
+                    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&h2));
+                    Bs[16 * h + 2 * q][r] = f.x;
+                    Bs[16 * h + 2 * q + 1][r] = f.y;
+                }
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < SK; ++kk) {
+                float av[8], bv[16];
+                const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+                av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+                av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4 + 64 * q]);
+                    bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
+                }
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+            }
+        }
+        // outputs: rows ty*8 + a, columns tx*4 + 64*qq + r
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int row = w.x * BM + ty * 8 + a;
+            if (row >= g.rows_alloc) continue;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int col = w.y * BN + tx * 4 + 64 * qq;
+                if (col + 4 > g.cols_alloc) continue;
+                if (g.mode == TC_GEMM_GAMMA) {
+                    uint16_t* dst = reinterpret_cast<uint16_t*>(g.C) + (size_t)row * g.ldc + col;
+                    const uint32_t p0 = (uint32_t)__float2uint_rn(acc[a][4 * qq]) |
+                                        ((uint32_t)__float2uint_rn(acc[a][4 * qq + 1]) << 16);
+                    const uint32_t p1 = (uint32_t)__float2uint_rn(acc[a][4 * qq + 2]) |
+                                        ((uint32_t)__float2uint_rn(acc[a][4 * qq + 3]) << 16);
+                    *reinterpret_cast<uint2*>(dst) = make_uint2(p0, p1);
+                } else {
+                    float* dst = reinterpret_cast<float*>(g.C) + (size_t)row * g.ldc + col;
+                    atomicAdd(reinterpret_cast<float4*>(dst),
+                              make_float4(acc[a][4 * qq], acc[a][4 * qq + 1], acc[a][4 * qq + 2],
+                                          acc[a][4 * qq + 3]));
+                }
+            }
+        }
+    }
+}
+
+// S_cat / S_cat^T as FP8 one-hot operands from the colours (zeroed first).
+__global__ void k_onehot_build(tc_kparams P) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)P.D * P.n) return;
+    const int d = (int)(r / P.n), i = (int)(r % P.n);
+    const int col = d * P.k + P.c[r];
+    P.S8[(size_t)i * P.ldg + col] = 0x38;  // E4M3 1.0
+    P.S8T[(size_t)col * P.n_pad + i] = 0x38;
+}
+
+}  // namespace
+
+cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s) {
+    const long long rows = (long long)P.D * P.n;
+    k_onehot_build<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+int tc_gemm_tile_m() { return BM; }
+int tc_gemm_tile_n() { return BN; }
+int tc_gemm_tile_k() { return BK; }
+
+cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
+                              int num_sms, cudaStream_t s) {
+    const int smem = STAGES * STAGE_BYTES + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int grid = num_sms < g.n_units ? num_sms : g.n_units;
+    if (grid < 1) grid = 1;
+    k_gemm_tc<<<grid, TC_THREADS, smem, s>>>(tmX, tmY, g);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
+                                int num_sms, cudaStream_t s) {
+    int grid = 2 * num_sms < g.n_units ? 2 * num_sms : g.n_units;
+    if (grid < 1) grid = 1;
+    k_gemm_simt<<<grid, 256, 0, s>>>(X, Y, ldk, g);
+    return cudaGetLastError();
+}

@@ -59,6 +59,14 @@ struct tc_kparams {
     const float* powB;        // [0..D]: v^beta
     tc_dev_state* st;
     uint16_t* best;           // n best-so-far colours
+    // dense forms (NULL in the one-hot form)
+    const float* M32;         // n_pad x n_pad group concentration from a GEMM
+    int ldm;
+    const uint16_t* G16;      // n_pad x ldg gamma matrix A.S_cat from a GEMM
+    int ldg;
+    uint8_t* S8;              // n_pad x ldg one-hot S_cat, FP8 E4M3 (1.0 = 0x38)
+    uint8_t* S8T;             // ldg x n_pad its transpose
+    int n_pad;
     int* dbg_Mt;              // optional n x n group concentration output
     float* dbg_G;             // optional D x n x k grad_S L output
     int* dbg_gamma;           // optional D x n conflicting-neighbour counts
@@ -78,6 +86,27 @@ int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint
                       uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
                       CUtensorMapSwizzle swizzle);
 constexpr int TC_BT_BOX_ROWS = 128;  // rows per TMA box of the B column panel
+// Dense contractions (tc_dense.cu): C = X . Y^T over FP8 0/1 operands.
+#define TC_GEMM_GAMMA 0  /* C uint16, plain stores                      */
+#define TC_GEMM_MTILDE 1 /* C float, atomic adds (K may be split)       */
+struct tc_gemm_args {
+    const int4* units;  // (tile row, tile column, first K block, end K block)
+    int n_units;
+    int mode;
+    void* C;
+    int ldc;
+    int rows_alloc, cols_alloc;
+    int* err;
+};
+int tc_gemm_tile_m();
+int tc_gemm_tile_n();
+int tc_gemm_tile_k();
+cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
+                              int num_sms, cudaStream_t s);
+cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
+                                int num_sms, cudaStream_t s);
+cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s);
+
 int tc_pair_tile_edge();
 int tc_pair_tile_count(int n);
 int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem);

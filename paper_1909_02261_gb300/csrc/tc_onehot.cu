@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) wide[a][b] = 0u;
-    for (int w0 = 0; w0 < Dw; w0 += PAIR_CW) {
+    const bool from_gemm = P.M32 != nullptr;  // dense form: M~ came from a GEMM
+    for (int w0 = 0; w0 < (from_gemm ? 0 : Dw); w0 += PAIR_CW) {
         const int cw = min(PAIR_CW, Dw - w0);
         __syncthreads();
         for (int e = tid; e < PT * cw; e += PAIR_THREADS) {
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
             float bb = 0.f;
             int mt = 0;
             if (i < n && m < n && (I < M || ml >= il)) {
-                mt = (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
+                mt = from_gemm ? __float2int_rn(P.M32[(size_t)i * P.ldm + m])
+                               : (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
                 const bool edge = (P.adj[(size_t)i * P.adj_words + (m >> 5)] >> (m & 31)) & 1u;
                 if (m == i) {
                     mt = D;
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
                         var += P.powB[D];
                     }
                 } else if (edge) {
-                    bb = fmaf(cA, P.lutA[mt], 1.0f);
+                    // the A.S term enters through B only in the one-hot form
+                    bb = from_gemm ? cA * P.lutA[mt] : fmaf(cA, P.lutA[mt], 1.0f);
                     kap += 2.0f * P.powA[mt];
                 } else {
                     bb = -cB * P.lutB[mt];
@@ -401,27 +404,61 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     fe = block_sum<long long>(fe, sh_ll);
     if (threadIdx.x == 0) P.feq[d] = (int)fe;
     __syncthreads();
-    // stable counting sort of the vertices by colour (warp 0, 32 at a time)
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    // stable counting sort of the vertices by colour: each warp owns a
+    // contiguous chunk; per-warp colour counts give every (warp, colour) its
+    // base, and ranks within 32-vertex rounds come from warp matching
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
+    int* wcnt = reinterpret_cast<int*>(s_bits);  // nwp x k, before the bitmaps
+    for (int e = threadIdx.x; e < nwp * k; e += blockDim.x) wcnt[e] = 0;
+    __syncthreads();
+    const int chunk = (n + nwp - 1) / nwp;
+    const int cbeg = min(n, warp * chunk), cend = min(n, cbeg + chunk);
+    for (int base = cbeg; base < cend; base += 32) {
+        const int i = base + lane;
+        const unsigned valid = __ballot_sync(0xffffffffu, i < cend);
+        if (i < cend) {
+            const int col = cd[i];
+            const unsigned peers = __match_any_sync(valid, col);
+            if ((__ffs(peers) - 1) == lane) wcnt[warp * k + col] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        int run = s_cur[j];
+        for (int w = 0; w < nwp; ++w) {
+            const int c = wcnt[w * k + j];
+            wcnt[w * k + j] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    {
         uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
-        for (int base = 0; base < n; base += 32) {
+        for (int base = cbeg; base < cend; base += 32) {
             const int i = base + lane;
-            const unsigned valid = __ballot_sync(0xffffffffu, i < n);
-            if (i < n) {
+            const unsigned valid = __ballot_sync(0xffffffffu, i < cend);
+            if (i < cend) {
                 const int col = cd[i];
                 const unsigned peers = __match_any_sync(valid, col);
                 const int rank = __popc(peers & ((1u << lane) - 1u));
-                pd[s_cur[col] + rank] = (uint16_t)i;
+                pd[wcnt[warp * k + col] + rank] = (uint16_t)i;
                 __syncwarp(valid);
-                if ((__ffs(peers) - 1) == lane) s_cur[col] += __popc(peers);
+                if ((__ffs(peers) - 1) == lane) wcnt[warp * k + col] += __popc(peers);
             }
             __syncwarp();
         }
     }
-    // conflicts (eq. 1) by colour bitmaps, cls_colours colours per pass
+    // conflicts (eq. 1): from the gamma matrix of the dense form, else by
+    // colour bitmaps (cls_colours colours per pass), one warp per vertex
     long long twice = 0;
-    for (int cb = 0; cb < k; cb += cls_colours) {
+    if (P.G16)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int g = P.G16[(size_t)i * P.ldg + (size_t)d * k + cd[i]];
+            twice += g;
+            if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
+        }
+    for (int cb = 0; cb < (P.G16 ? 0 : k); cb += cls_colours) {
         const int ce = min(k, cb + cls_colours);
         __syncthreads();
         for (int e = threadIdx.x; e < (ce - cb) * aw; e += blockDim.x) s_bits[e] = 0u;
@@ -431,15 +468,19 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
             if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * aw + (i >> 5)], 1u << (i & 31));
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = warp; i < n; i += nwp) {
             const int col = cd[i];
-            if (col < cb || col >= ce) continue;
+            if (col < cb || col >= ce) continue;  // uniform per warp
             const uint32_t* ar = P.adj + (size_t)i * aw;
             const uint32_t* xr = s_bits + (col - cb) * aw;
             int g = 0;
-            for (int w = 0; w < aw; ++w) g += __popc(__ldg(ar + w) & xr[w]);
-            twice += g;
-            if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
+            for (int w = lane; w < aw; w += 32) g += __popc(__ldg(ar + w) & xr[w]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+            if (lane == 0) {
+                twice += g;
+                if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
+            }
         }
     }
     twice = block_sum<long long>(twice, sh_ll);
@@ -572,6 +613,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     const int8_t* Ed = P.E + (size_t)d * k;
     const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
     const int bstride = BTS ? 32 : P.ldb;
+    const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
     int j = 0;
     int next_end = __ldg(of + 1);
     while (j < k && next_end == 0) {  // leading empty classes
@@ -593,7 +635,8 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
         for (int q = 0; q < 8; ++q) {
             acc[q & 3] += b[q];
             if (p0 + q + 1 == next_end) {  // class j ends here (uniform branch)
-                Gs[j * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + nut * (float)__ldg(Ed + j);
+                const float gam = grow ? (float)__ldg(grow + j) : 0.f;  // dense form: A.S
+                Gs[j * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + nut * (float)__ldg(Ed + j) + gam;
                 acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
                 ++j;
                 next_end = j < k ? __ldg(of + j + 1) : INT_MAX;  // no class left
@@ -673,8 +716,231 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     } else {
         for (int e = lane; e < rows * k; e += 32) P.W[wbase + e] = Ws[e];
     }
-    if (lane < rows) store_colour(P, d, i0 + lane, newc);
+    if (lane < rows) {
+        const int i = i0 + lane;
+        if (P.S8) {  // dense form: move the one-hot entry of (d, i) in both operands
+            const int old = P.c[(size_t)d * n + i];
+            if (old != newc) {
+                const size_t co = (size_t)d * k + old, cn = (size_t)d * k + newc;
+                P.S8[(size_t)i * P.ldg + co] = 0;
+                P.S8[(size_t)i * P.ldg + cn] = 0x38;  // E4M3 1.0
+                P.S8T[co * P.n_pad + i] = 0;
+                P.S8T[cn * P.n_pad + i] = 0x38;
+            }
+        }
+        store_colour(P, d, i, newc);
+    }
     __syncwarp();
+}
+
+// Register variant for k <= 32 KQ (KQ = 1..4): the class sums go to a
+// padded shared tile Gs[j][33], then the warp updates the 32 rows one at a
+// time, lanes across colours, with the weight rows streamed straight from
+// global memory through an 8-row register prefetch ring (no shared W tile,
+// which doubles the resident warps).
+template <int KQ>
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <bool BTS, int KQ>
+__device__ __forceinline__ void update_item_rows(const tc_kparams& P, const float* Bt, float* Gs, int T, int d,
+                                                 float nut, bool smooth, int debug_only) {
+    constexpr int PF = 8;  // rows in flight
+    const int n = P.n, k = P.k;
+    const int lane = threadIdx.x & 31;
+    const int i0 = T * 32;
+    const int rows = min(32, n - i0);
+
+    // Phase A: Gs[j][lane] = grad_S L[d, i0 + lane, j] by class-length loops
+    const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
+    const int* of = P.off + (size_t)d * (k + 1);
+    const int8_t* Ed = P.E + (size_t)d * k;
+    const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
+    const int bstride = BTS ? 32 : P.ldb;
+    const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
+    int s = 0;
+    for (int j = 0; j < k; ++j) {
+        const int e = __ldg(of + j + 1);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int p = s;
+        for (; p + 4 <= e; p += 4) {
+            const int m0 = __ldg(pm + p), m1 = __ldg(pm + p + 1), m2 = __ldg(pm + p + 2), m3 = __ldg(pm + p + 3);
+            a0 += Bl[m0 * bstride];
+            a1 += Bl[m1 * bstride];
+            a2 += Bl[m2 * bstride];
+            a3 += Bl[m3 * bstride];
+        }
+        for (; p < e; ++p) a0 += Bl[__ldg(pm + p) * bstride];
+        float g = ((a0 + a1) + (a2 + a3)) + nut * (float)__ldg(Ed + j);
+        if (grow) g += (float)__ldg(grow + j);
+        Gs[j * 33 + lane] = g;
+        s = e;
+    }
+    __syncwarp();
+    if (debug_only) {
+        if (lane < rows) {
+            float* gd = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
+            for (int jj = 0; jj < k; ++jj) gd[jj] = Gs[jj * 33 + lane];
+        }
+        __syncwarp();
+        return;
+    }
+
+    // Phase B: rows of the tile, lanes across colours j = lane + 32 q
+    float* Wt = P.W + ((size_t)d * n + i0) * k;
+    float ring[PF][KQ];
+#pragma unroll
+    for (int r = 0; r < PF; ++r)
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int j = lane + 32 * q;
+            ring[r][q] = (r < rows && j < k) ? Wt[(size_t)r * k + j] : 0.f;
+        }
+    int mycol = 0;
+    for (int r0 = 0; r0 < rows; r0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int r = r0 + u;
+            if (r >= rows) break;
+            float x[KQ], gq[KQ];
+            float mx = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int j = lane + 32 * q;
+                x[q] = j < k ? ring[u][q] : -INFINITY;
+                gq[q] = j < k ? Gs[j * 33 + r] : 0.f;
+                mx = fmaxf(mx, x[q]);
+            }
+            // prefetch row r + PF into the freed slot
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int j = lane + 32 * q;
+                ring[u][q] = (r + PF < rows && j < k) ? Wt[(size_t)(r + PF) * k + j] : 0.f;
+            }
+            mx = warp_max_f<KQ>(mx);
+            float ev[KQ], Z = 0.f, num = 0.f;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                ev[q] = (lane + 32 * q < k) ? __expf(x[q] - mx) : 0.f;
+                Z += ev[q];
+                num = fmaf(ev[q], gq[q], num);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                Z += __shfl_xor_sync(0xffffffffu, Z, o);
+                num += __shfl_xor_sync(0xffffffffu, num, o);
+            }
+            const float invZ = 1.0f / Z;
+            const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
+            float bv = -INFINITY;
+            int bj = k;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int j = lane + 32 * q;
+                if (j < k) {
+                    const float sj = ev[q] * invZ;
+                    float wn = x[q] - P.eta * (sj * (gq[q] - dot));
+                    if (smooth) wn = wn / P.rho;
+                    Wt[(size_t)r * k + j] = wn;
+                    if (wn > bv) {  // j increases with q: first maximum wins
+                        bv = wn;
+                        bj = j;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (ob > bv || (ob == bv && oj < bj)) {
+                    bv = ob;
+                    bj = oj;
+                }
+            }
+            if (lane == r) mycol = bj >= k ? 0 : bj;
+        }
+    }
+    if (lane < rows) {
+        const int i = i0 + lane;
+        if (P.S8) {  // dense form: move the one-hot entry of (d, i) in both operands
+            const int old = P.c[(size_t)d * n + i];
+            if (old != mycol) {
+                const size_t co = (size_t)d * k + old, cn = (size_t)d * k + mycol;
+                P.S8[(size_t)i * P.ldg + co] = 0;
+                P.S8[(size_t)i * P.ldg + cn] = 0x38;
+                P.S8T[co * P.n_pad + i] = 0;
+                P.S8T[cn * P.n_pad + i] = 0x38;
+            }
+        }
+        store_colour(P, d, i, mycol);
+    }
+    __syncwarp();
+}
+
+template <bool BTS, int KQ>
+__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
+    k_update_rows(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block, int debug_only) {
+    tc_dev_state* st = P.st;
+    if (!debug_only && st->stop) return;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ __align__(8) uint64_t s_bbar;
+    const int n = P.n, D = P.D, k = P.k;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nbox = (n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS;
+    float* Bt = sm;
+    float* Gs = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * (33 * k);
+    unsigned bphase = 0;
+    if (BTS && threadIdx.x == 0) {
+        mbar_init(&s_bbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+    const long long t = st->t;
+    const float nut = (float)((double)P.nu * (double)t);
+    const bool smooth = ((t + 1) % P.nb_iter) == 0;
+    const int nT = (n + 31) / 32;
+    const long long Q = (long long)nT * D;
+    long long q = (long long)blockIdx.x * items_per_block;
+    const long long qend = min(Q, q + items_per_block);
+    while (q < qend) {
+        const int T = (int)(q / D);
+        const long long seg_end = min(qend, (long long)(T + 1) * D);
+        if (BTS) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
+                for (int b = 0; b < nbox; ++b)
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS),
+                        "r"(smem_u32(&s_bbar))
+                        : "memory");
+            }
+            mbar_wait_bounded(&s_bbar, bphase, &st->err);
+            bphase ^= 1u;
+        }
+        for (long long qq = q + warp; qq < seg_end; qq += nw)
+            update_item_rows<BTS, KQ>(P, Bt, Gs, T, (int)(qq - (long long)T * D), nut, smooth, debug_only);
+        q = seg_end;
+    }
+    if (!debug_only) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned ticket = atomicAdd(&st->done_update, 1u);
+            if (ticket == gridDim.x - 1) {
+                st->done_update = 0u;
+                st->t = t + 1;
+                __threadfence();
+            }
+        }
+    }
 }
 
 template <bool BTS, bool BULK>
@@ -763,9 +1029,10 @@ int tc_pair_tile_count(int n) {
 }
 
 int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem) {
-    // per warp: Gs (32 x k) + Ws (32 x k) floats + one mbarrier (16 B);
-    // the B panel: whole TMA boxes of TC_BT_BOX_ROWS x 32 floats
-    const long long per_warp = 4ll * (64ll * k + 4);
+    // per warp, k <= 128: Gs (k x 33) floats; larger k: Gs (32 x k) + Ws
+    // (32 x k) floats + one mbarrier (16 B).  The B panel: whole TMA boxes
+    // of TC_BT_BOX_ROWS x 32 floats.
+    const long long per_warp = k <= 128 ? 4ll * 33 * k : 4ll * (64ll * k + 4);
     const long long bt = 4ll * 32 * ((n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
     int w = 0, bts = 0;
     if (bt + per_warp <= kSmemOptin) {
@@ -810,7 +1077,10 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     int colours = (int)((160ll << 10) / row);
     if (colours > P.k) colours = P.k;
     if (colours < 1) colours = 1;
-    const int smem = (int)(colours * row);
+    long long smem_ll = colours * row;
+    const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // per-warp colour counts
+    if (smem_ll < counts) smem_ll = counts;
+    const int smem = (int)smem_ll;
     cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_classes<<<P.D, CLS_THREADS, smem, s>>>(P, colours);
@@ -821,6 +1091,16 @@ template <bool BTS, bool BULK>
 static cudaError_t launch_update_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps,
                                    int smem, int per_block, cudaStream_t s, int debug_only) {
     auto fn = k_update<BTS, BULK>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
+    return cudaGetLastError();
+}
+
+template <bool BTS, int KQ>
+static cudaError_t launch_rows_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps,
+                                 int smem, int per_block, cudaStream_t s, int debug_only) {
+    auto fn = k_update_rows<BTS, KQ>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
@@ -839,6 +1119,19 @@ cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int nu
     // bulk copies need 16-byte aligned, 16-byte multiple tiles: n k % 4 == 0
     // (tile starts are (d n + 32 T) k floats, tile sizes rows k floats)
     const bool bulk = ((long long)P.n * P.k) % 4 == 0 && (((uintptr_t)P.W) & 15) == 0;
+    if (P.k <= 128) {
+        const int kq = (P.k + 31) / 32;
+#define TC_ROWS(KQ)                                                                                    \
+    return bts ? launch_rows_t<true, KQ>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)    \
+               : launch_rows_t<false, KQ>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
+        switch (kq) {
+            case 1: TC_ROWS(1);
+            case 2: TC_ROWS(2);
+            case 3: TC_ROWS(3);
+            default: TC_ROWS(4);
+        }
+#undef TC_ROWS
+    }
     if (bts)
         return bulk ? launch_update_t<true, true>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
                     : launch_update_t<true, false>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only);

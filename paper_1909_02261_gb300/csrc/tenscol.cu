@@ -51,6 +51,21 @@ struct tc_ctx {
     uint16_t* d_best = nullptr;
     int ldb = 0;
     alignas(64) CUtensorMap tmB;  // B column panels for k_update
+    // dense forms: FP8 operands, GEMM outputs, tensor maps, work units
+    std::vector<int> h_rowptr, h_colidx;
+    int n_pad = 0, ldg = 0;
+    uint8_t* d_A8 = nullptr;
+    uint8_t* d_S8 = nullptr;
+    uint8_t* d_S8T = nullptr;
+    uint16_t* d_G16 = nullptr;
+    float* d_M32 = nullptr;
+    int4* d_units_g = nullptr;
+    int4* d_units_m = nullptr;
+    int n_units_g = 0, n_units_m = 0;
+    alignas(64) CUtensorMap tmA8;
+    alignas(64) CUtensorMap tmS8T;
+    alignas(64) CUtensorMap tmS8x;
+    alignas(64) CUtensorMap tmS8y;
     // CUDA graph of graph_chunk iterations
     int graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -125,8 +140,21 @@ void drop_graph_exec(tc_ctx* c) {
     c->gexec = nullptr;
 }
 
+void free_dense(tc_ctx* c) {
+    dfree(c->d_A8);
+    dfree(c->d_S8);
+    dfree(c->d_S8T);
+    dfree(c->d_G16);
+    dfree(c->d_M32);
+    dfree(c->d_units_g);
+    dfree(c->d_units_m);
+    c->n_units_g = c->n_units_m = 0;
+    c->n_pad = c->ldg = 0;
+}
+
 void free_population(tc_ctx* c) {
     drop_graph_exec(c);
+    free_dense(c);
     dfree(c->d_W);
     dfree(c->d_c);
     dfree(c->d_cT);
@@ -160,7 +188,8 @@ int check_params(const tc_params* p) {
     if (!(p->alpha > 1.f) || !(p->beta > 1.f)) return TC_ERR_ARG;
     if (!(p->lambda_ >= 0.f) || !(p->mu >= 0.f) || !(p->nu >= 0.f) || !(p->sigma0 >= 0.f))
         return TC_ERR_ARG;
-    if (p->form != TC_FORM_ONEHOT) return TC_ERR_UNSUPPORTED;
+    if (p->form != TC_FORM_ONEHOT && p->form != TC_FORM_DENSE_FP8 && p->form != TC_FORM_DENSE_FP32)
+        return TC_ERR_UNSUPPORTED;
     return TC_OK;
 }
 
@@ -207,7 +236,97 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.powB = c->d_lut + 3 * D1;
     P.st = c->d_st;
     P.best = c->d_best;
+    if (c->p.form != TC_FORM_ONEHOT && c->d_M32) {
+        P.M32 = c->d_M32;
+        P.ldm = c->n_pad;
+        P.G16 = c->d_G16;
+        P.ldg = c->ldg;
+        P.S8 = c->d_S8;
+        P.S8T = c->d_S8T;
+        P.n_pad = c->n_pad;
+    }
     return P;
+}
+
+// Dense forms: FP8 adjacency, one-hot operands, GEMM outputs, tensor maps and
+// the work units of the two contractions.  n_pad is a multiple of both GEMM
+// tile edges, ldg (the padded D k) a multiple of the column tile.
+int setup_dense(tc_ctx* c) {
+    free_dense(c);
+    const int BMt = tc_gemm_tile_m(), BNt = tc_gemm_tile_n(), BKt = tc_gemm_tile_k();
+    const int n = c->n;
+    const int n_pad = (n + BNt - 1) / BNt * BNt;
+    const long long Kc = (long long)c->D * c->k;
+    const long long ldg = (Kc + BNt - 1) / BNt * BNt;
+    if (ldg > (1ll << 31) / 4) return TC_ERR_UNSUPPORTED;
+    int rc;
+    if ((rc = dalloc(&c->d_A8, (size_t)n_pad * n_pad)) || (rc = dalloc(&c->d_S8, (size_t)n_pad * ldg)) ||
+        (rc = dalloc(&c->d_S8T, (size_t)ldg * n_pad)) || (rc = dalloc(&c->d_G16, (size_t)n_pad * ldg)) ||
+        (rc = dalloc(&c->d_M32, (size_t)n_pad * n_pad))) {
+        free_dense(c);
+        return rc;
+    }
+    c->n_pad = n_pad;
+    c->ldg = (int)ldg;
+    std::vector<uint8_t> a8((size_t)n_pad * n_pad, 0);
+    for (int i = 0; i < n; ++i)
+        for (int e = c->h_rowptr[i]; e < c->h_rowptr[i + 1]; ++e) a8[(size_t)i * n_pad + c->h_colidx[e]] = 0x38;
+    // work units: Gamma over all tiles (row tiles fastest, so neighbouring
+    // CTAs share the S_cat^T tile), M~ over the tiles touching the upper
+    // triangle with K split to give every SM work
+    std::vector<int4> ug, um;
+    const int mt = n_pad / BMt, ntg = (int)(ldg / BNt), ntm = n_pad / BNt;
+    for (int bn = 0; bn < ntg; ++bn)
+        for (int bm = 0; bm < mt; ++bm) ug.push_back(make_int4(bm, bn, 0, n_pad / BKt));
+    std::vector<int2> tri;
+    for (int bn = 0; bn < ntm; ++bn)
+        for (int bm = 0; bm < mt; ++bm)
+            if ((long long)bn * BNt + BNt - 1 >= (long long)bm * BMt) tri.push_back(make_int2(bm, bn));
+    const int kblocks = (int)(ldg / BKt);
+    int split = (int)((c->num_sms + tri.size() - 1) / tri.size());
+    split = std::max(1, std::min(split, kblocks));
+    for (int sidx = 0; sidx < split; ++sidx)
+        for (auto& tt : tri) {
+            const int k0 = (int)((long long)kblocks * sidx / split), k1 = (int)((long long)kblocks * (sidx + 1) / split);
+            if (k1 > k0) um.push_back(make_int4(tt.x, tt.y, k0, k1));
+        }
+    if ((rc = dalloc(&c->d_units_g, ug.size())) || (rc = dalloc(&c->d_units_m, um.size()))) {
+        free_dense(c);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_A8, a8.data(), a8.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_units_g, ug.data(), ug.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_units_m, um.data(), um.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_dense(c);
+        return cuda_status(e);
+    }
+    c->n_units_g = (int)ug.size();
+    c->n_units_m = (int)um.size();
+    const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
+    if ((rc = tc_encode_tmap_2d(&c->tmA8, u8, c->d_A8, n_pad, n_pad, n_pad, BKt, BMt, sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, BNt, sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, BNt, sw))) {
+        free_dense(c);
+        return rc;
+    }
+    return TC_OK;
+}
+
+// Rebuilds the FP8 one-hot operands from the current colours.
+cudaError_t rebuild_onehot(tc_ctx* c) {
+    if (!c->d_S8) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->d_S8, 0, (size_t)c->n_pad * c->ldg, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_S8T, 0, (size_t)c->ldg * c->n_pad, c->stream);
+    if (e == cudaSuccess) e = tc_launch_onehot_build(make_kparams(c, 0), c->stream);
+    c->launches += 1;
+    return e;
 }
 
 // The LUTs of the pair terms over the integer values v = 0..D of m~ (eq. 5,
@@ -291,14 +410,43 @@ void free_events(tc_ctx* c) {
     c->spare.clear();
 }
 
+// The two dense contractions of the dense forms: M~ (into d_M32) and Gamma
+// (into d_G16), on the tensor cores (FP8) or the CUDA cores (FP32).
+int launch_dense_gemms(tc_ctx* c, int which) {
+    tc_gemm_args gm = {c->d_units_m, c->n_units_m, TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
+                       &c->d_st->err};
+    tc_gemm_args gg = {c->d_units_g, c->n_units_g, TC_GEMM_GAMMA, c->d_G16, c->ldg, c->n_pad, c->ldg,
+                       &c->d_st->err};
+    const bool tc = c->p.form == TC_FORM_DENSE_FP8;
+    if (which == 0) {
+        TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, c->stream));
+        TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->num_sms, c->stream)
+                      : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, c->stream);
+        }));
+    } else {
+        TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->num_sms, c->stream)
+                      : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, c->stream);
+        }));
+    }
+    return TC_OK;
+}
+
 int launch_iteration(tc_ctx* c) {
     if (fault("launch")) return TC_ERR_INJECTED;
     tc_kparams P = make_kparams(c, 1);
+    const bool dense = P.M32 != nullptr;
+    int rc;
+    if (dense && (rc = launch_dense_gemms(c, 0))) return rc;
     TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
+    if (dense && (rc = launch_dense_gemms(c, 1))) return rc;
     TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
     TC_CHECK(timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->tmB, c->num_sms, c->stream, 0); }));
     return TC_OK;
 }
+
+int launches_per_iteration(const tc_ctx* c) { return c->p.form == TC_FORM_ONEHOT ? 3 : 5; }
 
 int read_state(tc_ctx* c, tc_dev_state* h) {
     TC_CHECK(cudaMemcpyAsync(h, c->d_st, sizeof(*h), cudaMemcpyDeviceToHost, c->stream));
@@ -530,6 +678,8 @@ int tc_init_graph(tc_ctx* c, int n, const int32_t* rowptr, const int32_t* colidx
     c->n = n;
     c->nnz = (long long)ci.size();
     c->adj_words = aw;
+    c->h_rowptr = rp;
+    c->h_colidx = ci;
     c->n_tiles = (int)tiles.size();
     return TC_OK;
 }
@@ -593,7 +743,11 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
         return cuda_status(e);
     }
     rc = upload_luts(c);
+    if (!rc && p.form != TC_FORM_ONEHOT) rc = setup_dense(c);
+    if (!rc && rebuild_onehot(c) != cudaSuccess) rc = TC_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = TC_ERR_CUDA;
     if (rc) {
+        (void)cudaGetLastError();
         free_population(c);
         return rc;
     }
@@ -610,7 +764,17 @@ int tc_set_params(tc_ctx* c, const tc_params* p) {
     tc_params old = c->p;
     c->p = *p;
     rc = upload_luts(c);
+    if (!rc && p->form != old.form) {
+        if (p->form == TC_FORM_ONEHOT) {
+            free_dense(c);
+        } else if (!c->d_M32) {
+            rc = setup_dense(c);
+            if (!rc && rebuild_onehot(c) != cudaSuccess) rc = TC_ERR_CUDA;
+            if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = TC_ERR_CUDA;
+        }
+    }
     if (rc) {
+        (void)cudaGetLastError();
         c->p = old;
         upload_luts(c);
         return rc;
@@ -640,7 +804,7 @@ int tc_step(tc_ctx* c, int64_t n_iters, int64_t* iters_done) {
                 if (rc) return rc;
             }
             TC_CHECK(cudaGraphLaunch(c->gexec, c->stream));
-            c->launches += 3ll * c->graph_chunk;
+            c->launches += (long long)launches_per_iteration(c) * c->graph_chunk;
             left -= c->graph_chunk;
             since_poll += c->graph_chunk;
         } else {
@@ -721,6 +885,7 @@ static int set_state_common(tc_ctx* c, const float* W, const int64_t* t, cudaMem
     TC_CHECK(cudaMemsetAsync(&c->d_st->stop, 0, sizeof(int), c->stream));
     TC_CHECK(tc_launch_assign(make_kparams(c, 0), c->stream));
     c->launches += 1;
+    TC_CHECK(rebuild_onehot(c));
     TC_CHECK(cudaStreamSynchronize(c->stream));
     return TC_OK;
 }
@@ -768,7 +933,11 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
     P.dbg_Mt = d_mt;
     P.dbg_G = d_G;
     P.dbg_gamma = d_gam;
-    cudaError_t e = tc_launch_pairs(P, c->stream);
+    const bool dense = P.M32 != nullptr;
+    cudaError_t e = cudaSuccess;
+    if (dense && launch_dense_gemms(c, 0)) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
+    if (e == cudaSuccess && dense && launch_dense_gemms(c, 1)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
     if (e == cudaSuccess && G) e = tc_launch_update(P, c->tmB, c->num_sms, c->stream, 1);
     c->launches += 2 + (G ? 1 : 0);
@@ -794,6 +963,7 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
         loss[2] = h.varpi;
         loss[3] = (float)h.fcolor_sum;
     }
+    if (e == cudaSuccess && !loss) e = cudaMemcpy(&h, c->d_st, sizeof(h), cudaMemcpyDeviceToHost);
     dfree(d_mt);
     dfree(d_G);
     dfree(d_gam);
@@ -801,7 +971,7 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
         (void)cudaGetLastError();
         return cuda_status(e);
     }
-    return TC_OK;
+    return h.err ? h.err : TC_OK;
 }
 
 int tc_step_async(tc_ctx* c, int64_t n_iters) {
@@ -813,7 +983,7 @@ int tc_step_async(tc_ctx* c, int64_t n_iters) {
         if (c->graph_chunk > 0 && n_iters - it >= c->graph_chunk) {
             if (!c->gexec && (rc = build_graph_exec(c))) return rc;
             TC_CHECK(cudaGraphLaunch(c->gexec, c->stream));
-            c->launches += 3ll * c->graph_chunk;
+            c->launches += (long long)launches_per_iteration(c) * c->graph_chunk;
             it += c->graph_chunk;
         } else {
             if ((rc = launch_iteration(c))) return rc;

@@ -51,3 +51,30 @@ def loss_close(gpu_loss, ref, po, t, rtol=1e-5):
 def _approx(x, rtol):
     import pytest
     return pytest.approx(x, rel=rtol, abs=1e-30)
+
+
+def check_iteration(ctx, rp, ci, p, t, want_G=True):
+    """Evaluate + one step on the GPU vs one oracle step from the GPU's own
+    weights: exact colours / conflicts / equity / M~, G and W within W_RTOL."""
+    W0, t0 = ctx.tc_get_state()
+    assert t0 == t
+    po = oracle_params(p)
+    ev = ctx.tc_evaluate(want_G=want_G)
+    ref = O.step(rp, ci, W0, po, t, stop_on_legal=False)
+    assert np.array_equal(ev["colors"], ref["colors"])
+    assert np.array_equal(ev["gamma_own"], ref["gamma_own"])
+    assert np.array_equal(ev["f_color"], ref["f_color"])
+    assert np.array_equal(ev["f_eq"], ref["f_eq"])
+    assert np.array_equal(ev["Mt"], ref["Mt"])
+    loss_close(ev["loss"], ref, po, t)
+    if want_G:
+        assert g_rel_error(ev["G"], ref["G"]) <= W_RTOL
+    assert ctx.tc_step(1) == 1
+    W1, t1 = ctx.tc_get_state()
+    assert t1 == t + 1
+    err = w_step_rel_error(W1, ref, po, t)
+    assert err <= W_RTOL, err
+    # the next assignment (argmax epilogue of the update) equals Step 1 on W1
+    ev1 = ctx.tc_evaluate(want_G=False, want_M=False)
+    assert np.array_equal(ev1["colors"], O.assign(W1))
+    return ref, err

@@ -12,7 +12,7 @@ from oracle import oracle as O
 from paper_1909_02261_gb300 import inputs
 from paper_1909_02261_gb300.tenscol import TC_ECP, TC_KCOL, TensCol, TensColError, params
 
-from helpers import W_RTOL, g_rel_error, loss_close, oracle_params, w_step_rel_error
+from helpers import W_RTOL, check_iteration, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -25,32 +25,6 @@ def make_ctx(rp, ci, D, k, p, W=None, t=0, seed=1):
     if W is not None:
         ctx.tc_set_state(W, t)
     return ctx
-
-
-def check_iteration(ctx, rp, ci, p, t, want_G=True):
-    """Evaluate + one step on the GPU vs one oracle step from the same W."""
-    W0, t0 = ctx.tc_get_state()
-    assert t0 == t
-    po = oracle_params(p)
-    ev = ctx.tc_evaluate(want_G=want_G)
-    ref = O.step(rp, ci, W0, po, t, stop_on_legal=False)
-    assert np.array_equal(ev["colors"], ref["colors"])
-    assert np.array_equal(ev["gamma_own"], ref["gamma_own"])
-    assert np.array_equal(ev["f_color"], ref["f_color"])
-    assert np.array_equal(ev["f_eq"], ref["f_eq"])
-    assert np.array_equal(ev["Mt"], ref["Mt"])
-    loss_close(ev["loss"], ref, po, t)
-    if want_G:
-        assert g_rel_error(ev["G"], ref["G"]) <= W_RTOL
-    assert ctx.tc_step(1) == 1
-    W1, t1 = ctx.tc_get_state()
-    assert t1 == t + 1
-    err = w_step_rel_error(W1, ref, po, t)
-    assert err <= W_RTOL, err
-    # the next assignment (argmax epilogue of the update) equals Step 1 on W1
-    ev1 = ctx.tc_evaluate(want_G=False, want_M=False)
-    assert np.array_equal(ev1["colors"], O.assign(W1))
-    return ref, err
 
 
 @pytest.mark.parametrize("t", [0, 4, 37])
