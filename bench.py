@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-baseline-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     return ap.parse_args()
 
 
@@ -219,42 +220,49 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            ctx.tc_step_async(1)
-            flush.zero_()
-        stream.synchronize()
-        ctx.tc_set_timing(True)
-        launches0 = ctx.tc_launch_count()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        sampler = ClockSampler(local)
-        sampler.start()
-        time.sleep(0.3)  # first samples before load
-        barrier()
-        torch.cuda.synchronize()
-        wall0 = time.perf_counter()
-        for a, b in evs:
-            a.record(stream)
-            ctx.tc_step_async(1)
-            b.record(stream)
-            flush.zero_()
-        stream.synchronize()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        barrier()
-        clocks = sampler.stop()
-        step_ms = [a.elapsed_time(b) for a, b in evs]
-        launches = ctx.tc_launch_count() - launches0
-        kms, kcnt = ctx.tc_kernel_times()
-        ctx.tc_set_timing(False)
-    total_ms = float(sum(step_ms))
+    def time_steps(steps, warmup, sample_clocks):
+        """W untimed + `steps` timed iterations, each bracketed by events on
+        the library's stream, L2 flushed between them."""
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                ctx.tc_step_async(1)
+                flush.zero_()
+            stream.synchronize()
+            ctx.tc_set_timing(True)
+            launches0 = ctx.tc_launch_count()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            sampler = ClockSampler(local) if sample_clocks else None
+            if sampler:
+                sampler.start()
+                time.sleep(0.3)  # first samples before load
+            barrier()
+            torch.cuda.synchronize()
+            wall0 = time.perf_counter()
+            for a, b in evs:
+                a.record(stream)
+                ctx.tc_step_async(1)
+                b.record(stream)
+                flush.zero_()
+            stream.synchronize()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - wall0
+            barrier()
+            clocks = sampler.stop() if sampler else None
+            step_ms = [a.elapsed_time(b) for a, b in evs]
+            launches = ctx.tc_launch_count() - launches0
+            kms, kcnt = ctx.tc_kernel_times()
+            ctx.tc_set_timing(False)
+        return float(sum(step_ms)), kms, kcnt, launches, wall, clocks
+
+    total_ms, kms, kcnt, launches, wall, clocks = time_steps(args.steps, args.warmup, True)
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     W_, t_now = ctx.tc_get_state()
     assert t_now == args.warmup + args.steps, (t_now, args.warmup, args.steps)
+    W_ = None
     value = world * D * args.steps / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers: per step the weights go
@@ -280,6 +288,43 @@ def run_ours(args):
     e2e_value = world * D * len(e2e_times) / e2e_total if e2e_times else None
     h2d = Wh.nbytes
     d2h = Wh.nbytes + 4 * n + 64
+
+    # the dense forms of the same step on the same workload: A.S and S S^T as
+    # FP8 tcgen05 GEMMs, and as FP32 CUDA-core GEMMs (fewer timed steps: the
+    # FP32 form takes ~1 ms per step)
+    forms = {"onehot": {"value": value, "ms_per_step": total_ms / args.steps}}
+    tensor_roof = None
+    if not args.no_forms and world == 1:
+        peaks = measured_peaks()
+        for name, form, steps in (("dense_fp8", T.TC_FORM_DENSE_FP8, min(args.steps, 1000)),
+                                  ("dense_fp32", T.TC_FORM_DENSE_FP32, min(args.steps, 60))):
+            pf = T.params(T.TC_KCOL, stop_on_legal=0, form=form)
+            ctx.tc_set_params(pf)
+            tms, fk, fc, _, _, _ = time_steps(steps, 3, False)
+            rec = {"value": D * steps / (tms / 1e3), "ms_per_step": tms / steps,
+                   "kernels_us": {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * fk[q] / max(1, fc[q])
+                                  for q in range(len(fk)) if fc[q] > 0}}
+            forms[name] = rec
+            if form == T.TC_FORM_DENSE_FP8:
+                # algorithmic flops: Gamma = A S (n x n x Dk) and the symmetric
+                # half of M~ = S S^T (n (n + 1) / 2 x Dk), 2 flops per MAC
+                fl_g = 2.0 * n * n * D * k
+                fl_m = 2.0 * (n * (n + 1) / 2) * D * k
+                us_g = rec["kernels_us"].get("gemm_gamma")
+                us_m = rec["kernels_us"].get("gemm_mtilde")
+                bf16 = peaks["bf16_tflops"] if peaks else 1900.0
+                peak8 = 2.0 * bf16  # FP8 dense = 2 x BF16 dense (nominal 4.5 / 2.25 PF)
+                if us_g and us_m:
+                    ach = (fl_g + fl_m) / ((us_g + us_m) * 1e-6) / 1e12
+                    tensor_roof = {"bound": "tensor", "achieved": ach, "peak": peak8,
+                                   "unit": "TFLOP/s", "frac": ach / peak8, "traffic": None,
+                                   "kernels": ["gemm_gamma", "gemm_mtilde"],
+                                   "gamma_tflops": fl_g / (us_g * 1e-6) / 1e12,
+                                   "mtilde_tflops": fl_m / (us_m * 1e-6) / 1e12,
+                                   "peak_source": ("measured bf16 x 2 (fp8/bf16 nominal ratio)"
+                                                   if peaks else "fallback")}
+        ctx.tc_set_params(p)
+        forms["chosen"] = max((f for f in forms if f != "chosen"), key=lambda f: forms[f]["value"])
 
     # roofline of the dominant kernel
     kid = int(np.argmax(kms))
@@ -314,6 +359,8 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "roofline": roof,
+        "roofline_tensor": tensor_roof,
+        "forms": forms,
         "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -85,6 +85,8 @@ def _declare(L):
     L.orc_run.restype = _ll
     L.orc_run.argtypes = [_i, _i, _i, _p, _p, C.POINTER(Params), C.POINTER(_ll), _ll,
                           _i, _p, _p, C.POINTER(_ll), C.POINTER(_ll)]
+    L.orc_relaxed.argtypes = [_i, _i, _i, _p, _p, C.POINTER(Params), _ll, C.c_double, _p, _p, _p,
+                              _p]
     L.orc_check_conflicts.restype = _ll
     L.orc_check_conflicts.argtypes = [_ll, _p, _p, _p]
     L.orc_check_equity.restype = _ll
@@ -238,6 +240,19 @@ def run(rowptr, colidx, W, params: Params, t0: int, max_iter: int, stop_on_legal
     if done < 0:
         raise ValueError(f"oracle run failed with code {done}")
     return dict(W=W, t=t.value, iters=done, best_colors=best, best_f=bf.value, best_t=bt.value)
+
+
+def relaxed(rowptr, colidx, W, params: Params, t: int, tau: float, want_grad: bool = True):
+    """Relaxed loss at S = softmax(W / tau) and its exact gradient (FP64)."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    W = _f64(W)
+    D, n, k = W.shape
+    loss = C.c_double()
+    g = np.empty_like(W) if want_grad else None
+    M = np.empty((n, n), np.float64)
+    _check(lib().orc_relaxed(D, n, k, _ptr(rowptr), _ptr(colidx), C.byref(params), t, tau,
+                             _ptr(W), C.byref(loss), _ptr(g), _ptr(M)), "relaxed")
+    return loss.value, g, M
 
 
 def check_conflicts(edges_u, edges_v, coloring) -> int:

@@ -437,6 +437,101 @@ long long orc_run(int D, int n, int k, const int *adj_off, const int *adj,
     return done;
 }
 
+int orc_relaxed(int D, int n, int k, const int *adj_off, const int *adj,
+                const orc_params *p, long long t, double tau, const double *W,
+                double *loss, double *gradW, double *Mt)
+{
+    if (D < 1 || n < 1 || k < 1 || !p || !W || !(tau > 0.0))
+        return ORC_EBADARG;
+    const size_t Dnk = (size_t)D * n * k, nn = (size_t)n * n;
+    double *S = (double *)malloc(sizeof(double) * Dnk);
+    double *M = (double *)calloc(nn, sizeof(double));
+    double *Bp = (double *)malloc(sizeof(double) * nn);
+    unsigned char *mark = (unsigned char *)calloc((size_t)n, 1);
+    if (!S || !M || !Bp || !mark) {
+        free(S); free(M); free(Bp); free(mark);
+        return ORC_ENOMEM;
+    }
+    /* S = softmax(W / tau) over colours */
+    for (size_t r = 0; r < (size_t)D * n; ++r) {
+        const double *w = W + r * k;
+        double mx = w[0] / tau;
+        for (int j = 1; j < k; ++j)
+            if (w[j] / tau > mx)
+                mx = w[j] / tau;
+        double z = 0.0;
+        for (int j = 0; j < k; ++j) {
+            S[r * k + j] = exp(w[j] / tau - mx);
+            z += S[r * k + j];
+        }
+        for (int j = 0; j < k; ++j)
+            S[r * k + j] /= z;
+    }
+    /* eq. 4 with M_d = S_d S_d^T */
+    for (int d = 0; d < D; ++d)
+        for (int i = 0; i < n; ++i)
+            for (int m = 0; m < n; ++m) {
+                const double *a = S + ((size_t)d * n + i) * k, *b = S + ((size_t)d * n + m) * k;
+                double dot = 0.0;
+                for (int j = 0; j < k; ++j)
+                    dot += a[j] * b[j];
+                M[(size_t)i * n + m] += dot;
+            }
+    /* loss (eq. 7) and the pair coefficients of eq. 13 */
+    const double tt = (double)t;
+    double fc = 0.0, ks = 0.0, vs = 0.0;
+    for (int i = 0; i < n; ++i) {
+        mark_row(i, adj_off, adj, mark, 1);
+        for (int m = 0; m < n; ++m) {
+            const double x = M[(size_t)i * n + m];
+            double b = 0.0;
+            if (mark[m]) {
+                fc += 0.5 * x;
+                ks += pow(x, p->alpha);
+                b = 1.0 + 2.0 * p->alpha * p->lambda_ * tt * pow(x, p->alpha - 1.0);
+            } else if (m != i || p->bonus_diag) {
+                vs += pow(x, p->beta);
+                b = -2.0 * p->beta * p->mu * tt * pow(x, p->beta - 1.0);
+            }
+            Bp[(size_t)i * n + m] = b;
+        }
+        mark_row(i, adj_off, adj, mark, 0);
+    }
+    if (loss)
+        *loss = fc + p->lambda_ * tt * ks - p->mu * tt * vs;
+    if (gradW) {
+        /* grad_S L = B' . S_d (eq. 13), then the softmax Jacobian / tau */
+        double *g = (double *)malloc(sizeof(double) * (size_t)k);
+        if (!g) {
+            free(S); free(M); free(Bp); free(mark);
+            return ORC_ENOMEM;
+        }
+        for (int d = 0; d < D; ++d)
+            for (int i = 0; i < n; ++i) {
+                for (int j = 0; j < k; ++j)
+                    g[j] = 0.0;
+                for (int m = 0; m < n; ++m) {
+                    const double b = Bp[(size_t)i * n + m];
+                    const double *sm = S + ((size_t)d * n + m) * k;
+                    for (int j = 0; j < k; ++j)
+                        g[j] += b * sm[j];
+                }
+                const double *si = S + ((size_t)d * n + i) * k;
+                double dot = 0.0;
+                for (int j = 0; j < k; ++j)
+                    dot += si[j] * g[j];
+                double *gw = gradW + ((size_t)d * n + i) * k;
+                for (int j = 0; j < k; ++j)
+                    gw[j] = si[j] * (g[j] - dot) / tau;
+            }
+        free(g);
+    }
+    if (Mt)
+        memcpy(Mt, M, sizeof(double) * nn);
+    free(S); free(M); free(Bp); free(mark);
+    return 0;
+}
+
 long long orc_check_conflicts(long long n_edges, const int *u, const int *v,
                               const int *coloring)
 {

@@ -102,6 +102,16 @@ long long orc_run(int D, int n, int k, const int *adj_off, const int *adj,
                   int stop_on_legal, double *W,
                   int *best_colors, long long *best_f, long long *best_t);
 
+/* Relaxation used to check gradients (Section 3.6): S = softmax(W / tau)
+ * row-wise, real valued, and eq. 7 with its GCP terms evaluated literally on
+ * it (M_d = S_d S_d^T, M~ = sum_d M_d, nu = 0):
+ *   loss = 1/2 sum_{i,m} a_im M~_im + lambda t kappa - mu t varpi.
+ * gradW (may be NULL) = d loss / d W by the chain rule through eq. 13 and
+ * the softmax Jacobian with temperature tau.  Also returns M~ if Mt != NULL. */
+int orc_relaxed(int D, int n, int k, const int *adj_off, const int *adj,
+                const orc_params *p, long long t, double tau, const double *W,
+                double *loss, double *gradW, double *Mt);
+
 /* Checker: recount conflicts edge by edge from an edge list (u[e], v[e]),
  * and the equity deviation of a single colouring. */
 long long orc_check_conflicts(long long n_edges, const int *u, const int *v,

@@ -375,3 +375,40 @@ def test_step_fitness_includes_equity_only_for_ecp():
     assert g["f_min"] == g["f_color"].min()
     assert e["f_min"] == (e["f_color"] + e["f_eq"]).min()
     assert e["d_star"] == int(np.argmin(e["f_color"] + e["f_eq"]))
+
+
+@pytest.mark.parametrize("alpha,beta,diag", [(2.5, 1.2, 1), (1.5, 2.0, 0)])
+def test_relaxed_gradient_is_central_difference(alpha, beta, diag):
+    """The relaxed loss (eq. 7 on S = softmax(W / tau)) and its analytic
+    gradient (eq. 13 through the softmax Jacobian): central differences,
+    h = 1e-3, FP64, on every weight of a small population."""
+    D, n, k, t, tau = 3, 12, 4, 9, 0.5
+    rp, ci = inputs.gnp(n, 0.5, seed=51)
+    W = np.random.default_rng(52).normal(0, 0.3, (D, n, k))
+    p = O.make_params(alpha=alpha, beta=beta, lambda_=2e-2, mu=1e-2, bonus_diag=diag)
+    L0, g, M = O.relaxed(rp, ci, W, p, t, tau)
+    # M~ of the relaxation is the library product of the softmax rows
+    S = np.exp(W / tau - (W / tau).max(axis=2, keepdims=True))
+    S /= S.sum(axis=2, keepdims=True)
+    assert np.allclose(M, np.einsum("dij,dmj->im", S, S), rtol=1e-13, atol=1e-13)
+    h = 1e-3
+    for d in range(D):
+        for i in range(n):
+            for j in range(k):
+                Wp, Wm = W.copy(), W.copy()
+                Wp[d, i, j] += h
+                Wm[d, i, j] -= h
+                fd = (O.relaxed(rp, ci, Wp, p, t, tau, False)[0] -
+                      O.relaxed(rp, ci, Wm, p, t, tau, False)[0]) / (2 * h)
+                assert g[d, i, j] == pytest.approx(fd, rel=1e-5, abs=1e-7), (d, i, j)
+
+
+def test_relaxed_loss_at_sharp_softmax_is_one_hot_loss():
+    """As tau -> 0 the relaxation reaches the one-hot loss of the same W."""
+    D, n, k, t = 4, 20, 5, 3
+    rp, ci = inputs.gnp(n, 0.4, seed=61)
+    W = np.random.default_rng(62).normal(0, 1.0, (D, n, k))
+    p = O.make_params(lambda_=1e-2, mu=1e-3)
+    L_relax, _, _ = O.relaxed(rp, ci, W, p, t, 1e-4, want_grad=False)
+    L_hard = O.step(rp, ci, W, p, t, want_G=False)["loss"]
+    assert L_relax == pytest.approx(L_hard, rel=1e-9)
