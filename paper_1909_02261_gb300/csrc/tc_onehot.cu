@@ -468,19 +468,26 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
             if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * aw + (i >> 5)], 1u << (i & 31));
         }
         __syncthreads();
-        for (int i = warp; i < n; i += nwp) {
+        // one vertex per thread: its adjacency-row words are independent
+        // loads, so a warp keeps 32 rows in flight
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int col = cd[i];
-            if (col < cb || col >= ce) continue;  // uniform per warp
+            if (col < cb || col >= ce) continue;
             const uint32_t* ar = P.adj + (size_t)i * aw;
             const uint32_t* xr = s_bits + (col - cb) * aw;
-            int g = 0;
-            for (int w = lane; w < aw; w += 32) g += __popc(__ldg(ar + w) & xr[w]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-            if (lane == 0) {
-                twice += g;
-                if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
+            int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+            int w = 0;
+            for (; w + 4 <= aw; w += 4) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(ar + w));
+                g0 += __popc(a.x & xr[w]);
+                g1 += __popc(a.y & xr[w + 1]);
+                g2 += __popc(a.z & xr[w + 2]);
+                g3 += __popc(a.w & xr[w + 3]);
             }
+            for (; w < aw; ++w) g0 += __popc(__ldg(ar + w) & xr[w]);
+            const int g = (g0 + g1) + (g2 + g3);
+            twice += g;
+            if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
         }
     }
     twice = block_sum<long long>(twice, sh_ll);
@@ -758,6 +765,18 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
     const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
     const int* of = P.off + (size_t)d * (k + 1);
     const int8_t* Ed = P.E + (size_t)d * k;
+    // bring the item's vertex order, class offsets and equity signs into L1
+    // in parallel (one 128-byte line per lane) instead of one L2 round trip
+    // per line as the walk reaches it
+    {
+        const int lp = (2 * n + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
+        for (int l = lane; l < lp + lo + le; l += 32) {
+            const char* a = l < lp ? (const char*)pm + 128 * l
+                                   : (l < lp + lo ? (const char*)of + 128 * (l - lp)
+                                                  : (const char*)Ed + 128 * (l - lp - lo));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+        }
+    }
     const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
     const int bstride = BTS ? 32 : P.ldb;
     const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
@@ -797,7 +816,7 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
 #pragma unroll
         for (int q = 0; q < KQ; ++q) {
             const int j = lane + 32 * q;
-            ring[r][q] = (r < rows && j < k) ? Wt[(size_t)r * k + j] : 0.f;
+            ring[r][q] = (r < rows && j < k) ? __ldcg(Wt + (size_t)r * k + j) : 0.f;
         }
     int mycol = 0;
     for (int r0 = 0; r0 < rows; r0 += PF) {
@@ -818,7 +837,7 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
                 const int j = lane + 32 * q;
-                ring[u][q] = (r + PF < rows && j < k) ? Wt[(size_t)(r + PF) * k + j] : 0.f;
+                ring[u][q] = (r + PF < rows && j < k) ? __ldcg(Wt + (size_t)(r + PF) * k + j) : 0.f;
             }
             mx = warp_max_f<KQ>(mx);
             float ev[KQ], Z = 0.f, num = 0.f;
@@ -844,7 +863,7 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
                     const float sj = ev[q] * invZ;
                     float wn = x[q] - P.eta * (sj * (gq[q] - dot));
                     if (smooth) wn = wn / P.rho;
-                    Wt[(size_t)r * k + j] = wn;
+                    __stcg(Wt + (size_t)r * k + j, wn);
                     if (wn > bv) {  // j increases with q: first maximum wins
                         bv = wn;
                         bj = j;

@@ -595,7 +595,7 @@ int tc_init_graph(tc_ctx* c, int n, const int32_t* rowptr, const int32_t* colidx
     if (!rowptr && !dense) return TC_ERR_ARG;
     if (rowptr && !colidx && rowptr[n] > 0) return TC_ERR_ARG;
     // host-side CSR + bitmask, validated
-    const int aw = (n + 31) / 32;
+    const int aw = (n + 127) / 128 * 4;  // bitmask rows padded to 16 bytes
     std::vector<uint32_t> bits((size_t)n * aw, 0u);
     std::vector<int> rp(n + 1, 0), ci;
     if (rowptr) {
