@@ -181,6 +181,25 @@ int tc_step_async(tc_ctx *ctx, int64_t n_iters);
 int tc_set_timing(tc_ctx *ctx, int on);
 int tc_kernel_times(tc_ctx *ctx, double *ms, int64_t *count);
 
+/* Hand-written backward of the straight-through estimator (eq. 12-13) for
+ * the current population at the current t: gradW_dev[D*n*k] (device) gets
+ * grad_W L = S^ (.) (grad_S L - (S^ (.) grad_S L) J) with S^ = softmax(W)
+ * and grad_S L of eq. 13 at the one-hot S = g(W), computed by the same code
+ * as the fused update (which applies W <- W - eta grad_W L with one rounding
+ * per operation, so the two agree bit for bit).  loss_dev[3] (device, may
+ * be NULL) gets L (eq. 7), kappa (eq. 5), varpi (eq. 6).  W, t and the
+ * best-so-far are unchanged. */
+int tc_st_grad_dev(tc_ctx *ctx, float *gradW_dev, float *loss_dev);
+
+/* Relaxation used to check the gradient (Section 3.6): S = softmax(W_dev /
+ * tau) row-wise (real valued), eq. 7's GCP terms on it with M_d = S_d S_d^T
+ * (nu ignored): loss_dev[4] = L, kappa, varpi, f_color; gradW_dev = dL/dW
+ * (eq. 13 through the softmax Jacobian).  Device pointers of D*n*k floats;
+ * uses the graph and parameters of the context, k <= 128.  Allocates and
+ * frees its own temporaries; the population is not touched. */
+int tc_relaxed_dev(tc_ctx *ctx, const float *W_dev, float tau, int64_t t, float *loss_dev,
+                   float *gradW_dev);
+
 /* Number of device kernel launches issued by this context since creation
  * (for launch accounting in benchmarks). */
 int tc_launch_count(tc_ctx *ctx, int64_t *count);

@@ -35,7 +35,7 @@ struct tc_kparams {
     int ct_bytes;     // bytes per colour in cT: 1 when k <= 255, else 2
     int adj_words;    // 32-bit words per adjacency-bitmask row
     int problem, nb_iter, bonus_diag, stop_on_legal, commit;
-    float eta, rho, lambda_, mu, nu;
+    float eta, rho, lambda_, mu, nu, alpha, beta;
     float* W;                 // D x n x k
     uint16_t* c;              // D x n colours
     uint16_t* cT;             // n x Dp colours (vertex-major, ct_bytes each), pads all-ones
@@ -47,6 +47,7 @@ struct tc_kparams {
     uint16_t* perm;           // D x perm_stride vertices sorted by colour (stable)
     int perm_stride;          // n rounded up to a multiple of 8 (16-byte rows)
     int* off;                 // D x (k + 1) colour-class offsets into perm
+    uint16_t* cls;            // D x k non-empty colour classes in increasing order
     int8_t* E;                // D x k equity gradient signs (eq. 14)
     int* fcolor;              // D conflicts (eq. 1)
     int* feq;                 // D equity fitness (eq. 3)
@@ -106,6 +107,10 @@ cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, co
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);
 cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s);
+
+int tc_relaxed_run(const tc_kparams& P, const float* W, float tau, long long t, float* loss, float* gradW,
+                   float* S, float* M, float* Bp, float* part, cudaStream_t s);
+int tc_relaxed_partials(int n);
 
 int tc_pair_tile_edge();
 int tc_pair_tile_count(int n);

@@ -449,6 +449,30 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
             __syncwarp();
         }
     }
+    // mark the last vertex of every non-empty class (bit 15 of its entry)
+    // and list the non-empty classes in order, for the flat walk of k_update
+    __syncthreads();
+    {
+        uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
+        for (int j = threadIdx.x; j < k; j += blockDim.x)
+            if (s_hist[j] > 0) pd[od[j + 1] - 1] |= (uint16_t)0x8000u;
+        // exclusive scan of the non-empty flags (contiguous chunks per thread)
+        int cnt = 0;
+        for (int j = j0; j < j1; ++j) cnt += s_hist[j] > 0;
+        __syncthreads();
+        s_scan[threadIdx.x] = cnt;
+        __syncthreads();
+        for (int o = 1; o < CLS_THREADS; o <<= 1) {
+            const int v = threadIdx.x >= o ? s_scan[threadIdx.x - o] : 0;
+            __syncthreads();
+            s_scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int r = s_scan[threadIdx.x] - cnt;
+        uint16_t* cl = P.cls + (size_t)d * k;
+        for (int j = j0; j < j1; ++j)
+            if (s_hist[j] > 0) cl[r++] = (uint16_t)j;
+    }
     // conflicts (eq. 1): from the gamma matrix of the dense form, else by
     // colour bitmaps (cls_colours colours per pass), one warp per vertex
     long long twice = 0;
@@ -602,7 +626,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     const unsigned wbytes = (unsigned)(rows * k * 4);
 
     // 1. weight tile -> Ws
-    if (!debug_only) {
+    if (debug_only != 1) {
         if (BULK) {
             if (lane == 0) {
                 bulk_wait_read();  // the previous item's store has read Ws
@@ -635,7 +659,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
         float b[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int m = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFF;
+            const int m = (wv[q >> 1] >> (16 * (q & 1))) & 0x7FFF;  // bit 15 marks class ends
             b[q] = (p0 + q < n) ? Bl[m * bstride] : 0.f;
         }
 #pragma unroll
@@ -656,7 +680,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
         }
     }
     __syncwarp();
-    if (debug_only) {
+    if (debug_only == 1) {
         if (lane < rows) {
             float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
             for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
@@ -701,9 +725,14 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
 #pragma unroll 4
         for (int q = 0; q < k; ++q) {
             const float w = wr[jj];
-            const float s = __expf(w - mx) * invZ;
-            float wn = w - P.eta * (s * (gr[jj * 32] - dot));
-            if (smooth) wn = wn / P.rho;
+            const float gw = __fmul_rn(__fmul_rn(__expf(w - mx), invZ), __fsub_rn(gr[jj * 32], dot));
+            if (debug_only == 2) {
+                P.dbg_G[((size_t)d * n + i0 + lane) * k + jj] = gw;
+                jj = (jj + 1 == k) ? 0 : jj + 1;
+                continue;
+            }
+            float wn = __fsub_rn(w, __fmul_rn(P.eta, gw));
+            if (smooth) wn = __fdiv_rn(wn, P.rho);
             wr[jj] = wn;
             if (wn > bestv || (wn == bestv && jj < newc)) {
                 bestv = wn;
@@ -714,6 +743,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
         if (newc >= k) newc = 0;
     }
     __syncwarp();
+    if (debug_only == 2) return;
 
     // 4. write back
     if (BULK) {
@@ -745,11 +775,19 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
 // time, lanes across colours, with the weight rows streamed straight from
 // global memory through an 8-row register prefetch ring (no shared W tile,
 // which doubles the resident warps).
-template <int KQ>
-__device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+// Order-preserving map of floats to signed ints (for a < b: key(a) < key(b);
+// -0 and +0 map apart, which is harmless for a maximum).
+__device__ __forceinline__ int float_key(float x) {
+    const int b = __float_as_int(x);
+    return b ^ ((b >> 31) & 0x7FFFFFFF);
+}
+
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7FFFFFFF)); }
+
+// Warp maximum of a float through one redux.sync on its integer key.
+__device__ __forceinline__ float warp_max_key(float v) {
+    const unsigned u = (unsigned)float_key(v) ^ 0x80000000u;  // signed -> unsigned order
+    return key_float((int)(__reduce_max_sync(0xffffffffu, u) ^ 0x80000000u));
 }
 
 template <bool BTS, int KQ>
@@ -761,45 +799,63 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
 
-    // Phase A: Gs[j][lane] = grad_S L[d, i0 + lane, j] by class-length loops
+    // Phase A: Gs[j][lane] = grad_S L[d, i0 + lane, j].  Gs is first filled
+    // with the terms that do not depend on the class members (nu t E_dj, and
+    // the gamma matrix in the dense form; both are all there is for an empty
+    // class), then the vertices of d are streamed in colour order, 8 per
+    // 16-byte load, and each class sum is added at its marked last vertex.
     const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
-    const int* of = P.off + (size_t)d * (k + 1);
+    const uint16_t* cl = P.cls + (size_t)d * k;
     const int8_t* Ed = P.E + (size_t)d * k;
-    // bring the item's vertex order, class offsets and equity signs into L1
-    // in parallel (one 128-byte line per lane) instead of one L2 round trip
-    // per line as the walk reaches it
     {
-        const int lp = (2 * n + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
-        for (int l = lane; l < lp + lo + le; l += 32) {
+        const int lp = (2 * n + 127) / 128, lc = (2 * k + 127) / 128, le = (k + 127) / 128;
+        for (int l = lane; l < lp + lc + le; l += 32) {
             const char* a = l < lp ? (const char*)pm + 128 * l
-                                   : (l < lp + lo ? (const char*)of + 128 * (l - lp)
-                                                  : (const char*)Ed + 128 * (l - lp - lo));
+                                   : (l < lp + lc ? (const char*)cl + 128 * (l - lp)
+                                                  : (const char*)Ed + 128 * (l - lp - lc));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
         }
     }
     const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
     const int bstride = BTS ? 32 : P.ldb;
     const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-    int s = 0;
     for (int j = 0; j < k; ++j) {
-        const int e = __ldg(of + j + 1);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int p = s;
-        for (; p + 4 <= e; p += 4) {
-            const int m0 = __ldg(pm + p), m1 = __ldg(pm + p + 1), m2 = __ldg(pm + p + 2), m3 = __ldg(pm + p + 3);
-            a0 += Bl[m0 * bstride];
-            a1 += Bl[m1 * bstride];
-            a2 += Bl[m2 * bstride];
-            a3 += Bl[m3 * bstride];
+        float g0 = nut * (float)__ldg(Ed + j);
+        if (grow) g0 += (float)__ldg(grow + j);
+        Gs[j * 33 + lane] = g0;
+    }
+    float acc = 0.f;
+    int ci = 0;
+    int jcur = __ldg(cl);
+    for (int p0 = 0; p0 < n; p0 += 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(pm + p0));
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+        float b[8];
+        uint32_t ends = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t e = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            const bool ok = p0 + q < n;
+            b[q] = ok ? Bl[(int)(e & 0x7FFFu) * bstride] : 0.f;
+            ends |= (ok ? (e >> 15) : 0u) << q;
         }
-        for (; p < e; ++p) a0 += Bl[__ldg(pm + p) * bstride];
-        float g = ((a0 + a1) + (a2 + a3)) + nut * (float)__ldg(Ed + j);
-        if (grow) g += (float)__ldg(grow + j);
-        Gs[j * 33 + lane] = g;
-        s = e;
+        if (ends == 0) {  // no class ends in these 8 vertices
+            acc += ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                acc += b[q];
+                if ((ends >> q) & 1u) {
+                    Gs[jcur * 33 + lane] += acc;
+                    acc = 0.f;
+                    ++ci;
+                    jcur = __ldg(cl + min(ci, k - 1));
+                }
+            }
+        }
     }
     __syncwarp();
-    if (debug_only) {
+    if (debug_only == 1) {
         if (lane < rows) {
             float* gd = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
             for (int jj = 0; jj < k; ++jj) gd[jj] = Gs[jj * 33 + lane];
@@ -839,7 +895,7 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
                 const int j = lane + 32 * q;
                 ring[u][q] = (r + PF < rows && j < k) ? __ldcg(Wt + (size_t)(r + PF) * k + j) : 0.f;
             }
-            mx = warp_max_f<KQ>(mx);
+            mx = warp_max_key(mx);
             float ev[KQ], Z = 0.f, num = 0.f;
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
@@ -860,9 +916,15 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
             for (int q = 0; q < KQ; ++q) {
                 const int j = lane + 32 * q;
                 if (j < k) {
-                    const float sj = ev[q] * invZ;
-                    float wn = x[q] - P.eta * (sj * (gq[q] - dot));
-                    if (smooth) wn = wn / P.rho;
+                    // eq. 12, then the descent step and eq. 8, each rounded once
+                    // (no contraction): W_next == W - eta * gW holds bit for bit
+                    const float gw = __fmul_rn(__fmul_rn(ev[q], invZ), __fsub_rn(gq[q], dot));
+                    if (debug_only == 2) {
+                        P.dbg_G[((size_t)d * n + i0 + r) * k + j] = gw;
+                        continue;
+                    }
+                    float wn = __fsub_rn(x[q], __fmul_rn(P.eta, gw));
+                    if (smooth) wn = __fdiv_rn(wn, P.rho);
                     __stcg(Wt + (size_t)r * k + j, wn);
                     if (wn > bv) {  // j increases with q: first maximum wins
                         bv = wn;
@@ -870,17 +932,18 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
                     }
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                if (ob > bv || (ob == bv && oj < bj)) {
-                    bv = ob;
-                    bj = oj;
-                }
+            {  // argmax, lowest colour on ties: max of the value, then min colour
+                const unsigned key = (unsigned)float_key(bv + 0.0f) ^ 0x80000000u;  // -0 counts as +0
+                const unsigned best = __reduce_max_sync(0xffffffffu, key);
+                const int mine = key == best ? bj : k;
+                bj = (int)__reduce_min_sync(0xffffffffu, (unsigned)mine);
             }
             if (lane == r) mycol = bj >= k ? 0 : bj;
         }
+    }
+    if (debug_only == 2) {
+        __syncwarp();
+        return;
     }
     if (lane < rows) {
         const int i = i0 + lane;

@@ -42,6 +42,7 @@ struct tc_ctx {
     float* d_B = nullptr;
     uint16_t* d_perm = nullptr;
     int* d_off = nullptr;
+    uint16_t* d_cls = nullptr;
     int8_t* d_E = nullptr;
     int* d_fcolor = nullptr;
     int* d_feq = nullptr;
@@ -161,6 +162,7 @@ void free_population(tc_ctx* c) {
     dfree(c->d_B);
     dfree(c->d_perm);
     dfree(c->d_off);
+    dfree(c->d_cls);
     dfree(c->d_E);
     dfree(c->d_fcolor);
     dfree(c->d_feq);
@@ -212,6 +214,8 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.lambda_ = c->p.lambda_;
     P.mu = c->p.mu;
     P.nu = c->p.nu;
+    P.alpha = c->p.alpha;
+    P.beta = c->p.beta;
     P.W = c->d_W;
     P.c = c->d_c;
     P.cT = c->d_cT;
@@ -223,6 +227,7 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.perm = c->d_perm;
     P.perm_stride = (c->n + 7) & ~7;
     P.off = c->d_off;
+    P.cls = c->d_cls;
     P.E = c->d_E;
     P.fcolor = c->d_fcolor;
     P.feq = c->d_feq;
@@ -703,7 +708,7 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     const size_t Dnk = (size_t)D * n * k;
     if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) ||
         (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)n * ((n + 3) & ~3))) ||
-        (rc = dalloc(&c->d_perm, (size_t)D * ((n + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
+        (rc = dalloc(&c->d_perm, (size_t)D * ((n + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) || (rc = dalloc(&c->d_cls, (size_t)D * k)) ||
         (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
         (rc = dalloc(&c->d_lut, 4 * (size_t)(D + 1))) || (rc = dalloc(&c->d_st, 1)) ||
@@ -1015,6 +1020,51 @@ int tc_kernel_times(tc_ctx* c, double* ms, int64_t* count) {
         if (ms) ms[q] = c->kms[q];
         if (count) count[q] = c->kcount[q];
     }
+    return TC_OK;
+}
+
+int tc_st_grad_dev(tc_ctx* c, float* gradW_dev, float* loss_dev) {
+    if (!c || !gradW_dev) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    tc_kparams P = make_kparams(c, 0);
+    P.dbg_G = gradW_dev;
+    const bool dense = P.M32 != nullptr;
+    int rc;
+    if (dense && (rc = launch_dense_gemms(c, 0))) return rc;
+    TC_CHECK(tc_launch_pairs(P, c->stream));
+    if (dense && (rc = launch_dense_gemms(c, 1))) return rc;
+    TC_CHECK(tc_launch_classes(P, c->stream));
+    TC_CHECK(tc_launch_update(P, c->tmB, c->num_sms, c->stream, 2));
+    c->launches += 3;
+    if (loss_dev)  // loss, kappa, varpi are consecutive floats of the state
+        TC_CHECK(cudaMemcpyAsync(loss_dev, &c->d_st->loss, 3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    tc_dev_state h;
+    rc = read_state(c, &h);
+    if (rc) return rc;
+    return h.err ? h.err : TC_OK;
+}
+
+int tc_relaxed_dev(tc_ctx* c, const float* W_dev, float tau, int64_t t, float* loss_dev, float* gradW_dev) {
+    if (!c || !W_dev || !loss_dev || !gradW_dev || !(tau > 0.f) || t < 0) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    if (c->k > 128) return TC_ERR_UNSUPPORTED;
+    DeviceGuard g(c->device);
+    const int n = c->n;
+    float *S = nullptr, *M = nullptr, *Bp = nullptr, *part = nullptr;
+    int rc;
+    if ((rc = dalloc(&S, (size_t)c->D * n * c->k)) || (rc = dalloc(&M, (size_t)n * n)) ||
+        (rc = dalloc(&Bp, (size_t)n * n)) || (rc = dalloc(&part, 3 * (size_t)tc_relaxed_partials(n)))) {
+        dfree(S); dfree(M); dfree(Bp); dfree(part);
+        return rc;
+    }
+    rc = tc_relaxed_run(make_kparams(c, 0), W_dev, tau, t, loss_dev, gradW_dev, S, M, Bp, part, c->stream);
+    c->launches += 5;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    dfree(S); dfree(M); dfree(Bp); dfree(part);
+    if (rc) return rc;
+    TC_CHECK(e);
     return TC_OK;
 }
 

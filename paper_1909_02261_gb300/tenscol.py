@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
         "tc_step_async": (C.c_int, [vp, i64]),
         "tc_set_timing": (C.c_int, [vp, C.c_int]),
         "tc_kernel_times": (C.c_int, [vp, vp, vp]),
+        "tc_st_grad_dev": (C.c_int, [vp, vp, vp]),
+        "tc_relaxed_dev": (C.c_int, [vp, vp, C.c_float, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -233,6 +235,14 @@ class TensCol:
         cnt = np.zeros(8, np.int64)
         _ck(self._L.tc_kernel_times(self.h, _ptr(ms), _ptr(cnt)), "tc_kernel_times")
         return ms, cnt
+
+    def tc_st_grad_dev(self, gradW_ptr: int, loss_ptr: int | None):
+        _ck(self._L.tc_st_grad_dev(self.h, C.c_void_p(gradW_ptr),
+                                   None if loss_ptr is None else C.c_void_p(loss_ptr)), "tc_st_grad_dev")
+
+    def tc_relaxed_dev(self, W_ptr: int, tau: float, t: int, loss_ptr: int, gradW_ptr: int):
+        _ck(self._L.tc_relaxed_dev(self.h, C.c_void_p(W_ptr), tau, t, C.c_void_p(loss_ptr),
+                                   C.c_void_p(gradW_ptr)), "tc_relaxed_dev")
 
     def tc_launch_count(self) -> int:
         c = C.c_int64()
