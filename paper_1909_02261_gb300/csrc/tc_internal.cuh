@@ -42,12 +42,12 @@ struct tc_kparams {
     const uint32_t* adj;      // n x adj_words adjacency bitmask
     const int* rowptr;        // CSR
     const int* colidx;
-    float* B;                 // n x ldb pair coefficients of eq. 13 (symmetric)
+    float* B;                 // (n + 1) x ldb pair coefficients of eq. 13 (symmetric); row n = 0
     int ldb;                  // row stride of B: n rounded up to a multiple of 4
-    uint16_t* perm;           // D x perm_stride vertices sorted by colour (stable)
-    int perm_stride;          // n rounded up to a multiple of 8 (16-byte rows)
-    int* off;                 // D x (k + 1) colour-class offsets into perm
-    uint16_t* cls;            // D x k non-empty colour classes in increasing order
+    uint16_t* perm;           // D x perm_stride vertices sorted by colour (stable), every
+                              // class padded to a multiple of 4 with vertex n
+    int perm_stride;          // n + 3k rounded up to a multiple of 8
+    int* off;                 // D x (k + 1) padded colour-class offsets into perm
     int8_t* E;                // D x k equity gradient signs (eq. 14)
     int* fcolor;              // D conflicts (eq. 1)
     int* feq;                 // D equity fitness (eq. 3)

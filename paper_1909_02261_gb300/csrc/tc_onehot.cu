@@ -257,7 +257,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
 }
 
 // ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
 // block-wide helpers for k_classes (CLS_THREADS threads)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -352,11 +351,15 @@ __device__ void finalize_population(const tc_kparams& P) {
     if (threadIdx.x == 0) st->done_classes = 0u;
 }
 
-// k_classes: one individual per block.  Class sizes and offsets, equity
-// (eq. 3, eq. 14), the stable counting sort, and the exact conflicts of
-// eq. 1: with X_j the bitmap of the vertices coloured j, vertex i has
-// gamma_d(i) = popcount(A_i & X_{c_d(i)}) conflicting neighbours.
-// Dynamic shared memory holds the bitmaps of `cls_colours` colours at a time.
+// ---------------------------------------------------------------------------
+// k_classes: one individual per block.  Class sizes, equity (eq. 3, eq. 14),
+// a stable counting sort of the vertices by colour into `perm` with every
+// class padded to a multiple of 4 entries (padding = vertex n, a zero row of
+// the pair matrix), the exact conflicts of eq. 1 (with X_j the bitmap of the
+// vertices coloured j, vertex i has popcount(A_i & X_{c_d(i)}) conflicting
+// neighbours), and, in the last block, the population reduction.
+// Dynamic shared memory: the individual's colours, then the per-warp colour
+// counts of the sort or the bitmaps of `cls_colours` colours at a time.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_colours) {
     if (P.commit && P.st->stop) return;
@@ -365,18 +368,22 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     __shared__ int s_scan[CLS_THREADS];
     __shared__ long long sh_ll[CLS_THREADS / 32];
     __shared__ int s_last;
-    extern __shared__ uint32_t s_bits[];  // cls_colours x adj_words
+    extern __shared__ __align__(16) uint32_t s_dyn[];
     const int n = P.n, k = P.k, d = blockIdx.x, aw = P.adj_words;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
+    uint16_t* cs = reinterpret_cast<uint16_t*>(s_dyn);          // n colours
+    uint32_t* s_bits = s_dyn + ((n + 7) / 8) * 4;               // after the colours
     const uint16_t* cd = P.c + (size_t)d * n;
     for (int j = threadIdx.x; j < k; j += blockDim.x) s_hist[j] = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cs[i] = cd[i];
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[cd[i]], 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[cs[i]], 1);
     __syncthreads();
-    // exclusive scan of the class sizes: contiguous chunks per thread
+    // exclusive scan of the padded class sizes: contiguous chunks per thread
     const int per = (k + CLS_THREADS - 1) / CLS_THREADS;
     const int j0 = threadIdx.x * per, j1 = min(k, j0 + per);
     int local = 0;
-    for (int j = j0; j < j1; ++j) local += s_hist[j];
+    for (int j = j0; j < j1; ++j) local += (s_hist[j] + 3) & ~3;
     s_scan[threadIdx.x] = local;
     __syncthreads();
     for (int o = 1; o < CLS_THREADS; o <<= 1) {  // Hillis-Steele inclusive scan
@@ -387,12 +394,15 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     }
     int run = s_scan[threadIdx.x] - local;
     int* od = P.off + (size_t)d * (k + 1);
+    uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
     for (int j = j0; j < j1; ++j) {
+        const int h = s_hist[j], ph = (h + 3) & ~3;
         od[j] = run;
         s_cur[j] = run;
-        run += s_hist[j];
+        for (int q = h; q < ph; ++q) pd[run + q] = (uint16_t)n;  // padding entries
+        run += ph;
     }
-    if (threadIdx.x == 0) od[k] = n;
+    if (threadIdx.x == CLS_THREADS - 1) od[k] = s_scan[CLS_THREADS - 1];
     // equity fitness (eq. 3) and its gradient sign (eq. 14)
     const int c1 = n / k, c2 = (n + k - 1) / k;
     long long fe = 0;
@@ -404,11 +414,10 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     fe = block_sum<long long>(fe, sh_ll);
     if (threadIdx.x == 0) P.feq[d] = (int)fe;
     __syncthreads();
-    // stable counting sort of the vertices by colour: each warp owns a
-    // contiguous chunk; per-warp colour counts give every (warp, colour) its
-    // base, and ranks within 32-vertex rounds come from warp matching
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
-    int* wcnt = reinterpret_cast<int*>(s_bits);  // nwp x k, before the bitmaps
+    // stable counting sort: each warp owns a contiguous chunk of vertices;
+    // per-warp colour counts give every (warp, colour) its base, ranks within
+    // 32-vertex rounds come from warp matching
+    int* wcnt = reinterpret_cast<int*>(s_bits);  // nwp x k
     for (int e = threadIdx.x; e < nwp * k; e += blockDim.x) wcnt[e] = 0;
     __syncthreads();
     const int chunk = (n + nwp - 1) / nwp;
@@ -417,7 +426,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
         const int i = base + lane;
         const unsigned valid = __ballot_sync(0xffffffffu, i < cend);
         if (i < cend) {
-            const int col = cd[i];
+            const int col = cs[i];
             const unsigned peers = __match_any_sync(valid, col);
             if ((__ffs(peers) - 1) == lane) wcnt[warp * k + col] += __popc(peers);
         }
@@ -425,60 +434,33 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     }
     __syncthreads();
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        int run = s_cur[j];
+        int r = s_cur[j];
         for (int w = 0; w < nwp; ++w) {
             const int c = wcnt[w * k + j];
-            wcnt[w * k + j] = run;
-            run += c;
+            wcnt[w * k + j] = r;
+            r += c;
         }
     }
     __syncthreads();
-    {
-        uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
-        for (int base = cbeg; base < cend; base += 32) {
-            const int i = base + lane;
-            const unsigned valid = __ballot_sync(0xffffffffu, i < cend);
-            if (i < cend) {
-                const int col = cd[i];
-                const unsigned peers = __match_any_sync(valid, col);
-                const int rank = __popc(peers & ((1u << lane) - 1u));
-                pd[wcnt[warp * k + col] + rank] = (uint16_t)i;
-                __syncwarp(valid);
-                if ((__ffs(peers) - 1) == lane) wcnt[warp * k + col] += __popc(peers);
-            }
-            __syncwarp();
+    for (int base = cbeg; base < cend; base += 32) {
+        const int i = base + lane;
+        const unsigned valid = __ballot_sync(0xffffffffu, i < cend);
+        if (i < cend) {
+            const int col = cs[i];
+            const unsigned peers = __match_any_sync(valid, col);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            pd[wcnt[warp * k + col] + rank] = (uint16_t)i;
+            __syncwarp(valid);
+            if ((__ffs(peers) - 1) == lane) wcnt[warp * k + col] += __popc(peers);
         }
-    }
-    // mark the last vertex of every non-empty class (bit 15 of its entry)
-    // and list the non-empty classes in order, for the flat walk of k_update
-    __syncthreads();
-    {
-        uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
-        for (int j = threadIdx.x; j < k; j += blockDim.x)
-            if (s_hist[j] > 0) pd[od[j + 1] - 1] |= (uint16_t)0x8000u;
-        // exclusive scan of the non-empty flags (contiguous chunks per thread)
-        int cnt = 0;
-        for (int j = j0; j < j1; ++j) cnt += s_hist[j] > 0;
-        __syncthreads();
-        s_scan[threadIdx.x] = cnt;
-        __syncthreads();
-        for (int o = 1; o < CLS_THREADS; o <<= 1) {
-            const int v = threadIdx.x >= o ? s_scan[threadIdx.x - o] : 0;
-            __syncthreads();
-            s_scan[threadIdx.x] += v;
-            __syncthreads();
-        }
-        int r = s_scan[threadIdx.x] - cnt;
-        uint16_t* cl = P.cls + (size_t)d * k;
-        for (int j = j0; j < j1; ++j)
-            if (s_hist[j] > 0) cl[r++] = (uint16_t)j;
+        __syncwarp();
     }
     // conflicts (eq. 1): from the gamma matrix of the dense form, else by
-    // colour bitmaps (cls_colours colours per pass), one warp per vertex
+    // colour bitmaps, cls_colours colours per pass, one vertex per thread
     long long twice = 0;
     if (P.G16)
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int g = P.G16[(size_t)i * P.ldg + (size_t)d * k + cd[i]];
+            const int g = P.G16[(size_t)i * P.ldg + (size_t)d * k + cs[i]];
             twice += g;
             if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
         }
@@ -488,27 +470,24 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
         for (int e = threadIdx.x; e < (ce - cb) * aw; e += blockDim.x) s_bits[e] = 0u;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int col = cd[i];
+            const int col = cs[i];
             if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * aw + (i >> 5)], 1u << (i & 31));
         }
         __syncthreads();
-        // one vertex per thread: its adjacency-row words are independent
-        // loads, so a warp keeps 32 rows in flight
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int col = cd[i];
+            const int col = cs[i];
             if (col < cb || col >= ce) continue;
-            const uint32_t* ar = P.adj + (size_t)i * aw;
+            const uint4* ar = reinterpret_cast<const uint4*>(P.adj + (size_t)i * aw);
             const uint32_t* xr = s_bits + (col - cb) * aw;
             int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-            int w = 0;
-            for (; w + 4 <= aw; w += 4) {
-                const uint4 a = __ldg(reinterpret_cast<const uint4*>(ar + w));
-                g0 += __popc(a.x & xr[w]);
-                g1 += __popc(a.y & xr[w + 1]);
-                g2 += __popc(a.z & xr[w + 2]);
-                g3 += __popc(a.w & xr[w + 3]);
+#pragma unroll 4
+            for (int w = 0; w < aw / 4; ++w) {
+                const uint4 a4 = __ldg(ar + w);
+                g0 += __popc(a4.x & xr[4 * w]);
+                g1 += __popc(a4.y & xr[4 * w + 1]);
+                g2 += __popc(a4.z & xr[4 * w + 2]);
+                g3 += __popc(a4.w & xr[4 * w + 3]);
             }
-            for (; w < aw; ++w) g0 += __popc(__ldg(ar + w) & xr[w]);
             const int g = (g0 + g1) + (g2 + g3);
             twice += g;
             if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
@@ -529,6 +508,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
         finalize_population(P);
     }
 }
+
 
 // ---------------------------------------------------------------------------
 
@@ -614,6 +594,46 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// grad_S L of vertex i0 + lane for every colour of individual d (eq. 13):
+// class j occupies the padded range [of[j], of[j+1]) of the colour-sorted
+// vertices (length a multiple of 4; padding points at the zero row n of B),
+// so each class is a loop of 4-wide chunks: one 8-byte index load and four
+// independent shared-memory loads.  Gs[j * gstride + lane] receives the class
+// sum + nu t E_dj (+ the gamma-matrix entry in the dense forms).
+__device__ __forceinline__ void class_sums(const uint16_t* pm, const int* of, const int8_t* Ed,
+                                           const uint16_t* grow, const float* Bl, int bstride, float nut,
+                                           int k, float* Gs, int gstride, int lane) {
+    int s = 0;
+    int e = __ldg(of + 1);
+    for (int j = 0; j < k; ++j) {
+        const int e_next = (j + 2 <= k) ? __ldg(of + j + 2) : 0;  // next bound, ahead of use
+        float extra = nut * (float)__ldg(Ed + j);
+        if (grow) extra += (float)__ldg(grow + j);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int p = s; p < e; p += 4) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(pm + p));
+            a0 += Bl[(int)(v.x & 0xFFFFu) * bstride];
+            a1 += Bl[(int)(v.x >> 16) * bstride];
+            a2 += Bl[(int)(v.y & 0xFFFFu) * bstride];
+            a3 += Bl[(int)(v.y >> 16) * bstride];
+        }
+        Gs[j * gstride + lane] = ((a0 + a1) + (a2 + a3)) + extra;
+        s = e;
+        e = e_next;
+    }
+}
+
+__device__ __forceinline__ void prefetch_item(const uint16_t* pm, int plen, const int* of, int k, const int8_t* Ed,
+                                              int lane) {
+    const int lp = (2 * plen + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
+    for (int l = lane; l < lp + lo + le; l += 32) {
+        const char* a = l < lp ? (const char*)pm + 128 * l
+                               : (l < lp + lo ? (const char*)of + 128 * (l - lp)
+                                              : (const char*)Ed + 128 * (l - lp - lo));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+    }
+}
+
 template <bool BTS, bool BULK>
 __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt, float* Gs, float* Ws,
                                             uint64_t* bar, unsigned& phase, int T, int d, float nut,
@@ -638,47 +658,14 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
         }
     }
 
-    // 2. grad_S L rows by colour-class segment sums
+    // 2. grad_S L rows by colour-class sums
     const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
     const int* of = P.off + (size_t)d * (k + 1);
     const int8_t* Ed = P.E + (size_t)d * k;
+    prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
     const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-    const int bstride = BTS ? 32 : P.ldb;
     const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-    int j = 0;
-    int next_end = __ldg(of + 1);
-    while (j < k && next_end == 0) {  // leading empty classes
-        Gs[j * 32 + lane] = nut * (float)__ldg(Ed + j);
-        ++j;
-        next_end = j < k ? __ldg(of + j + 1) : INT_MAX;
-    }
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int p0 = 0; p0 < n; p0 += 8) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(pm + p0));
-        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-        float b[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int m = (wv[q >> 1] >> (16 * (q & 1))) & 0x7FFF;  // bit 15 marks class ends
-            b[q] = (p0 + q < n) ? Bl[m * bstride] : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            acc[q & 3] += b[q];
-            if (p0 + q + 1 == next_end) {  // class j ends here (uniform branch)
-                const float gam = grow ? (float)__ldg(grow + j) : 0.f;  // dense form: A.S
-                Gs[j * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + nut * (float)__ldg(Ed + j) + gam;
-                acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
-                ++j;
-                next_end = j < k ? __ldg(of + j + 1) : INT_MAX;  // no class left
-                while (j < k && next_end == p0 + q + 1) {  // empty classes
-                    Gs[j * 32 + lane] = nut * (float)__ldg(Ed + j);
-                    ++j;
-                    next_end = j < k ? __ldg(of + j + 1) : INT_MAX;
-                }
-            }
-        }
-    }
+    class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 32, lane);
     __syncwarp();
     if (debug_only == 1) {
         if (lane < rows) {
@@ -799,61 +786,14 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
 
-    // Phase A: Gs[j][lane] = grad_S L[d, i0 + lane, j].  Gs is first filled
-    // with the terms that do not depend on the class members (nu t E_dj, and
-    // the gamma matrix in the dense form; both are all there is for an empty
-    // class), then the vertices of d are streamed in colour order, 8 per
-    // 16-byte load, and each class sum is added at its marked last vertex.
+    // Phase A: Gs[j][lane] = grad_S L[d, i0 + lane, j] by colour-class sums
     const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
-    const uint16_t* cl = P.cls + (size_t)d * k;
+    const int* of = P.off + (size_t)d * (k + 1);
     const int8_t* Ed = P.E + (size_t)d * k;
-    {
-        const int lp = (2 * n + 127) / 128, lc = (2 * k + 127) / 128, le = (k + 127) / 128;
-        for (int l = lane; l < lp + lc + le; l += 32) {
-            const char* a = l < lp ? (const char*)pm + 128 * l
-                                   : (l < lp + lc ? (const char*)cl + 128 * (l - lp)
-                                                  : (const char*)Ed + 128 * (l - lp - lc));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-        }
-    }
+    prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
     const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-    const int bstride = BTS ? 32 : P.ldb;
     const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-    for (int j = 0; j < k; ++j) {
-        float g0 = nut * (float)__ldg(Ed + j);
-        if (grow) g0 += (float)__ldg(grow + j);
-        Gs[j * 33 + lane] = g0;
-    }
-    float acc = 0.f;
-    int ci = 0;
-    int jcur = __ldg(cl);
-    for (int p0 = 0; p0 < n; p0 += 8) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(pm + p0));
-        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-        float b[8];
-        uint32_t ends = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t e = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            const bool ok = p0 + q < n;
-            b[q] = ok ? Bl[(int)(e & 0x7FFFu) * bstride] : 0.f;
-            ends |= (ok ? (e >> 15) : 0u) << q;
-        }
-        if (ends == 0) {  // no class ends in these 8 vertices
-            acc += ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                acc += b[q];
-                if ((ends >> q) & 1u) {
-                    Gs[jcur * 33 + lane] += acc;
-                    acc = 0.f;
-                    ++ci;
-                    jcur = __ldg(cl + min(ci, k - 1));
-                }
-            }
-        }
-    }
+    class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 33, lane);
     __syncwarp();
     if (debug_only == 1) {
         if (lane < rows) {
@@ -971,7 +911,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     __shared__ __align__(8) uint64_t s_bbar;
     const int n = P.n, D = P.D, k = P.k;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nbox = (n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS;
+    const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
     float* Bt = sm;
     float* Gs = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * (33 * k);
     unsigned bphase = 0;
@@ -1034,7 +974,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     __shared__ __align__(8) uint64_t s_bbar;  // completion of the B panel copy
     const int n = P.n, D = P.D, k = P.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nbox = (n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS;
+    const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
     float* Bt = sm;
     float* Gs = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * (64 * k + 4);
     float* Ws = Gs + 32 * k;
@@ -1115,7 +1055,7 @@ int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem)
     // (32 x k) floats + one mbarrier (16 B).  The B panel: whole TMA boxes
     // of TC_BT_BOX_ROWS x 32 floats.
     const long long per_warp = k <= 128 ? 4ll * 33 * k : 4ll * (64ll * k + 4);
-    const long long bt = 4ll * 32 * ((n + TC_BT_BOX_ROWS - 1) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
+    const long long bt = 4ll * 32 * ((n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
     int w = 0, bts = 0;
     if (bt + per_warp <= kSmemOptin) {
         bts = 1;
@@ -1162,6 +1102,7 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     long long smem_ll = colours * row;
     const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // per-warp colour counts
     if (smem_ll < counts) smem_ll = counts;
+    smem_ll += 16ll * ((P.n + 7) / 8);  // the individual's colours
     const int smem = (int)smem_ll;
     cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -42,7 +42,6 @@ struct tc_ctx {
     float* d_B = nullptr;
     uint16_t* d_perm = nullptr;
     int* d_off = nullptr;
-    uint16_t* d_cls = nullptr;
     int8_t* d_E = nullptr;
     int* d_fcolor = nullptr;
     int* d_feq = nullptr;
@@ -162,7 +161,6 @@ void free_population(tc_ctx* c) {
     dfree(c->d_B);
     dfree(c->d_perm);
     dfree(c->d_off);
-    dfree(c->d_cls);
     dfree(c->d_E);
     dfree(c->d_fcolor);
     dfree(c->d_feq);
@@ -225,9 +223,8 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.B = c->d_B;
     P.ldb = c->ldb;
     P.perm = c->d_perm;
-    P.perm_stride = (c->n + 7) & ~7;
+    P.perm_stride = (c->n + 3 * c->k + 7) & ~7;
     P.off = c->d_off;
-    P.cls = c->d_cls;
     P.E = c->d_E;
     P.fcolor = c->d_fcolor;
     P.feq = c->d_feq;
@@ -707,8 +704,8 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     const int Dp = (D + 3) & ~3;
     const size_t Dnk = (size_t)D * n * k;
     if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) ||
-        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)n * ((n + 3) & ~3))) ||
-        (rc = dalloc(&c->d_perm, (size_t)D * ((n + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) || (rc = dalloc(&c->d_cls, (size_t)D * k)) ||
+        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
+        (rc = dalloc(&c->d_perm, (size_t)D * ((n + 3 * k + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
         (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
         (rc = dalloc(&c->d_lut, 4 * (size_t)(D + 1))) || (rc = dalloc(&c->d_st, 1)) ||
@@ -734,6 +731,8 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     st.best_d = -1;
     st.best_t = -1;
     cudaError_t e = cudaMemsetAsync(c->d_cT, 0xFF, sizeof(uint16_t) * (size_t)n * Dp, c->stream);
+    if (e == cudaSuccess)  // row n of B is the zero row the padded classes point at
+        e = cudaMemsetAsync(c->d_B, 0, sizeof(float) * (size_t)(n + 1) * ((n + 3) & ~3), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * D, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_best, 0, sizeof(uint16_t) * n, c->stream);
     if (e == cudaSuccess)
