@@ -326,10 +326,15 @@ def run_ours(args):
         ctx.tc_set_params(p)
         forms["chosen"] = max((f for f in forms if f != "chosen"), key=lambda f: forms[f]["value"])
 
-    # roofline of the dominant kernel
+    # roofline of the dominant stage: the gradient + update stage (k_update,
+    # preceded by k_gsum when the gradient tiles are computed separately)
     kid = int(np.argmax(kms))
     name = T.KERNEL_NAMES.get(kid, f"kid{kid}")
     avg_ms = kms[kid] / max(1, kcnt[kid])
+    if kid in (T.TC_KID_UPDATE, T.TC_KID_GSUM) and kcnt[T.TC_KID_GSUM] > 0:
+        kid = T.TC_KID_UPDATE
+        name = "k_gsum+k_update"
+        avg_ms = (kms[T.TC_KID_UPDATE] + kms[T.TC_KID_GSUM]) / max(1, kcnt[T.TC_KID_UPDATE])
     peaks = measured_peaks()
     if kid == T.TC_KID_UPDATE:
         alg = algorithmic_update_bytes(n, k, D)

@@ -171,6 +171,7 @@ int tc_step_async(tc_ctx *ctx, int64_t n_iters);
 #define TC_KID_UPDATE 2  /* fused gradient gather + softmax-ST update        */
 #define TC_KID_GEMM_M 3  /* dense forms: M~ = S S^T GEMM                     */
 #define TC_KID_GEMM_G 4  /* dense forms: Gamma = A S GEMM                    */
+#define TC_KID_GSUM 5    /* grad_S L tiles (class sums of the pair matrix)   */
 #define TC_NUM_KID 8
 
 /* Per-kernel device timing with CUDA events recorded around every launch

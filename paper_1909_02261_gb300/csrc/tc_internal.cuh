@@ -35,9 +35,11 @@ struct tc_kparams {
     int ct_bytes;     // bytes per colour in cT: 1 when k <= 255, else 2
     int adj_words;    // 32-bit words per adjacency-bitmask row
     int problem, nb_iter, bonus_diag, stop_on_legal, commit;
+    int csr_walk;     // grad_S L by adjacency lists (mu = 0, sparse graph)
     float eta, rho, lambda_, mu, nu, alpha, beta;
     float* W;                 // D x n x k
     uint16_t* c;              // D x n colours
+    uint16_t* c_snap;         // D x n colours of the iteration, for the adjacency walk
     uint16_t* cT;             // n x Dp colours (vertex-major, ct_bytes each), pads all-ones
     const uint32_t* adj;      // n x adj_words adjacency bitmask
     const int* rowptr;        // CSR
@@ -70,6 +72,7 @@ struct tc_kparams {
     int n_pad;
     int* dbg_Mt;              // optional n x n group concentration output
     float* dbg_G;             // optional D x n x k grad_S L output
+    float* Gbuf;              // D x nT x k x 32 grad_S L tiles of the split update
     int* dbg_gamma;           // optional D x n conflicting-neighbour counts
 };
 
@@ -81,6 +84,9 @@ cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int num_sms,
                              cudaStream_t s, int debug_only);
+cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s);
+cudaError_t tc_launch_update_split(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,
+                                   int debug_only);
 // Tiled 2-D tensor map (TMA) over a row-major matrix: `inner` elements per
 // row (contiguous), `outer` rows, `row_bytes` between rows (multiple of 16).
 int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint64_t inner,

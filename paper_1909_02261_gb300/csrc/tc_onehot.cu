@@ -21,6 +21,7 @@
 //              next Step 1 argmax, one 32-vertex tile of one individual per
 //              warp, W streamed through shared memory once.
 #include <limits.h>
+#include <algorithm>
 #include <math.h>
 #include <stdio.h>
 
@@ -28,8 +29,9 @@
 
 namespace {
 
-constexpr int PT = 64;              // pair tile edge
-constexpr int PAIR_THREADS = 256;   // 16 x 16 threads, 4 x 4 pairs each
+constexpr int PT = 32;              // pair tile edge
+constexpr int PP = PT / 16;         // pairs per thread along each tile edge
+constexpr int PAIR_THREADS = 256;   // 16 x 16 threads, PP x PP pairs each
 constexpr int PAIR_CW = 64;         // colour words per chunk (< 256: lane counters)
 constexpr int CLS_THREADS = 256;
 constexpr int UPD_MAX_WARPS = 8;
@@ -116,7 +118,7 @@ __global__ void k_assign(tc_kparams P) {
 }
 
 // ---------------------------------------------------------------------------
-// k_pairs: one 64x64 tile (I <= M) of vertex pairs per block, 4x4 pairs per
+// k_pairs: one 32x32 tile (I <= M) of vertex pairs per block, 2x2 pairs per
 // thread.  Colours are packed 4 (8-bit, k <= 255) or 2 (16-bit) to a word of
 // cT; equal colours are counted without branches: x = a ^ b has a zero lane
 // exactly where the colours agree, and ~(((x & 0x7f..) + 0x7f..) | x) sets
@@ -139,11 +141,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     const int Dw = P.Dp * CB / 4;
     const uint32_t* cTw = reinterpret_cast<const uint32_t*>(P.cT);
 
-    uint32_t wide[4][4];
+    uint32_t wide[PP][PP];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < PP; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) wide[a][b] = 0u;
+        for (int b = 0; b < PP; ++b) wide[a][b] = 0u;
     const bool from_gemm = P.M32 != nullptr;  // dense form: M~ came from a GEMM
     for (int w0 = 0; w0 < (from_gemm ? 0 : Dw); w0 += PAIR_CW) {
         const int cw = min(PAIR_CW, Dw - w0);
@@ -155,22 +157,22 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
             s_b[r][w] = mm < n ? cTw[(size_t)mm * Dw + w0 + w] : 0u;
         }
         __syncthreads();
-        uint32_t acc[4][4];
+        uint32_t acc[PP][PP];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < PP; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = 0u;
+            for (int b = 0; b < PP; ++b) acc[a][b] = 0u;
         for (int w = 0; w < cw; ++w) {
-            uint32_t av[4], bv[4];
+            uint32_t av[PP], bv[PP];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < PP; ++r) {
                 av[r] = s_a[ty + 16 * r][w];
                 bv[r] = s_b[tx + 16 * r][w];
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < PP; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
+                for (int b = 0; b < PP; ++b) {
                     const uint32_t x = av[a] ^ bv[b];
                     const uint32_t y = (x & LOW) + LOW;
                     acc[a][b] += (~(y | x) & HIGH) >> SH;
@@ -178,9 +180,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
         }
         // fold the per-lane chunk counters (< 256) into two 16-bit lanes
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < PP; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
+            for (int b = 0; b < PP; ++b)
                 wide[a][b] += CB == 1 ? (acc[a][b] & 0x00FF00FFu) + ((acc[a][b] >> 8) & 0x00FF00FFu)
                                       : acc[a][b];
     }
@@ -195,10 +197,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     float(*s_t)[PT + 1] = reinterpret_cast<float(*)[PT + 1]>(&s_a[0][0]);
     int(*s_m)[PT + 1] = reinterpret_cast<int(*)[PT + 1]>(&s_b[0][0]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < PP; ++a) {
         const int il = ty + 16 * a, i = I * PT + il;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < PP; ++b) {
             const int ml = tx + 16 * b, m = M * PT + ml;
             float bb = 0.f;
             int mt = 0;
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     __syncthreads();
     // transposed counterpart B[m][i] = B[i][m] for the strictly-lower half
     for (int e = tid; e < PT * PT; e += PAIR_THREADS) {
-        const int ml = e >> 6, il = e & 63;
+        const int ml = e / PT, il = e % PT;
         const int mm = M * PT + ml, ii = I * PT + il;
         if (mm < n && ii < n && (I < M || il < ml)) {
             P.B[(size_t)mm * P.ldb + ii] = s_t[ml][il];
@@ -375,7 +377,13 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     uint32_t* s_bits = s_dyn + ((n + 7) / 8) * 4;               // after the colours
     const uint16_t* cd = P.c + (size_t)d * n;
     for (int j = threadIdx.x; j < k; j += blockDim.x) s_hist[j] = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) cs[i] = cd[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint16_t c = cd[i];
+        cs[i] = c;
+        // the adjacency-list walk of k_update reads this iteration's colours
+        // while k_update overwrites c with the next ones: give it a snapshot
+        if (P.csr_walk) P.c_snap[(size_t)d * n + i] = c;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[cs[i]], 1);
     __syncthreads();
@@ -623,6 +631,38 @@ __device__ __forceinline__ void class_sums(const uint16_t* pm, const int* of, co
     }
 }
 
+// Sparse form of the same sums, used when B vanishes off the edges (mu = 0:
+// no bonus term, so B_im = 0 unless a_im = 1): vertex i0 + lane walks its
+// adjacency list (CSR) and adds B_im into the colour of each neighbour m,
+// D 2|E| additions per iteration instead of D n^2.
+__device__ __forceinline__ void neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
+                                               const int8_t* Ed, const uint16_t* grow, const float* Bl,
+                                               int bstride, float nut, int k, float* Gs, int gstride, int lane,
+                                               int i, bool valid) {
+    for (int j = 0; j < k; ++j) {
+        float g0 = nut * (float)__ldg(Ed + j);
+        if (grow) g0 += (float)__ldg(grow + j);
+        Gs[j * gstride + lane] = g0;
+    }
+    if (!valid) return;
+    const int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+        const int m0 = __ldg(colidx + e), m1 = __ldg(colidx + e + 1), m2 = __ldg(colidx + e + 2),
+                  m3 = __ldg(colidx + e + 3);
+        const int c0 = __ldg(cd + m0), c1 = __ldg(cd + m1), c2 = __ldg(cd + m2), c3 = __ldg(cd + m3);
+        const float b0 = Bl[m0 * bstride], b1 = Bl[m1 * bstride], b2 = Bl[m2 * bstride], b3 = Bl[m3 * bstride];
+        Gs[c0 * gstride + lane] += b0;
+        Gs[c1 * gstride + lane] += b1;
+        Gs[c2 * gstride + lane] += b2;
+        Gs[c3 * gstride + lane] += b3;
+    }
+    for (; e < e1; ++e) {
+        const int m = __ldg(colidx + e);
+        Gs[__ldg(cd + m) * gstride + lane] += Bl[m * bstride];
+    }
+}
+
 __device__ __forceinline__ void prefetch_item(const uint16_t* pm, int plen, const int* of, int k, const int8_t* Ed,
                                               int lane) {
     const int lp = (2 * plen + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
@@ -634,7 +674,7 @@ __device__ __forceinline__ void prefetch_item(const uint16_t* pm, int plen, cons
     }
 }
 
-template <bool BTS, bool BULK>
+template <bool BTS, bool BULK, bool GIN>
 __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt, float* Gs, float* Ws,
                                             uint64_t* bar, unsigned& phase, int T, int d, float nut,
                                             bool smooth, int debug_only) {
@@ -645,8 +685,34 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     const size_t wbase = ((size_t)d * n + i0) * k;
     const unsigned wbytes = (unsigned)(rows * k * 4);
 
+    if (GIN) {
+        // grad_S L tile computed by k_gsum: [k][32] floats, contiguous
+        const unsigned gbytes = (unsigned)(k * 32 * 4);
+        const float* gsrc = P.Gbuf + ((size_t)d * ((n + 31) / 32) + T) * k * 32;
+        const bool wtoo = debug_only != 1 && BULK;
+        if (lane == 0) {
+            bulk_wait_read();  // the previous item's store has read Ws
+            mbar_expect_tx(bar, gbytes + (wtoo ? wbytes : 0u));
+            bulk_load(Gs, gsrc, gbytes, bar);
+            if (wtoo) bulk_load(Ws, P.W + wbase, wbytes, bar);
+        }
+        if (debug_only != 1 && !BULK)
+            for (int e = lane; e < rows * k; e += 32) Ws[e] = P.W[wbase + e];
+        mbar_wait_bounded(bar, phase, &P.st->err);
+        phase ^= 1u;
+        __syncwarp();
+        if (debug_only == 1) {
+            if (lane < rows) {
+                float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
+                for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
+            }
+            __syncwarp();
+            return;
+        }
+    }
+
     // 1. weight tile -> Ws
-    if (debug_only != 1) {
+    if (!GIN && debug_only != 1) {
         if (BULK) {
             if (lane == 0) {
                 bulk_wait_read();  // the previous item's store has read Ws
@@ -659,15 +725,22 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     }
 
     // 2. grad_S L rows by colour-class sums
-    const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
-    const int* of = P.off + (size_t)d * (k + 1);
-    const int8_t* Ed = P.E + (size_t)d * k;
-    prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
-    const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-    const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-    class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 32, lane);
+    if (!GIN) {
+        const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
+        const int* of = P.off + (size_t)d * (k + 1);
+        const int8_t* Ed = P.E + (size_t)d * k;
+        prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
+        const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
+        const uint16_t* grow =
+            (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
+        if (P.csr_walk)
+            neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k,
+                           Gs, 32, lane, i0 + lane, lane < rows);
+        else
+            class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 32, lane);
+    }
     __syncwarp();
-    if (debug_only == 1) {
+    if (!GIN && debug_only == 1) {
         if (lane < rows) {
             float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
             for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
@@ -677,7 +750,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt
     }
 
     // 3. per-row softmax straight-through step (lane = row)
-    if (BULK) {
+    if (BULK && !GIN) {
         mbar_wait_bounded(bar, phase, &P.st->err);
         phase ^= 1u;
     } else {
@@ -793,7 +866,11 @@ __device__ __forceinline__ void update_item_rows(const tc_kparams& P, const floa
     prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
     const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
     const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-    class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 33, lane);
+    if (P.csr_walk)
+        neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 33,
+                       lane, i0 + lane, lane < rows);
+    else
+        class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 33, lane);
     __syncwarp();
     if (debug_only == 1) {
         if (lane < rows) {
@@ -965,7 +1042,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     }
 }
 
-template <bool BTS, bool BULK>
+template <bool BTS, bool BULK, bool GIN>
 __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     k_update(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block, int debug_only) {
     tc_dev_state* st = P.st;
@@ -980,7 +1057,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     float* Ws = Gs + 32 * k;
     uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + 32 * k);
     unsigned phase = 0, bphase = 0;
-    if (BULK && lane == 0) {
+    if ((BULK || GIN) && lane == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -1020,8 +1097,8 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
             bphase ^= 1u;
         }
         for (long long qq = q + warp; qq < seg_end; qq += nw)
-            update_item<BTS, BULK>(P, Bt, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), nut,
-                                   smooth, debug_only);
+            update_item<BTS, BULK, GIN>(P, Bt, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), nut,
+                                        smooth, debug_only);
         q = seg_end;
     }
     if (BULK && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores done
@@ -1036,6 +1113,84 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
                 __threadfence();
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_gsum: Step 3-ii alone.  grad_S L for every (32-vertex tile, individual)
+// item into the tile buffer Gbuf[(d * nT + T) * k * 32 + j * 32 + lane]
+// (coalesced 128-byte rows), so k_update can stream it with bulk copies.
+// Without per-warp tiles the B panel leaves room for 16 warps per SM; the
+// adjacency walk (CSR) accumulates in a shared tile per warp instead.
+// ---------------------------------------------------------------------------
+constexpr int GSUM_MAX_WARPS = 16;
+
+template <bool BTS, bool CSR>
+__global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
+    k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block) {
+    tc_dev_state* st = P.st;
+    if (P.commit && st->stop) return;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ __align__(8) uint64_t s_bbar;
+    const int n = P.n, D = P.D, k = P.k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
+    float* Bt = sm;
+    float* Gw = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * 32 * k;  // CSR only
+    unsigned bphase = 0;
+    if (BTS && threadIdx.x == 0) {
+        mbar_init(&s_bbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+    const long long t = st->t;
+    const float nut = (float)((double)P.nu * (double)t);
+    const int nT = (n + 31) / 32;
+    const long long Q = (long long)nT * D;
+    long long q = (long long)blockIdx.x * items_per_block;
+    const long long qend = min(Q, q + items_per_block);
+    while (q < qend) {
+        const int T = (int)(q / D);
+        const long long seg_end = min(qend, (long long)(T + 1) * D);
+        if (BTS) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
+                for (int b = 0; b < nbox; ++b)
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS),
+                        "r"(smem_u32(&s_bbar))
+                        : "memory");
+            }
+            mbar_wait_bounded(&s_bbar, bphase, &st->err);
+            bphase ^= 1u;
+        }
+        const int i0 = T * 32, rows = min(32, n - i0);
+        for (long long qq = q + warp; qq < seg_end; qq += nw) {
+            const int d = (int)(qq - (long long)T * D);
+            const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
+            const int* of = P.off + (size_t)d * (k + 1);
+            const int8_t* Ed = P.E + (size_t)d * k;
+            prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
+            const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
+            const uint16_t* grow =
+                (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
+            float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32;
+            if (CSR) {
+                neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut,
+                               k, Gw, 32, lane, i0 + lane, lane < rows);
+                __syncwarp();
+                for (int j = 0; j < k; ++j) Gout[j * 32 + lane] = Gw[j * 32 + lane];
+                __syncwarp();
+            } else {
+                class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gout, 32, lane);
+            }
+        }
+        q = seg_end;
     }
 }
 
@@ -1113,7 +1268,7 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
 template <bool BTS, bool BULK>
 static cudaError_t launch_update_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps,
                                    int smem, int per_block, cudaStream_t s, int debug_only) {
-    auto fn = k_update<BTS, BULK>;
+    auto fn = k_update<BTS, BULK, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
@@ -1128,6 +1283,60 @@ static cudaError_t launch_rows_t(const tc_kparams& P, const CUtensorMap& tmB, in
     if (e != cudaSuccess) return e;
     fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
     return cudaGetLastError();
+}
+
+template <bool BTS, bool CSR>
+static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps, int smem,
+                                 int per_block, cudaStream_t s) {
+    auto fn = k_gsum<BTS, CSR>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block);
+    return cudaGetLastError();
+}
+
+// grad_S L tiles (k_gsum) into P.Gbuf: the B panel in shared memory when it
+// fits, 16 warps, or fewer with the per-warp tiles of the adjacency walk.
+cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s) {
+    const long long bt = 4ll * 32 * ((P.n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
+    const long long per_warp = P.csr_walk ? 4ll * 32 * P.k : 0;
+    bool bts = bt + per_warp <= kSmemOptin;
+    const long long base = bts ? bt : 0;
+    int warps = GSUM_MAX_WARPS;
+    if (per_warp > 0) warps = (int)std::min<long long>(GSUM_MAX_WARPS, (kSmemOptin - base) / per_warp);
+    if (warps < 1) return cudaErrorInvalidValue;
+    const int smem = (int)(base + per_warp * warps);
+    const long long items = (long long)((P.n + 31) / 32) * P.D;
+    long long blocks = std::min<long long>(num_sms, items);
+    if (blocks < 1) blocks = 1;
+    const int per_block = (int)((items + blocks - 1) / blocks);
+    if (P.csr_walk)
+        return bts ? launch_gsum_t<true, true>(P, tmB, (int)blocks, warps, smem, per_block, s)
+                   : launch_gsum_t<false, true>(P, tmB, (int)blocks, warps, smem, per_block, s);
+    return bts ? launch_gsum_t<true, false>(P, tmB, (int)blocks, warps, smem, per_block, s)
+               : launch_gsum_t<false, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
+}
+
+// The update of the split pipeline: grad_S L tiles from P.Gbuf, weight tiles
+// streamed by bulk copies, one item per warp at a time.
+cudaError_t tc_launch_update_split(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,
+                                   int debug_only) {
+    const long long per_warp = 4ll * (64ll * P.k + 4);
+    int warps = (int)std::min<long long>(UPD_MAX_WARPS, kSmemOptin / per_warp);
+    if (warps < 1) return cudaErrorInvalidValue;
+    const int smem = (int)(per_warp * warps);
+    const long long items = (long long)((P.n + 31) / 32) * P.D;
+    long long blocks = std::min<long long>(num_sms, items);
+    if (blocks < 1) blocks = 1;
+    const int per_block = (int)((items + blocks - 1) / blocks);
+    const bool bulk = ((long long)P.n * P.k) % 4 == 0 && (((uintptr_t)P.W) & 15) == 0;
+    auto launch = [&](auto fn) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        fn<<<(int)blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
+        return cudaGetLastError();
+    };
+    return bulk ? launch(k_update<false, true, true>) : launch(k_update<false, false, true>);
 }
 
 cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,

@@ -38,8 +38,11 @@ struct tc_ctx {
     tc_params p{};
     float* d_W = nullptr;
     uint16_t* d_c = nullptr;
+    uint16_t* d_csnap = nullptr;
     uint16_t* d_cT = nullptr;
     float* d_B = nullptr;
+    float* d_Gbuf = nullptr;  // grad_S L tiles of the split update
+    int split = 1;            // 1: k_gsum + k_update, 0: one fused kernel
     uint16_t* d_perm = nullptr;
     int* d_off = nullptr;
     int8_t* d_E = nullptr;
@@ -157,8 +160,10 @@ void free_population(tc_ctx* c) {
     free_dense(c);
     dfree(c->d_W);
     dfree(c->d_c);
+    dfree(c->d_csnap);
     dfree(c->d_cT);
     dfree(c->d_B);
+    dfree(c->d_Gbuf);
     dfree(c->d_perm);
     dfree(c->d_off);
     dfree(c->d_E);
@@ -216,11 +221,13 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.beta = c->p.beta;
     P.W = c->d_W;
     P.c = c->d_c;
+    P.c_snap = c->d_csnap;
     P.cT = c->d_cT;
     P.adj = c->d_adj;
     P.rowptr = c->d_rowptr;
     P.colidx = c->d_colidx;
     P.B = c->d_B;
+    P.Gbuf = c->d_Gbuf;
     P.ldb = c->ldb;
     P.perm = c->d_perm;
     P.perm_stride = (c->n + 3 * c->k + 7) & ~7;
@@ -238,6 +245,9 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.powB = c->d_lut + 3 * D1;
     P.st = c->d_st;
     P.best = c->d_best;
+    // with mu = 0 the pair matrix vanishes off the edges; below a density of
+    // 1/8 walking the adjacency lists beats walking all n vertices per class
+    P.csr_walk = c->p.mu == 0.0f && c->nnz * 8 < (long long)c->n * c->n;
     if (c->p.form != TC_FORM_ONEHOT && c->d_M32) {
         P.M32 = c->d_M32;
         P.ldm = c->n_pad;
@@ -435,6 +445,17 @@ int launch_dense_gemms(tc_ctx* c, int which) {
     return TC_OK;
 }
 
+// Step 3-ii + Step 4: k_gsum then k_update (split), or the fused kernel.
+cudaError_t launch_grad_update(tc_ctx* c, const tc_kparams& P, int debug_only) {
+    if (c->split) {
+        cudaError_t e = timed(c, TC_KID_GSUM, [&] { return tc_launch_gsum(P, c->tmB, c->num_sms, c->stream); });
+        if (e != cudaSuccess) return e;
+        return timed(c, TC_KID_UPDATE,
+                     [&] { return tc_launch_update_split(P, c->tmB, c->num_sms, c->stream, debug_only); });
+    }
+    return timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->tmB, c->num_sms, c->stream, debug_only); });
+}
+
 int launch_iteration(tc_ctx* c) {
     if (fault("launch")) return TC_ERR_INJECTED;
     tc_kparams P = make_kparams(c, 1);
@@ -444,11 +465,11 @@ int launch_iteration(tc_ctx* c) {
     TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
     if (dense && (rc = launch_dense_gemms(c, 1))) return rc;
     TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
-    TC_CHECK(timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->tmB, c->num_sms, c->stream, 0); }));
+    TC_CHECK(launch_grad_update(c, P, 0));
     return TC_OK;
 }
 
-int launches_per_iteration(const tc_ctx* c) { return c->p.form == TC_FORM_ONEHOT ? 3 : 5; }
+int launches_per_iteration(const tc_ctx* c) { return (c->p.form == TC_FORM_ONEHOT ? 3 : 5) + c->split; }
 
 int read_state(tc_ctx* c, tc_dev_state* h) {
     TC_CHECK(cudaMemcpyAsync(h, c->d_st, sizeof(*h), cudaMemcpyDeviceToHost, c->stream));
@@ -567,6 +588,8 @@ int tc_create(tc_ctx** out, int device) {
         return TC_ERR_CUDA;
     }
     c->stream = c->own;
+    const char* uv = getenv("TC_UPDATE_VARIANT");
+    if (uv && strcmp(uv, "fused") == 0) c->split = 0;
     *out = c;
     return TC_OK;
 }
@@ -703,8 +726,9 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     const int n = c->n;
     const int Dp = (D + 3) & ~3;
     const size_t Dnk = (size_t)D * n * k;
-    if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) ||
+    if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) || (rc = dalloc(&c->d_csnap, (size_t)D * n)) ||
         (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
+        (rc = dalloc(&c->d_Gbuf, (size_t)D * ((n + 31) / 32) * 32 * k)) ||
         (rc = dalloc(&c->d_perm, (size_t)D * ((n + 3 * k + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
         (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
@@ -943,8 +967,8 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
     if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
     if (e == cudaSuccess && dense && launch_dense_gemms(c, 1)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
-    if (e == cudaSuccess && G) e = tc_launch_update(P, c->tmB, c->num_sms, c->stream, 1);
-    c->launches += 2 + (G ? 1 : 0);
+    if (e == cudaSuccess && G) e = launch_grad_update(c, P, 1);
+    c->launches += 2;
     std::vector<uint16_t> hc;
     tc_dev_state h;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1034,8 +1058,8 @@ int tc_st_grad_dev(tc_ctx* c, float* gradW_dev, float* loss_dev) {
     TC_CHECK(tc_launch_pairs(P, c->stream));
     if (dense && (rc = launch_dense_gemms(c, 1))) return rc;
     TC_CHECK(tc_launch_classes(P, c->stream));
-    TC_CHECK(tc_launch_update(P, c->tmB, c->num_sms, c->stream, 2));
-    c->launches += 3;
+    TC_CHECK(launch_grad_update(c, P, 2));
+    c->launches += 2;
     if (loss_dev)  // loss, kappa, varpi are consecutive floats of the state
         TC_CHECK(cudaMemcpyAsync(loss_dev, &c->d_st->loss, 3 * sizeof(float), cudaMemcpyDeviceToDevice,
                                  c->stream));

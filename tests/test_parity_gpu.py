@@ -213,3 +213,16 @@ def test_dense_and_csr_inputs_agree():
             c.tc_set_state(W, 2)
             c.tc_step(3)
         assert np.array_equal(a.tc_get_state()[0], b.tc_get_state()[0])
+
+
+@pytest.mark.parametrize("name", ["ecp_gnp1000p01_k25_D128", "ecp_gnp1000p09_k230_D128"])
+def test_full_size_ecp_workloads(name):
+    """The ECP workloads: G(1000, 0.1), k = 25 (mu = 0, so the gradient walks
+    the adjacency lists) and G(1000, 0.9), k = 230 (alpha = 1.5; k > 128
+    update path), D = 128, nu = 1e-5, compared in full on one iteration."""
+    w = inputs.WORKLOADS[name]
+    rp, ci, _ = inputs.workload_graph(name)
+    W = inputs.init_weights(w["D"], w["n"], w["k"], 0.01, seed=w["w_seed"])
+    p = params(TC_ECP, stop_on_legal=0, alpha=w.get("alpha", 2.5))
+    with make_ctx(rp, ci, w["D"], w["k"], p, W, 321) as ctx:
+        check_iteration(ctx, rp, ci, p, 321, want_G=True)
