@@ -87,6 +87,27 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, unsigned parity, volatile 
     }
 }
 
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA load of one box delivered to the same shared-memory offset of every CTA
+// in `mask` of the cluster, completing bytes on each CTA's own barrier there.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(b)), "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -116,6 +137,16 @@ __device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t 
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives on the barrier at the same offset in every CTA of `mask` once the
+// MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* b, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            su32(b)),
+        "h"(mask)
         : "memory");
 }
 
@@ -170,6 +201,10 @@ __device__ __forceinline__ void store_chunk(const tc_gemm_args& g, int row, int 
     }
 }
 
+// CL > 1: the CL CTAs of a cluster take CL units that share the column tile
+// and K range (consecutive in the unit list); each loads 1/CL of the B tile
+// and multicasts it to all, so B crosses L2 once per cluster.
+template <int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               tc_gemm_args g) {
@@ -181,10 +216,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ volatile int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
+    const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
+    const int group = blockIdx.x / CL, ngroups = gridDim.x / CL;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             bar_init(&full[s], 1);
-            bar_init(&empty[s], 1);
+            bar_init(&empty[s], CL);  // one MMA commit from every CTA of the cluster
         }
         for (int a = 0; a < 2; ++a) {
             bar_init(&tfull[a], 1);
@@ -202,6 +240,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();  // peers' barriers initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
@@ -209,7 +248,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {  // TMA producer
             unsigned gk = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < g.n_units && ok; u += gridDim.x) {
+            for (int u = group * CL + (int)crank; u < g.n_units && ok; u += ngroups * CL) {
                 const int4 w = g.units[u];
                 for (int kb = w.z; kb < w.w; ++kb, ++gk) {
                     const int s = gk % STAGES;
@@ -218,7 +257,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     uint8_t* sa = smem + s * STAGE_BYTES;
                     bar_expect_tx(&full[s], STAGE_BYTES);
                     tma_load_2d(sa, &tmX, kb * BK, w.x * BM, &full[s]);
-                    tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN, &full[s]);
+                    if (CL == 1)
+                        tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN, &full[s]);
+                    else  // my slice of the shared B tile, to every CTA of the cluster
+                        tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), &tmY, kb * BK,
+                                       w.y * BN + (int)crank * (BN / CL), &full[s], cmask);
                 }
             }
         }
@@ -226,7 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {  // MMA issuer
             unsigned gk = 0, ui = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < g.n_units && ok; u += gridDim.x, ++ui) {
+            for (int u = group * CL + (int)crank; u < g.n_units && ok; u += ngroups * CL, ++ui) {
                 const int4 w = g.units[u];
                 const int a = ui & 1;
                 const unsigned ua = ui >> 1;
@@ -243,7 +286,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < BK / 32; ++kk)  // +32 bytes = +2 in the address field
                         mma_f8(dt, ad + 2 * kk, bd + 2 * kk, (kb > w.z || kk > 0) ? 1 : 0);
-                    mma_commit(&empty[s]);  // stage s is free once these MMAs finish
+                    if (CL == 1)
+                        mma_commit(&empty[s]);  // stage s is free once these MMAs finish
+                    else
+                        mma_commit_mc(&empty[s], cmask);  // ... in every CTA it was multicast to
                 }
                 if (ok) mma_commit(&tfull[a]);
             }
@@ -261,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int q = warp & 3;
         const int row_in_tile = 32 * q + lane;
         unsigned ui = 0;
-        for (int u = blockIdx.x; u < g.n_units; u += gridDim.x, ++ui) {
+        for (int u = group * CL + (int)crank; u < g.n_units; u += ngroups * CL, ++ui) {
             const int4 w = g.units[u];
             const int a = ui & 1;
             const unsigned ua = ui >> 1;
@@ -281,6 +327,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();  // no CTA leaves while peers may still write into it
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -404,15 +451,39 @@ int tc_gemm_tile_m() { return BM; }
 int tc_gemm_tile_n() { return BN; }
 int tc_gemm_tile_k() { return BK; }
 
-cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int num_sms, cudaStream_t s) {
+template <int CL>
+static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g, int num_sms,
+                             cudaStream_t s) {
     const int smem = STAGES * STAGE_BYTES + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int grid = num_sms < g.n_units ? num_sms : g.n_units;
-    if (grid < 1) grid = 1;
-    k_gemm_tc<<<grid, TC_THREADS, smem, s>>>(tmX, tmY, g);
-    return cudaGetLastError();
+    int groups = num_sms / CL < g.n_units / CL ? num_sms / CL : g.n_units / CL;
+    if (groups < 1) groups = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(groups * CL);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gemm_tc<CL>, tmX, tmY, g);
+}
+
+// `cluster`: CTAs sharing each B tile (1, 2 or 4); the unit list must come
+// in groups of that many units with equal column tile and K range, and tmY's
+// box must hold BN / cluster rows.
+cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
+                              int num_sms, int cluster, cudaStream_t s) {
+    switch (cluster) {
+        case 4: return launch_tc<4>(tmX, tmY, g, num_sms, s);
+        case 2: return launch_tc<2>(tmX, tmY, g, num_sms, s);
+        default: return launch_tc<1>(tmX, tmY, g, num_sms, s);
+    }
 }
 
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,

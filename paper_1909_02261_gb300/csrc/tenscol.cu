@@ -65,6 +65,7 @@ struct tc_ctx {
     int4* d_units_g = nullptr;
     int4* d_units_m = nullptr;
     int n_units_g = 0, n_units_m = 0;
+    int cl_g = 1, cl_m = 1;  // cluster sizes sharing B tiles (Gamma, M~)
     alignas(64) CUtensorMap tmA8;
     alignas(64) CUtensorMap tmS8T;
     alignas(64) CUtensorMap tmS8x;
@@ -294,6 +295,10 @@ int setup_dense(tc_ctx* c) {
     for (int bn = 0; bn < ntm; ++bn)
         for (int bm = 0; bm < mt; ++bm)
             if ((long long)bn * BNt + BNt - 1 >= (long long)bm * BMt) tri.push_back(make_int2(bm, bn));
+    // Gamma units come as columns of mt row tiles: clusters of 4 (or 2) row
+    // tiles share each S_cat^T tile; M~ tiles come in row pairs per column
+    c->cl_g = (mt % 4 == 0) ? 4 : 2;
+    c->cl_m = 2;
     const int kblocks = (int)(ldg / BKt);
     int split = (int)((c->num_sms + tri.size() - 1) / tri.size());
     split = std::max(1, std::min(split, kblocks));
@@ -322,9 +327,9 @@ int setup_dense(tc_ctx* c) {
     const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
     if ((rc = tc_encode_tmap_2d(&c->tmA8, u8, c->d_A8, n_pad, n_pad, n_pad, BKt, BMt, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, BNt, sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, BNt / c->cl_g, sw)) ||
         (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, BNt, sw))) {
+        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, BNt / c->cl_m, sw))) {
         free_dense(c);
         return rc;
     }
@@ -433,12 +438,12 @@ int launch_dense_gemms(tc_ctx* c, int which) {
     if (which == 0) {
         TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, c->stream));
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->num_sms, c->stream)
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->num_sms, c->cl_m, c->stream)
                       : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, c->stream);
         }));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->num_sms, c->stream)
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->num_sms, c->cl_g, c->stream)
                       : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, c->stream);
         }));
     }
