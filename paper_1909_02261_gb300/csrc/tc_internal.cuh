@@ -46,7 +46,7 @@ struct tc_kparams {
     const int* colidx;
     float* B;                 // (n + 1) x ldb pair coefficients of eq. 13 (symmetric); row n = 0
     int ldb;                  // row stride of B: n rounded up to a multiple of 4
-    uint16_t* perm;           // D x perm_stride vertices sorted by colour (stable), every
+    uint32_t* perm;           // D x perm_stride vertices sorted by colour (stable), every
                               // class padded to a multiple of 4 with vertex n
     int perm_stride;          // n + 3k rounded up to a multiple of 8
     int* off;                 // D x (k + 1) padded colour-class offsets into perm
@@ -82,11 +82,8 @@ cudaError_t tc_launch_init_weights(float* W, long long count, unsigned long long
 cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s);
-cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int num_sms,
-                             cudaStream_t s, int debug_only);
 cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s);
-cudaError_t tc_launch_update_split(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,
-                                   int debug_only);
+cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only);
 // Tiled 2-D tensor map (TMA) over a row-major matrix: `inner` elements per
 // row (contiguous), `outer` rows, `row_bytes` between rows (multiple of 16).
 int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint64_t inner,
@@ -120,4 +117,4 @@ int tc_relaxed_partials(int n);
 
 int tc_pair_tile_edge();
 int tc_pair_tile_count(int n);
-int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem);
+int tc_update_fits(int k);

@@ -402,12 +402,12 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     }
     int run = s_scan[threadIdx.x] - local;
     int* od = P.off + (size_t)d * (k + 1);
-    uint16_t* pd = P.perm + (size_t)d * P.perm_stride;
+    uint32_t* pd = P.perm + (size_t)d * P.perm_stride;
     for (int j = j0; j < j1; ++j) {
         const int h = s_hist[j], ph = (h + 3) & ~3;
         od[j] = run;
         s_cur[j] = run;
-        for (int q = h; q < ph; ++q) pd[run + q] = (uint16_t)n;  // padding entries
+        for (int q = h; q < ph; ++q) pd[run + q] = (uint32_t)n;  // padding entries
         run += ph;
     }
     if (threadIdx.x == CLS_THREADS - 1) od[k] = s_scan[CLS_THREADS - 1];
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
             const int col = cs[i];
             const unsigned peers = __match_any_sync(valid, col);
             const int rank = __popc(peers & ((1u << lane) - 1u));
-            pd[wcnt[warp * k + col] + rank] = (uint16_t)i;
+            pd[wcnt[warp * k + col] + rank] = (uint32_t)i;
             __syncwarp(valid);
             if ((__ffs(peers) - 1) == lane) wcnt[warp * k + col] += __popc(peers);
         }
@@ -519,21 +519,18 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
 
 
 // ---------------------------------------------------------------------------
-
-// k_update: Step 3-ii + Step 4 for (32-vertex tile, individual) items.
-//
-// A block owns a contiguous range of items (tile-major), keeps the tile's 32
-// columns of B in shared memory (BTS) and gives one item at a time to each
-// warp.  Per item the warp
-//   1. starts a bulk async copy (TMA, cp.async.bulk) of the item's 32 x k
-//      weight rows (contiguous in W) into its shared tile Ws;
-//   2. walks the individual's vertices in colour order (8 per 16-byte load)
-//      summing B_im per class into Gs[j][lane] (grad_S L, lane = vertex);
-//   3. waits for the copy, then each lane updates its own row: softmax,
-//      straight-through gradient, descent step, smoothing, argmax;
-//   4. writes the row tile back with a bulk async store.
-// Rows are read at a lane-dependent rotation of the colour index so that the
-// 32 lanes hit 32 different banks for any k.
+// Step 3-ii and Step 4 run as two kernels over (32-vertex tile, individual)
+// items, tile-major:
+//   k_gsum    grad_S L of eq. 13 for the item's 32 vertices and all k colours
+//             into Gbuf[item][j][lane] (coalesced 128-byte rows).  A block
+//             owns a contiguous run of items and keeps the tile's 32 columns
+//             of B in shared memory (2-D TMA boxes); each warp sums B over the
+//             individual's colour classes, one vertex per lane.
+//   k_update  streams the item's grad_S tile and its 32 x k weight rows into
+//             shared memory with bulk async copies, each lane updates its own
+//             row (softmax, straight-through gradient of eq. 12, descent step,
+//             smoothing of eq. 8, the next argmax) and the rows go back with a
+//             bulk async store.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -578,8 +575,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return false;
 }
 
-__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, unsigned bytes,
-                                          uint64_t* bar) {
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, unsigned bytes, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
             "r"(smem_u32(smem_dst)),
@@ -602,15 +598,18 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// grad_S L of vertex i0 + lane for every colour of individual d (eq. 13):
-// class j occupies the padded range [of[j], of[j+1]) of the colour-sorted
-// vertices (length a multiple of 4; padding points at the zero row n of B),
-// so each class is a loop of 4-wide chunks: one 8-byte index load and four
-// independent shared-memory loads.  Gs[j * gstride + lane] receives the class
-// sum + nu t E_dj (+ the gamma-matrix entry in the dense forms).
-__device__ __forceinline__ void class_sums(const uint16_t* pm, const int* of, const int8_t* Ed,
-                                           const uint16_t* grow, const float* Bl, int bstride, float nut,
-                                           int k, float* Gs, int gstride, int lane) {
+// grad_S L of one vertex (i0 + lane) for every colour of one individual
+// (eq. 13): class j occupies the padded range [of[j], of[j+1]) of the
+// colour-sorted vertices (length a multiple of 4; padding is vertex n, a zero
+// row of B), so a class is a loop of 4-wide chunks: one 16-byte index load
+// and four independent loads of B.  BS > 0: B rows BS floats apart (the
+// shared panel), else `bstride`.  Gout[j * 32] receives the class sum + nu t
+// E_dj (+ the gamma-matrix entry in the dense forms).
+template <int BS>
+__device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const int8_t* Ed,
+                                           const uint16_t* grow, const float* Bl, int bstride, float nut, int k,
+                                           float* Gout) {
+    const int bs = BS > 0 ? BS : bstride;
     int s = 0;
     int e = __ldg(of + 1);
     for (int j = 0; j < k; ++j) {
@@ -618,31 +617,31 @@ __device__ __forceinline__ void class_sums(const uint16_t* pm, const int* of, co
         float extra = nut * (float)__ldg(Ed + j);
         if (grow) extra += (float)__ldg(grow + j);
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 2
         for (int p = s; p < e; p += 4) {
-            const uint2 v = __ldg(reinterpret_cast<const uint2*>(pm + p));
-            a0 += Bl[(int)(v.x & 0xFFFFu) * bstride];
-            a1 += Bl[(int)(v.x >> 16) * bstride];
-            a2 += Bl[(int)(v.y & 0xFFFFu) * bstride];
-            a3 += Bl[(int)(v.y >> 16) * bstride];
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(pm + p));
+            a0 += Bl[(int)v.x * bs];
+            a1 += Bl[(int)v.y * bs];
+            a2 += Bl[(int)v.z * bs];
+            a3 += Bl[(int)v.w * bs];
         }
-        Gs[j * gstride + lane] = ((a0 + a1) + (a2 + a3)) + extra;
+        Gout[j * 32] = ((a0 + a1) + (a2 + a3)) + extra;
         s = e;
         e = e_next;
     }
 }
 
 // Sparse form of the same sums, used when B vanishes off the edges (mu = 0:
-// no bonus term, so B_im = 0 unless a_im = 1): vertex i0 + lane walks its
-// adjacency list (CSR) and adds B_im into the colour of each neighbour m,
-// D 2|E| additions per iteration instead of D n^2.
+// no bonus term, so B_im = 0 unless a_im = 1): vertex i walks its adjacency
+// list (CSR) and adds B_im into the colour of each neighbour, D 2|E|
+// additions per iteration instead of D n^2.  Accumulates in Gs[j * 32].
 __device__ __forceinline__ void neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
                                                const int8_t* Ed, const uint16_t* grow, const float* Bl,
-                                               int bstride, float nut, int k, float* Gs, int gstride, int lane,
-                                               int i, bool valid) {
+                                               int bstride, float nut, int k, float* Gs, int i, bool valid) {
     for (int j = 0; j < k; ++j) {
         float g0 = nut * (float)__ldg(Ed + j);
         if (grow) g0 += (float)__ldg(grow + j);
-        Gs[j * gstride + lane] = g0;
+        Gs[j * 32] = g0;
     }
     if (!valid) return;
     const int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
@@ -652,20 +651,22 @@ __device__ __forceinline__ void neighbour_sums(const int* rowptr, const int* col
                   m3 = __ldg(colidx + e + 3);
         const int c0 = __ldg(cd + m0), c1 = __ldg(cd + m1), c2 = __ldg(cd + m2), c3 = __ldg(cd + m3);
         const float b0 = Bl[m0 * bstride], b1 = Bl[m1 * bstride], b2 = Bl[m2 * bstride], b3 = Bl[m3 * bstride];
-        Gs[c0 * gstride + lane] += b0;
-        Gs[c1 * gstride + lane] += b1;
-        Gs[c2 * gstride + lane] += b2;
-        Gs[c3 * gstride + lane] += b3;
+        Gs[c0 * 32] += b0;
+        Gs[c1 * 32] += b1;
+        Gs[c2 * 32] += b2;
+        Gs[c3 * 32] += b3;
     }
     for (; e < e1; ++e) {
         const int m = __ldg(colidx + e);
-        Gs[__ldg(cd + m) * gstride + lane] += Bl[m * bstride];
+        Gs[__ldg(cd + m) * 32] += Bl[m * bstride];
     }
 }
 
-__device__ __forceinline__ void prefetch_item(const uint16_t* pm, int plen, const int* of, int k, const int8_t* Ed,
+// One 128-byte line per lane: the item's sorted vertices, class offsets and
+// equity signs arrive in L1 in parallel instead of one L2 round trip per line.
+__device__ __forceinline__ void prefetch_item(const uint32_t* pm, int plen, const int* of, int k, const int8_t* Ed,
                                               int lane) {
-    const int lp = (2 * plen + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
+    const int lp = (4 * plen + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
     for (int l = lane; l < lp + lo + le; l += 32) {
         const char* a = l < lp ? (const char*)pm + 128 * l
                                : (l < lp + lo ? (const char*)of + 128 * (l - lp)
@@ -674,454 +675,9 @@ __device__ __forceinline__ void prefetch_item(const uint16_t* pm, int plen, cons
     }
 }
 
-template <bool BTS, bool BULK, bool GIN>
-__device__ __forceinline__ void update_item(const tc_kparams& P, const float* Bt, float* Gs, float* Ws,
-                                            uint64_t* bar, unsigned& phase, int T, int d, float nut,
-                                            bool smooth, int debug_only) {
-    const int n = P.n, k = P.k;
-    const int lane = threadIdx.x & 31;
-    const int i0 = T * 32;
-    const int rows = min(32, n - i0);
-    const size_t wbase = ((size_t)d * n + i0) * k;
-    const unsigned wbytes = (unsigned)(rows * k * 4);
-
-    if (GIN) {
-        // grad_S L tile computed by k_gsum: [k][32] floats, contiguous
-        const unsigned gbytes = (unsigned)(k * 32 * 4);
-        const float* gsrc = P.Gbuf + ((size_t)d * ((n + 31) / 32) + T) * k * 32;
-        const bool wtoo = debug_only != 1 && BULK;
-        if (lane == 0) {
-            bulk_wait_read();  // the previous item's store has read Ws
-            mbar_expect_tx(bar, gbytes + (wtoo ? wbytes : 0u));
-            bulk_load(Gs, gsrc, gbytes, bar);
-            if (wtoo) bulk_load(Ws, P.W + wbase, wbytes, bar);
-        }
-        if (debug_only != 1 && !BULK)
-            for (int e = lane; e < rows * k; e += 32) Ws[e] = P.W[wbase + e];
-        mbar_wait_bounded(bar, phase, &P.st->err);
-        phase ^= 1u;
-        __syncwarp();
-        if (debug_only == 1) {
-            if (lane < rows) {
-                float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
-                for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
-            }
-            __syncwarp();
-            return;
-        }
-    }
-
-    // 1. weight tile -> Ws
-    if (!GIN && debug_only != 1) {
-        if (BULK) {
-            if (lane == 0) {
-                bulk_wait_read();  // the previous item's store has read Ws
-                mbar_expect_tx(bar, wbytes);
-                bulk_load(Ws, P.W + wbase, wbytes, bar);
-            }
-        } else {
-            for (int e = lane; e < rows * k; e += 32) Ws[e] = P.W[wbase + e];
-        }
-    }
-
-    // 2. grad_S L rows by colour-class sums
-    if (!GIN) {
-        const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
-        const int* of = P.off + (size_t)d * (k + 1);
-        const int8_t* Ed = P.E + (size_t)d * k;
-        prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
-        const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-        const uint16_t* grow =
-            (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-        if (P.csr_walk)
-            neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k,
-                           Gs, 32, lane, i0 + lane, lane < rows);
-        else
-            class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 32, lane);
-    }
-    __syncwarp();
-    if (!GIN && debug_only == 1) {
-        if (lane < rows) {
-            float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
-            for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
-        }
-        __syncwarp();
-        return;
-    }
-
-    // 3. per-row softmax straight-through step (lane = row)
-    if (BULK && !GIN) {
-        mbar_wait_bounded(bar, phase, &P.st->err);
-        phase ^= 1u;
-    } else {
-        __syncwarp();
-    }
-    int newc = 0;
-    if (lane < rows) {
-        float* wr = Ws + lane * k;
-        const float* gr = Gs + lane;
-        const int j0 = lane % k;
-        float mx = -INFINITY;
-        int jj = j0;
-#pragma unroll 4
-        for (int q = 0; q < k; ++q) {
-            mx = fmaxf(mx, wr[jj]);
-            jj = (jj + 1 == k) ? 0 : jj + 1;
-        }
-        float Z = 0.f, num = 0.f;
-        jj = j0;
-#pragma unroll 4
-        for (int q = 0; q < k; ++q) {
-            const float e = __expf(wr[jj] - mx);
-            Z += e;
-            num = fmaf(e, gr[jj * 32], num);
-            jj = (jj + 1 == k) ? 0 : jj + 1;
-        }
-        const float invZ = 1.0f / Z;
-        const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
-        float bestv = -INFINITY;
-        newc = k;
-        jj = j0;
-#pragma unroll 4
-        for (int q = 0; q < k; ++q) {
-            const float w = wr[jj];
-            const float gw = __fmul_rn(__fmul_rn(__expf(w - mx), invZ), __fsub_rn(gr[jj * 32], dot));
-            if (debug_only == 2) {
-                P.dbg_G[((size_t)d * n + i0 + lane) * k + jj] = gw;
-                jj = (jj + 1 == k) ? 0 : jj + 1;
-                continue;
-            }
-            float wn = __fsub_rn(w, __fmul_rn(P.eta, gw));
-            if (smooth) wn = __fdiv_rn(wn, P.rho);
-            wr[jj] = wn;
-            if (wn > bestv || (wn == bestv && jj < newc)) {
-                bestv = wn;
-                newc = jj;
-            }
-            jj = (jj + 1 == k) ? 0 : jj + 1;
-        }
-        if (newc >= k) newc = 0;
-    }
-    __syncwarp();
-    if (debug_only == 2) return;
-
-    // 4. write back
-    if (BULK) {
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) bulk_store(P.W + wbase, Ws, wbytes);
-    } else {
-        for (int e = lane; e < rows * k; e += 32) P.W[wbase + e] = Ws[e];
-    }
-    if (lane < rows) {
-        const int i = i0 + lane;
-        if (P.S8) {  // dense form: move the one-hot entry of (d, i) in both operands
-            const int old = P.c[(size_t)d * n + i];
-            if (old != newc) {
-                const size_t co = (size_t)d * k + old, cn = (size_t)d * k + newc;
-                P.S8[(size_t)i * P.ldg + co] = 0;
-                P.S8[(size_t)i * P.ldg + cn] = 0x38;  // E4M3 1.0
-                P.S8T[co * P.n_pad + i] = 0;
-                P.S8T[cn * P.n_pad + i] = 0x38;
-            }
-        }
-        store_colour(P, d, i, newc);
-    }
-    __syncwarp();
-}
-
-// Register variant for k <= 32 KQ (KQ = 1..4): the class sums go to a
-// padded shared tile Gs[j][33], then the warp updates the 32 rows one at a
-// time, lanes across colours, with the weight rows streamed straight from
-// global memory through an 8-row register prefetch ring (no shared W tile,
-// which doubles the resident warps).
-// Order-preserving map of floats to signed ints (for a < b: key(a) < key(b);
-// -0 and +0 map apart, which is harmless for a maximum).
-__device__ __forceinline__ int float_key(float x) {
-    const int b = __float_as_int(x);
-    return b ^ ((b >> 31) & 0x7FFFFFFF);
-}
-
-__device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7FFFFFFF)); }
-
-// Warp maximum of a float through one redux.sync on its integer key.
-__device__ __forceinline__ float warp_max_key(float v) {
-    const unsigned u = (unsigned)float_key(v) ^ 0x80000000u;  // signed -> unsigned order
-    return key_float((int)(__reduce_max_sync(0xffffffffu, u) ^ 0x80000000u));
-}
-
-template <bool BTS, int KQ>
-__device__ __forceinline__ void update_item_rows(const tc_kparams& P, const float* Bt, float* Gs, int T, int d,
-                                                 float nut, bool smooth, int debug_only) {
-    constexpr int PF = 8;  // rows in flight
-    const int n = P.n, k = P.k;
-    const int lane = threadIdx.x & 31;
-    const int i0 = T * 32;
-    const int rows = min(32, n - i0);
-
-    // Phase A: Gs[j][lane] = grad_S L[d, i0 + lane, j] by colour-class sums
-    const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
-    const int* of = P.off + (size_t)d * (k + 1);
-    const int8_t* Ed = P.E + (size_t)d * k;
-    prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
-    const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-    const uint16_t* grow = (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-    if (P.csr_walk)
-        neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 33,
-                       lane, i0 + lane, lane < rows);
-    else
-        class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gs, 33, lane);
-    __syncwarp();
-    if (debug_only == 1) {
-        if (lane < rows) {
-            float* gd = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
-            for (int jj = 0; jj < k; ++jj) gd[jj] = Gs[jj * 33 + lane];
-        }
-        __syncwarp();
-        return;
-    }
-
-    // Phase B: rows of the tile, lanes across colours j = lane + 32 q
-    float* Wt = P.W + ((size_t)d * n + i0) * k;
-    float ring[PF][KQ];
-#pragma unroll
-    for (int r = 0; r < PF; ++r)
-#pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int j = lane + 32 * q;
-            ring[r][q] = (r < rows && j < k) ? __ldcg(Wt + (size_t)r * k + j) : 0.f;
-        }
-    int mycol = 0;
-    for (int r0 = 0; r0 < rows; r0 += PF) {
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const int r = r0 + u;
-            if (r >= rows) break;
-            float x[KQ], gq[KQ];
-            float mx = -INFINITY;
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                const int j = lane + 32 * q;
-                x[q] = j < k ? ring[u][q] : -INFINITY;
-                gq[q] = j < k ? Gs[j * 33 + r] : 0.f;
-                mx = fmaxf(mx, x[q]);
-            }
-            // prefetch row r + PF into the freed slot
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                const int j = lane + 32 * q;
-                ring[u][q] = (r + PF < rows && j < k) ? __ldcg(Wt + (size_t)(r + PF) * k + j) : 0.f;
-            }
-            mx = warp_max_key(mx);
-            float ev[KQ], Z = 0.f, num = 0.f;
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                ev[q] = (lane + 32 * q < k) ? __expf(x[q] - mx) : 0.f;
-                Z += ev[q];
-                num = fmaf(ev[q], gq[q], num);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                Z += __shfl_xor_sync(0xffffffffu, Z, o);
-                num += __shfl_xor_sync(0xffffffffu, num, o);
-            }
-            const float invZ = 1.0f / Z;
-            const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
-            float bv = -INFINITY;
-            int bj = k;
-#pragma unroll
-            for (int q = 0; q < KQ; ++q) {
-                const int j = lane + 32 * q;
-                if (j < k) {
-                    // eq. 12, then the descent step and eq. 8, each rounded once
-                    // (no contraction): W_next == W - eta * gW holds bit for bit
-                    const float gw = __fmul_rn(__fmul_rn(ev[q], invZ), __fsub_rn(gq[q], dot));
-                    if (debug_only == 2) {
-                        P.dbg_G[((size_t)d * n + i0 + r) * k + j] = gw;
-                        continue;
-                    }
-                    float wn = __fsub_rn(x[q], __fmul_rn(P.eta, gw));
-                    if (smooth) wn = __fdiv_rn(wn, P.rho);
-                    __stcg(Wt + (size_t)r * k + j, wn);
-                    if (wn > bv) {  // j increases with q: first maximum wins
-                        bv = wn;
-                        bj = j;
-                    }
-                }
-            }
-            {  // argmax, lowest colour on ties: max of the value, then min colour
-                const unsigned key = (unsigned)float_key(bv + 0.0f) ^ 0x80000000u;  // -0 counts as +0
-                const unsigned best = __reduce_max_sync(0xffffffffu, key);
-                const int mine = key == best ? bj : k;
-                bj = (int)__reduce_min_sync(0xffffffffu, (unsigned)mine);
-            }
-            if (lane == r) mycol = bj >= k ? 0 : bj;
-        }
-    }
-    if (debug_only == 2) {
-        __syncwarp();
-        return;
-    }
-    if (lane < rows) {
-        const int i = i0 + lane;
-        if (P.S8) {  // dense form: move the one-hot entry of (d, i) in both operands
-            const int old = P.c[(size_t)d * n + i];
-            if (old != mycol) {
-                const size_t co = (size_t)d * k + old, cn = (size_t)d * k + mycol;
-                P.S8[(size_t)i * P.ldg + co] = 0;
-                P.S8[(size_t)i * P.ldg + cn] = 0x38;
-                P.S8T[co * P.n_pad + i] = 0;
-                P.S8T[cn * P.n_pad + i] = 0x38;
-            }
-        }
-        store_colour(P, d, i, mycol);
-    }
-    __syncwarp();
-}
-
-template <bool BTS, int KQ>
-__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
-    k_update_rows(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block, int debug_only) {
-    tc_dev_state* st = P.st;
-    if (!debug_only && st->stop) return;
-    extern __shared__ __align__(1024) float sm[];
-    __shared__ __align__(8) uint64_t s_bbar;
-    const int n = P.n, D = P.D, k = P.k;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
-    float* Bt = sm;
-    float* Gs = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * (33 * k);
-    unsigned bphase = 0;
-    if (BTS && threadIdx.x == 0) {
-        mbar_init(&s_bbar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fence_proxy_async();
-    }
-    __syncthreads();
-    const long long t = st->t;
-    const float nut = (float)((double)P.nu * (double)t);
-    const bool smooth = ((t + 1) % P.nb_iter) == 0;
-    const int nT = (n + 31) / 32;
-    const long long Q = (long long)nT * D;
-    long long q = (long long)blockIdx.x * items_per_block;
-    const long long qend = min(Q, q + items_per_block);
-    while (q < qend) {
-        const int T = (int)(q / D);
-        const long long seg_end = min(qend, (long long)(T + 1) * D);
-        if (BTS) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
-                for (int b = 0; b < nbox; ++b)
-                    asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
-                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS),
-                        "r"(smem_u32(&s_bbar))
-                        : "memory");
-            }
-            mbar_wait_bounded(&s_bbar, bphase, &st->err);
-            bphase ^= 1u;
-        }
-        for (long long qq = q + warp; qq < seg_end; qq += nw)
-            update_item_rows<BTS, KQ>(P, Bt, Gs, T, (int)(qq - (long long)T * D), nut, smooth, debug_only);
-        q = seg_end;
-    }
-    if (!debug_only) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned ticket = atomicAdd(&st->done_update, 1u);
-            if (ticket == gridDim.x - 1) {
-                st->done_update = 0u;
-                st->t = t + 1;
-                __threadfence();
-            }
-        }
-    }
-}
-
-template <bool BTS, bool BULK, bool GIN>
-__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
-    k_update(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block, int debug_only) {
-    tc_dev_state* st = P.st;
-    if (!debug_only && st->stop) return;
-    extern __shared__ __align__(1024) float sm[];
-    __shared__ __align__(8) uint64_t s_bbar;  // completion of the B panel copy
-    const int n = P.n, D = P.D, k = P.k;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
-    float* Bt = sm;
-    float* Gs = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * (64 * k + 4);
-    float* Ws = Gs + 32 * k;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + 32 * k);
-    unsigned phase = 0, bphase = 0;
-    if ((BULK || GIN) && lane == 0) {
-        mbar_init(bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fence_proxy_async();
-    }
-    if (BTS && threadIdx.x == 0) {
-        mbar_init(&s_bbar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        fence_proxy_async();
-    }
-    __syncthreads();
-    const long long t = st->t;
-    const float nut = (float)((double)P.nu * (double)t);
-    const bool smooth = ((t + 1) % P.nb_iter) == 0;
-    const int nT = (n + 31) / 32;
-    const long long Q = (long long)nT * D;
-    long long q = (long long)blockIdx.x * items_per_block;
-    const long long qend = min(Q, q + items_per_block);
-    while (q < qend) {
-        const int T = (int)(q / D);
-        const long long seg_end = min(qend, (long long)(T + 1) * D);
-        if (BTS) {
-            // B[0..n) x [32 T, 32 T + 32) -> Bt by 2-D TMA boxes (zero filled
-            // past the matrix edge); the panel is symmetric-transposed B
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
-                for (int b = 0; b < nbox; ++b)
-                    asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
-                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS),
-                        "r"(smem_u32(&s_bbar))
-                        : "memory");
-            }
-            mbar_wait_bounded(&s_bbar, bphase, &st->err);
-            bphase ^= 1u;
-        }
-        for (long long qq = q + warp; qq < seg_end; qq += nw)
-            update_item<BTS, BULK, GIN>(P, Bt, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), nut,
-                                        smooth, debug_only);
-        q = seg_end;
-    }
-    if (BULK && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores done
-    if (!debug_only) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned ticket = atomicAdd(&st->done_update, 1u);
-            if (ticket == gridDim.x - 1) {
-                st->done_update = 0u;
-                st->t = t + 1;
-                __threadfence();
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// k_gsum: Step 3-ii alone.  grad_S L for every (32-vertex tile, individual)
-// item into the tile buffer Gbuf[(d * nT + T) * k * 32 + j * 32 + lane]
-// (coalesced 128-byte rows), so k_update can stream it with bulk copies.
-// Without per-warp tiles the B panel leaves room for 16 warps per SM; the
-// adjacency walk (CSR) accumulates in a shared tile per warp instead.
+// k_gsum: one block per SM, 16 warps (the adjacency walk keeps a shared
+// 32 x k accumulator per warp and runs fewer).
 // ---------------------------------------------------------------------------
 constexpr int GSUM_MAX_WARPS = 16;
 
@@ -1154,6 +710,8 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         const int T = (int)(q / D);
         const long long seg_end = min(qend, (long long)(T + 1) * D);
         if (BTS) {
+            // B[0..n] x [32 T, 32 T + 32) -> Bt by 2-D TMA boxes, zero filled
+            // past the matrix edge; B is symmetric, so these are its columns
             __syncthreads();
             if (threadIdx.x == 0) {
                 fence_proxy_async();
@@ -1172,25 +730,184 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         const int i0 = T * 32, rows = min(32, n - i0);
         for (long long qq = q + warp; qq < seg_end; qq += nw) {
             const int d = (int)(qq - (long long)T * D);
-            const uint16_t* pm = P.perm + (size_t)d * P.perm_stride;
+            const uint32_t* pm = P.perm + (size_t)d * P.perm_stride;
             const int* of = P.off + (size_t)d * (k + 1);
             const int8_t* Ed = P.E + (size_t)d * k;
-            prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
+            if (!CSR) prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
             const uint16_t* grow =
                 (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
-            float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32;
+            float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
             if (CSR) {
                 neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut,
-                               k, Gw, 32, lane, i0 + lane, lane < rows);
+                               k, Gw + lane, i0 + lane, lane < rows);
                 __syncwarp();
-                for (int j = 0; j < k; ++j) Gout[j * 32 + lane] = Gw[j * 32 + lane];
+                for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
                 __syncwarp();
+            } else if (BTS) {
+                class_sums<32>(pm, of, Ed, grow, Bl, 32, nut, k, Gout);
             } else {
-                class_sums(pm, of, Ed, grow, Bl, BTS ? 32 : P.ldb, nut, k, Gout, 32, lane);
+                class_sums<0>(pm, of, Ed, grow, Bl, P.ldb, nut, k, Gout);
             }
         }
         q = seg_end;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_update: per item, bulk copies bring the grad_S tile ([k][32], contiguous)
+// and the weight rows ([32][k], contiguous in W) into the warp's shared
+// tiles; lane r updates row r.  The row is read starting at colour r mod k
+// (two wrap-free loops) so that the 32 lanes hit different banks.
+// debug_only: 1 = copy grad_S L to P.dbg_G; 2 = write grad_W L to P.dbg_G
+// instead of updating W.
+// ---------------------------------------------------------------------------
+template <bool BULK>
+__device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, uint64_t* bar,
+                                            unsigned& phase, int T, int d, bool smooth, int debug_only) {
+    const int n = P.n, k = P.k;
+    const int lane = threadIdx.x & 31;
+    const int i0 = T * 32;
+    const int rows = min(32, n - i0);
+    const size_t wbase = ((size_t)d * n + i0) * k;
+    const unsigned wbytes = (unsigned)(rows * k * 4);
+    const unsigned gbytes = (unsigned)(k * 32 * 4);
+    const float* gsrc = P.Gbuf + ((size_t)d * ((n + 31) / 32) + T) * k * 32;
+    const bool wtoo = debug_only != 1 && BULK;
+    if (lane == 0) {
+        bulk_wait_read();  // the previous item's store has read Ws
+        mbar_expect_tx(bar, gbytes + (wtoo ? wbytes : 0u));
+        bulk_load(Gs, gsrc, gbytes, bar);
+        if (wtoo) bulk_load(Ws, P.W + wbase, wbytes, bar);
+    }
+    if (debug_only != 1 && !BULK)
+        for (int e = lane; e < rows * k; e += 32) Ws[e] = P.W[wbase + e];
+    mbar_wait_bounded(bar, phase, &P.st->err);
+    phase ^= 1u;
+    __syncwarp();
+    if (debug_only == 1) {
+        if (lane < rows) {
+            float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
+            for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
+        }
+        __syncwarp();
+        return;
+    }
+    int newc = 0;
+    if (lane < rows) {
+        float* wr = Ws + lane * k;
+        const float* gr = Gs + lane;
+        const int j0 = lane % k;
+        float mx = -INFINITY;
+#pragma unroll 4
+        for (int j = j0; j < k; ++j) mx = fmaxf(mx, wr[j]);
+#pragma unroll 4
+        for (int j = 0; j < j0; ++j) mx = fmaxf(mx, wr[j]);
+        float Z = 0.f, num = 0.f;
+#pragma unroll 4
+        for (int j = j0; j < k; ++j) {
+            const float e = __expf(wr[j] - mx);
+            Z += e;
+            num = fmaf(e, gr[j * 32], num);
+        }
+#pragma unroll 4
+        for (int j = 0; j < j0; ++j) {
+            const float e = __expf(wr[j] - mx);
+            Z += e;
+            num = fmaf(e, gr[j * 32], num);
+        }
+        const float invZ = 1.0f / Z;
+        const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
+        float bestv = -INFINITY;
+        newc = k;
+        // eq. 12, the descent step and eq. 8, each rounded once (no
+        // contraction): W_next == W - eta * gW holds bit for bit
+        auto step = [&](int j) {
+            const float w = wr[j];
+            const float gw = __fmul_rn(__fmul_rn(__expf(w - mx), invZ), __fsub_rn(gr[j * 32], dot));
+            if (debug_only == 2) {
+                P.dbg_G[((size_t)d * n + i0 + lane) * k + j] = gw;
+                return;
+            }
+            float wn = __fsub_rn(w, __fmul_rn(P.eta, gw));
+            if (smooth) wn = __fdiv_rn(wn, P.rho);
+            wr[j] = wn;
+            if (wn > bestv || (wn == bestv && j < newc)) {
+                bestv = wn;
+                newc = j;
+            }
+        };
+#pragma unroll 4
+        for (int j = j0; j < k; ++j) step(j);
+#pragma unroll 4
+        for (int j = 0; j < j0; ++j) step(j);
+        if (newc >= k) newc = 0;
+    }
+    __syncwarp();
+    if (debug_only == 2) return;
+    if (BULK) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) bulk_store(P.W + wbase, Ws, wbytes);
+    } else {
+        for (int e = lane; e < rows * k; e += 32) P.W[wbase + e] = Ws[e];
+    }
+    if (lane < rows) {
+        const int i = i0 + lane;
+        if (P.S8) {  // dense forms: move the one-hot entry of (d, i) in both operands
+            const int old = P.c[(size_t)d * n + i];
+            if (old != newc) {
+                const size_t co = (size_t)d * k + old, cn = (size_t)d * k + newc;
+                P.S8[(size_t)i * P.ldg + co] = 0;
+                P.S8[(size_t)i * P.ldg + cn] = 0x38;  // E4M3 1.0
+                P.S8T[co * P.n_pad + i] = 0;
+                P.S8T[cn * P.n_pad + i] = 0x38;
+            }
+        }
+        store_colour(P, d, i, newc);
+    }
+    __syncwarp();
+}
+
+template <bool BULK>
+__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, int items_per_block, int debug_only) {
+    tc_dev_state* st = P.st;
+    if (!debug_only && st->stop) return;
+    extern __shared__ __align__(1024) float sm[];
+    const int n = P.n, D = P.D, k = P.k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float* Gs = sm + (size_t)warp * (64 * k + 4);
+    float* Ws = Gs + 32 * k;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + 32 * k);
+    unsigned phase = 0;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncwarp();
+    const long long t = st->t;
+    const bool smooth = ((t + 1) % P.nb_iter) == 0;
+    const int nT = (n + 31) / 32;
+    const long long Q = (long long)nT * D;
+    const long long q0 = (long long)blockIdx.x * items_per_block;
+    const long long qend = min(Q, q0 + items_per_block);
+    for (long long qq = q0 + warp; qq < qend; qq += nw) {
+        const int T = (int)(qq / D);
+        update_item<BULK>(P, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), smooth, debug_only);
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
+    if (!debug_only) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned ticket = atomicAdd(&st->done_update, 1u);
+            if (ticket == gridDim.x - 1) {
+                st->done_update = 0u;
+                st->t = t + 1;
+                __threadfence();
+            }
+        }
     }
 }
 
@@ -1205,26 +922,9 @@ int tc_pair_tile_count(int n) {
     return T * (T + 1) / 2;
 }
 
-int tc_update_config(int n, int k, int* warps, int* smem_bytes, int* bt_in_smem) {
-    // per warp, k <= 128: Gs (k x 33) floats; larger k: Gs (32 x k) + Ws
-    // (32 x k) floats + one mbarrier (16 B).  The B panel: whole TMA boxes
-    // of TC_BT_BOX_ROWS x 32 floats.
-    const long long per_warp = k <= 128 ? 4ll * 33 * k : 4ll * (64ll * k + 4);
-    const long long bt = 4ll * 32 * ((n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
-    int w = 0, bts = 0;
-    if (bt + per_warp <= kSmemOptin) {
-        bts = 1;
-        w = (int)((kSmemOptin - bt) / per_warp);
-    } else {
-        w = (int)(kSmemOptin / per_warp);
-    }
-    w = w > UPD_MAX_WARPS ? UPD_MAX_WARPS : w;
-    if (w < 1) return TC_ERR_UNSUPPORTED;
-    *warps = w;
-    *bt_in_smem = bts;
-    *smem_bytes = (int)((bts ? bt : 0) + per_warp * w);
-    return TC_OK;
-}
+// Whether a population of this shape fits the update kernel (one warp's
+// grad_S and weight tiles in shared memory).
+int tc_update_fits(int k) { return 4ll * (64ll * k + 4) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
 
 cudaError_t tc_launch_init_weights(float* W, long long count, unsigned long long seed, float sigma0,
                                    cudaStream_t s) {
@@ -1265,26 +965,6 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <bool BTS, bool BULK>
-static cudaError_t launch_update_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps,
-                                   int smem, int per_block, cudaStream_t s, int debug_only) {
-    auto fn = k_update<BTS, BULK, false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
-    return cudaGetLastError();
-}
-
-template <bool BTS, int KQ>
-static cudaError_t launch_rows_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps,
-                                 int smem, int per_block, cudaStream_t s, int debug_only) {
-    auto fn = k_update_rows<BTS, KQ>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
-    return cudaGetLastError();
-}
-
 template <bool BTS, bool CSR>
 static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps, int smem,
                                  int per_block, cudaStream_t s) {
@@ -1300,7 +980,7 @@ static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, in
 cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s) {
     const long long bt = 4ll * 32 * ((P.n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
     const long long per_warp = P.csr_walk ? 4ll * 32 * P.k : 0;
-    bool bts = bt + per_warp <= kSmemOptin;
+    const bool bts = bt + per_warp <= kSmemOptin;
     const long long base = bts ? bt : 0;
     int warps = GSUM_MAX_WARPS;
     if (per_warp > 0) warps = (int)std::min<long long>(GSUM_MAX_WARPS, (kSmemOptin - base) / per_warp);
@@ -1317,57 +997,24 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
                : launch_gsum_t<false, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
 }
 
-// The update of the split pipeline: grad_S L tiles from P.Gbuf, weight tiles
-// streamed by bulk copies, one item per warp at a time.
-cudaError_t tc_launch_update_split(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,
-                                   int debug_only) {
+// k_update: as many warps as fit one warp's two tiles in shared memory (<= 8).
+cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only) {
     const long long per_warp = 4ll * (64ll * P.k + 4);
-    int warps = (int)std::min<long long>(UPD_MAX_WARPS, kSmemOptin / per_warp);
+    const int warps = (int)std::min<long long>(UPD_MAX_WARPS, kSmemOptin / per_warp);
     if (warps < 1) return cudaErrorInvalidValue;
     const int smem = (int)(per_warp * warps);
     const long long items = (long long)((P.n + 31) / 32) * P.D;
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;
     const int per_block = (int)((items + blocks - 1) / blocks);
+    // bulk copies of the weight rows need 16-byte aligned, 16-byte multiple
+    // tiles: n k % 4 == 0 (tile starts (d n + 32 T) k floats, sizes rows k)
     const bool bulk = ((long long)P.n * P.k) % 4 == 0 && (((uintptr_t)P.W) & 15) == 0;
     auto launch = [&](auto fn) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        fn<<<(int)blocks, warps * 32, smem, s>>>(P, tmB, per_block, debug_only);
+        fn<<<(int)blocks, warps * 32, smem, s>>>(P, per_block, debug_only);
         return cudaGetLastError();
     };
-    return bulk ? launch(k_update<false, true, true>) : launch(k_update<false, false, true>);
+    return bulk ? launch(k_update<true>) : launch(k_update<false>);
 }
-
-cudaError_t tc_launch_update(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s,
-                             int debug_only) {
-    int warps = 0, smem = 0, bts = 0;
-    if (tc_update_config(P.n, P.k, &warps, &smem, &bts) != TC_OK) return cudaErrorInvalidValue;
-    const long long items = (long long)((P.n + 31) / 32) * P.D;
-    long long blocks = num_sms;  // one resident block per SM (shared-memory bound)
-    if (blocks > items) blocks = items;
-    if (blocks < 1) blocks = 1;
-    const int per_block = (int)((items + blocks - 1) / blocks);
-    // bulk copies need 16-byte aligned, 16-byte multiple tiles: n k % 4 == 0
-    // (tile starts are (d n + 32 T) k floats, tile sizes rows k floats)
-    const bool bulk = ((long long)P.n * P.k) % 4 == 0 && (((uintptr_t)P.W) & 15) == 0;
-    if (P.k <= 128) {
-        const int kq = (P.k + 31) / 32;
-#define TC_ROWS(KQ)                                                                                    \
-    return bts ? launch_rows_t<true, KQ>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)    \
-               : launch_rows_t<false, KQ>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
-        switch (kq) {
-            case 1: TC_ROWS(1);
-            case 2: TC_ROWS(2);
-            case 3: TC_ROWS(3);
-            default: TC_ROWS(4);
-        }
-#undef TC_ROWS
-    }
-    if (bts)
-        return bulk ? launch_update_t<true, true>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
-                    : launch_update_t<true, false>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only);
-    return bulk ? launch_update_t<false, true>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only)
-                : launch_update_t<false, false>(P, tmB, (int)blocks, warps, smem, per_block, s, debug_only);
-}
-

@@ -41,9 +41,8 @@ struct tc_ctx {
     uint16_t* d_csnap = nullptr;
     uint16_t* d_cT = nullptr;
     float* d_B = nullptr;
-    float* d_Gbuf = nullptr;  // grad_S L tiles of the split update
-    int split = 1;            // 1: k_gsum + k_update, 0: one fused kernel
-    uint16_t* d_perm = nullptr;
+    float* d_Gbuf = nullptr;  // grad_S L tiles between k_gsum and k_update
+    uint32_t* d_perm = nullptr;
     int* d_off = nullptr;
     int8_t* d_E = nullptr;
     int* d_fcolor = nullptr;
@@ -450,15 +449,11 @@ int launch_dense_gemms(tc_ctx* c, int which) {
     return TC_OK;
 }
 
-// Step 3-ii + Step 4: k_gsum then k_update (split), or the fused kernel.
+// Step 3-ii (k_gsum) then Step 4 (k_update).
 cudaError_t launch_grad_update(tc_ctx* c, const tc_kparams& P, int debug_only) {
-    if (c->split) {
-        cudaError_t e = timed(c, TC_KID_GSUM, [&] { return tc_launch_gsum(P, c->tmB, c->num_sms, c->stream); });
-        if (e != cudaSuccess) return e;
-        return timed(c, TC_KID_UPDATE,
-                     [&] { return tc_launch_update_split(P, c->tmB, c->num_sms, c->stream, debug_only); });
-    }
-    return timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->tmB, c->num_sms, c->stream, debug_only); });
+    cudaError_t e = timed(c, TC_KID_GSUM, [&] { return tc_launch_gsum(P, c->tmB, c->num_sms, c->stream); });
+    if (e != cudaSuccess) return e;
+    return timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->num_sms, c->stream, debug_only); });
 }
 
 int launch_iteration(tc_ctx* c) {
@@ -474,7 +469,7 @@ int launch_iteration(tc_ctx* c) {
     return TC_OK;
 }
 
-int launches_per_iteration(const tc_ctx* c) { return (c->p.form == TC_FORM_ONEHOT ? 3 : 5) + c->split; }
+int launches_per_iteration(const tc_ctx* c) { return c->p.form == TC_FORM_ONEHOT ? 4 : 6; }
 
 int read_state(tc_ctx* c, tc_dev_state* h) {
     TC_CHECK(cudaMemcpyAsync(h, c->d_st, sizeof(*h), cudaMemcpyDeviceToHost, c->stream));
@@ -593,8 +588,6 @@ int tc_create(tc_ctx** out, int device) {
         return TC_ERR_CUDA;
     }
     c->stream = c->own;
-    const char* uv = getenv("TC_UPDATE_VARIANT");
-    if (uv && strcmp(uv, "fused") == 0) c->split = 0;
     *out = c;
     return TC_OK;
 }
@@ -723,8 +716,7 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     else tc_params_default(&p, TC_KCOL);
     int rc = check_params(&p);
     if (rc) return rc;
-    int w, sm, bts;
-    if (tc_update_config(c->n, k, &w, &sm, &bts) != TC_OK) return TC_ERR_UNSUPPORTED;
+    if (tc_update_fits(k) != TC_OK) return TC_ERR_UNSUPPORTED;
     DeviceGuard g(c->device);
     TC_CHECK(cudaStreamSynchronize(c->stream));
     free_population(c);
