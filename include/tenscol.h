@@ -201,6 +201,29 @@ int tc_st_grad_dev(tc_ctx *ctx, float *gradW_dev, float *loss_dev);
 int tc_relaxed_dev(tc_ctx *ctx, const float *W_dev, float tau, int64_t t, float *loss_dev,
                    float *gradW_dev);
 
+/* For callers that cannot allocate device memory (code inside a CUDA-graph
+ * capture that must not call cudaMalloc, a process sharing a device whose
+ * memory pool it does not own, a fixed-budget embedding).  The paper has no
+ * counterpart: this is a library service.  Computes, with no allocation of
+ * any kind, the population pair terms of a population given as colours:
+ * colors_dev[D*n] (device, uint16, individual-major: colour of vertex i in
+ * individual d at d*n + i), adj_dev[n*n] (device, uint8 0/1, symmetric,
+ * zero diagonal), and writes out_dev[0] = kappa (eq. 5) and out_dev[1] =
+ * varpi (eq. 6, diagonal of bar A included iff bonus_diag) in FP32 (device).
+ * Its scratch is a file-scope device array of TC_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits; n above
+ * TC_NOALLOC_MAX_N is rejected with TC_ERR_ARG.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  Every call shares the one array and
+ * clears its completion counter first: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  Runs
+ * on the given stream (NULL: the legacy default stream) of the current
+ * device and returns without waiting. */
+#define TC_NOALLOC_MAX_N 8192
+#define TC_NOALLOC_SCRATCH_BYTES 264192
+int tc_pair_terms_noalloc(int n, int D, const uint16_t *colors_dev, const uint8_t *adj_dev, float alpha,
+                          float beta, int bonus_diag, float *out_dev, void *stream);
+
 /* Number of device kernel launches issued by this context since creation
  * (for launch accounting in benchmarks). */
 int tc_launch_count(tc_ctx *ctx, int64_t *count);

@@ -90,6 +90,8 @@ def load(build_if_missing: bool = True):
         "tc_kernel_times": (C.c_int, [vp, vp, vp]),
         "tc_st_grad_dev": (C.c_int, [vp, vp, vp]),
         "tc_relaxed_dev": (C.c_int, [vp, vp, C.c_float, i64, vp, vp]),
+        "tc_pair_terms_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_float, C.c_float, C.c_int, vp,
+                                            vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -114,6 +116,14 @@ def _ck(rc: int, what: str):
 
 def _ptr(a):
     return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def tc_pair_terms_noalloc(n: int, D: int, colors_ptr: int, adj_ptr: int, alpha: float, beta: float,
+                          bonus_diag: int, out_ptr: int, stream_handle: int | None = None):
+    """Device pointers in, no allocation: kappa and varpi into out_ptr[0:2]."""
+    _ck(load().tc_pair_terms_noalloc(n, D, C.c_void_p(colors_ptr), C.c_void_p(adj_ptr), alpha, beta,
+                                     bonus_diag, C.c_void_p(out_ptr), stream_handle),
+        "tc_pair_terms_noalloc")
 
 
 def params(problem: int = TC_KCOL, **kw) -> tc_params:
