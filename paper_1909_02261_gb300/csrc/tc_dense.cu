@@ -452,37 +452,71 @@ int tc_gemm_tile_n() { return BN; }
 int tc_gemm_tile_k() { return BK; }
 
 template <int CL>
-static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g, int num_sms,
-                             cudaStream_t s) {
-    const int smem = STAGES * STAGE_BYTES + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int groups = num_sms / CL < g.n_units / CL ? num_sms / CL : g.n_units / CL;
-    if (groups < 1) groups = 1;
+static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(groups * CL);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = STAGES * STAGE_BYTES + 1024;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <int CL>
+static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g, int slots,
+                             cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         STAGES * STAGE_BYTES + 1024);
+    if (e != cudaSuccess) return e;
+    int groups = slots < g.n_units / CL ? slots : g.n_units / CL;
+    if (groups < 1) groups = 1;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tc_config<CL>(groups, s, attr);
     return cudaLaunchKernelEx(&cfg, k_gemm_tc<CL>, tmX, tmY, g);
+}
+
+template <int CL>
+static int slots_tc(int num_sms) {
+    // clusters must sit inside one GPC, so fewer than num_sms / CL of them
+    // may be resident at once: a grid sized past that runs a second wave
+    if (cudaFuncSetAttribute(k_gemm_tc<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             STAGES * STAGE_BYTES + 1024) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return num_sms / CL;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tc_config<CL>(num_sms / CL, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<CL>, &cfg) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        return num_sms / CL;
+    }
+    return n < num_sms / CL ? n : num_sms / CL;
+}
+
+int tc_gemm_cluster_slots(int cluster, int num_sms) {
+    switch (cluster) {
+        case 4: return slots_tc<4>(num_sms);
+        case 2: return slots_tc<2>(num_sms);
+        default: return slots_tc<1>(num_sms);
+    }
 }
 
 // `cluster`: CTAs sharing each B tile (1, 2 or 4); the unit list must come
 // in groups of that many units with equal column tile and K range, and tmY's
-// box must hold BN / cluster rows.
+// box must hold BN / cluster rows.  `slots`: clusters launched at most (one
+// wave, from tc_gemm_cluster_slots).
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int num_sms, int cluster, cudaStream_t s) {
+                              int slots, int cluster, cudaStream_t s) {
     switch (cluster) {
-        case 4: return launch_tc<4>(tmX, tmY, g, num_sms, s);
-        case 2: return launch_tc<2>(tmX, tmY, g, num_sms, s);
-        default: return launch_tc<1>(tmX, tmY, g, num_sms, s);
+        case 4: return launch_tc<4>(tmX, tmY, g, slots, s);
+        case 2: return launch_tc<2>(tmX, tmY, g, slots, s);
+        default: return launch_tc<1>(tmX, tmY, g, slots, s);
     }
 }
 

@@ -37,7 +37,7 @@ struct tc_kparams {
     int problem, nb_iter, bonus_diag, stop_on_legal, commit;
     int csr_walk;     // grad_S L by adjacency lists (mu = 0, sparse graph)
     float eta, rho, lambda_, mu, nu, alpha, beta;
-    float* W;                 // D x n x k
+    float* W;                 // weights, tile-transposed (tc_w_index)
     uint16_t* c;              // D x n colours
     uint16_t* c_snap;         // D x n colours of the iteration, for the adjacency walk
     uint16_t* cT;             // n x Dp colours (vertex-major, ct_bytes each), pads all-ones
@@ -76,8 +76,21 @@ struct tc_kparams {
     int* dbg_gamma;           // optional D x n conflicting-neighbour counts
 };
 
+// The weight tensor W (D x n x k) is kept on the device tile-transposed:
+// vertex tiles of 32 rows, each stored colour-major, so that a 32-row tile
+// of one individual is one contiguous k x 32 block (one bulk copy) in which
+// the 32 rows of one colour are one 128-byte line.  Rows n .. 32 nT - 1 of
+// the last tile are padding (zero, never read).
+constexpr int TC_WT = 32;
+__host__ __device__ inline size_t tc_w_index(int d, int i, int j, int nT, int k) {
+    return (((size_t)d * nT + i / TC_WT) * k + j) * TC_WT + (i % TC_WT);
+}
+// src (standard D x n x k) -> dst (tiled) when to_tiled, else back.
+cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled,
+                               cudaStream_t s);
+
 // Launchers (tc_onehot.cu).  All return cudaGetLastError() of the launch.
-cudaError_t tc_launch_init_weights(float* W, long long count, unsigned long long seed,
+cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long long seed,
                                    float sigma0, cudaStream_t s);
 cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s);
@@ -106,7 +119,8 @@ int tc_gemm_tile_m();
 int tc_gemm_tile_n();
 int tc_gemm_tile_k();
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int num_sms, int cluster, cudaStream_t s);
+                              int slots, int cluster, cudaStream_t s);
+int tc_gemm_cluster_slots(int cluster, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);
 cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s);

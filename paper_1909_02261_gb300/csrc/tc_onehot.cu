@@ -66,7 +66,10 @@ __device__ __forceinline__ float u01(uint32_t x) {  // (0, 1), exact in float
     return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f);
 }
 
-__global__ void k_init_weights(float* W, long long count, unsigned long long seed, float sigma0) {
+// Element e of the standard D x n x k order draws from Philox counter e / 4
+// (lane e % 4), whatever layout the values are stored in.
+__global__ void k_init_weights(float* W, int D, int n, int k, unsigned long long seed, float sigma0) {
+    const long long count = (long long)D * n * k;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g * 4 >= count) return;
     const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), 0u, 0u),
@@ -86,9 +89,34 @@ __global__ void k_init_weights(float* W, long long count, unsigned long long see
         z[2] = rad * c;
         z[3] = rad * s;
     }
+    const int nT = (n + TC_WT - 1) / TC_WT;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (g * 4 + q < count) W[g * 4 + q] = z[q] * sigma0;
+    for (int q = 0; q < 4; ++q) {
+        const long long e = g * 4 + q;
+        if (e >= count) break;
+        const long long row = e / k;
+        const int j = (int)(e - row * k), d = (int)(row / n), i = (int)(row - (long long)d * n);
+        W[tc_w_index(d, i, j, nT, k)] = z[q] * sigma0;
+    }
+}
+
+// Standard (D x n x k) <-> tile-transposed weights, one thread per tiled
+// element (padding rows: written as 0 going in, skipped coming out).
+__global__ void k_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled) {
+    const int nT = (n + TC_WT - 1) / TC_WT;
+    const long long total = (long long)D * nT * k * TC_WT;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int r = (int)(t % TC_WT);
+    const long long q = t / TC_WT;
+    const int j = (int)(q % k);
+    const long long dT = q / k;
+    const int d = (int)(dT / nT), i = (int)(dT % nT) * TC_WT + r;
+    const size_t e = ((size_t)d * n + i) * k + j;
+    if (to_tiled)
+        dst[t] = i < n ? src[e] : 0.f;
+    else if (i < n)
+        dst[e] = src[t];
 }
 
 // Step 1 (Section 3.4) for a fresh W: c_d(i) = lowest j with maximal w.
@@ -104,17 +132,18 @@ __device__ __forceinline__ void store_colour(const tc_kparams& P, int d, int i, 
 __global__ void k_assign(tc_kparams P) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (long long)P.D * P.n) return;
-    const float* w = P.W + r * P.k;
+    const int d = (int)(r / P.n), i = (int)(r % P.n);
+    const float* w = P.W + tc_w_index(d, i, 0, (P.n + TC_WT - 1) / TC_WT, P.k);
     int best = 0;
     float bv = w[0];
     for (int j = 1; j < P.k; ++j) {
-        const float v = w[j];
+        const float v = w[j * TC_WT];
         if (v > bv) {
             bv = v;
             best = j;
         }
     }
-    store_colour(P, (int)(r / P.n), (int)(r % P.n), best);
+    store_colour(P, d, i, best);
 }
 
 // ---------------------------------------------------------------------------
@@ -472,21 +501,22 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
             twice += g;
             if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
         }
+    const int bw = aw | 1;  // odd bitmap row stride: threads on different colours, different banks
     for (int cb = 0; cb < (P.G16 ? 0 : k); cb += cls_colours) {
         const int ce = min(k, cb + cls_colours);
         __syncthreads();
-        for (int e = threadIdx.x; e < (ce - cb) * aw; e += blockDim.x) s_bits[e] = 0u;
+        for (int e = threadIdx.x; e < (ce - cb) * bw; e += blockDim.x) s_bits[e] = 0u;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int col = cs[i];
-            if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * aw + (i >> 5)], 1u << (i & 31));
+            if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * bw + (i >> 5)], 1u << (i & 31));
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int col = cs[i];
             if (col < cb || col >= ce) continue;
             const uint4* ar = reinterpret_cast<const uint4*>(P.adj + (size_t)i * aw);
-            const uint32_t* xr = s_bits + (col - cb) * aw;
+            const uint32_t* xr = s_bits + (col - cb) * bw;
             int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
 #pragma unroll 4
             for (int w = 0; w < aw / 4; ++w) {
@@ -603,23 +633,33 @@ __device__ __forceinline__ void fence_proxy_async() {
 // colour-sorted vertices (length a multiple of 4; padding is vertex n, a zero
 // row of B), so a class is a loop of 4-wide chunks: one 16-byte index load
 // and four independent loads of B.  BS > 0: B rows BS floats apart (the
-// shared panel), else `bstride`.  Gout[j * 32] receives the class sum + nu t
+// shared panel), else `bstride`.  STG: pm, of and xs (= nu t E_dj) are the
+// warp's shared-memory copies; else pm, of in global memory and xs unused
+// (Ed, nut give the equity term).  Gout[j * 32] receives the class sum + nu t
 // E_dj (+ the gamma-matrix entry in the dense forms).
-template <int BS>
-__device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const int8_t* Ed,
+template <int BS, bool STG>
+__device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const float* xs, const int8_t* Ed,
                                            const uint16_t* grow, const float* Bl, int bstride, float nut, int k,
                                            float* Gout) {
     const int bs = BS > 0 ? BS : bstride;
     int s = 0;
-    int e = __ldg(of + 1);
+    int e = STG ? of[1] : __ldg(of + 1);
     for (int j = 0; j < k; ++j) {
-        const int e_next = (j + 2 <= k) ? __ldg(of + j + 2) : 0;  // next bound, ahead of use
-        float extra = nut * (float)__ldg(Ed + j);
+        int e_next;
+        float extra;
+        if (STG) {
+            e_next = of[j + 2 <= k ? j + 2 : k];
+            extra = xs[j];
+        } else {
+            e_next = (j + 2 <= k) ? __ldg(of + j + 2) : 0;  // next bound, ahead of use
+            extra = nut * (float)__ldg(Ed + j);
+        }
         if (grow) extra += (float)__ldg(grow + j);
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 2
         for (int p = s; p < e; p += 4) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(pm + p));
+            const uint4 v = STG ? *reinterpret_cast<const uint4*>(pm + p)
+                                : __ldg(reinterpret_cast<const uint4*>(pm + p));
             a0 += Bl[(int)v.x * bs];
             a1 += Bl[(int)v.y * bs];
             a2 += Bl[(int)v.z * bs];
@@ -681,7 +721,13 @@ __device__ __forceinline__ void prefetch_item(const uint32_t* pm, int plen, cons
 // ---------------------------------------------------------------------------
 constexpr int GSUM_MAX_WARPS = 16;
 
-template <bool BTS, bool CSR>
+// Per-warp staging (STG): the item's colour-sorted vertices, class offsets
+// and equity terms, copied to shared memory once per item.
+__host__ __device__ inline int gsum_stage_words(int perm_stride, int k) {
+    return perm_stride + ((k + 1 + 3) & ~3) + ((k + 3) & ~3);
+}
+
+template <bool BTS, bool CSR, bool STG>
 __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block) {
     tc_dev_state* st = P.st;
@@ -693,6 +739,10 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
     float* Bt = sm;
     float* Gw = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * 32 * k;  // CSR only
+    uint32_t* ps = reinterpret_cast<uint32_t*>(sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) +
+                                               (size_t)warp * gsum_stage_words(P.perm_stride, k));  // STG only
+    int* os = reinterpret_cast<int*>(ps + P.perm_stride);
+    float* xs = reinterpret_cast<float*>(os + ((k + 1 + 3) & ~3));
     unsigned bphase = 0;
     if (BTS && threadIdx.x == 0) {
         mbar_init(&s_bbar, 1);
@@ -733,7 +783,18 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const uint32_t* pm = P.perm + (size_t)d * P.perm_stride;
             const int* of = P.off + (size_t)d * (k + 1);
             const int8_t* Ed = P.E + (size_t)d * k;
-            if (!CSR) prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
+            if (STG) {
+                __syncwarp();  // the previous item's reads are done
+                const uint4* src = reinterpret_cast<const uint4*>(pm);
+                uint4* dst = reinterpret_cast<uint4*>(ps);
+#pragma unroll 4
+                for (int l = lane; l < P.perm_stride / 4; l += 32) dst[l] = __ldg(src + l);
+                for (int j = lane; j <= k; j += 32) os[j] = __ldg(of + j);
+                for (int j = lane; j < k; j += 32) xs[j] = nut * (float)__ldg(Ed + j);
+                __syncwarp();
+            } else if (!CSR) {
+                prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
+            }
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
             const uint16_t* grow =
                 (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
@@ -744,10 +805,15 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 __syncwarp();
                 for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
                 __syncwarp();
+            } else if (STG) {
+                if (BTS)
+                    class_sums<32, true>(ps, os, xs, Ed, grow, Bl, 32, nut, k, Gout);
+                else
+                    class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, Gout);
             } else if (BTS) {
-                class_sums<32>(pm, of, Ed, grow, Bl, 32, nut, k, Gout);
+                class_sums<32, false>(pm, of, nullptr, Ed, grow, Bl, 32, nut, k, Gout);
             } else {
-                class_sums<0>(pm, of, Ed, grow, Bl, P.ldb, nut, k, Gout);
+                class_sums<0, false>(pm, of, nullptr, Ed, grow, Bl, P.ldb, nut, k, Gout);
             }
         }
         q = seg_end;
@@ -755,33 +821,34 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
 }
 
 // ---------------------------------------------------------------------------
-// k_update: per item, bulk copies bring the grad_S tile ([k][32], contiguous)
-// and the weight rows ([32][k], contiguous in W) into the warp's shared
-// tiles; lane r updates row r.  The row is read starting at colour r mod k
-// (two wrap-free loops) so that the 32 lanes hit different banks.
+// k_update: per item, bulk copies bring the grad_S tile and the weight tile
+// (both [k][32], contiguous: the tile-transposed weight layout) into the
+// warp's shared memory; lane r updates row r with loops uniform across the
+// warp and free of bank conflicts, and the tile goes back with a bulk store.
 // debug_only: 1 = copy grad_S L to P.dbg_G; 2 = write grad_W L to P.dbg_G
 // instead of updating W.
 // ---------------------------------------------------------------------------
-template <bool BULK>
+// One warp's shared memory in k_update, in floats: Gs [k][32] and Ws [k][32]
+// (each 128 k bytes, so both stay 16-byte aligned for the bulk copies), then
+// the mbarrier.
+__host__ __device__ constexpr int upd_bar_offset(int k) { return 64 * k; }
+__host__ __device__ constexpr int upd_warp_floats(int k) { return 64 * k + 4; }
+
 __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, uint64_t* bar,
                                             unsigned& phase, int T, int d, bool smooth, int debug_only) {
     const int n = P.n, k = P.k;
     const int lane = threadIdx.x & 31;
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
-    const size_t wbase = ((size_t)d * n + i0) * k;
-    const unsigned wbytes = (unsigned)(rows * k * 4);
-    const unsigned gbytes = (unsigned)(k * 32 * 4);
-    const float* gsrc = P.Gbuf + ((size_t)d * ((n + 31) / 32) + T) * k * 32;
-    const bool wtoo = debug_only != 1 && BULK;
+    const size_t tile = ((size_t)d * ((n + 31) / 32) + T) * k * 32;  // same offset in Gbuf and W
+    const unsigned bytes = (unsigned)(k * 32 * 4);
     if (lane == 0) {
-        bulk_wait_read();  // the previous item's store has read Ws
-        mbar_expect_tx(bar, gbytes + (wtoo ? wbytes : 0u));
-        bulk_load(Gs, gsrc, gbytes, bar);
-        if (wtoo) bulk_load(Ws, P.W + wbase, wbytes, bar);
+        bulk_wait_read();     // the previous item's store has read Ws
+        fence_proxy_async();  // and the warp's reads of Gs, Ws come before the new copies
+        mbar_expect_tx(bar, debug_only == 1 ? bytes : 2 * bytes);
+        bulk_load(Gs, P.Gbuf + tile, bytes, bar);
+        if (debug_only != 1) bulk_load(Ws, P.W + tile, bytes, bar);
     }
-    if (debug_only != 1 && !BULK)
-        for (int e = lane; e < rows * k; e += 32) Ws[e] = P.W[wbase + e];
     mbar_wait_bounded(bar, phase, &P.st->err);
     phase ^= 1u;
     __syncwarp();
@@ -795,63 +862,61 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     }
     int newc = 0;
     if (lane < rows) {
-        float* wr = Ws + lane * k;
+        float* wr = Ws + lane;
         const float* gr = Gs + lane;
-        const int j0 = lane % k;
-        float mx = -INFINITY;
-#pragma unroll 4
-        for (int j = j0; j < k; ++j) mx = fmaxf(mx, wr[j]);
-#pragma unroll 4
-        for (int j = 0; j < j0; ++j) mx = fmaxf(mx, wr[j]);
-        float Z = 0.f, num = 0.f;
-#pragma unroll 4
-        for (int j = j0; j < k; ++j) {
-            const float e = __expf(wr[j] - mx);
-            Z += e;
-            num = fmaf(e, gr[j * 32], num);
+        // four independent chains per reduction (latency, not issue, bounds
+        // a lane's row otherwise)
+        float m4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        int j = 0;
+        for (; j + 4 <= k; j += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m4[u] = fmaxf(m4[u], wr[(j + u) * 32]);
+        for (; j < k; ++j) m4[0] = fmaxf(m4[0], wr[j * 32]);
+        const float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
+        float z4[4] = {0.f, 0.f, 0.f, 0.f}, n4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (j = 0; j + 4 <= k; j += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float e = __expf(wr[(j + u) * 32] - mx);
+                z4[u] += e;
+                n4[u] = fmaf(e, gr[(j + u) * 32], n4[u]);
+            }
+        for (; j < k; ++j) {
+            const float e = __expf(wr[j * 32] - mx);
+            z4[0] += e;
+            n4[0] = fmaf(e, gr[j * 32], n4[0]);
         }
-#pragma unroll 4
-        for (int j = 0; j < j0; ++j) {
-            const float e = __expf(wr[j] - mx);
-            Z += e;
-            num = fmaf(e, gr[j * 32], num);
-        }
+        const float Z = (z4[0] + z4[1]) + (z4[2] + z4[3]);
+        const float num = (n4[0] + n4[1]) + (n4[2] + n4[3]);
         const float invZ = 1.0f / Z;
         const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
         float bestv = -INFINITY;
-        newc = k;
-        // eq. 12, the descent step and eq. 8, each rounded once (no
-        // contraction): W_next == W - eta * gW holds bit for bit
-        auto step = [&](int j) {
-            const float w = wr[j];
+#pragma unroll 4
+        for (j = 0; j < k; ++j) {
+            // eq. 12, the descent step and eq. 8, each rounded once (no
+            // contraction): W_next == W - eta * gW holds bit for bit
+            const float w = wr[j * 32];
             const float gw = __fmul_rn(__fmul_rn(__expf(w - mx), invZ), __fsub_rn(gr[j * 32], dot));
             if (debug_only == 2) {
                 P.dbg_G[((size_t)d * n + i0 + lane) * k + j] = gw;
-                return;
+                continue;
             }
             float wn = __fsub_rn(w, __fmul_rn(P.eta, gw));
             if (smooth) wn = __fdiv_rn(wn, P.rho);
-            wr[j] = wn;
-            if (wn > bestv || (wn == bestv && j < newc)) {
+            wr[j * 32] = wn;
+            if (wn > bestv) {  // first maximum wins
                 bestv = wn;
                 newc = j;
             }
-        };
-#pragma unroll 4
-        for (int j = j0; j < k; ++j) step(j);
-#pragma unroll 4
-        for (int j = 0; j < j0; ++j) step(j);
-        if (newc >= k) newc = 0;
+        }
     }
-    __syncwarp();
-    if (debug_only == 2) return;
-    if (BULK) {
-        fence_proxy_async();
+    if (debug_only == 2) {
         __syncwarp();
-        if (lane == 0) bulk_store(P.W + wbase, Ws, wbytes);
-    } else {
-        for (int e = lane; e < rows * k; e += 32) P.W[wbase + e] = Ws[e];
+        return;
     }
+    fence_proxy_async();  // this lane's writes of Ws, visible to the bulk store
+    __syncwarp();
+    if (lane == 0) bulk_store(P.W + tile, Ws, bytes);
     if (lane < rows) {
         const int i = i0 + lane;
         if (P.S8) {  // dense forms: move the one-hot entry of (d, i) in both operands
@@ -869,16 +934,15 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     __syncwarp();
 }
 
-template <bool BULK>
 __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, int items_per_block, int debug_only) {
     tc_dev_state* st = P.st;
     if (!debug_only && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
     const int n = P.n, D = P.D, k = P.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float* Gs = sm + (size_t)warp * (64 * k + 4);
+    float* Gs = sm + (size_t)warp * upd_warp_floats(k);
     float* Ws = Gs + 32 * k;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(Ws + 32 * k);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Gs + upd_bar_offset(k));
     unsigned phase = 0;
     if (lane == 0) {
         mbar_init(bar, 1);
@@ -894,7 +958,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, 
     const long long qend = min(Q, q0 + items_per_block);
     for (long long qq = q0 + warp; qq < qend; qq += nw) {
         const int T = (int)(qq / D);
-        update_item<BULK>(P, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), smooth, debug_only);
+        update_item(P, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), smooth, debug_only);
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
     if (!debug_only) {
@@ -924,13 +988,20 @@ int tc_pair_tile_count(int n) {
 
 // Whether a population of this shape fits the update kernel (one warp's
 // grad_S and weight tiles in shared memory).
-int tc_update_fits(int k) { return 4ll * (64ll * k + 4) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
+int tc_update_fits(int k) { return 4ll * upd_warp_floats(k) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
 
-cudaError_t tc_launch_init_weights(float* W, long long count, unsigned long long seed, float sigma0,
+cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long long seed, float sigma0,
                                    cudaStream_t s) {
-    const long long groups = (count + 3) / 4;
+    const long long groups = ((long long)D * n * k + 3) / 4;
     const int th = 256;
-    k_init_weights<<<(unsigned)((groups + th - 1) / th), th, 0, s>>>(W, count, seed, sigma0);
+    k_init_weights<<<(unsigned)((groups + th - 1) / th), th, 0, s>>>(W, D, n, k, seed, sigma0);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled,
+                               cudaStream_t s) {
+    const long long total = (long long)D * ((n + TC_WT - 1) / TC_WT) * k * TC_WT;
+    k_w_layout<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, dst, D, n, k, to_tiled);
     return cudaGetLastError();
 }
 
@@ -950,7 +1021,7 @@ cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     // colour bitmaps in dynamic shared memory, at most ~160 KB per pass
-    const long long row = 4ll * P.adj_words;
+    const long long row = 4ll * (P.adj_words | 1);
     int colours = (int)((160ll << 10) / row);
     if (colours > P.k) colours = P.k;
     if (colours < 1) colours = 1;
@@ -965,10 +1036,10 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <bool BTS, bool CSR>
+template <bool BTS, bool CSR, bool STG>
 static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps, int smem,
                                  int per_block, cudaStream_t s) {
-    auto fn = k_gsum<BTS, CSR>;
+    auto fn = k_gsum<BTS, CSR, STG>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block);
@@ -976,12 +1047,16 @@ static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, in
 }
 
 // grad_S L tiles (k_gsum) into P.Gbuf: the B panel in shared memory when it
-// fits, 16 warps, or fewer with the per-warp tiles of the adjacency walk.
+// fits, 16 warps, or fewer with the per-warp tiles of the adjacency walk; the
+// class walk stages each item in shared memory when 8 or more warps fit so.
 cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s) {
     const long long bt = 4ll * 32 * ((P.n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
-    const long long per_warp = P.csr_walk ? 4ll * 32 * P.k : 0;
+    const long long stage = 4ll * gsum_stage_words(P.perm_stride, P.k);
+    long long per_warp = P.csr_walk ? 4ll * 32 * P.k : 0;
     const bool bts = bt + per_warp <= kSmemOptin;
     const long long base = bts ? bt : 0;
+    const bool stg = !P.csr_walk && base + 8 * stage <= kSmemOptin;
+    if (stg) per_warp = stage;
     int warps = GSUM_MAX_WARPS;
     if (per_warp > 0) warps = (int)std::min<long long>(GSUM_MAX_WARPS, (kSmemOptin - base) / per_warp);
     if (warps < 1) return cudaErrorInvalidValue;
@@ -991,15 +1066,18 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
     if (blocks < 1) blocks = 1;
     const int per_block = (int)((items + blocks - 1) / blocks);
     if (P.csr_walk)
-        return bts ? launch_gsum_t<true, true>(P, tmB, (int)blocks, warps, smem, per_block, s)
-                   : launch_gsum_t<false, true>(P, tmB, (int)blocks, warps, smem, per_block, s);
-    return bts ? launch_gsum_t<true, false>(P, tmB, (int)blocks, warps, smem, per_block, s)
-               : launch_gsum_t<false, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
+        return bts ? launch_gsum_t<true, true, false>(P, tmB, (int)blocks, warps, smem, per_block, s)
+                   : launch_gsum_t<false, true, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
+    if (stg)
+        return bts ? launch_gsum_t<true, false, true>(P, tmB, (int)blocks, warps, smem, per_block, s)
+                   : launch_gsum_t<false, false, true>(P, tmB, (int)blocks, warps, smem, per_block, s);
+    return bts ? launch_gsum_t<true, false, false>(P, tmB, (int)blocks, warps, smem, per_block, s)
+               : launch_gsum_t<false, false, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
 }
 
 // k_update: as many warps as fit one warp's two tiles in shared memory (<= 8).
 cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only) {
-    const long long per_warp = 4ll * (64ll * P.k + 4);
+    const long long per_warp = 4ll * upd_warp_floats(P.k);
     const int warps = (int)std::min<long long>(UPD_MAX_WARPS, kSmemOptin / per_warp);
     if (warps < 1) return cudaErrorInvalidValue;
     const int smem = (int)(per_warp * warps);
@@ -1007,14 +1085,8 @@ cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, i
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;
     const int per_block = (int)((items + blocks - 1) / blocks);
-    // bulk copies of the weight rows need 16-byte aligned, 16-byte multiple
-    // tiles: n k % 4 == 0 (tile starts (d n + 32 T) k floats, sizes rows k)
-    const bool bulk = ((long long)P.n * P.k) % 4 == 0 && (((uintptr_t)P.W) & 15) == 0;
-    auto launch = [&](auto fn) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        fn<<<(int)blocks, warps * 32, smem, s>>>(P, per_block, debug_only);
-        return cudaGetLastError();
-    };
-    return bulk ? launch(k_update<true>) : launch(k_update<false>);
+    cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_update<<<(int)blocks, warps * 32, smem, s>>>(P, per_block, debug_only);
+    return cudaGetLastError();
 }

@@ -64,7 +64,8 @@ struct tc_ctx {
     int4* d_units_g = nullptr;
     int4* d_units_m = nullptr;
     int n_units_g = 0, n_units_m = 0;
-    int cl_g = 1, cl_m = 1;  // cluster sizes sharing B tiles (Gamma, M~)
+    int cl_g = 1, cl_m = 1;      // cluster sizes sharing B tiles (Gamma, M~)
+    int slots_g = 0, slots_m = 0;  // clusters of those sizes resident at once
     alignas(64) CUtensorMap tmA8;
     alignas(64) CUtensorMap tmS8T;
     alignas(64) CUtensorMap tmS8x;
@@ -298,8 +299,10 @@ int setup_dense(tc_ctx* c) {
     // tiles share each S_cat^T tile; M~ tiles come in row pairs per column
     c->cl_g = (mt % 4 == 0) ? 4 : 2;
     c->cl_m = 2;
+    c->slots_g = tc_gemm_cluster_slots(c->cl_g, c->num_sms);
+    c->slots_m = tc_gemm_cluster_slots(c->cl_m, c->num_sms);
     const int kblocks = (int)(ldg / BKt);
-    int split = (int)((c->num_sms + tri.size() - 1) / tri.size());
+    int split = (int)((c->slots_m * c->cl_m + tri.size() - 1) / tri.size());
     split = std::max(1, std::min(split, kblocks));
     for (int sidx = 0; sidx < split; ++sidx)
         for (auto& tt : tri) {
@@ -437,12 +440,12 @@ int launch_dense_gemms(tc_ctx* c, int which) {
     if (which == 0) {
         TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, c->stream));
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->num_sms, c->cl_m, c->stream)
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->slots_m, c->cl_m, c->stream)
                       : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, c->stream);
         }));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->num_sms, c->cl_g, c->stream)
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->slots_g, c->cl_g, c->stream)
                       : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, c->stream);
         }));
     }
@@ -722,8 +725,8 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     free_population(c);
     const int n = c->n;
     const int Dp = (D + 3) & ~3;
-    const size_t Dnk = (size_t)D * n * k;
-    if ((rc = dalloc(&c->d_W, Dnk)) || (rc = dalloc(&c->d_c, (size_t)D * n)) || (rc = dalloc(&c->d_csnap, (size_t)D * n)) ||
+    const size_t Wtiled = (size_t)D * ((n + TC_WT - 1) / TC_WT) * TC_WT * k;
+    if ((rc = dalloc(&c->d_W, Wtiled)) || (rc = dalloc(&c->d_c, (size_t)D * n)) || (rc = dalloc(&c->d_csnap, (size_t)D * n)) ||
         (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
         (rc = dalloc(&c->d_Gbuf, (size_t)D * ((n + 31) / 32) * 32 * k)) ||
         (rc = dalloc(&c->d_perm, (size_t)D * ((n + 3 * k + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
@@ -758,7 +761,9 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_best, 0, sizeof(uint16_t) * n, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = tc_launch_init_weights(c->d_W, (long long)Dnk, seed, p.sigma0, c->stream);
+    if (e == cudaSuccess)  // padding rows of the last vertex tile stay zero
+        e = cudaMemsetAsync(c->d_W, 0, sizeof(float) * Wtiled, c->stream);
+    if (e == cudaSuccess) e = tc_launch_init_weights(c->d_W, D, n, k, seed, p.sigma0, c->stream);
     if (e == cudaSuccess) e = tc_launch_assign(make_kparams(c, 0), c->stream);
     c->launches += 2;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -881,7 +886,10 @@ int tc_get_state(tc_ctx* c, float* W, int64_t* t) {
     DeviceGuard g(c->device);
     if (W) {
         if (fault("copy")) return TC_ERR_INJECTED;
-        TC_CHECK(cudaMemcpyAsync(W, c->d_W, sizeof(float) * (size_t)c->D * c->n * c->k,
+        // untile into the grad_S buffer (free between iterations), then copy
+        TC_CHECK(tc_launch_w_layout(c->d_W, c->d_Gbuf, c->D, c->n, c->k, false, c->stream));
+        c->launches += 1;
+        TC_CHECK(cudaMemcpyAsync(W, c->d_Gbuf, sizeof(float) * (size_t)c->D * c->n * c->k,
                                  cudaMemcpyDeviceToHost, c->stream));
     }
     if (t) {
@@ -901,7 +909,13 @@ static int set_state_common(tc_ctx* c, const float* W, const int64_t* t, cudaMem
     DeviceGuard g(c->device);
     if (W) {
         if (fault("copy")) return TC_ERR_INJECTED;
-        TC_CHECK(cudaMemcpyAsync(c->d_W, W, sizeof(float) * (size_t)c->D * c->n * c->k, kind, c->stream));
+        const float* src = W;
+        if (kind == cudaMemcpyHostToDevice) {  // through the grad_S buffer
+            TC_CHECK(cudaMemcpyAsync(c->d_Gbuf, W, sizeof(float) * (size_t)c->D * c->n * c->k, kind, c->stream));
+            src = c->d_Gbuf;
+        }
+        TC_CHECK(tc_launch_w_layout(src, c->d_W, c->D, c->n, c->k, true, c->stream));
+        c->launches += 1;
     }
     if (t) {
         const long long tv = *t;
@@ -923,8 +937,8 @@ int tc_get_state_dev(tc_ctx* c, float* W_dev) {
     if (!c || !W_dev) return TC_ERR_ARG;
     if (!c->pop) return TC_ERR_STATE;
     DeviceGuard g(c->device);
-    TC_CHECK(cudaMemcpyAsync(W_dev, c->d_W, sizeof(float) * (size_t)c->D * c->n * c->k,
-                             cudaMemcpyDeviceToDevice, c->stream));
+    TC_CHECK(tc_launch_w_layout(c->d_W, W_dev, c->D, c->n, c->k, false, c->stream));
+    c->launches += 1;
     TC_CHECK(cudaStreamSynchronize(c->stream));
     return TC_OK;
 }
