@@ -34,7 +34,7 @@ constexpr int PP = PT / 16;         // pairs per thread along each tile edge
 constexpr int PAIR_THREADS = 256;   // 16 x 16 threads, PP x PP pairs each
 constexpr int PAIR_CW = 64;         // colour words per chunk (< 256: lane counters)
 constexpr int CLS_THREADS = 256;
-constexpr int UPD_MAX_WARPS = 8;
+constexpr int UPD_MAX_WARPS = 16;  // 8 pairs
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -822,81 +822,104 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
 
 // ---------------------------------------------------------------------------
 // k_update: per item, bulk copies bring the grad_S tile and the weight tile
-// (both [k][32], contiguous: the tile-transposed weight layout) into the
-// warp's shared memory; lane r updates row r with loops uniform across the
-// warp and free of bank conflicts, and the tile goes back with a bulk store.
+// (both [k][32], contiguous: the tile-transposed weight layout) into shared
+// memory; lane r of each warp of a pair updates its half of row r with loops
+// uniform across the warp and free of bank conflicts, and the tile goes back
+// with a bulk store.
 // debug_only: 1 = copy grad_S L to P.dbg_G; 2 = write grad_W L to P.dbg_G
 // instead of updating W.
 // ---------------------------------------------------------------------------
-// One warp's shared memory in k_update, in floats: Gs [k][32] and Ws [k][32]
-// (each 128 k bytes, so both stay 16-byte aligned for the bulk copies), then
-// the mbarrier.
-__host__ __device__ constexpr int upd_bar_offset(int k) { return 64 * k; }
-__host__ __device__ constexpr int upd_warp_floats(int k) { return 64 * k + 4; }
+// k_update works on each item with a PAIR of warps (latency, not issue,
+// bounds one lane walking a whole row): warp h of the pair takes the colours
+// [h kh, min(k, (h+1) kh)), kh = ceil(k / 2), of all 32 rows and the two
+// halves meet twice through shared memory (softmax sums, then argmax).
+// One pair's shared memory, in floats: Gs [k][32] and Ws [k][32] (each
+// 128 k bytes: 16-byte aligned for the bulk copies), the exchange slots
+// xa [2][2][32] (Z, num per half) and xb [2][2][32] (best value, colour per
+// half), then the mbarrier.
+__host__ __device__ constexpr int upd_xch_offset(int k) { return 64 * k; }
+__host__ __device__ constexpr int upd_bar_offset(int k) { return 64 * k + 256; }
+__host__ __device__ constexpr int upd_pair_floats(int k) { return 64 * k + 256 + 4; }
 
-__device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, uint64_t* bar,
-                                            unsigned& phase, int T, int d, bool smooth, int debug_only) {
+__device__ __forceinline__ float ex2_approx(float x) {  // 2^x, PTX ex2.approx
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void pair_sync(int pair) {  // the pair's 64 threads
+    asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
+}
+
+__device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, float* xa, float* xb,
+                                            uint64_t* bar, unsigned& phase, int pair, int h, int T, int d,
+                                            bool smooth, int debug_only) {
     const int n = P.n, k = P.k;
     const int lane = threadIdx.x & 31;
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
     const size_t tile = ((size_t)d * ((n + 31) / 32) + T) * k * 32;  // same offset in Gbuf and W
     const unsigned bytes = (unsigned)(k * 32 * 4);
-    if (lane == 0) {
+    const int kh = (k + 1) >> 1, jb = h * kh, je = min(k, jb + kh);
+    if (h == 0 && lane == 0) {
         bulk_wait_read();     // the previous item's store has read Ws
-        fence_proxy_async();  // and the warp's reads of Gs, Ws come before the new copies
+        fence_proxy_async();  // and the pair's reads of Gs, Ws come before the new copies
         mbar_expect_tx(bar, debug_only == 1 ? bytes : 2 * bytes);
         bulk_load(Gs, P.Gbuf + tile, bytes, bar);
         if (debug_only != 1) bulk_load(Ws, P.W + tile, bytes, bar);
     }
+    const bool live = lane < rows;
+    // the row maximum is the weight of the row's current colour: the colours
+    // are the argmax of W, kept in step with it by every update
+    const int cur = live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;
     mbar_wait_bounded(bar, phase, &P.st->err);
     phase ^= 1u;
-    __syncwarp();
     if (debug_only == 1) {
-        if (lane < rows) {
+        if (live) {
             float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
-            for (int jj = 0; jj < k; ++jj) g[jj] = Gs[jj * 32 + lane];
+            for (int jj = jb; jj < je; ++jj) g[jj] = Gs[jj * 32 + lane];
         }
-        __syncwarp();
+        pair_sync(pair);
         return;
     }
-    int newc = 0;
-    if (lane < rows) {
-        float* wr = Ws + lane;
-        const float* gr = Gs + lane;
-        // four independent chains per reduction (latency, not issue, bounds
-        // a lane's row otherwise)
-        float m4[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-        int j = 0;
-        for (; j + 4 <= k; j += 4)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) m4[u] = fmaxf(m4[u], wr[(j + u) * 32]);
-        for (; j < k; ++j) m4[0] = fmaxf(m4[0], wr[j * 32]);
-        const float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
-        float z4[4] = {0.f, 0.f, 0.f, 0.f}, n4[4] = {0.f, 0.f, 0.f, 0.f};
-        for (j = 0; j + 4 <= k; j += 4)
+    float* wr = Ws + lane;
+    const float* gr = Gs + lane;
+    constexpr float kL2E = 1.4426950408889634f;  // log2(e)
+    const float nml = live ? -wr[cur * 32] * kL2E : 0.f;
+    // softmax sums of this half: e_j = 2^(w_j log2 e - max log2 e)
+    float z4[4] = {0.f, 0.f, 0.f, 0.f}, n4[4] = {0.f, 0.f, 0.f, 0.f};
+    if (live) {
+        int j = jb;
+        for (; j + 4 <= je; j += 4)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float e = __expf(wr[(j + u) * 32] - mx);
+                const float e = ex2_approx(fmaf(wr[(j + u) * 32], kL2E, nml));
                 z4[u] += e;
                 n4[u] = fmaf(e, gr[(j + u) * 32], n4[u]);
             }
-        for (; j < k; ++j) {
-            const float e = __expf(wr[j * 32] - mx);
+        for (; j < je; ++j) {
+            const float e = ex2_approx(fmaf(wr[j * 32], kL2E, nml));
             z4[0] += e;
             n4[0] = fmaf(e, gr[j * 32], n4[0]);
         }
-        const float Z = (z4[0] + z4[1]) + (z4[2] + z4[3]);
-        const float num = (n4[0] + n4[1]) + (n4[2] + n4[3]);
-        const float invZ = 1.0f / Z;
-        const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
-        float bestv = -INFINITY;
+    }
+    xa[h * 64 + lane] = (z4[0] + z4[1]) + (z4[2] + z4[3]);
+    xa[h * 64 + 32 + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
+    pair_sync(pair);
+    const float Z = xa[lane] + xa[64 + lane];  // same order in both warps
+    const float num = xa[32 + lane] + xa[96 + lane];
+    const float invZ = 1.0f / Z;
+    const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
+    float bestv = -INFINITY;
+    int newc = jb;
+    if (live) {
 #pragma unroll 4
-        for (j = 0; j < k; ++j) {
+        for (int j = jb; j < je; ++j) {
             // eq. 12, the descent step and eq. 8, each rounded once (no
             // contraction): W_next == W - eta * gW holds bit for bit
             const float w = wr[j * 32];
-            const float gw = __fmul_rn(__fmul_rn(__expf(w - mx), invZ), __fsub_rn(gr[j * 32], dot));
+            const float sj = __fmul_rn(ex2_approx(fmaf(w, kL2E, nml)), invZ);
+            const float gw = __fmul_rn(sj, __fsub_rn(gr[j * 32], dot));
             if (debug_only == 2) {
                 P.dbg_G[((size_t)d * n + i0 + lane) * k + j] = gw;
                 continue;
@@ -911,27 +934,28 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
         }
     }
     if (debug_only == 2) {
-        __syncwarp();
+        pair_sync(pair);
         return;
     }
+    xb[h * 64 + lane] = bestv;
+    xb[h * 64 + 32 + lane] = __int_as_float(newc);
     fence_proxy_async();  // this lane's writes of Ws, visible to the bulk store
-    __syncwarp();
+    pair_sync(pair);
+    if (h != 0) return;
     if (lane == 0) bulk_store(P.W + tile, Ws, bytes);
-    if (lane < rows) {
+    // lower half wins ties: it holds the lower colours
+    if (xb[64 + lane] > xb[lane]) newc = __float_as_int(xb[96 + lane]);
+    if (live) {
         const int i = i0 + lane;
-        if (P.S8) {  // dense forms: move the one-hot entry of (d, i) in both operands
-            const int old = P.c[(size_t)d * n + i];
-            if (old != newc) {
-                const size_t co = (size_t)d * k + old, cn = (size_t)d * k + newc;
-                P.S8[(size_t)i * P.ldg + co] = 0;
-                P.S8[(size_t)i * P.ldg + cn] = 0x38;  // E4M3 1.0
-                P.S8T[co * P.n_pad + i] = 0;
-                P.S8T[cn * P.n_pad + i] = 0x38;
-            }
+        if (P.S8 && cur != newc) {  // dense forms: move the one-hot entry of (d, i) in both operands
+            const size_t co = (size_t)d * k + cur, cn = (size_t)d * k + newc;
+            P.S8[(size_t)i * P.ldg + co] = 0;
+            P.S8[(size_t)i * P.ldg + cn] = 0x38;  // E4M3 1.0
+            P.S8T[co * P.n_pad + i] = 0;
+            P.S8T[cn * P.n_pad + i] = 0x38;
         }
         store_colour(P, d, i, newc);
     }
-    __syncwarp();
 }
 
 __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, int items_per_block, int debug_only) {
@@ -939,28 +963,31 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, 
     if (!debug_only && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
     const int n = P.n, D = P.D, k = P.k;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float* Gs = sm + (size_t)warp * upd_warp_floats(k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, npairs = blockDim.x >> 6;
+    const int pair = warp >> 1, h = warp & 1;
+    float* Gs = sm + (size_t)pair * upd_pair_floats(k);
     float* Ws = Gs + 32 * k;
+    float* xa = Gs + upd_xch_offset(k);
+    float* xb = xa + 128;
     uint64_t* bar = reinterpret_cast<uint64_t*>(Gs + upd_bar_offset(k));
     unsigned phase = 0;
-    if (lane == 0) {
+    if (h == 0 && lane == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    __syncwarp();
+    __syncthreads();
     const long long t = st->t;
     const bool smooth = ((t + 1) % P.nb_iter) == 0;
     const int nT = (n + 31) / 32;
     const long long Q = (long long)nT * D;
     const long long q0 = (long long)blockIdx.x * items_per_block;
     const long long qend = min(Q, q0 + items_per_block);
-    for (long long qq = q0 + warp; qq < qend; qq += nw) {
+    for (long long qq = q0 + pair; qq < qend; qq += npairs) {
         const int T = (int)(qq / D);
-        update_item(P, Gs, Ws, bar, phase, T, (int)(qq - (long long)T * D), smooth, debug_only);
+        update_item(P, Gs, Ws, xa, xb, bar, phase, pair, h, T, (int)(qq - (long long)T * D), smooth, debug_only);
     }
-    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
+    if (h == 0 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
     if (!debug_only) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -988,7 +1015,7 @@ int tc_pair_tile_count(int n) {
 
 // Whether a population of this shape fits the update kernel (one warp's
 // grad_S and weight tiles in shared memory).
-int tc_update_fits(int k) { return 4ll * upd_warp_floats(k) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
+int tc_update_fits(int k) { return 4ll * upd_pair_floats(k) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
 
 cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long long seed, float sigma0,
                                    cudaStream_t s) {
@@ -1077,10 +1104,11 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
 
 // k_update: as many warps as fit one warp's two tiles in shared memory (<= 8).
 cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only) {
-    const long long per_warp = 4ll * upd_warp_floats(P.k);
-    const int warps = (int)std::min<long long>(UPD_MAX_WARPS, kSmemOptin / per_warp);
-    if (warps < 1) return cudaErrorInvalidValue;
-    const int smem = (int)(per_warp * warps);
+    const long long per_pair = 4ll * upd_pair_floats(P.k);
+    const int pairs = (int)std::min<long long>(UPD_MAX_WARPS / 2, kSmemOptin / per_pair);
+    if (pairs < 1) return cudaErrorInvalidValue;
+    const int warps = 2 * pairs;
+    const int smem = (int)(per_pair * pairs);
     const long long items = (long long)((P.n + 31) / 32) * P.D;
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;
