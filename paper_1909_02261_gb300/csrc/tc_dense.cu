@@ -179,20 +179,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
 
 // Epilogue of one row segment of 32 columns (values are exact integers).
 // Tiles never cross the padded allocation (n_pad rows, ldc columns).
+// Gamma entry (row i, column d k + j) in the tile-transposed layout: lanes
+// holding 32 consecutive rows of one 32-row tile write one 64-byte line.
+__device__ __forceinline__ uint16_t* gamma_at(const tc_gemm_args& g, int row, int col) {
+    const int kk = g.ldc, d = col / kk, j = col - d * kk;
+    return reinterpret_cast<uint16_t*>(g.C) + tc_gamma_index(d, row, j, g.rows_alloc / 32, kk);
+}
+
 __device__ __forceinline__ void store_chunk(const tc_gemm_args& g, int row, int col0, const uint32_t (&v)[32]) {
-    if (row >= g.rows_alloc || col0 + 32 > g.cols_alloc) return;
+    if (row >= g.rows_alloc) return;
     if (g.mode == TC_GEMM_GAMMA) {
-        uint4* d4 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(g.C) + (size_t)row * g.ldc + col0);
+        if (col0 >= g.cols_alloc) return;
+        const int kk = g.ldc;
+        const size_t dstep = (size_t)(g.rows_alloc / 32) * kk * 32;  // next individual
+        int j = col0 % kk;
+        uint16_t* p = gamma_at(g, row, col0) - (size_t)j * 32;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t pk[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                pk[e] = __float2uint_rn(__uint_as_float(v[8 * q + 2 * e])) |
-                        (__float2uint_rn(__uint_as_float(v[8 * q + 2 * e + 1])) << 16);
-            d4[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        for (int e = 0; e < 32; ++e) {
+            if (col0 + e < g.cols_alloc) p[j * 32] = (uint16_t)__float2uint_rn(__uint_as_float(v[e]));
+            if (++j == kk) {
+                j = 0;
+                p += dstep;
+            }
         }
     } else {
+        if (col0 + 32 > g.cols_alloc) return;
         float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + (size_t)row * g.ldc + col0);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -410,15 +421,13 @@ __global__ void __launch_bounds__(256, 1) k_gemm_simt(const uint8_t* X, const ui
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int col = w.y * BN + tx * 4 + 64 * qq;
-                if (col + 4 > g.cols_alloc) continue;
                 if (g.mode == TC_GEMM_GAMMA) {
-                    uint16_t* dst = reinterpret_cast<uint16_t*>(g.C) + (size_t)row * g.ldc + col;
-                    const uint32_t p0 = (uint32_t)__float2uint_rn(acc[a][4 * qq]) |
-                                        ((uint32_t)__float2uint_rn(acc[a][4 * qq + 1]) << 16);
-                    const uint32_t p1 = (uint32_t)__float2uint_rn(acc[a][4 * qq + 2]) |
-                                        ((uint32_t)__float2uint_rn(acc[a][4 * qq + 3]) << 16);
-                    *reinterpret_cast<uint2*>(dst) = make_uint2(p0, p1);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (col + r < g.cols_alloc)
+                            *gamma_at(g, row, col + r) = (uint16_t)__float2uint_rn(acc[a][4 * qq + r]);
                 } else {
+                    if (col + 4 > g.cols_alloc) continue;
                     float* dst = reinterpret_cast<float*>(g.C) + (size_t)row * g.ldc + col;
                     atomicAdd(reinterpret_cast<float4*>(dst),
                               make_float4(acc[a][4 * qq], acc[a][4 * qq + 1], acc[a][4 * qq + 2],

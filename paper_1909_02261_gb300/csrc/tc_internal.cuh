@@ -22,7 +22,7 @@ struct tc_dev_state {
     int best_d;
     int last_fmin;
     int last_dstar;
-    unsigned int done_classes;  // completion tickets (last-block patterns)
+    unsigned int done_eval;     // completion tickets (last-block patterns): k_pairs + k_classes blocks
     unsigned int done_update;
     float loss, kappa, varpi;
     int pad;
@@ -85,6 +85,13 @@ constexpr int TC_WT = 32;
 __host__ __device__ inline size_t tc_w_index(int d, int i, int j, int nT, int k) {
     return (((size_t)d * nT + i / TC_WT) * k + j) * TC_WT + (i % TC_WT);
 }
+// The gamma matrix of the dense forms (Gamma_d[i][j] = #neighbours of i in
+// colour j of individual d, uint16) uses the same tiling over the padded rows
+// (n_pad / 32 tiles): a 32-row tile of one individual is a contiguous k x 32
+// block, one 64-byte line per colour.
+__host__ __device__ inline size_t tc_gamma_index(int d, int i, int j, int nTp, int k) {
+    return (((size_t)d * nTp + i / 32) * k + j) * 32 + (i % 32);
+}
 // src (standard D x n x k) -> dst (tiled) when to_tiled, else back.
 cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled,
                                cudaStream_t s);
@@ -104,7 +111,7 @@ int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint
                       CUtensorMapSwizzle swizzle);
 constexpr int TC_BT_BOX_ROWS = 128;  // rows per TMA box of the B column panel
 // Dense contractions (tc_dense.cu): C = X . Y^T over FP8 0/1 operands.
-#define TC_GEMM_GAMMA 0  /* C uint16, plain stores                      */
+#define TC_GEMM_GAMMA 0  /* C uint16 tiled (tc_gamma_index), plain stores; ldc = k, cols_alloc = D k */
 #define TC_GEMM_MTILDE 1 /* C float, atomic adds (K may be split)       */
 struct tc_gemm_args {
     const int4* units;  // (tile row, tile column, first K block, end K block)

@@ -153,12 +153,16 @@ __global__ void k_assign(tc_kparams P) {
 // exactly where the colours agree, and ~(((x & 0x7f..) + 0x7f..) | x) sets
 // the top bit of precisely those lanes (no carry crosses a lane).
 // ---------------------------------------------------------------------------
+__device__ void finalize_population(const tc_kparams& P);
+static_assert(PAIR_THREADS == CLS_THREADS, "finalize_population runs in blocks of either kernel");
+
 template <int CB>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     if (P.commit && P.st->stop) return;
     __shared__ uint32_t s_a[PT][PAIR_CW + 1];
     __shared__ uint32_t s_b[PT][PAIR_CW + 1];
     __shared__ float s_red[2][PAIR_THREADS / 32];
+    __shared__ int s_last;
     constexpr uint32_t LOW = CB == 1 ? 0x7F7F7F7Fu : 0x7FFF7FFFu;
     constexpr uint32_t HIGH = CB == 1 ? 0x80808080u : 0x80008000u;
     constexpr int SH = CB == 1 ? 7 : 15;
@@ -284,6 +288,14 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
         }
         P.loss_part[2 * blockIdx.x] = ka;
         P.loss_part[2 * blockIdx.x + 1] = va;
+        __threadfence();
+        const unsigned ticket = atomicAdd(&P.st->done_eval, 1u);
+        s_last = (ticket == (unsigned)(P.n_pair_blocks + P.D) - 1u);
+    }
+    __syncthreads();
+    if (s_last) {  // the last of the k_pairs and k_classes blocks
+        __threadfence();
+        finalize_population(P);
     }
 }
 
@@ -318,7 +330,8 @@ __device__ unsigned long long block_min_u64(unsigned long long v, unsigned long 
     return s;
 }
 
-// Population reduction of one iteration, run by the last k_classes block:
+// Population reduction of one iteration, run by the last block of k_pairs
+// and k_classes:
 // min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test), the
 // best-so-far copy, the loss of eq. 7 and the stop flag.
 __device__ void finalize_population(const tc_kparams& P) {
@@ -379,7 +392,7 @@ __device__ void finalize_population(const tc_kparams& P) {
     if (s_better)
         for (int i = threadIdx.x; i < P.n; i += blockDim.x)
             P.best[i] = P.c[(size_t)s_dstar * P.n + i];
-    if (threadIdx.x == 0) st->done_classes = 0u;
+    if (threadIdx.x == 0) st->done_eval = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -497,7 +510,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     long long twice = 0;
     if (P.G16)
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int g = P.G16[(size_t)i * P.ldg + (size_t)d * k + cs[i]];
+            const int g = P.G16[tc_gamma_index(d, i, cs[i], P.n_pad / 32, k)];
             twice += g;
             if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
         }
@@ -533,12 +546,13 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     }
     twice = block_sum<long long>(twice, sh_ll);
     if (threadIdx.x == 0) P.fcolor[d] = (int)(twice / 2);
-    // completion ticket: the last block reduces the population
+    // completion ticket shared with k_pairs: the last block of either
+    // reduces the population
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned ticket = atomicAdd(&P.st->done_classes, 1u);
-        s_last = (ticket == gridDim.x - 1);
+        const unsigned ticket = atomicAdd(&P.st->done_eval, 1u);
+        s_last = (ticket == (unsigned)(P.n_pair_blocks + P.D) - 1u);
     }
     __syncthreads();
     if (s_last) {
@@ -624,6 +638,10 @@ __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+__device__ __forceinline__ void pair_sync(int pair) {  // warps 2 pair, 2 pair + 1 (named barrier pair + 1)
+    asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -640,11 +658,20 @@ __device__ __forceinline__ void fence_proxy_async() {
 template <int BS, bool STG>
 __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const float* xs, const int8_t* Ed,
                                            const uint16_t* grow, const float* Bl, int bstride, float nut, int k,
-                                           float* Gout) {
+                                           int jb, int je, float* Gout) {
     const int bs = BS > 0 ? BS : bstride;
-    int s = 0;
-    int e = STG ? of[1] : __ldg(of + 1);
-    for (int j = 0; j < k; ++j) {
+    if (jb >= je) return;
+    int s = STG ? of[jb] : __ldg(of + jb);
+    int e = STG ? of[jb + 1] : __ldg(of + jb + 1);
+    // gamma entries travel 4 classes ahead of use (an L2 round trip each)
+    uint16_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+    if (grow) {
+        g0 = __ldg(grow + (size_t)jb * 32);
+        if (jb + 1 < je) g1 = __ldg(grow + (size_t)(jb + 1) * 32);
+        if (jb + 2 < je) g2 = __ldg(grow + (size_t)(jb + 2) * 32);
+        if (jb + 3 < je) g3 = __ldg(grow + (size_t)(jb + 3) * 32);
+    }
+    for (int j = jb; j < je; ++j) {
         int e_next;
         float extra;
         if (STG) {
@@ -654,7 +681,13 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
             e_next = (j + 2 <= k) ? __ldg(of + j + 2) : 0;  // next bound, ahead of use
             extra = nut * (float)__ldg(Ed + j);
         }
-        if (grow) extra += (float)__ldg(grow + j);
+        if (grow) {
+            extra += (float)g0;
+            g0 = g1;
+            g1 = g2;
+            g2 = g3;
+            g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * 32) : (uint16_t)0;
+        }
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 2
         for (int p = s; p < e; p += 4) {
@@ -680,7 +713,7 @@ __device__ __forceinline__ void neighbour_sums(const int* rowptr, const int* col
                                                int bstride, float nut, int k, float* Gs, int i, bool valid) {
     for (int j = 0; j < k; ++j) {
         float g0 = nut * (float)__ldg(Ed + j);
-        if (grow) g0 += (float)__ldg(grow + j);
+        if (grow) g0 += (float)__ldg(grow + (size_t)j * 32);
         Gs[j * 32] = g0;
     }
     if (!valid) return;
@@ -719,10 +752,12 @@ __device__ __forceinline__ void prefetch_item(const uint32_t* pm, int plen, cons
 // k_gsum: one block per SM, 16 warps (the adjacency walk keeps a shared
 // 32 x k accumulator per warp and runs fewer).
 // ---------------------------------------------------------------------------
-constexpr int GSUM_MAX_WARPS = 16;
+constexpr int GSUM_MAX_WARPS = 30;  // the staged class walk: 15 warp pairs (named barriers 1..15)
 
-// Per-warp staging (STG): the item's colour-sorted vertices, class offsets
-// and equity terms, copied to shared memory once per item.
+// Staging (STG): the item's colour-sorted vertices, class offsets and equity
+// terms, copied to shared memory once per item by the PAIR of warps that
+// share it; warp h of the pair sums the colours [h kh, min(k, (h+1) kh)),
+// kh = ceil(k / 2).
 __host__ __device__ inline int gsum_stage_words(int perm_stride, int k) {
     return perm_stride + ((k + 1 + 3) & ~3) + ((k + 3) & ~3);
 }
@@ -739,8 +774,9 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
     float* Bt = sm;
     float* Gw = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * 32 * k;  // CSR only
+    const int unit = STG ? warp >> 1 : warp, nunits = STG ? nw >> 1 : nw, h = STG ? (warp & 1) : 0;
     uint32_t* ps = reinterpret_cast<uint32_t*>(sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) +
-                                               (size_t)warp * gsum_stage_words(P.perm_stride, k));  // STG only
+                                               (size_t)unit * gsum_stage_words(P.perm_stride, k));  // STG only
     int* os = reinterpret_cast<int*>(ps + P.perm_stride);
     float* xs = reinterpret_cast<float*>(os + ((k + 1 + 3) & ~3));
     unsigned bphase = 0;
@@ -778,26 +814,27 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             bphase ^= 1u;
         }
         const int i0 = T * 32, rows = min(32, n - i0);
-        for (long long qq = q + warp; qq < seg_end; qq += nw) {
+        for (long long qq = q + unit; qq < seg_end; qq += nunits) {
             const int d = (int)(qq - (long long)T * D);
             const uint32_t* pm = P.perm + (size_t)d * P.perm_stride;
             const int* of = P.off + (size_t)d * (k + 1);
             const int8_t* Ed = P.E + (size_t)d * k;
             if (STG) {
-                __syncwarp();  // the previous item's reads are done
+                pair_sync(unit);  // the pair's reads of the previous item are done
                 const uint4* src = reinterpret_cast<const uint4*>(pm);
                 uint4* dst = reinterpret_cast<uint4*>(ps);
+                const int t64 = h * 32 + lane;
 #pragma unroll 4
-                for (int l = lane; l < P.perm_stride / 4; l += 32) dst[l] = __ldg(src + l);
-                for (int j = lane; j <= k; j += 32) os[j] = __ldg(of + j);
-                for (int j = lane; j < k; j += 32) xs[j] = nut * (float)__ldg(Ed + j);
-                __syncwarp();
+                for (int l = t64; l < P.perm_stride / 4; l += 64) dst[l] = __ldg(src + l);
+                for (int j = t64; j <= k; j += 64) os[j] = __ldg(of + j);
+                for (int j = t64; j < k; j += 64) xs[j] = nut * (float)__ldg(Ed + j);
+                pair_sync(unit);
             } else if (!CSR) {
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
             }
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-            const uint16_t* grow =
-                (P.G16 && lane < rows) ? P.G16 + (size_t)(i0 + lane) * P.ldg + (size_t)d * k : nullptr;
+            // the item's gamma tile: colour j of row i0 + lane at grow[j * 32]
+            const uint16_t* grow = P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad / 32, k) : nullptr;
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
             if (CSR) {
                 neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut,
@@ -806,14 +843,15 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
                 __syncwarp();
             } else if (STG) {
+                const int kh = (k + 1) >> 1, jb = h * kh, je = min(k, jb + kh);
                 if (BTS)
-                    class_sums<32, true>(ps, os, xs, Ed, grow, Bl, 32, nut, k, Gout);
+                    class_sums<32, true>(ps, os, xs, Ed, grow, Bl, 32, nut, k, jb, je, Gout);
                 else
-                    class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, Gout);
+                    class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, jb, je, Gout);
             } else if (BTS) {
-                class_sums<32, false>(pm, of, nullptr, Ed, grow, Bl, 32, nut, k, Gout);
+                class_sums<32, false>(pm, of, nullptr, Ed, grow, Bl, 32, nut, k, 0, k, Gout);
             } else {
-                class_sums<0, false>(pm, of, nullptr, Ed, grow, Bl, P.ldb, nut, k, Gout);
+                class_sums<0, false>(pm, of, nullptr, Ed, grow, Bl, P.ldb, nut, k, 0, k, Gout);
             }
         }
         q = seg_end;
@@ -845,10 +883,6 @@ __device__ __forceinline__ float ex2_approx(float x) {  // 2^x, PTX ex2.approx
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-__device__ __forceinline__ void pair_sync(int pair) {  // the pair's 64 threads
-    asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
 }
 
 __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, float* xa, float* xb,
@@ -1082,12 +1116,19 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
     long long per_warp = P.csr_walk ? 4ll * 32 * P.k : 0;
     const bool bts = bt + per_warp <= kSmemOptin;
     const long long base = bts ? bt : 0;
-    const bool stg = !P.csr_walk && base + 8 * stage <= kSmemOptin;
-    if (stg) per_warp = stage;
+    const bool stg = !P.csr_walk && base + 4 * stage <= kSmemOptin;  // 4 pairs or more
     int warps = GSUM_MAX_WARPS;
-    if (per_warp > 0) warps = (int)std::min<long long>(GSUM_MAX_WARPS, (kSmemOptin - base) / per_warp);
+    long long smem_ll = base;
+    if (stg) {  // one staging area per warp pair
+        const int pairs = (int)std::min<long long>(GSUM_MAX_WARPS / 2, (kSmemOptin - base) / stage);
+        warps = 2 * pairs;
+        smem_ll += stage * pairs;
+    } else if (per_warp > 0) {
+        warps = (int)std::min<long long>(GSUM_MAX_WARPS, (kSmemOptin - base) / per_warp);
+        smem_ll += per_warp * warps;
+    }
     if (warps < 1) return cudaErrorInvalidValue;
-    const int smem = (int)(base + per_warp * warps);
+    const int smem = (int)smem_ll;
     const long long items = (long long)((P.n + 31) / 32) * P.D;
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;

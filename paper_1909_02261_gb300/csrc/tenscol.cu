@@ -384,14 +384,15 @@ cudaEvent_t take_event(tc_ctx* c) {
 
 // Launches one kernel through `fn`, bracketed by timing events when enabled.
 template <typename F>
-cudaError_t timed(tc_ctx* c, int kid, F fn) {
+cudaError_t timed(tc_ctx* c, int kid, F fn, cudaStream_t s = nullptr) {
+    if (!s) s = c->stream;
     const bool on = c->timing && !c->capturing;
     cudaEvent_t a = on ? take_event(c) : nullptr;
     cudaEvent_t b = on ? take_event(c) : nullptr;
-    if (a && b) cudaEventRecord(a, c->stream);
+    if (a && b) cudaEventRecord(a, s);
     cudaError_t e = fn();
     if (a && b) {
-        cudaEventRecord(b, c->stream);
+        cudaEventRecord(b, s);
         c->pending.push_back({kid, a, b});
     } else {
         if (a) c->spare.push_back(a);
@@ -431,23 +432,23 @@ void free_events(tc_ctx* c) {
 
 // The two dense contractions of the dense forms: M~ (into d_M32) and Gamma
 // (into d_G16), on the tensor cores (FP8) or the CUDA cores (FP32).
-int launch_dense_gemms(tc_ctx* c, int which) {
+int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
     tc_gemm_args gm = {c->d_units_m, c->n_units_m, TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
                        &c->d_st->err};
-    tc_gemm_args gg = {c->d_units_g, c->n_units_g, TC_GEMM_GAMMA, c->d_G16, c->ldg, c->n_pad, c->ldg,
+    tc_gemm_args gg = {c->d_units_g, c->n_units_g, TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
                        &c->d_st->err};
     const bool tc = c->p.form == TC_FORM_DENSE_FP8;
     if (which == 0) {
-        TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, c->stream));
+        TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, s));
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->slots_m, c->cl_m, c->stream)
-                      : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, c->stream);
-        }));
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->slots_m, c->cl_m, s)
+                      : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, s);
+        }, s));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->slots_g, c->cl_g, c->stream)
-                      : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, c->stream);
-        }));
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->slots_g, c->cl_g, s)
+                      : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, s);
+        }, s));
     }
     return TC_OK;
 }
@@ -464,9 +465,12 @@ int launch_iteration(tc_ctx* c) {
     tc_kparams P = make_kparams(c, 1);
     const bool dense = P.M32 != nullptr;
     int rc;
-    if (dense && (rc = launch_dense_gemms(c, 0))) return rc;
+    // k_pairs and k_classes share only the completion ticket (the last block
+    // of either reduces the population); one stream: run side by side they
+    // stretch the latency-bound k_classes more than they overlap
+    if (dense && (rc = launch_dense_gemms(c, 0, c->stream))) return rc;
     TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
-    if (dense && (rc = launch_dense_gemms(c, 1))) return rc;
+    if (dense && (rc = launch_dense_gemms(c, 1, c->stream))) return rc;
     TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
     TC_CHECK(launch_grad_update(c, P, 0));
     return TC_OK;
@@ -974,9 +978,9 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
     P.dbg_gamma = d_gam;
     const bool dense = P.M32 != nullptr;
     cudaError_t e = cudaSuccess;
-    if (dense && launch_dense_gemms(c, 0)) e = cudaErrorUnknown;
+    if (dense && launch_dense_gemms(c, 0, c->stream)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
-    if (e == cudaSuccess && dense && launch_dense_gemms(c, 1)) e = cudaErrorUnknown;
+    if (e == cudaSuccess && dense && launch_dense_gemms(c, 1, c->stream)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
     if (e == cudaSuccess && G) e = launch_grad_update(c, P, 1);
     c->launches += 2;
@@ -1065,9 +1069,9 @@ int tc_st_grad_dev(tc_ctx* c, float* gradW_dev, float* loss_dev) {
     P.dbg_G = gradW_dev;
     const bool dense = P.M32 != nullptr;
     int rc;
-    if (dense && (rc = launch_dense_gemms(c, 0))) return rc;
+    if (dense && (rc = launch_dense_gemms(c, 0, c->stream))) return rc;
     TC_CHECK(tc_launch_pairs(P, c->stream));
-    if (dense && (rc = launch_dense_gemms(c, 1))) return rc;
+    if (dense && (rc = launch_dense_gemms(c, 1, c->stream))) return rc;
     TC_CHECK(tc_launch_classes(P, c->stream));
     TC_CHECK(launch_grad_update(c, P, 2));
     c->launches += 2;
