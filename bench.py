@@ -59,11 +59,13 @@ def workload():
 
 
 def algorithmic_update_bytes(n, k, D):
-    """Bytes the fused update kernel must move per launch: W read + write
-    (2 n k 4 per individual), the colour-class permutation (2 n) and offsets
-    (4 (k+1)), the equity signs (k), the new colours in both layouts (2 x 2 n),
-    plus the n x n pair-coefficient matrix read once (4 n^2)."""
-    per_ind = 2 * n * k * 4 + 2 * n + 4 * (k + 1) + k + 4 * n
+    """Bytes the gradient + update stage (k_gsum, k_update) must move per
+    iteration: W read + write (2 n k 4 per individual), the colour-sorted
+    vertex list (4 n) and class offsets (4 (k+1)), the equity signs (k), the
+    new colours in both layouts (2 x 2 n), plus the n x n pair-coefficient
+    matrix read once (4 n^2).  The grad_S tiles passed between the two kernels
+    are not counted: the algorithm does not need them in memory."""
+    per_ind = 2 * n * k * 4 + 4 * n + 4 * (k + 1) + k + 4 * n
     return D * per_ind + 4 * n * n
 
 
