@@ -22,7 +22,7 @@ struct tc_dev_state {
     int best_d;
     int last_fmin;
     int last_dstar;
-    unsigned int done_eval;     // completion tickets (last-block patterns): k_pairs + k_classes blocks
+    unsigned int done_gsum;     // completion tickets (last-block patterns): k_gsum blocks
     unsigned int done_update;
     float loss, kappa, varpi;
     int pad;
@@ -95,6 +95,30 @@ __host__ __device__ inline size_t tc_gamma_index(int d, int i, int j, int nTp, i
 // src (standard D x n x k) -> dst (tiled) when to_tiled, else back.
 cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled,
                                cudaStream_t s);
+
+// Programmatic dependent launch: a kernel launched with tc_launch_pdl may be
+// scheduled while the previous kernel on the stream still runs; pdl_wait()
+// returns once that kernel has completed and its writes are visible (without
+// a programmatic dependency it returns at once).  pdl_trigger() lets the next
+// kernel be scheduled early; it orders nothing by itself.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t tc_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
 
 // Launchers (tc_onehot.cu).  All return cudaGetLastError() of the launch.
 cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long long seed,

@@ -153,16 +153,14 @@ __global__ void k_assign(tc_kparams P) {
 // exactly where the colours agree, and ~(((x & 0x7f..) + 0x7f..) | x) sets
 // the top bit of precisely those lanes (no carry crosses a lane).
 // ---------------------------------------------------------------------------
-__device__ void finalize_population(const tc_kparams& P);
-static_assert(PAIR_THREADS == CLS_THREADS, "finalize_population runs in blocks of either kernel");
-
 template <int CB>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
+    pdl_trigger();
+    pdl_wait();  // colours from the previous k_update
     if (P.commit && P.st->stop) return;
     __shared__ uint32_t s_a[PT][PAIR_CW + 1];
     __shared__ uint32_t s_b[PT][PAIR_CW + 1];
     __shared__ float s_red[2][PAIR_THREADS / 32];
-    __shared__ int s_last;
     constexpr uint32_t LOW = CB == 1 ? 0x7F7F7F7Fu : 0x7FFF7FFFu;
     constexpr uint32_t HIGH = CB == 1 ? 0x80808080u : 0x80008000u;
     constexpr int SH = CB == 1 ? 7 : 15;
@@ -288,19 +286,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
         }
         P.loss_part[2 * blockIdx.x] = ka;
         P.loss_part[2 * blockIdx.x + 1] = va;
-        __threadfence();
-        const unsigned ticket = atomicAdd(&P.st->done_eval, 1u);
-        s_last = (ticket == (unsigned)(P.n_pair_blocks + P.D) - 1u);
-    }
-    __syncthreads();
-    if (s_last) {  // the last of the k_pairs and k_classes blocks
-        __threadfence();
-        finalize_population(P);
     }
 }
 
 // ---------------------------------------------------------------------------
-// block-wide helpers for k_classes (CLS_THREADS threads)
+// block-wide helpers (any block size up to 1024 threads)
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ T block_sum(T v, T* sh) {
@@ -315,55 +305,66 @@ __device__ T block_sum(T v, T* sh) {
     return s;
 }
 
-__device__ unsigned long long block_min_u64(unsigned long long v, unsigned long long* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
-        v = u < v ? u : v;
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    unsigned long long s = sh[0];
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) s = sh[q] < s ? sh[q] : s;
-    return s;
-}
 
-// Population reduction of one iteration, run by the last block of k_pairs
-// and k_classes:
+// Population reduction of one iteration, run by the last k_gsum block:
 // min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test), the
 // best-so-far copy, the loss of eq. 7 and the stop flag.
 __device__ void finalize_population(const tc_kparams& P) {
-    __shared__ long long sh_ll[CLS_THREADS / 32];
-    __shared__ float sh_f[CLS_THREADS / 32];
-    __shared__ unsigned long long sh_u[CLS_THREADS / 32];
+    // one pass: per-thread partials, warp trees, then warp 0 over the warps
+    // (fixed order: deterministic for a given block size, at most 1024)
+    __shared__ long long sh_fc[32], sh_fe[32];
+    __shared__ unsigned long long sh_key[32];
+    __shared__ float sh_ka[32], sh_va[32];
     __shared__ int s_dstar, s_better;
     tc_dev_state* st = P.st;
-    const int D = P.D;
+    const int D = P.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     long long fc = 0, fe = 0;
     unsigned long long key = ~0ull;
+    float ka = 0.f, va = 0.f;
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
-        const int a = __ldcg(P.fcolor + d), b = __ldcg(P.feq + d);
+        // k_gsum summed gamma_d(i) over the vertices: each conflict twice
+        const int a = __ldcg(P.fcolor + d) / 2, b = __ldcg(P.feq + d);
+        P.fcolor[d] = a;
         fc += a;
         fe += b;
         const unsigned long long f = (unsigned long long)(a + (P.problem == TC_ECP ? b : 0));
         const unsigned long long kk = (f << 32) | (unsigned)d;
         key = kk < key ? kk : key;
     }
-    fc = block_sum<long long>(fc, sh_ll);
-    fe = block_sum<long long>(fe, sh_ll);
-    key = block_min_u64(key, sh_u);
-    float ka = 0.f, va = 0.f;
     for (int b = threadIdx.x; b < P.n_pair_blocks; b += blockDim.x) {
         ka += __ldcg(P.loss_part + 2 * b);
         va += __ldcg(P.loss_part + 2 * b + 1);
     }
-    ka = block_sum<float>(ka, sh_f);
-    va = block_sum<float>(va, sh_f);
-    const int fmin = (int)(key >> 32), dstar = (int)(key & 0xffffffffu);
-    const long long t = st->t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fc += __shfl_xor_sync(0xffffffffu, fc, o);
+        fe += __shfl_xor_sync(0xffffffffu, fe, o);
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, key, o);
+        key = u < key ? u : key;
+        ka += __shfl_xor_sync(0xffffffffu, ka, o);
+        va += __shfl_xor_sync(0xffffffffu, va, o);
+    }
+    if (lane == 0) {
+        sh_fc[warp] = fc;
+        sh_fe[warp] = fe;
+        sh_key[warp] = key;
+        sh_ka[warp] = ka;
+        sh_va[warp] = va;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        fc = fe = 0;
+        key = ~0ull;
+        ka = va = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            fc += sh_fc[w];
+            fe += sh_fe[w];
+            key = sh_key[w] < key ? sh_key[w] : key;
+            ka += sh_ka[w];
+            va += sh_va[w];
+        }
+        const int fmin = (int)(key >> 32), dstar = (int)(key & 0xffffffffu);
+        const long long t = st->t;
         const double tt = (double)t;
         st->loss = (float)fc + (float)((double)P.nu * tt) * (float)fe +
                    (float)((double)P.lambda_ * tt) * ka - (float)((double)P.mu * tt) * va;
@@ -378,7 +379,7 @@ __device__ void finalize_population(const tc_kparams& P) {
             if (st->best_f < 0 || fmin < st->best_f) {
                 better = 1;
                 st->best_f = fmin;
-                st->best_fcolor = __ldcg(P.fcolor + dstar);
+                st->best_fcolor = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
                 st->best_feq = __ldcg(P.feq + dstar);
                 st->best_d = dstar;
                 st->best_t = t;
@@ -392,31 +393,29 @@ __device__ void finalize_population(const tc_kparams& P) {
     if (s_better)
         for (int i = threadIdx.x; i < P.n; i += blockDim.x)
             P.best[i] = P.c[(size_t)s_dstar * P.n + i];
-    if (threadIdx.x == 0) st->done_eval = 0u;
+    if (threadIdx.x == 0) st->done_gsum = 0u;
 }
 
 // ---------------------------------------------------------------------------
-// k_classes: one individual per block.  Class sizes, equity (eq. 3, eq. 14),
-// a stable counting sort of the vertices by colour into `perm` with every
+// k_classes: one individual per block.  Class sizes, equity (eq. 3, eq. 14)
+// and a stable counting sort of the vertices by colour into `perm` with every
 // class padded to a multiple of 4 entries (padding = vertex n, a zero row of
-// the pair matrix), the exact conflicts of eq. 1 (with X_j the bitmap of the
-// vertices coloured j, vertex i has popcount(A_i & X_{c_d(i)}) conflicting
-// neighbours), and, in the last block, the population reduction.
-// Dynamic shared memory: the individual's colours, then the per-warp colour
-// counts of the sort or the bitmaps of `cls_colours` colours at a time.
+// the pair matrix).  Dynamic shared memory: the individual's colours, then
+// the per-warp colour counts of the sort.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_colours) {
+__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
+    pdl_trigger();
+    pdl_wait();
     if (P.commit && P.st->stop) return;
     __shared__ int s_hist[TC_MAX_K];
     __shared__ int s_cur[TC_MAX_K];
-    __shared__ int s_scan[CLS_THREADS];
+    __shared__ int s_scan[64];
     __shared__ long long sh_ll[CLS_THREADS / 32];
-    __shared__ int s_last;
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    const int n = P.n, k = P.k, d = blockIdx.x, aw = P.adj_words;
+    const int n = P.n, k = P.k, d = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
-    uint16_t* cs = reinterpret_cast<uint16_t*>(s_dyn);          // n colours
-    uint32_t* s_bits = s_dyn + ((n + 7) / 8) * 4;               // after the colours
+    uint16_t* cs = reinterpret_cast<uint16_t*>(s_dyn);  // n colours
+    int* wcnt = reinterpret_cast<int*>(s_dyn + ((n + 7) / 8) * 4);  // after the colours: nwp x k counts
     const uint16_t* cd = P.c + (size_t)d * n;
     for (int j = threadIdx.x; j < k; j += blockDim.x) s_hist[j] = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -429,20 +428,31 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[cs[i]], 1);
     __syncthreads();
-    // exclusive scan of the padded class sizes: contiguous chunks per thread
+    // exclusive scan of the padded class sizes: contiguous chunks per thread,
+    // warp shuffles, then the warp totals
     const int per = (k + CLS_THREADS - 1) / CLS_THREADS;
     const int j0 = threadIdx.x * per, j1 = min(k, j0 + per);
     int local = 0;
     for (int j = j0; j < j1; ++j) local += (s_hist[j] + 3) & ~3;
-    s_scan[threadIdx.x] = local;
-    __syncthreads();
-    for (int o = 1; o < CLS_THREADS; o <<= 1) {  // Hillis-Steele inclusive scan
-        const int v = threadIdx.x >= o ? s_scan[threadIdx.x - o] : 0;
-        __syncthreads();
-        s_scan[threadIdx.x] += v;
-        __syncthreads();
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
-    int run = s_scan[threadIdx.x] - local;
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int wt = lane < nwp ? s_scan[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, wt, o);
+            if (lane >= o) wt += v;
+        }
+        if (lane < nwp) s_scan[32 + lane] = wt;  // inclusive warp totals
+    }
+    __syncthreads();
+    int run = (warp > 0 ? s_scan[32 + warp - 1] : 0) + incl - local;
     int* od = P.off + (size_t)d * (k + 1);
     uint32_t* pd = P.perm + (size_t)d * P.perm_stride;
     for (int j = j0; j < j1; ++j) {
@@ -452,7 +462,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
         for (int q = h; q < ph; ++q) pd[run + q] = (uint32_t)n;  // padding entries
         run += ph;
     }
-    if (threadIdx.x == CLS_THREADS - 1) od[k] = s_scan[CLS_THREADS - 1];
+    if (threadIdx.x == CLS_THREADS - 1) od[k] = s_scan[32 + nwp - 1];
     // equity fitness (eq. 3) and its gradient sign (eq. 14)
     const int c1 = n / k, c2 = (n + k - 1) / k;
     long long fe = 0;
@@ -467,7 +477,6 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
     // stable counting sort: each warp owns a contiguous chunk of vertices;
     // per-warp colour counts give every (warp, colour) its base, ranks within
     // 32-vertex rounds come from warp matching
-    int* wcnt = reinterpret_cast<int*>(s_bits);  // nwp x k
     for (int e = threadIdx.x; e < nwp * k; e += blockDim.x) wcnt[e] = 0;
     __syncthreads();
     const int chunk = (n + nwp - 1) / nwp;
@@ -505,60 +514,8 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int cls_c
         }
         __syncwarp();
     }
-    // conflicts (eq. 1): from the gamma matrix of the dense form, else by
-    // colour bitmaps, cls_colours colours per pass, one vertex per thread
-    long long twice = 0;
-    if (P.G16)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int g = P.G16[tc_gamma_index(d, i, cs[i], P.n_pad / 32, k)];
-            twice += g;
-            if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
-        }
-    const int bw = aw | 1;  // odd bitmap row stride: threads on different colours, different banks
-    for (int cb = 0; cb < (P.G16 ? 0 : k); cb += cls_colours) {
-        const int ce = min(k, cb + cls_colours);
-        __syncthreads();
-        for (int e = threadIdx.x; e < (ce - cb) * bw; e += blockDim.x) s_bits[e] = 0u;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int col = cs[i];
-            if (col >= cb && col < ce) atomicOr(&s_bits[(col - cb) * bw + (i >> 5)], 1u << (i & 31));
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int col = cs[i];
-            if (col < cb || col >= ce) continue;
-            const uint4* ar = reinterpret_cast<const uint4*>(P.adj + (size_t)i * aw);
-            const uint32_t* xr = s_bits + (col - cb) * bw;
-            int g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-#pragma unroll 4
-            for (int w = 0; w < aw / 4; ++w) {
-                const uint4 a4 = __ldg(ar + w);
-                g0 += __popc(a4.x & xr[4 * w]);
-                g1 += __popc(a4.y & xr[4 * w + 1]);
-                g2 += __popc(a4.z & xr[4 * w + 2]);
-                g3 += __popc(a4.w & xr[4 * w + 3]);
-            }
-            const int g = (g0 + g1) + (g2 + g3);
-            twice += g;
-            if (P.dbg_gamma) P.dbg_gamma[(size_t)d * n + i] = g;
-        }
-    }
-    twice = block_sum<long long>(twice, sh_ll);
-    if (threadIdx.x == 0) P.fcolor[d] = (int)(twice / 2);
-    // completion ticket shared with k_pairs: the last block of either
-    // reduces the population
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned ticket = atomicAdd(&P.st->done_eval, 1u);
-        s_last = (ticket == (unsigned)(P.n_pair_blocks + P.D) - 1u);
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_population(P);
-    }
+    // conflicts (eq. 1) are counted by k_gsum, which walks these class lists
+    if (threadIdx.x == 0) P.fcolor[d] = 0;
 }
 
 
@@ -708,15 +665,18 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
 // no bonus term, so B_im = 0 unless a_im = 1): vertex i walks its adjacency
 // list (CSR) and adds B_im into the colour of each neighbour, D 2|E|
 // additions per iteration instead of D n^2.  Accumulates in Gs[j * 32].
-__device__ __forceinline__ void neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
-                                               const int8_t* Ed, const uint16_t* grow, const float* Bl,
-                                               int bstride, float nut, int k, float* Gs, int i, bool valid) {
+// Also counts gamma_d(i) (eq. 1): the neighbours sharing i's colour.
+__device__ __forceinline__ int neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
+                                              const int8_t* Ed, const uint16_t* grow, const float* Bl,
+                                              int bstride, float nut, int k, float* Gs, int i, bool valid) {
     for (int j = 0; j < k; ++j) {
         float g0 = nut * (float)__ldg(Ed + j);
         if (grow) g0 += (float)__ldg(grow + (size_t)j * 32);
         Gs[j * 32] = g0;
     }
-    if (!valid) return;
+    if (!valid) return 0;
+    const int ci = __ldg(cd + i);
+    int conf = 0;
     const int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
     int e = e0;
     for (; e + 4 <= e1; e += 4) {
@@ -728,11 +688,31 @@ __device__ __forceinline__ void neighbour_sums(const int* rowptr, const int* col
         Gs[c1 * 32] += b1;
         Gs[c2 * 32] += b2;
         Gs[c3 * 32] += b3;
+        conf += (c0 == ci) + (c1 == ci) + (c2 == ci) + (c3 == ci);
     }
     for (; e < e1; ++e) {
-        const int m = __ldg(colidx + e);
-        Gs[__ldg(cd + m) * 32] += Bl[m * bstride];
+        const int m = __ldg(colidx + e), cm = __ldg(cd + m);
+        Gs[cm * 32] += Bl[m * bstride];
+        conf += cm == ci;
     }
+    return conf;
+}
+
+// gamma_d(i) (eq. 1) from the individual's class lists: the members of i's
+// own class that are adjacent to i.  In the one-hot form the pair matrix
+// tells them apart exactly: B_im >= 1 on edges (1 + lambda t (...) >= 1) and
+// B_im <= 0 off them (-mu t (...) <= 0, the diagonal, the padding row).
+template <bool STG>
+__device__ __forceinline__ int own_class_conflicts(const uint32_t* pm, const int* of, int ci, const float* Bl,
+                                                   int bstride) {
+    const int s = STG ? of[ci] : __ldg(of + ci), e = STG ? of[ci + 1] : __ldg(of + ci + 1);
+    int conf = 0;
+    for (int p = s; p < e; p += 4) {  // padded class: whole 4-wide chunks
+        const uint4 v = STG ? *reinterpret_cast<const uint4*>(pm + p) : __ldg(reinterpret_cast<const uint4*>(pm + p));
+        conf += (Bl[(int)v.x * bstride] >= 0.5f) + (Bl[(int)v.y * bstride] >= 0.5f) +
+                (Bl[(int)v.z * bstride] >= 0.5f) + (Bl[(int)v.w * bstride] >= 0.5f);
+    }
+    return conf;
 }
 
 // One 128-byte line per lane: the item's sorted vertices, class offsets and
@@ -765,6 +745,8 @@ __host__ __device__ inline int gsum_stage_words(int perm_stride, int k) {
 template <bool BTS, bool CSR, bool STG>
 __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block) {
+    pdl_trigger();
+    pdl_wait();  // B from k_pairs, the class lists from k_classes
     tc_dev_state* st = P.st;
     if (P.commit && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
@@ -836,25 +818,65 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             // the item's gamma tile: colour j of row i0 + lane at grow[j * 32]
             const uint16_t* grow = P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad / 32, k) : nullptr;
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
+            const bool live = lane < rows;
+            const int bstride = BTS ? 32 : P.ldb;
+            const bool counter = !CSR && h == (STG ? 1 : 0);  // the warp that counts the conflicts
+            const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
+            int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
             if (CSR) {
-                neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, BTS ? 32 : P.ldb, nut,
-                               k, Gw + lane, i0 + lane, lane < rows);
+                conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, bstride, nut, k,
+                                      Gw + lane, i0 + lane, live);
                 __syncwarp();
                 for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
                 __syncwarp();
-            } else if (STG) {
-                const int kh = (k + 1) >> 1, jb = h * kh, je = min(k, jb + kh);
-                if (BTS)
-                    class_sums<32, true>(ps, os, xs, Ed, grow, Bl, 32, nut, k, jb, je, Gout);
-                else
-                    class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, jb, je, Gout);
-            } else if (BTS) {
-                class_sums<32, false>(pm, of, nullptr, Ed, grow, Bl, 32, nut, k, 0, k, Gout);
             } else {
-                class_sums<0, false>(pm, of, nullptr, Ed, grow, Bl, P.ldb, nut, k, 0, k, Gout);
+                // the counting warp takes a few colours fewer
+                const int kh = min(k, (k + 4) >> 1), jb = STG ? h * kh : 0, je = STG ? (h ? k : kh) : k;
+                if (STG) {
+                    if (BTS)
+                        class_sums<32, true>(ps, os, xs, Ed, grow, Bl, 32, nut, k, jb, je, Gout);
+                    else
+                        class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, jb, je, Gout);
+                } else if (BTS) {
+                    class_sums<32, false>(pm, of, nullptr, Ed, grow, Bl, 32, nut, k, 0, k, Gout);
+                } else {
+                    class_sums<0, false>(pm, of, nullptr, Ed, grow, Bl, P.ldb, nut, k, 0, k, Gout);
+                }
+                if (counter) {
+                    conf = 0;
+                    if (live) {
+                        if (P.G16)
+                            conf = __ldg(grow + (size_t)ci * 32);  // the gamma matrix of the dense forms
+                        else if (STG)
+                            conf = own_class_conflicts<true>(ps, os, ci, Bl, bstride);
+                        else
+                            conf = own_class_conflicts<false>(pm, of, ci, Bl, bstride);
+                    }
+                }
+            }
+            if (conf >= 0) {  // warp-uniform
+                if (P.dbg_gamma && live) P.dbg_gamma[(size_t)d * n + i0 + lane] = conf;
+                int sum = conf;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0 && sum) atomicAdd(P.fcolor + d, sum);  // twice the conflicts of the item's rows
             }
         }
         q = seg_end;
+    }
+    // completion ticket: the last block reduces the population (Algorithm 1's
+    // stop test, the best-so-far copy, the loss of eq. 7) before k_update
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(&st->done_gsum, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_population(P);
     }
 }
 
@@ -993,6 +1015,8 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
 }
 
 __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, int items_per_block, int debug_only) {
+    pdl_trigger();
+    pdl_wait();  // the grad_S tiles from k_gsum
     tc_dev_state* st = P.st;
     if (!debug_only && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
@@ -1074,27 +1098,16 @@ cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s) {
 
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
     if (P.ct_bytes == 1)
-        k_pairs<1><<<P.n_pair_blocks, PAIR_THREADS, 0, s>>>(P);
-    else
-        k_pairs<2><<<P.n_pair_blocks, PAIR_THREADS, 0, s>>>(P);
-    return cudaGetLastError();
+        return tc_launch_pdl(k_pairs<1>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
+    return tc_launch_pdl(k_pairs<2>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
 }
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
-    // colour bitmaps in dynamic shared memory, at most ~160 KB per pass
-    const long long row = 4ll * (P.adj_words | 1);
-    int colours = (int)((160ll << 10) / row);
-    if (colours > P.k) colours = P.k;
-    if (colours < 1) colours = 1;
-    long long smem_ll = colours * row;
     const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // per-warp colour counts
-    if (smem_ll < counts) smem_ll = counts;
-    smem_ll += 16ll * ((P.n + 7) / 8);  // the individual's colours
-    const int smem = (int)smem_ll;
+    const int smem = (int)(counts + 16ll * ((P.n + 7) / 8));  // + the individual's colours
     cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_classes<<<P.D, CLS_THREADS, smem, s>>>(P, colours);
-    return cudaGetLastError();
+    return tc_launch_pdl(k_classes, dim3(P.D), dim3(CLS_THREADS), smem, s, P);
 }
 
 template <bool BTS, bool CSR, bool STG>
@@ -1103,8 +1116,7 @@ static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, in
     auto fn = k_gsum<BTS, CSR, STG>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    fn<<<blocks, warps * 32, smem, s>>>(P, tmB, per_block);
-    return cudaGetLastError();
+    return tc_launch_pdl(fn, dim3(blocks), dim3(warps * 32), smem, s, P, tmB, per_block);
 }
 
 // grad_S L tiles (k_gsum) into P.Gbuf: the B panel in shared memory when it
@@ -1156,6 +1168,5 @@ cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, i
     const int per_block = (int)((items + blocks - 1) / blocks);
     cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_update<<<(int)blocks, warps * 32, smem, s>>>(P, per_block, debug_only);
-    return cudaGetLastError();
+    return tc_launch_pdl(k_update, dim3((unsigned)blocks), dim3(warps * 32), smem, s, P, per_block, debug_only);
 }

@@ -982,7 +982,10 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
     if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
     if (e == cudaSuccess && dense && launch_dense_gemms(c, 1, c->stream)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
-    if (e == cudaSuccess && G) e = launch_grad_update(c, P, 1);
+    // k_gsum counts the conflicts and reduces the population; k_update only
+    // copies grad_S L out (debug mode 1) when G is wanted
+    if (e == cudaSuccess)
+        e = G ? launch_grad_update(c, P, 1) : tc_launch_gsum(P, c->tmB, c->num_sms, c->stream);
     c->launches += 2;
     std::vector<uint16_t> hc;
     tc_dev_state h;
