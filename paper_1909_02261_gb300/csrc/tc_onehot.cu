@@ -34,7 +34,7 @@ constexpr int PP = PT / 16;         // pairs per thread along each tile edge
 constexpr int PAIR_THREADS = 256;   // 16 x 16 threads, PP x PP pairs each
 constexpr int PAIR_CW = 64;         // colour words per chunk (< 256: lane counters)
 constexpr int CLS_THREADS = 256;
-constexpr int UPD_MAX_WARPS = 16;  // 8 pairs
+constexpr int UPD_MAX_WARPS = 15;  // a producer warp and 7 pairs
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -309,13 +309,18 @@ __device__ T block_sum(T v, T* sh) {
 // Population reduction of one iteration, run by the last k_gsum block:
 // min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test), the
 // best-so-far copy, the loss of eq. 7 and the stop flag.
-__device__ void finalize_population(const tc_kparams& P) {
-    // one pass: per-thread partials, warp trees, then warp 0 over the warps
+// `scratch`: 1,104 bytes of shared memory the block no longer uses,
+// 8-byte aligned.
+__device__ void finalize_population(const tc_kparams& P, void* scratch) {
+    // one pass: per-thread partials, warp trees, then thread 0 over the warps
     // (fixed order: deterministic for a given block size, at most 1024)
-    __shared__ long long sh_fc[32], sh_fe[32];
-    __shared__ unsigned long long sh_key[32];
-    __shared__ float sh_ka[32], sh_va[32];
-    __shared__ int s_dstar, s_better;
+    long long* sh_fc = reinterpret_cast<long long*>(scratch);
+    long long* sh_fe = sh_fc + 32;
+    unsigned long long* sh_key = reinterpret_cast<unsigned long long*>(sh_fe + 32);
+    float* sh_ka = reinterpret_cast<float*>(sh_key + 32);
+    float* sh_va = sh_ka + 32;
+    int& s_dstar = *reinterpret_cast<int*>(sh_va + 32);
+    int& s_better = *(reinterpret_cast<int*>(sh_va + 32) + 1);
     tc_dev_state* st = P.st;
     const int D = P.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     long long fc = 0, fe = 0;
@@ -661,6 +666,59 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
     }
 }
 
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds_u32x4(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+// class_sums for the hot configuration (the tile's B columns and the item's
+// lists both in shared memory), on 32-bit shared addresses: the B entry of
+// vertex v for this lane sits at bl + 128 v.
+__device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, const float* xs,
+                                                  const uint16_t* grow, uint32_t bl, int k, int jb, int je,
+                                                  float* Gout) {
+    if (jb >= je) return;
+    uint32_t p = pm + 4u * (uint32_t)of[jb];
+    uint32_t e = pm + 4u * (uint32_t)of[jb + 1];
+    uint16_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;  // gamma entries, 4 classes ahead
+    if (grow) {
+        g0 = __ldg(grow + (size_t)jb * 32);
+        if (jb + 1 < je) g1 = __ldg(grow + (size_t)(jb + 1) * 32);
+        if (jb + 2 < je) g2 = __ldg(grow + (size_t)(jb + 2) * 32);
+        if (jb + 3 < je) g3 = __ldg(grow + (size_t)(jb + 3) * 32);
+    }
+    for (int j = jb; j < je; ++j) {
+        const uint32_t e_next = pm + 4u * (uint32_t)of[j + 2 <= k ? j + 2 : k];
+        float extra = xs[j];
+        if (grow) {
+            extra += (float)g0;
+            g0 = g1;
+            g1 = g2;
+            g2 = g3;
+            g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * 32) : (uint16_t)0;
+        }
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 2
+        for (; p < e; p += 16) {
+            const uint4 v = lds_u32x4(p);
+            a0 += lds_f32(bl + 128u * v.x);
+            a1 += lds_f32(bl + 128u * v.y);
+            a2 += lds_f32(bl + 128u * v.z);
+            a3 += lds_f32(bl + 128u * v.w);
+        }
+        Gout[j * 32] = ((a0 + a1) + (a2 + a3)) + extra;
+        p = e;
+        e = e_next;
+    }
+}
+
 // Sparse form of the same sums, used when B vanishes off the edges (mu = 0:
 // no bonus term, so B_im = 0 unless a_im = 1): vertex i walks its adjacency
 // list (CSR) and adds B_im into the colour of each neighbour, D 2|E|
@@ -834,7 +892,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 const int kh = min(k, (k + 4) >> 1), jb = STG ? h * kh : 0, je = STG ? (h ? k : kh) : k;
                 if (STG) {
                     if (BTS)
-                        class_sums<32, true>(ps, os, xs, Ed, grow, Bl, 32, nut, k, jb, je, Gout);
+                        class_sums_shared(smem_u32(ps), os, xs, grow, smem_u32(Bl), k, jb, je, Gout);
                     else
                         class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, jb, je, Gout);
                 } else if (BTS) {
@@ -876,7 +934,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     __syncthreads();
     if (s_last) {
         __threadfence();
-        finalize_population(P);
+        finalize_population(P, sm);  // the panel and staging areas are free now
     }
 }
 
@@ -889,17 +947,23 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
 // debug_only: 1 = copy grad_S L to P.dbg_G; 2 = write grad_W L to P.dbg_G
 // instead of updating W.
 // ---------------------------------------------------------------------------
-// k_update works on each item with a PAIR of warps (latency, not issue,
-// bounds one lane walking a whole row): warp h of the pair takes the colours
-// [h kh, min(k, (h+1) kh)), kh = ceil(k / 2), of all 32 rows and the two
-// halves meet twice through shared memory (softmax sums, then argmax).
-// One pair's shared memory, in floats: Gs [k][32] and Ws [k][32] (each
-// 128 k bytes: 16-byte aligned for the bulk copies), the exchange slots
-// xa [2][2][32] (Z, num per half) and xb [2][2][32] (best value, colour per
-// half), then the mbarrier.
-__host__ __device__ constexpr int upd_xch_offset(int k) { return 64 * k; }
-__host__ __device__ constexpr int upd_bar_offset(int k) { return 64 * k + 256; }
-__host__ __device__ constexpr int upd_pair_floats(int k) { return 64 * k + 256 + 4; }
+// k_update is warp-specialised.  Warp 0 streams the block's items through a
+// ring of S stages (grad_S tile and weight tile, each k x 32 floats and
+// contiguous in the tiled layouts) with bulk copies.  P pairs of warps take
+// the items in turn (latency, not issue, bounds one lane walking a whole
+// row): warp h of a pair updates the colours [jb, je) of all 32 rows in
+// place, lane r owning row r, and the two halves meet twice through shared
+// memory (softmax sums, then argmax); the producer writes each updated
+// weight tile back with a bulk store before its stage is refilled.
+// Shared memory: full[S], done[S] mbarriers, S stages of 64 k floats
+// ([Gs | Ws], 16-byte aligned), P exchange slots of 256 floats (xa [2][2][32]:
+// Z, num per half; xb [2][2][32]: best value, colour per half).
+constexpr int UPD_MAX_PAIRS = (UPD_MAX_WARPS - 1) / 2;
+constexpr int UPD_MAX_STAGES = 16;
+
+__host__ __device__ constexpr long long upd_smem_bytes(int k, int S, int P) {
+    return 16ll * S + 256ll * k * S + 1024ll * P;
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {  // 2^x, PTX ex2.approx
     float y;
@@ -907,29 +971,21 @@ __device__ __forceinline__ float ex2_approx(float x) {  // 2^x, PTX ex2.approx
     return y;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One item (32-row tile T of individual d) by warp h of pair `pair`, its
+// tiles already in Gs, Ws.  Returns with both warps done with the stage.
 __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, float* xa, float* xb,
-                                            uint64_t* bar, unsigned& phase, int pair, int h, int T, int d,
-                                            bool smooth, int debug_only) {
+                                            int pair, int h, int T, int d, int cur, bool smooth,
+                                            int debug_only) {
     const int n = P.n, k = P.k;
     const int lane = threadIdx.x & 31;
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
-    const size_t tile = ((size_t)d * ((n + 31) / 32) + T) * k * 32;  // same offset in Gbuf and W
-    const unsigned bytes = (unsigned)(k * 32 * 4);
     const int kh = (k + 1) >> 1, jb = h * kh, je = min(k, jb + kh);
-    if (h == 0 && lane == 0) {
-        bulk_wait_read();     // the previous item's store has read Ws
-        fence_proxy_async();  // and the pair's reads of Gs, Ws come before the new copies
-        mbar_expect_tx(bar, debug_only == 1 ? bytes : 2 * bytes);
-        bulk_load(Gs, P.Gbuf + tile, bytes, bar);
-        if (debug_only != 1) bulk_load(Ws, P.W + tile, bytes, bar);
-    }
     const bool live = lane < rows;
-    // the row maximum is the weight of the row's current colour: the colours
-    // are the argmax of W, kept in step with it by every update
-    const int cur = live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;
-    mbar_wait_bounded(bar, phase, &P.st->err);
-    phase ^= 1u;
     if (debug_only == 1) {
         if (live) {
             float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
@@ -941,6 +997,8 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     float* wr = Ws + lane;
     const float* gr = Gs + lane;
     constexpr float kL2E = 1.4426950408889634f;  // log2(e)
+    // the row maximum is the weight of the row's current colour: the colours
+    // are the argmax of W, kept in step with it by every update
     const float nml = live ? -wr[cur * 32] * kL2E : 0.f;
     // softmax sums of this half: e_j = 2^(w_j log2 e - max log2 e)
     float z4[4] = {0.f, 0.f, 0.f, 0.f}, n4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -995,10 +1053,9 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     }
     xb[h * 64 + lane] = bestv;
     xb[h * 64 + 32 + lane] = __int_as_float(newc);
-    fence_proxy_async();  // this lane's writes of Ws, visible to the bulk store
+    fence_proxy_async();  // this lane's writes of Ws, before the producer's bulk store
     pair_sync(pair);
     if (h != 0) return;
-    if (lane == 0) bulk_store(P.W + tile, Ws, bytes);
     // lower half wins ties: it holds the lower colours
     if (xb[64 + lane] > xb[lane]) newc = __float_as_int(xb[96 + lane]);
     if (live) {
@@ -1014,23 +1071,24 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     }
 }
 
-__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, int items_per_block, int debug_only) {
+__global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
+    k_update(tc_kparams P, int items_per_block, int S, int debug_only) {
     pdl_trigger();
     pdl_wait();  // the grad_S tiles from k_gsum
     tc_dev_state* st = P.st;
     if (!debug_only && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
     const int n = P.n, D = P.D, k = P.k;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, npairs = blockDim.x >> 6;
-    const int pair = warp >> 1, h = warp & 1;
-    float* Gs = sm + (size_t)pair * upd_pair_floats(k);
-    float* Ws = Gs + 32 * k;
-    float* xa = Gs + upd_xch_offset(k);
-    float* xb = xa + 128;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(Gs + upd_bar_offset(k));
-    unsigned phase = 0;
-    if (h == 0 && lane == 0) {
-        mbar_init(bar, 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, npairs = ((int)(blockDim.x >> 5) - 1) >> 1;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm);
+    uint64_t* done = full + S;
+    float* stages = sm + 4 * S;  // after 2 S mbarriers (16 S bytes)
+    float* xch = stages + (size_t)S * 64 * k;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(done + s, 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -1040,12 +1098,65 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1) k_update(tc_kparams P, 
     const int nT = (n + 31) / 32;
     const long long Q = (long long)nT * D;
     const long long q0 = (long long)blockIdx.x * items_per_block;
-    const long long qend = min(Q, q0 + items_per_block);
-    for (long long qq = q0 + pair; qq < qend; qq += npairs) {
+    const int R = (int)max(0ll, min(Q, q0 + items_per_block) - q0);
+    const unsigned bytes = (unsigned)(k * 32 * 4);
+    auto tile_of = [&](int r) {  // same offset in Gbuf and W
+        const long long qq = q0 + r;
         const int T = (int)(qq / D);
-        update_item(P, Gs, Ws, xa, xb, bar, phase, pair, h, T, (int)(qq - (long long)T * D), smooth, debug_only);
+        return ((size_t)(qq - (long long)T * D) * nT + T) * k * 32;
+    };
+    if (warp == 0) {
+        if (lane == 0) {  // producer: loads of item r, write-back of item r - S
+            for (int r = 0; r < R + S; ++r) {
+                const int s = r % S, u = r / S;
+                float* Gs = stages + (size_t)s * 64 * k;
+                if (u > 0 && r - S < R) {
+                    mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
+                    if (debug_only == 0) {
+                        bulk_store(P.W + tile_of(r - S), Gs + 32 * k, bytes);
+                        bulk_wait_read();  // the stage may be refilled once the store has read it
+                    }
+                }
+                if (r < R) {
+                    const size_t tile = tile_of(r);
+                    mbar_expect_tx(full + s, debug_only == 1 ? bytes : 2 * bytes);
+                    bulk_load(Gs, P.Gbuf + tile, bytes, full + s);
+                    if (debug_only != 1) bulk_load(Gs + 32 * k, P.W + tile, bytes, full + s);
+                }
+            }
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
+        }
+        __syncwarp();
+    } else {  // consumer pairs
+        const int pair = (warp - 1) >> 1, h = (warp - 1) & 1;
+        float* xa = xch + (size_t)pair * 256;
+        float* xb = xa + 128;
+        // the rows' current colours, one item ahead (an L2 round trip)
+        auto colour_of = [&](int r) {
+            const long long qq = q0 + r;
+            const int T = (int)(qq / D), d = (int)(qq - (long long)T * D), i = T * 32 + lane;
+            return i < n ? (int)__ldg(P.c + (size_t)d * n + i) : 0;
+        };
+        int cur_next = pair < R ? colour_of(pair) : 0;
+        for (int r = pair; r < R; r += npairs) {
+            const long long qq = q0 + r;
+            const int T = (int)(qq / D), d = (int)(qq - (long long)T * D);
+            const int s = r % S, u = r / S;
+            const int cur = cur_next;
+            if (r + npairs < R) cur_next = colour_of(r + npairs);
+            // A parity wait is only sound within one phase of the barrier.
+            // Another pair may still hold use u - 1 of this stage (the loads
+            // of use u - 1 were issued, since this pair's previous item,
+            // loaded later, was; their bytes may not have landed): wait for
+            // that use to be released first, then for use u's bytes.
+            if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
+            mbar_wait_bounded(full + s, (unsigned)u & 1u, &st->err);
+            float* Gs = stages + (size_t)s * 64 * k;
+            update_item(P, Gs, Gs + 32 * k, xa, xb, pair, h, T, d, cur, smooth, debug_only);
+            // both warps are past the pair's last barrier of the item
+            if (h == 0 && lane == 0) mbar_arrive(done + s);
+        }
     }
-    if (h == 0 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
     if (!debug_only) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1073,7 +1184,7 @@ int tc_pair_tile_count(int n) {
 
 // Whether a population of this shape fits the update kernel (one warp's
 // grad_S and weight tiles in shared memory).
-int tc_update_fits(int k) { return 4ll * upd_pair_floats(k) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
+int tc_update_fits(int k) { return upd_smem_bytes(k, 1, 1) <= kSmemOptin ? TC_OK : TC_ERR_UNSUPPORTED; }
 
 cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long long seed, float sigma0,
                                    cudaStream_t s) {
@@ -1140,7 +1251,7 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
         smem_ll += per_warp * warps;
     }
     if (warps < 1) return cudaErrorInvalidValue;
-    const int smem = (int)smem_ll;
+    const int smem = (int)std::max(smem_ll, 2048ll);  // the population reduction's scratch at least
     const long long items = (long long)((P.n + 31) / 32) * P.D;
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;
@@ -1155,18 +1266,24 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
                : launch_gsum_t<false, false, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
 }
 
-// k_update: as many warps as fit one warp's two tiles in shared memory (<= 8).
+// k_update: as many stages as fit (at most 16), two fewer consumer pairs
+// (at most 7) so that loads run ahead of the updates; one block per SM.
 cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only) {
-    const long long per_pair = 4ll * upd_pair_floats(P.k);
-    const int pairs = (int)std::min<long long>(UPD_MAX_WARPS / 2, kSmemOptin / per_pair);
-    if (pairs < 1) return cudaErrorInvalidValue;
-    const int warps = 2 * pairs;
-    const int smem = (int)(per_pair * pairs);
+    const long long per_stage = 16ll + 256ll * P.k;
+    int S = (int)std::min<long long>(UPD_MAX_STAGES, (kSmemOptin - 1024ll) / per_stage);
+    if (S < 1) return cudaErrorInvalidValue;
+    // two stages loading ahead of the pairs (fewer pairs measured slower:
+    // the update arithmetic is latency-bound per pair)
+    int pairs = S >= 4 ? std::min(UPD_MAX_PAIRS, S - 2) : std::max(1, S - 1);
+    while (S > 1 && upd_smem_bytes(P.k, S, pairs) > kSmemOptin) --S;
+    if (upd_smem_bytes(P.k, S, pairs) > kSmemOptin) return cudaErrorInvalidValue;
+    const int smem = (int)upd_smem_bytes(P.k, S, pairs);
     const long long items = (long long)((P.n + 31) / 32) * P.D;
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;
     const int per_block = (int)((items + blocks - 1) / blocks);
     cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return tc_launch_pdl(k_update, dim3((unsigned)blocks), dim3(warps * 32), smem, s, P, per_block, debug_only);
+    return tc_launch_pdl(k_update, dim3((unsigned)blocks), dim3((1 + 2 * pairs) * 32), smem, s, P, per_block, S,
+                         debug_only);
 }

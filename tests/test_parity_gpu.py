@@ -91,6 +91,21 @@ def test_ecp_step(n, k):
         check_iteration(ctx, rp, ci, p, 13)
 
 
+@pytest.mark.parametrize("n,p_edge,problem", [
+    (1700, 0.3, TC_KCOL),   # B columns of a tile in shared memory, class lists read from global memory
+    (2000, 0.3, TC_KCOL),   # B read from global memory (the panel no longer fits), class lists staged
+    (2000, 0.01, TC_ECP),   # mu = 0 on a sparse graph: adjacency-list walk, B from global memory
+])
+def test_large_n_gradient_paths(n, p_edge, problem):
+    """k_gsum's variants past the shared-memory sizes of the benchmark."""
+    rp, ci = inputs.gnp(n, p_edge, seed=n + 7)
+    D, k = 3, 20
+    W = inputs.init_weights(D, n, k, 0.05, seed=5)
+    p = params(problem, stop_on_legal=0, lambda_=1e-3, mu=1e-3 if problem == TC_KCOL else 0.0, nu=1e-3)
+    with make_ctx(rp, ci, D, k, p, W, 9) as ctx:
+        check_iteration(ctx, rp, ci, p, 9)
+
+
 def test_full_size_gnp1000_k90_D200_one_step():
     """The benchmark workload itself, compared in full on one iteration."""
     rp, ci = inputs.gnp(1000, 0.5, seed=2)
