@@ -5,7 +5,7 @@
  * learning for graph coloring problems") keeps D candidate k-colourings of a
  * graph G = (V, E), |V| = n, as a real weight tensor W (D x n x k,
  * Section 3.2) and advances all of them at once with one iteration of
- * Algorithm 1 (Section 3.3):
+ * Algorithm 1 (Sections 3.3, 3.9):
  *   Step 1  S = one_hot(argmax W)                           (Section 3.4)
  *   Step 2  conflicts / fitness f(S_d), equity f_eq (ECP)    (eq. 1-3)
  *   Step 3  group concentration M~ = sum_d S_d S_d^T, penalty kappa and
@@ -69,7 +69,7 @@ extern "C" {
 typedef struct {
     int problem;     /* TC_KCOL or TC_ECP                                    */
     float sigma0;    /* std of the N(0, sigma0) initial weights (Section 3.2)*/
-    float eta;       /* learning rate (Section 3.6)                          */
+    float eta;       /* learning rate (Section 3.7)                          */
     float alpha;     /* penalisation exponent, > 1 (eq. 5)                   */
     float lambda_;   /* penalisation weight (eq. 7)                          */
     float beta;      /* bonus exponent, > 1 (eq. 6)                          */
@@ -78,7 +78,7 @@ typedef struct {
     float rho;       /* smoothing divisor >= 1 (eq. 8); 1 disables smoothing */
     int nb_iter;     /* smoothing period in iterations (Step 4-iv)           */
     int stop_on_legal; /* 1: stop once min_d f(S_d) == 0 (Algorithm 1)       */
-    int bonus_diag;  /* 1: bar A = J - A keeps its diagonal (Section 3.5.2)  */
+    int bonus_diag;  /* 1: bar A = J - A keeps its diagonal (Section 3.6.2)  */
     int form;        /* TC_FORM_*                                            */
 } tc_params;
 
@@ -192,7 +192,7 @@ int tc_kernel_times(tc_ctx *ctx, double *ms, int64_t *count);
  * best-so-far are unchanged. */
 int tc_st_grad_dev(tc_ctx *ctx, float *gradW_dev, float *loss_dev);
 
-/* Relaxation used to check the gradient (Section 3.6): S = softmax(W_dev /
+/* Relaxation used to check the gradient (Section 3.8): S = softmax(W_dev /
  * tau) row-wise (real valued), eq. 7's GCP terms on it with M_d = S_d S_d^T
  * (nu ignored): loss_dev[4] = L, kappa, varpi, f_color; gradW_dev = dL/dW
  * (eq. 13 through the softmax Jacobian).  Device pointers of D*n*k floats;
@@ -231,6 +231,35 @@ int tc_launch_count(tc_ctx *ctx, int64_t *count);
 /* Enables (chunk > 0) or disables (chunk = 0) CUDA-graph replay of tc_step:
  * `chunk` iterations are captured once into one graph and replayed. */
 int tc_set_graph_chunk(tc_ctx *ctx, int chunk);
+
+/* Batches: several independent instances (graphs of uneven n, their own k,
+ * D, parameters and form), each a context with a population, stepped
+ * together by one CUDA-graph launch per `chunk` iterations.  Algorithm 1
+ * (Section 3.9) is run per instance exactly as tc_step runs it: every
+ * instance keeps its own t, best-so-far and stop flag, and an instance that
+ * has stopped on a legal colouring stays stopped while the others go on.  Inside the
+ * graph each instance's iterations form one branch, so small instances run
+ * side by side on the GPU.
+ *
+ * tc_batch_create: an empty batch on `device`.  TC_ERR_ARG for a bad device.
+ * tc_batch_add: appends `ctx` (not owned; it must outlive the batch or be
+ *   removed by destroying the batch).  The context must have a population
+ *   and live on the batch's device, else TC_ERR_STATE / TC_ERR_ARG.  A
+ *   context may belong to one batch at a time (TC_ERR_STATE otherwise).
+ * tc_batch_step: `n_iters` iterations of every member; `chunk` > 0
+ *   iterations are captured once into one graph (re-captured when a member's
+ *   configuration changed) and replayed, the remainder launched directly.
+ *   Returns once the work has completed, with the first member error (a
+ *   bounded device wait that expired: TC_ERR_TIMEOUT).  Members must not be
+ *   used concurrently by the caller during the call.
+ * tc_batch_size: number of members.
+ * tc_batch_destroy: releases the batch (not its members).  NULL is fine. */
+typedef struct tc_batch tc_batch;
+int tc_batch_create(tc_batch **out, int device);
+int tc_batch_add(tc_batch *batch, tc_ctx *ctx);
+int tc_batch_step(tc_batch *batch, int64_t n_iters, int chunk);
+int tc_batch_size(tc_batch *batch, int *count);
+int tc_batch_destroy(tc_batch *batch);
 
 /* Name of a status code (static storage). */
 const char *tc_strerror(int code);

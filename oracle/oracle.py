@@ -7,7 +7,7 @@ iteration of Goudet, Duval, Hao (TensCol), Algorithm 1, with numpy arrays.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, brute force, finite differences, the worked kappa example of
-Section 3.5.1); none is "parity unpinned".
+Section 3.6.1); none is "parity unpinned".
 """
 from __future__ import annotations
 

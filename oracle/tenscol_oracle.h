@@ -34,7 +34,7 @@ typedef struct {
     double nu;          /* equity weight          (eq. 7)                     */
     double rho;         /* smoothing divisor      (eq. 8)                     */
     int nb_iter;        /* smoothing period       (Step 4-iv)                 */
-    int bonus_diag;     /* 1: \bar A = J - A keeps its diagonal (Section 3.5.2)*/
+    int bonus_diag;     /* 1: \bar A = J - A keeps its diagonal (Section 3.6.2)*/
 } orc_params;
 
 /* Structural check of the adjacency lists: ids in range, no self loop,
@@ -102,7 +102,7 @@ long long orc_run(int D, int n, int k, const int *adj_off, const int *adj,
                   int stop_on_legal, double *W,
                   int *best_colors, long long *best_f, long long *best_t);
 
-/* Relaxation used to check gradients (Section 3.6): S = softmax(W / tau)
+/* Relaxation used to check gradients (Section 3.8): S = softmax(W / tau)
  * row-wise, real valued, and eq. 7 with its GCP terms evaluated literally on
  * it (M_d = S_d S_d^T, M~ = sum_d M_d, nu = 0):
  *   loss = 1/2 sum_{i,m} a_im M~_im + lambda t kappa - mu t varpi.

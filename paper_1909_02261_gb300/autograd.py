@@ -2,7 +2,7 @@
 
 ``OneHotLoss``   L(g(W)) of eq. 7 at the one-hot population S = g(W) with the
                  straight-through gradient of eq. 12-13 as its backward.
-``RelaxedLoss``  L(softmax(W / tau)) of the relaxation (Section 3.6) with its
+``RelaxedLoss``  L(softmax(W / tau)) of the relaxation (Section 3.8) with its
                  exact gradient as the backward.
 
 Both run entirely in libtenscol on the tensor's CUDA device; PyTorch only

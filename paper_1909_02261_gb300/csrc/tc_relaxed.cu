@@ -1,6 +1,6 @@
 // Relaxed loss of the TensCol iteration and its hand-written gradient, used to
 // check the differentiation of eq. 7 / eq. 13 (Goudet, Duval, Hao, Section
-// 3.6) against finite differences: S = softmax(W / tau) row-wise (real
+// 3.8) against finite differences: S = softmax(W / tau) row-wise (real
 // valued), eq. 7 with its GCP terms evaluated literally on S,
 //   L = 1/2 sum_{i,m} a_im M~_im + lambda t kappa(M~) - mu t varpi(M~),
 //   M~ = sum_d S_d S_d^T,

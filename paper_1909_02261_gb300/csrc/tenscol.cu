@@ -17,6 +17,8 @@
 
 #include "tc_internal.cuh"
 
+struct tc_batch;
+
 struct tc_ctx {
     int device = 0;
     int num_sms = 0;
@@ -73,6 +75,8 @@ struct tc_ctx {
     // CUDA graph of graph_chunk iterations
     int graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
+    long long gen = 0;          // bumped whenever captured work would go stale
+    tc_batch* batch = nullptr;  // the batch this context belongs to, if any
     // per-kernel event timing
     int timing = 0;
     bool capturing = false;
@@ -142,6 +146,7 @@ struct DeviceGuard {
 void drop_graph_exec(tc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
+    c->gen += 1;  // batches holding this context re-capture
 }
 
 void free_dense(tc_ctx* c) {
@@ -508,6 +513,88 @@ int build_graph_exec(tc_ctx* c) {
 
 }  // namespace
 
+// A batch: member contexts stepped together, one graph branch per member.
+struct tc_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<tc_ctx*> members;
+    std::vector<cudaEvent_t> joins;  // one per member
+    std::vector<long long> gens;     // members' generations at capture
+    int chunk = 0;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+void batch_drop_graph(tc_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+void batch_forget(tc_batch* b, tc_ctx* c) {
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i] == c) {
+            b->members.erase(b->members.begin() + i);
+            cudaEventDestroy(b->joins[i]);
+            b->joins.erase(b->joins.begin() + i);
+            break;
+        }
+    c->batch = nullptr;
+    batch_drop_graph(b);
+}
+
+// `iters` iterations of every member: fork from the batch stream, each
+// member's iterations on its own stream, join back.  Inside a capture the
+// member streams join the batch stream's capture through the fork event.
+int batch_launch(tc_batch* b, int iters, bool capture) {
+    TC_CHECK(cudaEventRecord(b->fork, b->stream));
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        tc_ctx* m = b->members[i];
+        TC_CHECK(cudaStreamWaitEvent(m->stream, b->fork, 0));
+        m->capturing = capture;
+        int rc = TC_OK;
+        for (int it = 0; it < iters && rc == TC_OK; ++it) rc = launch_iteration(m);
+        m->capturing = false;
+        if (rc) return rc;
+        TC_CHECK(cudaEventRecord(b->joins[i], m->stream));
+        TC_CHECK(cudaStreamWaitEvent(b->stream, b->joins[i], 0));
+    }
+    return TC_OK;
+}
+
+int batch_capture(tc_batch* b, int chunk) {
+    batch_drop_graph(b);
+    std::vector<long long> before(b->members.size());
+    for (size_t i = 0; i < b->members.size(); ++i) before[i] = b->members[i]->launches;
+    TC_CHECK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_launch(b, chunk, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    for (size_t i = 0; i < b->members.size(); ++i) b->members[i]->launches = before[i];  // counted at replay
+    if (rc != TC_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return rc != TC_OK ? rc : TC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    TC_CHECK(e);
+    b->chunk = chunk;
+    b->gens.resize(b->members.size());
+    for (size_t i = 0; i < b->members.size(); ++i) b->gens[i] = b->members[i]->gen;
+    return TC_OK;
+}
+
+bool batch_graph_current(const tc_batch* b, int chunk) {
+    if (!b->gexec || b->chunk != chunk || b->gens.size() != b->members.size()) return false;
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->gens[i] != b->members[i]->gen) return false;
+    return true;
+}
+
+}  // namespace
+
 int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint64_t inner,
                       uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
                       CUtensorMapSwizzle swizzle) {
@@ -603,6 +690,7 @@ int tc_destroy(tc_ctx* c) {
     if (!c) return TC_OK;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->batch) batch_forget(c->batch, c);
     free_graph(c);
     free_events(c);
     if (c->own) cudaStreamDestroy(c->own);
@@ -1120,6 +1208,94 @@ int tc_set_graph_chunk(tc_ctx* c, int chunk) {
     DeviceGuard g(c->device);
     drop_graph_exec(c);
     c->graph_chunk = chunk;
+    return TC_OK;
+}
+
+int tc_batch_create(tc_batch** out, int device) {
+    if (!out) return TC_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        (void)cudaGetLastError();
+        return TC_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return TC_ERR_ARG;
+    DeviceGuard g(device);
+    tc_batch* b = new (std::nothrow) tc_batch();
+    if (!b) return TC_ERR_OOM;
+    b->device = device;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (b->stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return TC_ERR_CUDA;
+    }
+    *out = b;
+    return TC_OK;
+}
+
+int tc_batch_add(tc_batch* b, tc_ctx* c) {
+    if (!b || !c) return TC_ERR_ARG;
+    if (c->device != b->device) return TC_ERR_ARG;
+    if (!c->pop || c->batch) return TC_ERR_STATE;
+    DeviceGuard g(b->device);
+    cudaEvent_t e = nullptr;
+    TC_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->members.push_back(c);
+    b->joins.push_back(e);
+    c->batch = b;
+    batch_drop_graph(b);
+    return TC_OK;
+}
+
+int tc_batch_size(tc_batch* b, int* count) {
+    if (!b || !count) return TC_ERR_ARG;
+    *count = (int)b->members.size();
+    return TC_OK;
+}
+
+int tc_batch_step(tc_batch* b, int64_t n_iters, int chunk) {
+    if (!b || n_iters < 0 || chunk < 0 || chunk > 100000) return TC_ERR_ARG;
+    for (tc_ctx* m : b->members)
+        if (!m->pop) return TC_ERR_STATE;
+    DeviceGuard g(b->device);
+    // earlier work of the members first; every member starts with its stop
+    // flag cleared, as tc_step does
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        tc_ctx* m = b->members[i];
+        TC_CHECK(cudaEventRecord(b->joins[i], m->stream));
+        TC_CHECK(cudaStreamWaitEvent(b->stream, b->joins[i], 0));
+        TC_CHECK(cudaMemsetAsync(&m->d_st->stop, 0, sizeof(int), b->stream));
+    }
+    const long long full = chunk > 0 ? n_iters / chunk : 0;
+    const int rem = (int)(n_iters - full * chunk);
+    int rc;
+    if (full > 0) {
+        if (!batch_graph_current(b, chunk) && (rc = batch_capture(b, chunk))) return rc;
+        for (long long f = 0; f < full; ++f) TC_CHECK(cudaGraphLaunch(b->gexec, b->stream));
+        for (tc_ctx* m : b->members) m->launches += (long long)launches_per_iteration(m) * chunk * full;
+    }
+    if (rem > 0 && (rc = batch_launch(b, rem, false))) return rc;
+    TC_CHECK(cudaStreamSynchronize(b->stream));
+    for (tc_ctx* m : b->members) {
+        tc_dev_state h;
+        if ((rc = read_state(m, &h))) return rc;
+        if (h.err) return h.err;
+    }
+    return TC_OK;
+}
+
+int tc_batch_destroy(tc_batch* b) {
+    if (!b) return TC_OK;
+    DeviceGuard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (tc_ctx* m : b->members) m->batch = nullptr;
+    batch_drop_graph(b);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
     return TC_OK;
 }
 

@@ -117,6 +117,23 @@ WORKLOADS = {
 }
 
 
+def batched_instances():
+    """The batched workload: G(4000, 0.5) with k = 290, D = 100, plus 8
+    instances of uneven n = 250, 500, ..., 2000 with p cycling 0.1 / 0.5 / 0.9
+    and k = round(n / 50), round(n / 12), round(n / 4.5) by density (the
+    ratios of the paper's DSJC1000.{1,5,9} colour counts), D = 100.  Graph
+    seeds 10, 11, ..., weight seeds 110, 111, ... .  Returns a list of
+    WORKLOADS-style dicts (kind "gnp", problem 0)."""
+    out = [dict(kind="gnp", n=4000, p=0.5, graph_seed=10, k=290, D=100, w_seed=110, problem=0)]
+    ratio = {0.1: 50.0, 0.5: 12.0, 0.9: 4.5}
+    for q in range(8):
+        n = 250 * (q + 1)
+        p = (0.1, 0.5, 0.9)[q % 3]
+        out.append(dict(kind="gnp", n=n, p=p, graph_seed=11 + q, k=max(2, int(round(n / ratio[p]))), D=100,
+                        w_seed=111 + q, problem=0))
+    return out
+
+
 def workload_graph(name: str):
     w = WORKLOADS[name]
     if w["kind"] == "gnp":

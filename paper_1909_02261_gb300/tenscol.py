@@ -92,6 +92,11 @@ def load(build_if_missing: bool = True):
         "tc_relaxed_dev": (C.c_int, [vp, vp, C.c_float, i64, vp, vp]),
         "tc_pair_terms_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_float, C.c_float, C.c_int, vp,
                                             vp]),
+        "tc_batch_create": (C.c_int, [P(vp), C.c_int]),
+        "tc_batch_add": (C.c_int, [vp, vp]),
+        "tc_batch_step": (C.c_int, [vp, i64, C.c_int]),
+        "tc_batch_size": (C.c_int, [vp, P(C.c_int)]),
+        "tc_batch_destroy": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -258,3 +263,45 @@ class TensCol:
         c = C.c_int64()
         _ck(self._L.tc_launch_count(self.h, C.byref(c)), "tc_launch_count")
         return c.value
+
+
+class TensColBatch:
+    """Several contexts (instances of uneven n, k, D) stepped together by one
+    CUDA-graph launch per `chunk` iterations (tc_batch_* of the C ABI).  The
+    member contexts stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, device: int = 0):
+        self._L = load()
+        h = C.c_void_p()
+        _ck(self._L.tc_batch_create(C.byref(h), device), "tc_batch_create")
+        self.h = h
+        self.members = []
+
+    def add(self, ctx: "TensCol"):
+        _ck(self._L.tc_batch_add(self.h, ctx.h), "tc_batch_add")
+        self.members.append(ctx)
+
+    def step(self, n_iters: int, chunk: int = 0):
+        _ck(self._L.tc_batch_step(self.h, n_iters, chunk), "tc_batch_step")
+
+    def size(self) -> int:
+        c = C.c_int()
+        _ck(self._L.tc_batch_size(self.h, C.byref(c)), "tc_batch_size")
+        return c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.tc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,7 +1,7 @@
 """Pins of the CPU oracle against facts fixed by the paper and by mathematics.
 
 Each test checks the oracle against something other than itself: the
-worked kappa example of Section 3.5.1, chromatic polynomials and other
+worked kappa example of Section 3.6.1, chromatic polynomials and other
 closed forms over the exhaustive population of all k^n colourings,
 library routines (numpy argmax / matmul) for the special cases they cover,
 central finite differences for the gradients of eq. 12 and eq. 13, and an
