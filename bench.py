@@ -310,6 +310,7 @@ def run_ours(args):
             tms, _, _, _, _, _ = time_steps(steps, 3, False, False)
             _, fk, fc, _, _, _ = time_steps(steps, 3, False, True)
             rec = {"value": D * steps / (tms / 1e3), "ms_per_step": tms / steps,
+                   "plan": ctx.tc_dense_plan(),
                    "kernels_us": {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * fk[q] / max(1, fc[q])
                                   for q in range(len(fk)) if fc[q] > 0}}
             forms[name] = rec

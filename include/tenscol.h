@@ -232,6 +232,24 @@ int tc_launch_count(tc_ctx *ctx, int64_t *count);
  * `chunk` iterations are captured once into one graph and replayed. */
 int tc_set_graph_chunk(tc_ctx *ctx, int chunk);
 
+/* The plan the autotuner chose for the dense contractions of this context
+ * (tc_init_population / tc_set_params time every candidate on the context's
+ * own operands and keep the fastest; the FP32 form keeps one fixed plan):
+ *   plan[0] Gamma column tile (128 or 256)   plan[1] Gamma cluster size
+ *   plan[2] M~ column tile                    plan[3] M~ cluster size
+ *   plan[4] M~ K splits                       plan[5] candidates timed
+ *   us[0], us[1]: best times of Gamma and M~ in microseconds (0 for FP32).
+ * TC_ERR_STATE when the context has no dense form. */
+int tc_dense_plan(tc_ctx *ctx, int32_t *plan, float *us);
+
+/* Pins the plan of the dense contractions: plan[0..4] as above (the FP8
+ * form accepts column tiles 128 / 256, Gamma clusters 1 / 2 / 4 dividing
+ * the row tiles, M~ clusters 1 / 2 (2 with 256-wide tiles), K splits
+ * 1 .. D k / 128; the FP32 form only 256, 1, 256, 1, s).  TC_ERR_ARG for a
+ * plan outside these, TC_ERR_STATE without a dense form.  Kept until the
+ * next tc_init_population or form change, which tune again. */
+int tc_dense_set_plan(tc_ctx *ctx, const int32_t *plan);
+
 /* Batches: several independent instances (graphs of uneven n, their own k,
  * D, parameters and form), each a context with a population, stepped
  * together by one CUDA-graph launch per `chunk` iterations.  Algorithm 1

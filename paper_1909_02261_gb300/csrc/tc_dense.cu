@@ -29,11 +29,22 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 128;  // BK in bytes = FP8 elements
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK, B_BYTES = BN * BK, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BK = 128;  // BK in bytes = FP8 elements
+constexpr int BN = 256;            // column tile of the FP32 comparator and the padding unit
 constexpr int TC_THREADS = 192;
-constexpr int TMEM_COLS = 512;  // two BN-column FP32 accumulators
+
+// Tile shapes of the tensor-core GEMM (the column tile BN_ is tuned per
+// context): the stage ring keeps about 192 KB of operands in flight.
+template <int BN_>
+struct TcShape {
+    static constexpr int STAGES = BN_ == 256 ? 4 : 6;
+    static constexpr int A_BYTES = BM * BK, B_BYTES = BN_ * BK, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN_;  // two BN_-column FP32 accumulators
+    // instruction descriptor: D = F32, A = B = E4M3, both K-major, M = BM, N = BN_
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -128,15 +139,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = E4M3, both K-major, M = BM, N = BN.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, int accumulate) {
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       int accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -215,10 +223,13 @@ __device__ __forceinline__ void store_chunk(const tc_gemm_args& g, int row, int 
 // CL > 1: the CL CTAs of a cluster take CL units that share the column tile
 // and K range (consecutive in the unit list); each loads 1/CL of the B tile
 // and multicasts it to all, so B crosses L2 once per cluster.
-template <int CL>
+template <int BN_, int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               tc_gemm_args g) {
+    using Sh = TcShape<BN_>;
+    constexpr int STAGES = Sh::STAGES, A_BYTES = Sh::A_BYTES, B_BYTES = Sh::B_BYTES,
+                  STAGE_BYTES = Sh::STAGE_BYTES, TMEM_COLS = Sh::TMEM_COLS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 128-byte swizzled tiles need 1024-byte aligned bases
     uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -269,10 +280,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     bar_expect_tx(&full[s], STAGE_BYTES);
                     tma_load_2d(sa, &tmX, kb * BK, w.x * BM, &full[s]);
                     if (CL == 1)
-                        tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN, &full[s]);
+                        tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN_, &full[s]);
                     else  // my slice of the shared B tile, to every CTA of the cluster
                         tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), &tmY, kb * BK,
-                                       w.y * BN + (int)crank * (BN / CL), &full[s], cmask);
+                                       w.y * BN_ + (int)crank * (BN_ / CL), &full[s], cmask);
                 }
             }
         }
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const unsigned ua = ui >> 1;
                 if (!(ok = bar_wait(&tempty[a], (ua & 1u) ^ 1u, &abort_flag, g.err))) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(a * BN);
+                const uint32_t dt = tmem + (uint32_t)(a * BN_);
                 for (int kb = w.z; kb < w.w; ++kb, ++gk) {
                     const int s = gk % STAGES;
                     const unsigned r = gk / STAGES;
@@ -296,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < BK / 32; ++kk)  // +32 bytes = +2 in the address field
-                        mma_f8(dt, ad + 2 * kk, bd + 2 * kk, (kb > w.z || kk > 0) ? 1 : 0);
+                        mma_f8(dt, ad + 2 * kk, bd + 2 * kk, Sh::IDESC, (kb > w.z || kk > 0) ? 1 : 0);
                     if (CL == 1)
                         mma_commit(&empty[s]);  // stage s is free once these MMAs finish
                     else
@@ -326,10 +337,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const int row = w.x * BM + row_in_tile;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = 0; c < BN_ / 32; ++c) {
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN + 32 * c), v);
-                store_chunk(g, row, w.y * BN + 32 * c, v);
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN_ + 32 * c), v);
+                store_chunk(g, row, w.y * BN_ + 32 * c, v);
             }
             tc_fence_before();
             __syncwarp();
@@ -460,12 +471,12 @@ int tc_gemm_tile_m() { return BM; }
 int tc_gemm_tile_n() { return BN; }
 int tc_gemm_tile_k() { return BK; }
 
-template <int CL>
+template <int BN_, int CL>
 static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(groups * CL);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = STAGES * STAGE_BYTES + 1024;
+    cfg.dynamicSmemBytes = TcShape<BN_>::SMEM;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
@@ -476,56 +487,71 @@ static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttrib
     return cfg;
 }
 
-template <int CL>
+template <int BN_, int CL>
 static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g, int slots,
                              cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         STAGES * STAGE_BYTES + 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN_, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcShape<BN_>::SMEM);
     if (e != cudaSuccess) return e;
     int groups = slots < g.n_units / CL ? slots : g.n_units / CL;
     if (groups < 1) groups = 1;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tc_config<CL>(groups, s, attr);
-    return cudaLaunchKernelEx(&cfg, k_gemm_tc<CL>, tmX, tmY, g);
+    cudaLaunchConfig_t cfg = tc_config<BN_, CL>(groups, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL>, tmX, tmY, g);
 }
 
-template <int CL>
+template <int BN_, int CL>
 static int slots_tc(int num_sms) {
     // clusters must sit inside one GPC, so fewer than num_sms / CL of them
     // may be resident at once: a grid sized past that runs a second wave
-    if (cudaFuncSetAttribute(k_gemm_tc<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             STAGES * STAGE_BYTES + 1024) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_gemm_tc<BN_, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcShape<BN_>::SMEM) != cudaSuccess) {
         (void)cudaGetLastError();
         return num_sms / CL;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tc_config<CL>(num_sms / CL, nullptr, attr);
+    cudaLaunchConfig_t cfg = tc_config<BN_, CL>(num_sms / CL, nullptr, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<CL>, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<BN_, CL>, &cfg) != cudaSuccess || n < 1) {
         (void)cudaGetLastError();
         return num_sms / CL;
     }
     return n < num_sms / CL ? n : num_sms / CL;
 }
 
-int tc_gemm_cluster_slots(int cluster, int num_sms) {
+int tc_gemm_cluster_slots(int cluster, int bn, int num_sms) {
+    if (bn == 128) {
+        switch (cluster) {
+            case 4: return slots_tc<128, 4>(num_sms);
+            case 2: return slots_tc<128, 2>(num_sms);
+            default: return slots_tc<128, 1>(num_sms);
+        }
+    }
     switch (cluster) {
-        case 4: return slots_tc<4>(num_sms);
-        case 2: return slots_tc<2>(num_sms);
-        default: return slots_tc<1>(num_sms);
+        case 4: return slots_tc<256, 4>(num_sms);
+        case 2: return slots_tc<256, 2>(num_sms);
+        default: return slots_tc<256, 1>(num_sms);
     }
 }
 
 // `cluster`: CTAs sharing each B tile (1, 2 or 4); the unit list must come
 // in groups of that many units with equal column tile and K range, and tmY's
-// box must hold BN / cluster rows.  `slots`: clusters launched at most (one
-// wave, from tc_gemm_cluster_slots).
+// box must hold bn / cluster rows.  `bn`: the column tile (128 or 256) the
+// units were cut with.  `slots`: clusters launched at most (one wave, from
+// tc_gemm_cluster_slots).
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int slots, int cluster, cudaStream_t s) {
+                              int slots, int cluster, int bn, cudaStream_t s) {
+    if (bn == 128) {
+        switch (cluster) {
+            case 4: return launch_tc<128, 4>(tmX, tmY, g, slots, s);
+            case 2: return launch_tc<128, 2>(tmX, tmY, g, slots, s);
+            default: return launch_tc<128, 1>(tmX, tmY, g, slots, s);
+        }
+    }
     switch (cluster) {
-        case 4: return launch_tc<4>(tmX, tmY, g, slots, s);
-        case 2: return launch_tc<2>(tmX, tmY, g, slots, s);
-        default: return launch_tc<1>(tmX, tmY, g, slots, s);
+        case 4: return launch_tc<256, 4>(tmX, tmY, g, slots, s);
+        case 2: return launch_tc<256, 2>(tmX, tmY, g, slots, s);
+        default: return launch_tc<256, 1>(tmX, tmY, g, slots, s);
     }
 }
 

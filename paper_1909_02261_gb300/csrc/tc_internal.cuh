@@ -150,8 +150,8 @@ int tc_gemm_tile_m();
 int tc_gemm_tile_n();
 int tc_gemm_tile_k();
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int slots, int cluster, cudaStream_t s);
-int tc_gemm_cluster_slots(int cluster, int num_sms);
+                              int slots, int cluster, int bn, cudaStream_t s);
+int tc_gemm_cluster_slots(int cluster, int bn, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);
 cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s);

@@ -67,7 +67,11 @@ struct tc_ctx {
     int4* d_units_m = nullptr;
     int n_units_g = 0, n_units_m = 0;
     int cl_g = 1, cl_m = 1;      // cluster sizes sharing B tiles (Gamma, M~)
+    int bn_g = 256, bn_m = 256;  // column tiles of the two contractions
+    int split_m = 1;             // K splits of M~
     int slots_g = 0, slots_m = 0;  // clusters of those sizes resident at once
+    int tune_candidates = 0;       // configurations timed by the autotuner
+    float tune_us_g = 0.f, tune_us_m = 0.f;  // their best times
     alignas(64) CUtensorMap tmA8;
     alignas(64) CUtensorMap tmS8T;
     alignas(64) CUtensorMap tmS8x;
@@ -266,21 +270,216 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     return P;
 }
 
-// Dense forms: FP8 adjacency, one-hot operands, GEMM outputs, tensor maps and
-// the work units of the two contractions.  n_pad is a multiple of both GEMM
-// tile edges, ldg (the padded D k) a multiple of the column tile.
+// Work units of Gamma = A . S_cat: every (row tile, column tile), row tiles
+// fastest so that `cl` consecutive units share the column tile.
+std::vector<int4> units_gamma(int mt, int nt, int kblocks) {
+    std::vector<int4> u;
+    for (int bn = 0; bn < nt; ++bn)
+        for (int bm = 0; bm < mt; ++bm) u.push_back(make_int4(bm, bn, 0, kblocks));
+    return u;
+}
+
+// Work units of M~ = S_cat . S_cat^T: the (row, column) tiles touching the
+// upper triangle, each K range split `split` ways (partial sums added with
+// atomics).  With bn = 2 BM every column holds an even number of such row
+// tiles, so row pairs share the column tile (clusters of 2).
+std::vector<int4> units_mtilde(int mt, int bn, int ntm, int kblocks, int split) {
+    const int BMt = tc_gemm_tile_m();
+    std::vector<int2> tri;
+    for (int c = 0; c < ntm; ++c)
+        for (int bm = 0; bm < mt; ++bm)
+            if ((long long)c * bn + bn - 1 >= (long long)bm * BMt) tri.push_back(make_int2(bm, c));
+    std::vector<int4> u;
+    for (int sidx = 0; sidx < split; ++sidx)
+        for (auto& tt : tri) {
+            const int k0 = (int)((long long)kblocks * sidx / split), k1 = (int)((long long)kblocks * (sidx + 1) / split);
+            if (k1 > k0) u.push_back(make_int4(tt.x, tt.y, k0, k1));
+        }
+    return u;
+}
+
+int upload_units(tc_ctx* c, int4* dst, const std::vector<int4>& u) {
+    TC_CHECK(cudaMemcpyAsync(dst, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+    return TC_OK;
+}
+
+// Whether a plan suits the context's dense form and sizes.
+bool plan_valid(const tc_ctx* c, int bn_g, int cl_g, int bn_m, int cl_m, int split) {
+    const int mt = c->n_pad / tc_gemm_tile_m(), km = c->ldg / tc_gemm_tile_k();
+    if (c->p.form == TC_FORM_DENSE_FP32)  // the CUDA-core comparator: 128 x 256 tiles
+        return bn_g == 256 && cl_g == 1 && bn_m == 256 && cl_m == 1 && split >= 1 && split <= km;
+    if ((bn_g != 128 && bn_g != 256) || (bn_m != 128 && bn_m != 256)) return false;
+    if ((cl_g != 1 && cl_g != 2 && cl_g != 4) || mt % cl_g) return false;
+    if ((cl_m != 1 && cl_m != 2) || (cl_m == 2 && bn_m != 256)) return false;
+    return split >= 1 && split <= km;
+}
+
+// Makes a plan current: unit lists, the multicast operands' tensor maps,
+// resident cluster counts.
+int apply_plan(tc_ctx* c, int bn_g, int cl_g, int bn_m, int cl_m, int split) {
+    const int BKt = tc_gemm_tile_k();
+    const int n_pad = c->n_pad, mt = n_pad / tc_gemm_tile_m();
+    const long long ldg = c->ldg;
+    const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
+    const std::vector<int4> ug = units_gamma(mt, (int)(ldg / bn_g), n_pad / BKt);
+    const std::vector<int4> um = units_mtilde(mt, bn_m, n_pad / bn_m, (int)(ldg / BKt), split);
+    int rc;
+    if ((rc = upload_units(c, c->d_units_g, ug)) || (rc = upload_units(c, c->d_units_m, um))) return rc;
+    if ((rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, bn_g / cl_g, sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, bn_m / cl_m, sw)))
+        return rc;
+    c->n_units_g = (int)ug.size();
+    c->n_units_m = (int)um.size();
+    c->bn_g = bn_g;
+    c->cl_g = cl_g;
+    c->bn_m = bn_m;
+    c->cl_m = cl_m;
+    c->split_m = split;
+    c->slots_g = tc_gemm_cluster_slots(cl_g, bn_g, c->num_sms);
+    c->slots_m = tc_gemm_cluster_slots(cl_m, bn_m, c->num_sms);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+// Autotuner of the FP8 tensor-core contractions: times every candidate
+// (column tile 128 or 256, cluster size sharing the B tile, K splits of M~)
+// on the context's own operands, one warm-up and three timed launches each,
+// and keeps the fastest (the shapes differ from instance to instance).  The
+// FP32 comparator keeps the 128 x 256 tiles.
+int plan_dense(tc_ctx* c) {
+    const int BMt = tc_gemm_tile_m(), BKt = tc_gemm_tile_k();
+    const int n_pad = c->n_pad;
+    const long long ldg = c->ldg;
+    const int mt = n_pad / BMt, kg = n_pad / BKt, km = (int)(ldg / BKt);
+    const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
+    int rc;
+    if ((rc = tc_encode_tmap_2d(&c->tmA8, u8, c->d_A8, n_pad, n_pad, n_pad, BKt, BMt, sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)))
+        return rc;
+    auto split_for = [&](int bn, int cl, int slots) {
+        const int tri = (int)units_mtilde(mt, bn, n_pad / bn, 1, 1).size();
+        return std::max(1, std::min((slots * cl + tri - 1) / tri, km));
+    };
+    struct Cand {
+        int bn, cl, split;
+    };
+    std::vector<Cand> cg, cm;
+    const bool tc = c->p.form == TC_FORM_DENSE_FP8;
+    if (tc) {
+        for (int bn : {256, 128})
+            for (int cl : {1, 2, 4})
+                if (mt % cl == 0) cg.push_back({bn, cl, 1});
+        for (int bn : {256, 128})
+            for (int cl : {1, 2}) {
+                if (cl == 2 && bn != 256) continue;
+                const int s0 = split_for(bn, cl, tc_gemm_cluster_slots(cl, bn, c->num_sms));
+                for (int sp : {std::max(1, s0 / 2), s0, std::min(km, 2 * s0)})
+                    if (cm.empty() || cm.back().bn != bn || cm.back().cl != cl || cm.back().split != sp)
+                        cm.push_back({bn, cl, sp});
+            }
+    } else {
+        cg.push_back({256, 1, 1});
+        cm.push_back({256, 1, split_for(256, 1, c->num_sms)});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TC_CHECK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        (void)cudaGetLastError();
+        return TC_ERR_CUDA;
+    }
+    // time one candidate: 1 warm-up + 3 launches, the fastest (ms), or a
+    // negative value when the launch configuration is refused
+    auto time_it = [&](auto launch) -> float {
+        if (launch() != cudaSuccess) {
+            (void)cudaGetLastError();
+            return -1.f;
+        }
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            float ms = 0.f;
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess || launch() != cudaSuccess ||
+                cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return -1.f;
+            }
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    float best_g = 1e30f, best_m = 1e30f;
+    Cand pick_g = cg[0], pick_m = cm[0];
+    int timed = 0;
+    rc = TC_OK;
+    for (const Cand& q : cg) {
+        if (!tc) break;
+        const std::vector<int4> u = units_gamma(mt, (int)(ldg / q.bn), kg);
+        CUtensorMap tmY;
+        const int slots = tc_gemm_cluster_slots(q.cl, q.bn, c->num_sms);
+        if ((rc = tc_encode_tmap_2d(&tmY, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, q.bn / q.cl, sw)) ||
+            (rc = upload_units(c, c->d_units_g, u)))
+            break;
+        tc_gemm_args g = {c->d_units_g, (int)u.size(), TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
+                          &c->d_st->err};
+        const float ms = time_it([&] { return tc_launch_gemm_tc(c->tmA8, tmY, g, slots, q.cl, q.bn, c->stream); });
+        ++timed;
+        if (ms >= 0.f && ms < best_g) {
+            best_g = ms;
+            pick_g = q;
+        }
+    }
+    for (const Cand& q : cm) {
+        if (!tc || rc) break;
+        const std::vector<int4> u = units_mtilde(mt, q.bn, n_pad / q.bn, km, q.split);
+        CUtensorMap tmY;
+        const int slots = tc_gemm_cluster_slots(q.cl, q.bn, c->num_sms);
+        if ((rc = tc_encode_tmap_2d(&tmY, u8, c->d_S8, ldg, n_pad, ldg, BKt, q.bn / q.cl, sw)) ||
+            (rc = upload_units(c, c->d_units_m, u)))
+            break;
+        tc_gemm_args g = {c->d_units_m, (int)u.size(), TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
+                          &c->d_st->err};
+        const float ms = time_it([&] { return tc_launch_gemm_tc(c->tmS8x, tmY, g, slots, q.cl, q.bn, c->stream); });
+        ++timed;
+        if (ms >= 0.f && ms < best_m) {
+            best_m = ms;
+            pick_m = q;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (tc && (best_g >= 1e30f || best_m >= 1e30f)) return TC_ERR_CUDA;  // no configuration ran
+    if ((rc = apply_plan(c, pick_g.bn, pick_g.cl, pick_m.bn, pick_m.cl, pick_m.split))) return rc;
+    c->tune_candidates = timed;
+    c->tune_us_g = tc ? 1e3f * best_g : 0.f;
+    c->tune_us_m = tc ? 1e3f * best_m : 0.f;
+    return TC_OK;
+}
+
+// Dense forms: FP8 adjacency, one-hot operands, GEMM outputs, then the plan
+// of the two contractions (plan_dense).  n_pad is a multiple of every GEMM
+// tile edge, ldg (the padded D k) a multiple of the widest column tile.
 int setup_dense(tc_ctx* c) {
     free_dense(c);
-    const int BMt = tc_gemm_tile_m(), BNt = tc_gemm_tile_n(), BKt = tc_gemm_tile_k();
+    const int BMt = tc_gemm_tile_m(), BNt = tc_gemm_tile_n();
     const int n = c->n;
     const int n_pad = (n + BNt - 1) / BNt * BNt;
     const long long Kc = (long long)c->D * c->k;
     const long long ldg = (Kc + BNt - 1) / BNt * BNt;
     if (ldg > (1ll << 31) / 4) return TC_ERR_UNSUPPORTED;
+    // unit lists sized for the most units any valid plan uses (128-wide
+    // tiles, M~ split to single K blocks)
+    const int mt = n_pad / BMt;
+    const size_t max_ug = (size_t)mt * (size_t)(ldg / 128);
+    const size_t max_um = (size_t)mt * (size_t)(n_pad / 128) * (size_t)(ldg / tc_gemm_tile_k());
     int rc;
     if ((rc = dalloc(&c->d_A8, (size_t)n_pad * n_pad)) || (rc = dalloc(&c->d_S8, (size_t)n_pad * ldg)) ||
         (rc = dalloc(&c->d_S8T, (size_t)ldg * n_pad)) || (rc = dalloc(&c->d_G16, (size_t)n_pad * ldg)) ||
-        (rc = dalloc(&c->d_M32, (size_t)n_pad * n_pad))) {
+        (rc = dalloc(&c->d_M32, (size_t)n_pad * n_pad)) || (rc = dalloc(&c->d_units_g, max_ug)) ||
+        (rc = dalloc(&c->d_units_m, max_um))) {
         free_dense(c);
         return rc;
     }
@@ -289,59 +488,21 @@ int setup_dense(tc_ctx* c) {
     std::vector<uint8_t> a8((size_t)n_pad * n_pad, 0);
     for (int i = 0; i < n; ++i)
         for (int e = c->h_rowptr[i]; e < c->h_rowptr[i + 1]; ++e) a8[(size_t)i * n_pad + c->h_colidx[e]] = 0x38;
-    // work units: Gamma over all tiles (row tiles fastest, so neighbouring
-    // CTAs share the S_cat^T tile), M~ over the tiles touching the upper
-    // triangle with K split to give every SM work
-    std::vector<int4> ug, um;
-    const int mt = n_pad / BMt, ntg = (int)(ldg / BNt), ntm = n_pad / BNt;
-    for (int bn = 0; bn < ntg; ++bn)
-        for (int bm = 0; bm < mt; ++bm) ug.push_back(make_int4(bm, bn, 0, n_pad / BKt));
-    std::vector<int2> tri;
-    for (int bn = 0; bn < ntm; ++bn)
-        for (int bm = 0; bm < mt; ++bm)
-            if ((long long)bn * BNt + BNt - 1 >= (long long)bm * BMt) tri.push_back(make_int2(bm, bn));
-    // Gamma units come as columns of mt row tiles: clusters of 4 (or 2) row
-    // tiles share each S_cat^T tile; M~ tiles come in row pairs per column
-    c->cl_g = (mt % 4 == 0) ? 4 : 2;
-    c->cl_m = 2;
-    c->slots_g = tc_gemm_cluster_slots(c->cl_g, c->num_sms);
-    c->slots_m = tc_gemm_cluster_slots(c->cl_m, c->num_sms);
-    const int kblocks = (int)(ldg / BKt);
-    int split = (int)((c->slots_m * c->cl_m + tri.size() - 1) / tri.size());
-    split = std::max(1, std::min(split, kblocks));
-    for (int sidx = 0; sidx < split; ++sidx)
-        for (auto& tt : tri) {
-            const int k0 = (int)((long long)kblocks * sidx / split), k1 = (int)((long long)kblocks * (sidx + 1) / split);
-            if (k1 > k0) um.push_back(make_int4(tt.x, tt.y, k0, k1));
-        }
-    if ((rc = dalloc(&c->d_units_g, ug.size())) || (rc = dalloc(&c->d_units_m, um.size()))) {
-        free_dense(c);
-        return rc;
-    }
     cudaError_t e = cudaMemcpyAsync(c->d_A8, a8.data(), a8.size(), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->d_units_g, ug.data(), ug.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->d_units_m, um.data(), um.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         free_dense(c);
         return cuda_status(e);
     }
-    c->n_units_g = (int)ug.size();
-    c->n_units_m = (int)um.size();
-    const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
-    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
-    if ((rc = tc_encode_tmap_2d(&c->tmA8, u8, c->d_A8, n_pad, n_pad, n_pad, BKt, BMt, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, BNt / c->cl_g, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, BNt / c->cl_m, sw))) {
+    if ((rc = plan_dense(c))) {
+        (void)cudaGetLastError();
         free_dense(c);
         return rc;
     }
     return TC_OK;
 }
+
 
 // Rebuilds the FP8 one-hot operands from the current colours.
 cudaError_t rebuild_onehot(tc_ctx* c) {
@@ -446,12 +607,12 @@ int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
     if (which == 0) {
         TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, s));
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->slots_m, c->cl_m, s)
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->slots_m, c->cl_m, c->bn_m, s)
                       : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, s);
         }, s));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->slots_g, c->cl_g, s)
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->slots_g, c->cl_g, c->bn_g, s)
                       : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, s);
         }, s));
     }
@@ -893,12 +1054,21 @@ int tc_set_params(tc_ctx* c, const tc_params* p) {
             rc = setup_dense(c);
             if (!rc && rebuild_onehot(c) != cudaSuccess) rc = TC_ERR_CUDA;
             if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = TC_ERR_CUDA;
+        } else {
+            rc = plan_dense(c);  // the other dense form: its own tiles
         }
     }
     if (rc) {
         (void)cudaGetLastError();
         c->p = old;
         upload_luts(c);
+        // a dense form keeps a plan that matches its own kernels
+        if (old.form != TC_FORM_ONEHOT && c->d_M32 && plan_dense(c) != TC_OK) {
+            (void)cudaGetLastError();
+            free_dense(c);
+            c->p.form = TC_FORM_ONEHOT;
+        }
+        drop_graph_exec(c);
         return rc;
     }
     drop_graph_exec(c);
@@ -1208,6 +1378,39 @@ int tc_set_graph_chunk(tc_ctx* c, int chunk) {
     DeviceGuard g(c->device);
     drop_graph_exec(c);
     c->graph_chunk = chunk;
+    return TC_OK;
+}
+
+int tc_dense_plan(tc_ctx* c, int32_t* plan, float* us) {
+    if (!c || !plan) return TC_ERR_ARG;
+    if (!c->pop || !c->d_M32) return TC_ERR_STATE;
+    plan[0] = c->bn_g;
+    plan[1] = c->cl_g;
+    plan[2] = c->bn_m;
+    plan[3] = c->cl_m;
+    plan[4] = c->split_m;
+    plan[5] = c->tune_candidates;
+    if (us) {
+        us[0] = c->tune_us_g;
+        us[1] = c->tune_us_m;
+    }
+    return TC_OK;
+}
+
+int tc_dense_set_plan(tc_ctx* c, const int32_t* plan) {
+    if (!c || !plan) return TC_ERR_ARG;
+    if (!c->pop || !c->d_M32) return TC_ERR_STATE;
+    if (!plan_valid(c, plan[0], plan[1], plan[2], plan[3], plan[4])) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    const int old[5] = {c->bn_g, c->cl_g, c->bn_m, c->cl_m, c->split_m};
+    int rc = apply_plan(c, plan[0], plan[1], plan[2], plan[3], plan[4]);
+    if (rc) {
+        (void)cudaGetLastError();
+        apply_plan(c, old[0], old[1], old[2], old[3], old[4]);
+        return rc;
+    }
+    drop_graph_exec(c);
     return TC_OK;
 }
 

@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
         "tc_relaxed_dev": (C.c_int, [vp, vp, C.c_float, i64, vp, vp]),
         "tc_pair_terms_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_float, C.c_float, C.c_int, vp,
                                             vp]),
+        "tc_dense_plan": (C.c_int, [vp, vp, vp]),
+        "tc_dense_set_plan": (C.c_int, [vp, vp]),
         "tc_batch_create": (C.c_int, [P(vp), C.c_int]),
         "tc_batch_add": (C.c_int, [vp, vp]),
         "tc_batch_step": (C.c_int, [vp, i64, C.c_int]),
@@ -258,6 +260,19 @@ class TensCol:
     def tc_relaxed_dev(self, W_ptr: int, tau: float, t: int, loss_ptr: int, gradW_ptr: int):
         _ck(self._L.tc_relaxed_dev(self.h, C.c_void_p(W_ptr), tau, t, C.c_void_p(loss_ptr),
                                    C.c_void_p(gradW_ptr)), "tc_relaxed_dev")
+
+    def tc_dense_plan(self):
+        """The autotuned plan of the dense contractions (see tenscol.h)."""
+        plan = np.zeros(6, np.int32)
+        us = np.zeros(2, np.float32)
+        _ck(self._L.tc_dense_plan(self.h, _ptr(plan), _ptr(us)), "tc_dense_plan")
+        return dict(gamma_tile_n=int(plan[0]), gamma_cluster=int(plan[1]), mtilde_tile_n=int(plan[2]),
+                    mtilde_cluster=int(plan[3]), mtilde_splits=int(plan[4]), candidates=int(plan[5]),
+                    gamma_us=float(us[0]), mtilde_us=float(us[1]))
+
+    def tc_dense_set_plan(self, gamma_tile_n, gamma_cluster, mtilde_tile_n, mtilde_cluster, mtilde_splits):
+        plan = np.array([gamma_tile_n, gamma_cluster, mtilde_tile_n, mtilde_cluster, mtilde_splits], np.int32)
+        _ck(self._L.tc_dense_set_plan(self.h, _ptr(plan)), "tc_dense_set_plan")
 
     def tc_launch_count(self) -> int:
         c = C.c_int64()
