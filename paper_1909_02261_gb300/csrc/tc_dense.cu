@@ -31,7 +31,7 @@ namespace {
 
 constexpr int BM = 128, BK = 128;  // BK in bytes = FP8 elements
 constexpr int BN = 256;            // column tile of the FP32 comparator and the padding unit
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 224;  // producer, MMA, four epilogue warps, output warp
 
 // Tile shapes of the tensor-core GEMM (the column tile BN_ is tuned per
 // context): the stage ring keeps about 192 KB of operands in flight.
@@ -43,7 +43,7 @@ struct TcShape {
     // instruction descriptor: D = F32, A = B = E4M3, both K-major, M = BM, N = BN_
     static constexpr uint32_t IDESC =
         (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 32768 + 1024;  // + output staging, alignment
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -185,39 +185,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Epilogue of one row segment of 32 columns (values are exact integers).
-// Tiles never cross the padded allocation (n_pad rows, ldc columns).
-// Gamma entry (row i, column d k + j) in the tile-transposed layout: lanes
-// holding 32 consecutive rows of one 32-row tile write one 64-byte line.
+// Gamma entry (row i, column d k + j) in the transposed layout: column-major
+// over the padded rows (used by the FP32 comparator's direct stores).
 __device__ __forceinline__ uint16_t* gamma_at(const tc_gemm_args& g, int row, int col) {
-    const int kk = g.ldc, d = col / kk, j = col - d * kk;
-    return reinterpret_cast<uint16_t*>(g.C) + tc_gamma_index(d, row, j, g.rows_alloc / 32, kk);
+    return reinterpret_cast<uint16_t*>(g.C) + (size_t)col * g.rows_alloc + row;
 }
 
-__device__ __forceinline__ void store_chunk(const tc_gemm_args& g, int row, int col0, const uint32_t (&v)[32]) {
-    if (row >= g.rows_alloc) return;
-    if (g.mode == TC_GEMM_GAMMA) {
-        if (col0 >= g.cols_alloc) return;
-        const int kk = g.ldc;
-        const size_t dstep = (size_t)(g.rows_alloc / 32) * kk * 32;  // next individual
-        int j = col0 % kk;
-        uint16_t* p = gamma_at(g, row, col0) - (size_t)j * 32;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            if (col0 + e < g.cols_alloc) p[j * 32] = (uint16_t)__float2uint_rn(__uint_as_float(v[e]));
-            if (++j == kk) {
-                j = 0;
-                p += dstep;
-            }
-        }
-    } else {
-        if (col0 + 32 > g.cols_alloc) return;
-        float4* d4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.C) + (size_t)row * g.ldc + col0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            atomicAdd(d4 + q, make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])));
-    }
+// Output staging of the tensor-core epilogue: 32 KB after the operand ring,
+// four 8 KB buffers of [32 columns][128 rows] uint16 for Gamma (one TMA store
+// each), or two 16 KB buffers of [128 rows][32 floats], 128-byte swizzled, for
+// M~ (one TMA reduce-add each: the split-K partial sums add up in L2).
+constexpr int STG_BYTES = 32768;
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(su32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(su32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void st_shared_u16(uint32_t a, uint16_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 
 // CL > 1: the CL CTAs of a cluster take CL units that share the column tile
@@ -226,14 +233,14 @@ __device__ __forceinline__ void store_chunk(const tc_gemm_args& g, int row, int 
 template <int BN_, int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-              tc_gemm_args g) {
+              const __grid_constant__ CUtensorMap tmC, tc_gemm_args g) {
     using Sh = TcShape<BN_>;
     constexpr int STAGES = Sh::STAGES, A_BYTES = Sh::A_BYTES, B_BYTES = Sh::B_BYTES,
                   STAGE_BYTES = Sh::STAGE_BYTES, TMEM_COLS = Sh::TMEM_COLS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 128-byte swizzled tiles need 1024-byte aligned bases
     uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain, sfull[4], sempty[4];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -249,6 +256,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int a = 0; a < 2; ++a) {
             bar_init(&tfull[a], 1);
             bar_init(&tempty[a], 4);
+        }
+        for (int b = 0; b < 4; ++b) {
+            bar_init(&sfull[b], 4);   // the four epilogue warps staged their rows
+            bar_init(&sempty[b], 1);  // the TMA store / reduce has read the buffer
         }
         bar_init(&drain, 1);
         abort_flag = 0;
@@ -325,27 +336,81 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         }
-    } else {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ...
+    } else if (warp < 6) {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ...
+        // Each 32-column chunk goes through a shared-memory buffer: every warp
+        // writes its 32 rows, then the output warp sends the 128-row block
+        // with one TMA store (Gamma) or reduce-add (M~).
         const int q = warp & 3;
         const int row_in_tile = 32 * q + lane;
-        unsigned ui = 0;
+        const bool gamma = g.mode == TC_GEMM_GAMMA;
+        const int nb = gamma ? 4 : 2;
+        const uint32_t bytes_b = gamma ? 8192u : 16384u;
+        const uint32_t stg = su32(smem + STAGES * STAGE_BYTES);
+        unsigned ui = 0, gc = 0;  // unit and chunk counters
         for (int u = group * CL + (int)crank; u < g.n_units; u += ngroups * CL, ++ui) {
-            const int4 w = g.units[u];
             const int a = ui & 1;
             const unsigned ua = ui >> 1;
             if (!bar_wait(&tfull[a], ua & 1u, &abort_flag, g.err)) break;
             tc_fence_after();
-            const int row = w.x * BM + row_in_tile;
 #pragma unroll 1
-            for (int c = 0; c < BN_ / 32; ++c) {
+            for (int c = 0; c < BN_ / 32; ++c, ++gc) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN_ + 32 * c), v);
-                store_chunk(g, row, w.y * BN_ + 32 * c, v);
+                const int b = (int)(gc % (unsigned)nb);
+                const unsigned use = gc / (unsigned)nb;
+                // the buffer is free once the output warp's TMA operation read it
+                bar_wait(&sempty[b], (use & 1u) ^ 1u, &abort_flag, g.err);
+                if (gamma) {  // [32 columns][128 rows] uint16
+                    const uint32_t base = stg + (uint32_t)b * bytes_b + 2u * (uint32_t)row_in_tile;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        st_shared_u16(base + 256u * (uint32_t)e, (uint16_t)__float2uint_rn(__uint_as_float(v[e])));
+                } else {  // [128 rows][32 floats], 16-byte chunks swizzled by row mod 8
+                    const uint32_t base = stg + (uint32_t)b * bytes_b + 128u * (uint32_t)row_in_tile;
+#pragma unroll
+                    for (int h = 0; h < 8; ++h)
+                        st_shared_v4(base + 16u * (uint32_t)(h ^ (row_in_tile & 7)), v[4 * h], v[4 * h + 1],
+                                     v[4 * h + 2], v[4 * h + 3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the TMA unit
+                __syncwarp();
+                if (lane == 0) bar_arrive(&sfull[b]);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(&tempty[a]);
         }
+    } else if (lane == 0) {  // output warp: TMA store / reduce of each staged chunk
+        const bool gamma = g.mode == TC_GEMM_GAMMA;
+        const int nb = gamma ? 4 : 2;
+        const int bytes_b = gamma ? 8192 : 16384;
+        uint8_t* stg = smem + STAGES * STAGE_BYTES;
+        unsigned gc = 0;
+        bool ok = true;
+        for (int u = group * CL + (int)crank; u < g.n_units && ok; u += ngroups * CL) {
+            const int4 w = g.units[u];
+            for (int c = 0; c < BN_ / 32; ++c, ++gc) {
+                const int b = (int)(gc % (unsigned)nb);
+                if (!(ok = bar_wait(&sfull[b], (gc / (unsigned)nb) & 1u, &abort_flag, g.err))) break;
+                const int col0 = w.y * BN_ + 32 * c;
+                if (gamma) {
+                    if (col0 < g.cols_alloc)  // columns past D k are padding: not stored
+                        tma_store_2d(&tmC, w.x * BM, col0, stg + b * bytes_b);
+                    else
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");  // an empty group keeps the count
+                } else {
+                    tma_reduce_add_2d(&tmC, col0, w.x * BM, stg + b * bytes_b);
+                }
+                // every group but the newest nb - 1 has read its buffer: the
+                // chunk nb - 1 back may be overwritten
+                if (gamma)
+                    asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+                else
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                if (gc + 1 >= (unsigned)nb) bar_arrive(&sempty[(gc + 1 - (unsigned)nb) % (unsigned)nb]);
+            }
+        }
+        bulk_wait_all();  // the output is in global memory before the CTA exits
     }
     tc_fence_before();
     __syncthreads();
@@ -488,8 +553,8 @@ static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttrib
 }
 
 template <int BN_, int CL>
-static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g, int slots,
-                             cudaStream_t s) {
+static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                             const tc_gemm_args& g, int slots, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN_, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TcShape<BN_>::SMEM);
     if (e != cudaSuccess) return e;
@@ -497,7 +562,7 @@ static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, con
     if (groups < 1) groups = 1;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = tc_config<BN_, CL>(groups, s, attr);
-    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL>, tmX, tmY, g);
+    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL>, tmX, tmY, tmC, g);
 }
 
 template <int BN_, int CL>
@@ -538,20 +603,22 @@ int tc_gemm_cluster_slots(int cluster, int bn, int num_sms) {
 // in groups of that many units with equal column tile and K range, and tmY's
 // box must hold bn / cluster rows.  `bn`: the column tile (128 or 256) the
 // units were cut with.  `slots`: clusters launched at most (one wave, from
-// tc_gemm_cluster_slots).
-cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int slots, int cluster, int bn, cudaStream_t s) {
+// tc_gemm_cluster_slots).  tmC: the output, Gamma transposed [D k][n_pad]
+// uint16 with 128 x 32 boxes, or M~ [n_pad][n_pad] f32 with 32 x 128 boxes,
+// 128-byte swizzled.
+cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                              const tc_gemm_args& g, int slots, int cluster, int bn, cudaStream_t s) {
     if (bn == 128) {
         switch (cluster) {
-            case 4: return launch_tc<128, 4>(tmX, tmY, g, slots, s);
-            case 2: return launch_tc<128, 2>(tmX, tmY, g, slots, s);
-            default: return launch_tc<128, 1>(tmX, tmY, g, slots, s);
+            case 4: return launch_tc<128, 4>(tmX, tmY, tmC, g, slots, s);
+            case 2: return launch_tc<128, 2>(tmX, tmY, tmC, g, slots, s);
+            default: return launch_tc<128, 1>(tmX, tmY, tmC, g, slots, s);
         }
     }
     switch (cluster) {
-        case 4: return launch_tc<256, 4>(tmX, tmY, g, slots, s);
-        case 2: return launch_tc<256, 2>(tmX, tmY, g, slots, s);
-        default: return launch_tc<256, 1>(tmX, tmY, g, slots, s);
+        case 4: return launch_tc<256, 4>(tmX, tmY, tmC, g, slots, s);
+        case 2: return launch_tc<256, 2>(tmX, tmY, tmC, g, slots, s);
+        default: return launch_tc<256, 1>(tmX, tmY, tmC, g, slots, s);
     }
 }
 

@@ -86,11 +86,12 @@ __host__ __device__ inline size_t tc_w_index(int d, int i, int j, int nT, int k)
     return (((size_t)d * nT + i / TC_WT) * k + j) * TC_WT + (i % TC_WT);
 }
 // The gamma matrix of the dense forms (Gamma_d[i][j] = #neighbours of i in
-// colour j of individual d, uint16) uses the same tiling over the padded rows
-// (n_pad / 32 tiles): a 32-row tile of one individual is a contiguous k x 32
-// block, one 64-byte line per colour.
-__host__ __device__ inline size_t tc_gamma_index(int d, int i, int j, int nTp, int k) {
-    return (((size_t)d * nTp + i / 32) * k + j) * 32 + (i % 32);
+// colour j of individual d, uint16) is stored transposed, column-major over
+// the padded rows: entry (d, i, j) at (d k + j) n_pad + i.  A run of 32 rows
+// of one colour is one 64-byte line, and a 32-column x 128-row block of the
+// GEMM output is one TMA box.
+__host__ __device__ inline size_t tc_gamma_index(int d, int i, int j, int n_pad, int k) {
+    return ((size_t)d * k + j) * (size_t)n_pad + (size_t)i;
 }
 // src (standard D x n x k) -> dst (tiled) when to_tiled, else back.
 cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled,
@@ -135,7 +136,7 @@ int tc_encode_tmap_2d(CUtensorMap* out, CUtensorMapDataType dt, void* base, uint
                       CUtensorMapSwizzle swizzle);
 constexpr int TC_BT_BOX_ROWS = 128;  // rows per TMA box of the B column panel
 // Dense contractions (tc_dense.cu): C = X . Y^T over FP8 0/1 operands.
-#define TC_GEMM_GAMMA 0  /* C uint16 tiled (tc_gamma_index), plain stores; ldc = k, cols_alloc = D k */
+#define TC_GEMM_GAMMA 0  /* C uint16 transposed (tc_gamma_index); ldc = k, cols_alloc = D k */
 #define TC_GEMM_MTILDE 1 /* C float, atomic adds (K may be split)       */
 struct tc_gemm_args {
     const int4* units;  // (tile row, tile column, first K block, end K block)
@@ -149,8 +150,8 @@ struct tc_gemm_args {
 int tc_gemm_tile_m();
 int tc_gemm_tile_n();
 int tc_gemm_tile_k();
-cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const tc_gemm_args& g,
-                              int slots, int cluster, int bn, cudaStream_t s);
+cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                              const tc_gemm_args& g, int slots, int cluster, int bn, cudaStream_t s);
 int tc_gemm_cluster_slots(int cluster, int bn, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);

@@ -619,8 +619,8 @@ __device__ __forceinline__ void fence_proxy_async() {
 // E_dj (+ the gamma-matrix entry in the dense forms).
 template <int BS, bool STG>
 __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const float* xs, const int8_t* Ed,
-                                           const uint16_t* grow, const float* Bl, int bstride, float nut, int k,
-                                           int jb, int je, float* Gout) {
+                                           const uint16_t* grow, int gstride, const float* Bl, int bstride,
+                                           float nut, int k, int jb, int je, float* Gout) {
     const int bs = BS > 0 ? BS : bstride;
     if (jb >= je) return;
     int s = STG ? of[jb] : __ldg(of + jb);
@@ -628,10 +628,10 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
     // gamma entries travel 4 classes ahead of use (an L2 round trip each)
     uint16_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;
     if (grow) {
-        g0 = __ldg(grow + (size_t)jb * 32);
-        if (jb + 1 < je) g1 = __ldg(grow + (size_t)(jb + 1) * 32);
-        if (jb + 2 < je) g2 = __ldg(grow + (size_t)(jb + 2) * 32);
-        if (jb + 3 < je) g3 = __ldg(grow + (size_t)(jb + 3) * 32);
+        g0 = __ldg(grow + (size_t)jb * gstride);
+        if (jb + 1 < je) g1 = __ldg(grow + (size_t)(jb + 1) * gstride);
+        if (jb + 2 < je) g2 = __ldg(grow + (size_t)(jb + 2) * gstride);
+        if (jb + 3 < je) g3 = __ldg(grow + (size_t)(jb + 3) * gstride);
     }
     for (int j = jb; j < je; ++j) {
         int e_next;
@@ -648,7 +648,7 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
             g0 = g1;
             g1 = g2;
             g2 = g3;
-            g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * 32) : (uint16_t)0;
+            g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * gstride) : (uint16_t)0;
         }
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 2
@@ -682,17 +682,17 @@ __device__ __forceinline__ uint4 lds_u32x4(uint32_t a) {
 // lists both in shared memory), on 32-bit shared addresses: the B entry of
 // vertex v for this lane sits at bl + 128 v.
 __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, const float* xs,
-                                                  const uint16_t* grow, uint32_t bl, int k, int jb, int je,
-                                                  float* Gout) {
+                                                  const uint16_t* grow, int gstride, uint32_t bl, int k, int jb,
+                                                  int je, float* Gout) {
     if (jb >= je) return;
     uint32_t p = pm + 4u * (uint32_t)of[jb];
     uint32_t e = pm + 4u * (uint32_t)of[jb + 1];
     uint16_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;  // gamma entries, 4 classes ahead
     if (grow) {
-        g0 = __ldg(grow + (size_t)jb * 32);
-        if (jb + 1 < je) g1 = __ldg(grow + (size_t)(jb + 1) * 32);
-        if (jb + 2 < je) g2 = __ldg(grow + (size_t)(jb + 2) * 32);
-        if (jb + 3 < je) g3 = __ldg(grow + (size_t)(jb + 3) * 32);
+        g0 = __ldg(grow + (size_t)jb * gstride);
+        if (jb + 1 < je) g1 = __ldg(grow + (size_t)(jb + 1) * gstride);
+        if (jb + 2 < je) g2 = __ldg(grow + (size_t)(jb + 2) * gstride);
+        if (jb + 3 < je) g3 = __ldg(grow + (size_t)(jb + 3) * gstride);
     }
     for (int j = jb; j < je; ++j) {
         const uint32_t e_next = pm + 4u * (uint32_t)of[j + 2 <= k ? j + 2 : k];
@@ -702,7 +702,7 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
             g0 = g1;
             g1 = g2;
             g2 = g3;
-            g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * 32) : (uint16_t)0;
+            g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * gstride) : (uint16_t)0;
         }
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 2
@@ -725,11 +725,11 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
 // additions per iteration instead of D n^2.  Accumulates in Gs[j * 32].
 // Also counts gamma_d(i) (eq. 1): the neighbours sharing i's colour.
 __device__ __forceinline__ int neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
-                                              const int8_t* Ed, const uint16_t* grow, const float* Bl,
+                                              const int8_t* Ed, const uint16_t* grow, int gstride, const float* Bl,
                                               int bstride, float nut, int k, float* Gs, int i, bool valid) {
     for (int j = 0; j < k; ++j) {
         float g0 = nut * (float)__ldg(Ed + j);
-        if (grow) g0 += (float)__ldg(grow + (size_t)j * 32);
+        if (grow) g0 += (float)__ldg(grow + (size_t)j * gstride);
         Gs[j * 32] = g0;
     }
     if (!valid) return 0;
@@ -873,8 +873,9 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
             }
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
-            // the item's gamma tile: colour j of row i0 + lane at grow[j * 32]
-            const uint16_t* grow = P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad / 32, k) : nullptr;
+            // the item's gamma entries: colour j of row i0 + lane at grow[j * gstride]
+            const uint16_t* grow = P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad, k) : nullptr;
+            const int gstride = P.n_pad;
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
             const bool live = lane < rows;
             const int bstride = BTS ? 32 : P.ldb;
@@ -882,7 +883,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
             if (CSR) {
-                conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, Bl, bstride, nut, k,
+                conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, gstride, Bl, bstride, nut, k,
                                       Gw + lane, i0 + lane, live);
                 __syncwarp();
                 for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
@@ -892,19 +893,19 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 const int kh = min(k, (k + 4) >> 1), jb = STG ? h * kh : 0, je = STG ? (h ? k : kh) : k;
                 if (STG) {
                     if (BTS)
-                        class_sums_shared(smem_u32(ps), os, xs, grow, smem_u32(Bl), k, jb, je, Gout);
+                        class_sums_shared(smem_u32(ps), os, xs, grow, gstride, smem_u32(Bl), k, jb, je, Gout);
                     else
-                        class_sums<0, true>(ps, os, xs, Ed, grow, Bl, P.ldb, nut, k, jb, je, Gout);
+                        class_sums<0, true>(ps, os, xs, Ed, grow, gstride, Bl, P.ldb, nut, k, jb, je, Gout);
                 } else if (BTS) {
-                    class_sums<32, false>(pm, of, nullptr, Ed, grow, Bl, 32, nut, k, 0, k, Gout);
+                    class_sums<32, false>(pm, of, nullptr, Ed, grow, gstride, Bl, 32, nut, k, 0, k, Gout);
                 } else {
-                    class_sums<0, false>(pm, of, nullptr, Ed, grow, Bl, P.ldb, nut, k, 0, k, Gout);
+                    class_sums<0, false>(pm, of, nullptr, Ed, grow, gstride, Bl, P.ldb, nut, k, 0, k, Gout);
                 }
                 if (counter) {
                     conf = 0;
                     if (live) {
                         if (P.G16)
-                            conf = __ldg(grow + (size_t)ci * 32);  // the gamma matrix of the dense forms
+                            conf = __ldg(grow + (size_t)ci * gstride);  // the gamma matrix of the dense forms
                         else if (STG)
                             conf = own_class_conflicts<true>(ps, os, ci, Bl, bstride);
                         else

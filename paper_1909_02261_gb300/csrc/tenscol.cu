@@ -76,6 +76,8 @@ struct tc_ctx {
     alignas(64) CUtensorMap tmS8T;
     alignas(64) CUtensorMap tmS8x;
     alignas(64) CUtensorMap tmS8y;
+    alignas(64) CUtensorMap tmG16;  // output of Gamma (TMA store)
+    alignas(64) CUtensorMap tmM32;  // output of M~ (TMA reduce-add)
     // CUDA graph of graph_chunk iterations
     int graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -356,7 +358,13 @@ int plan_dense(tc_ctx* c) {
     const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
     int rc;
     if ((rc = tc_encode_tmap_2d(&c->tmA8, u8, c->d_A8, n_pad, n_pad, n_pad, BKt, BMt, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)))
+        (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)) ||
+        // outputs: Gamma transposed [D k][n_pad] uint16 in 128-row x 32-column
+        // boxes, M~ [n_pad][n_pad] f32 in 32-column x 128-row swizzled boxes
+        (rc = tc_encode_tmap_2d(&c->tmG16, CU_TENSOR_MAP_DATA_TYPE_UINT16, c->d_G16, n_pad,
+                                (uint64_t)c->D * c->k, 2ull * n_pad, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) ||
+        (rc = tc_encode_tmap_2d(&c->tmM32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->d_M32, n_pad, n_pad, 4ull * n_pad, 32,
+                                128, sw)))
         return rc;
     auto split_for = [&](int bn, int cl, int slots) {
         const int tri = (int)units_mtilde(mt, bn, n_pad / bn, 1, 1).size();
@@ -424,7 +432,8 @@ int plan_dense(tc_ctx* c) {
             break;
         tc_gemm_args g = {c->d_units_g, (int)u.size(), TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
                           &c->d_st->err};
-        const float ms = time_it([&] { return tc_launch_gemm_tc(c->tmA8, tmY, g, slots, q.cl, q.bn, c->stream); });
+        const float ms =
+            time_it([&] { return tc_launch_gemm_tc(c->tmA8, tmY, c->tmG16, g, slots, q.cl, q.bn, c->stream); });
         ++timed;
         if (ms >= 0.f && ms < best_g) {
             best_g = ms;
@@ -441,7 +450,8 @@ int plan_dense(tc_ctx* c) {
             break;
         tc_gemm_args g = {c->d_units_m, (int)u.size(), TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
                           &c->d_st->err};
-        const float ms = time_it([&] { return tc_launch_gemm_tc(c->tmS8x, tmY, g, slots, q.cl, q.bn, c->stream); });
+        const float ms =
+            time_it([&] { return tc_launch_gemm_tc(c->tmS8x, tmY, c->tmM32, g, slots, q.cl, q.bn, c->stream); });
         ++timed;
         if (ms >= 0.f && ms < best_m) {
             best_m = ms;
@@ -607,12 +617,12 @@ int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
     if (which == 0) {
         TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, s));
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, gm, c->slots_m, c->cl_m, c->bn_m, s)
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, c->tmM32, gm, c->slots_m, c->cl_m, c->bn_m, s)
                       : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, s);
         }, s));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, gg, c->slots_g, c->cl_g, c->bn_g, s)
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, c->tmG16, gg, c->slots_g, c->cl_g, c->bn_g, s)
                       : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, s);
         }, s));
     }
