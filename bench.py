@@ -146,7 +146,7 @@ def cpu_oracle_rate(rp, ci, w, iters):
     from paper_1909_02261_gb300 import inputs
     W = inputs.init_weights(w["D"], w["n"], w["k"], 0.01, seed=w["w_seed"])
     po = O.make_params(rho=100.0)
-    O.run(rp, ci, W[:1, :50], po, 0, 1, stop_on_legal=False)  # load/compile outside timing
+    O.run(rp, ci, W[:1], po, 0, 1, stop_on_legal=False)  # load/compile outside timing
     t0 = time.perf_counter()
     r = O.run(rp, ci, W, po, 0, iters, stop_on_legal=False)
     dt = time.perf_counter() - t0

@@ -198,6 +198,11 @@ def update(W, G, params: Params, t: int):
     return W, gW
 
 
+def _check_graph_size(rowptr, n):
+    if len(rowptr) - 1 != n:
+        raise ValueError(f"graph has {len(rowptr) - 1} vertices, weights have {n}")
+
+
 def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
          want_G: bool = True):
     """One iteration of Algorithm 1 on a copy of W (float32 or float64 input).
@@ -207,6 +212,7 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
     rowptr, colidx = _i32(rowptr), _i32(colidx)
     W = _f64(W).copy()
     D, n, k = W.shape
+    _check_graph_size(rowptr, n)
     out = dict(
         colors=np.empty((D, n), np.int32), gamma_own=np.empty((D, n), np.int32),
         f_color=np.empty((D,), np.int64), f_eq=np.empty((D,), np.int64),
@@ -231,6 +237,7 @@ def run(rowptr, colidx, W, params: Params, t0: int, max_iter: int, stop_on_legal
     rowptr, colidx = _i32(rowptr), _i32(colidx)
     W = _f64(W).copy()
     D, n, k = W.shape
+    _check_graph_size(rowptr, n)
     t = C.c_longlong(t0)
     best = np.zeros((n,), np.int32)
     bf, bt = C.c_longlong(-1), C.c_longlong(-1)
@@ -247,6 +254,7 @@ def relaxed(rowptr, colidx, W, params: Params, t: int, tau: float, want_grad: bo
     rowptr, colidx = _i32(rowptr), _i32(colidx)
     W = _f64(W)
     D, n, k = W.shape
+    _check_graph_size(rowptr, n)
     loss = C.c_double()
     g = np.empty_like(W) if want_grad else None
     M = np.empty((n, n), np.float64)
