@@ -232,6 +232,21 @@ int tc_launch_count(tc_ctx *ctx, int64_t *count);
  * `chunk` iterations are captured once into one graph and replayed. */
 int tc_set_graph_chunk(tc_ctx *ctx, int chunk);
 
+/* k-descent: the GCP (or, with problem = TC_ECP, the ECP) approached as a
+ * series of k-COL problems for decreasing k (Section 2 and the opening of
+ * Section 3: every k with a legal colouring is an upper bound of the
+ * chromatic, resp. equitable chromatic, number).  For k = k_start,
+ * k_start - 1, ..., k_min: a fresh population of D individuals (seed + k),
+ * Algorithm 1 with stop_on_legal for at most max_iters iterations; a legal
+ * colouring (f_color = 0, and f_eq = 0 for the ECP) moves on to k - 1, the
+ * first k without one within the budget ends the descent.  *p as for
+ * tc_init_population (NULL: Table 2 for TC_KCOL); stop_on_legal is forced
+ * on.  Outputs (any may be NULL): *k_best the smallest k solved (-1 if
+ * none), coloring[n] its legal colouring, *iters_total the iterations run.
+ * The context keeps the population of the last k tried. */
+int tc_kdescent(tc_ctx *ctx, uint64_t seed, int D, int k_start, int k_min, int64_t max_iters,
+                const tc_params *p, int32_t *k_best, int32_t *coloring, int64_t *iters_total);
+
 /* The plan the autotuner chose for the dense contractions of this context
  * (tc_init_population / tc_set_params time every candidate on the context's
  * own operands and keep the fastest; the FP32 form keeps one fixed plan):

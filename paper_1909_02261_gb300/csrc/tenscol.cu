@@ -382,10 +382,16 @@ int plan_dense(tc_ctx* c) {
         for (int bn : {256, 128})
             for (int cl : {1, 2}) {
                 if (cl == 2 && bn != 256) continue;
-                const int s0 = split_for(bn, cl, tc_gemm_cluster_slots(cl, bn, c->num_sms));
-                for (int sp : {std::max(1, s0 / 2), s0, std::min(km, 2 * s0)})
-                    if (cm.empty() || cm.back().bn != bn || cm.back().cl != cl || cm.back().split != sp)
-                        cm.push_back({bn, cl, sp});
+                // splits around the one that fills the resident CTAs: those
+                // that give one or two full waves, and fewer (less reduction)
+                const int slots = tc_gemm_cluster_slots(cl, bn, c->num_sms) * cl;
+                const int tri = (int)units_mtilde(mt, bn, n_pad / bn, 1, 1).size();
+                std::vector<int> sps = {std::max(1, slots / tri), std::max(1, 2 * slots / tri),
+                                        split_for(bn, cl, slots / cl), std::max(1, slots / tri / 2)};
+                std::sort(sps.begin(), sps.end());
+                sps.erase(std::unique(sps.begin(), sps.end()), sps.end());
+                for (int sp : sps)
+                    if (sp <= km) cm.push_back({bn, cl, sp});
             }
     } else {
         cg.push_back({256, 1, 1});
@@ -1388,6 +1394,36 @@ int tc_set_graph_chunk(tc_ctx* c, int chunk) {
     DeviceGuard g(c->device);
     drop_graph_exec(c);
     c->graph_chunk = chunk;
+    return TC_OK;
+}
+
+int tc_kdescent(tc_ctx* c, uint64_t seed, int D, int k_start, int k_min, int64_t max_iters, const tc_params* p_in,
+                int32_t* k_best, int32_t* coloring, int64_t* iters_total) {
+    if (k_best) *k_best = -1;
+    if (iters_total) *iters_total = 0;
+    if (!c || D < 1 || k_min < 1 || k_start < k_min || k_start > TC_MAX_K || max_iters < 1) return TC_ERR_ARG;
+    if (c->n < 1) return TC_ERR_STATE;
+    tc_params p;
+    if (p_in) p = *p_in;
+    else tc_params_default(&p, TC_KCOL);
+    p.stop_on_legal = 1;
+    int rc = check_params(&p);
+    if (rc) return rc;
+    std::vector<int32_t> col(c->n);
+    long long total = 0;
+    for (int k = k_start; k >= k_min; --k) {
+        if ((rc = tc_init_population(c, seed + (uint64_t)k, D, k, &p))) return rc;
+        int64_t done = 0;
+        if ((rc = tc_step(c, max_iters, &done))) return rc;
+        total += done;
+        if (iters_total) *iters_total = total;
+        int64_t conf = -1, eq = -1;
+        if ((rc = tc_best(c, col.data(), &conf, &eq, nullptr, nullptr))) return rc;
+        const bool legal = conf == 0 && (p.problem != TC_ECP || eq == 0);
+        if (!legal) break;
+        if (k_best) *k_best = k;
+        if (coloring) memcpy(coloring, col.data(), sizeof(int32_t) * (size_t)c->n);
+    }
     return TC_OK;
 }
 

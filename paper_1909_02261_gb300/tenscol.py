@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
         "tc_relaxed_dev": (C.c_int, [vp, vp, C.c_float, i64, vp, vp]),
         "tc_pair_terms_noalloc": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_float, C.c_float, C.c_int, vp,
                                             vp]),
+        "tc_kdescent": (C.c_int, [vp, C.c_uint64, C.c_int, C.c_int, C.c_int, i64, P(tc_params), P(i32), vp,
+                                  P(i64)]),
         "tc_dense_plan": (C.c_int, [vp, vp, vp]),
         "tc_dense_set_plan": (C.c_int, [vp, vp]),
         "tc_batch_create": (C.c_int, [P(vp), C.c_int]),
@@ -260,6 +262,18 @@ class TensCol:
     def tc_relaxed_dev(self, W_ptr: int, tau: float, t: int, loss_ptr: int, gradW_ptr: int):
         _ck(self._L.tc_relaxed_dev(self.h, C.c_void_p(W_ptr), tau, t, C.c_void_p(loss_ptr),
                                    C.c_void_p(gradW_ptr)), "tc_relaxed_dev")
+
+    def tc_kdescent(self, seed: int, D: int, k_start: int, k_min: int, max_iters: int,
+                    p: tc_params | None = None):
+        """Decreasing-k descent: (k_best or -1, its colouring or None, iterations run)."""
+        kb, it = C.c_int32(), C.c_int64()
+        col = np.empty(self.n, np.int32)
+        _ck(self._L.tc_kdescent(self.h, seed, D, k_start, k_min, max_iters, None if p is None else C.byref(p),
+                                C.byref(kb), _ptr(col), C.byref(it)), "tc_kdescent")
+        # the context keeps the population of the last k tried
+        last = k_min if kb.value == k_min else (kb.value - 1 if kb.value > 0 else k_start)
+        self.D, self.k = D, last
+        return kb.value, (col if kb.value > 0 else None), it.value
 
     def tc_dense_plan(self):
         """The autotuned plan of the dense contractions (see tenscol.h)."""
