@@ -140,6 +140,24 @@ def traffic_record(kernel, src_files):
     return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == h.hexdigest() else None
 
 
+def slowest_rank(x, device):
+    """Max of x over the ranks of the process group (the slowest replica's
+    time sets the whole job's); x itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, D, steps, seconds):
+    """individual-steps/s of the whole job: every rank steps its own population
+    of D individuals `steps` times (independent replicas, weak scaling)."""
+    return world * D * steps / seconds
+
+
 def cpu_oracle_rate(rp, ci, w, iters):
     """The oracle as it stands: `iters` full iterations, single thread."""
     from oracle import oracle as O
@@ -260,17 +278,14 @@ def run_ours(args):
         return float(sum(step_ms)), kms, kcnt, launches, wall, clocks
 
     total_ms, _, _, launches, wall, clocks = time_steps(args.steps, args.warmup, True, False)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest_rank(total_ms, dev)
     # per-kernel CUDA-event times on the library's stream, same workload
     ksteps = min(args.steps, 1000)
     kernel_pass_ms, kms, kcnt, _, _, _ = time_steps(ksteps, 3, False, True)
     W_, t_now = ctx.tc_get_state()
     assert t_now == args.warmup + args.steps + 3 + ksteps, (t_now, args.warmup, args.steps)
     W_ = None
-    value = world * D * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, D, args.steps, total_ms / 1e3)
 
     # end to end through the C ABI with host buffers: per step the weights go
     # host -> device, one iteration runs, the weights and the best colouring
@@ -287,12 +302,8 @@ def run_ours(args):
         best = ctx.tc_best()
         if s >= 2:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_total = float(sum(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * D * len(e2e_times) / e2e_total if e2e_times else None
+    e2e_total = slowest_rank(float(sum(e2e_times)), dev)
+    e2e_value = whole_job_rate(world, D, len(e2e_times), e2e_total) if e2e_times else None
     h2d = Wh.nbytes
     d2h = Wh.nbytes + 4 * n + 64
 
