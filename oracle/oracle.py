@@ -6,8 +6,10 @@ gcc on first use (into ``oracle/_build/``) and wraps each step of the
 iteration of Goudet, Duval, Hao (TensCol), Algorithm 1, with numpy arrays.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-(closed forms, brute force, finite differences, the worked kappa example of
-Section 3.6.1); none is "parity unpinned".
+and, for the k-partitioning problems of Section 7, by
+``tests/test_oracle_partition_pins.py`` (closed forms, brute force, finite
+differences, the worked kappa example of Section 3.6.1); none is "parity
+unpinned".
 """
 from __future__ import annotations
 
@@ -77,11 +79,13 @@ def _declare(L):
     L.orc_fitness.argtypes = [_i, _i, _i, _p, _p, _p, _p, _p]
     L.orc_equity.argtypes = [_i, _i, _i, _p, _p, _p, _p]
     L.orc_mtilde.argtypes = [_i, _i, _p, _p]
+    L.orc_cut.argtypes = [_i, _i, _p, _p, _p, _p]
+    L.orc_mbar.argtypes = [_i, _i, _p, _p]
     L.orc_penalty_bonus.argtypes = [_i, _p, _p, _p, C.c_double, C.c_double, _i, _p, _p]
     L.orc_grad_S.argtypes = [_i, _i, _i, _p, _p, _p, _p, _p, C.POINTER(Params), _ll, _p]
     L.orc_update.argtypes = [_i, _i, _i, C.POINTER(Params), _ll, _p, _p, _p]
     L.orc_step.argtypes = [_i, _i, _i, _p, _p, C.POINTER(Params), _ll, _i, _p,
-                           _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
+                           _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
     L.orc_run.restype = _ll
     L.orc_run.argtypes = [_i, _i, _i, _p, _p, C.POINTER(Params), C.POINTER(_ll), _ll,
                           _i, _p, _p, C.POINTER(_ll), C.POINTER(_ll)]
@@ -106,7 +110,8 @@ def _f64(a):
 
 
 def make_params(**kw) -> Params:
-    """Parameter block; defaults are the GCP column of Table 2 (rho = 100)."""
+    """Parameter block; defaults are the GCP column of Table 2 (rho = 100).
+    problem: 0 k-COL, 1 ECP, 2 k-partitioning, 3 balanced k-partitioning."""
     d = dict(problem=0, sigma0=0.01, eta=1e-3, alpha=2.5, lambda_=1e-5,
              beta=1.2, mu=1e-6, nu=0.0, rho=100.0, nb_iter=5, bonus_diag=1)
     if "lambda" in kw:
@@ -159,6 +164,24 @@ def equity(colors, k):
     E = np.empty((D, k), np.int32)
     _check(lib().orc_equity(D, n, k, _ptr(colors), _ptr(sizes), _ptr(f), _ptr(E)), "equity")
     return sizes, f, E
+
+
+def cut(rowptr, colidx, colors):
+    """Cut edges per individual (k-partitioning fitness, Section 7)."""
+    rowptr, colidx, colors = _i32(rowptr), _i32(colidx), _i32(colors)
+    D, n = colors.shape
+    f = np.empty((D,), np.int64)
+    _check(lib().orc_cut(D, n, _ptr(rowptr), _ptr(colidx), _ptr(colors), _ptr(f)), "cut")
+    return f
+
+
+def mbar(colors):
+    """sum_d (J - M_d): pairs in different groups, per individual count."""
+    colors = _i32(colors)
+    D, n = colors.shape
+    M = np.empty((n, n), np.int32)
+    _check(lib().orc_mbar(D, n, _ptr(colors), _ptr(M)), "mbar")
+    return M
 
 
 def mtilde(colors):
@@ -216,7 +239,7 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
     out = dict(
         colors=np.empty((D, n), np.int32), gamma_own=np.empty((D, n), np.int32),
         f_color=np.empty((D,), np.int64), f_eq=np.empty((D,), np.int64),
-        Mt=np.empty((n, n), np.int32),
+        f_cut=np.empty((D,), np.int64), Mt=np.empty((n, n), np.int32),
         G=np.empty((D, n, k), np.float64) if want_G else None,
         gW=np.empty((D, n, k), np.float64) if want_G else None)
     loss, kappa, varpi = C.c_double(), C.c_double(), C.c_double()
@@ -224,7 +247,8 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
     _check(lib().orc_step(D, n, k, _ptr(rowptr), _ptr(colidx), C.byref(params), t,
                           int(stop_on_legal), _ptr(W),
                           _ptr(out["colors"]), _ptr(out["gamma_own"]), _ptr(out["f_color"]),
-                          _ptr(out["f_eq"]), _ptr(out["Mt"]), _ptr(out["G"]), _ptr(out["gW"]),
+                          _ptr(out["f_eq"]), _ptr(out["f_cut"]), _ptr(out["Mt"]), _ptr(out["G"]),
+                          _ptr(out["gW"]),
                           C.byref(loss), C.byref(kappa), C.byref(varpi),
                           C.byref(fmin), C.byref(dstar), C.byref(upd)), "step")
     out.update(W=W, loss=loss.value, kappa=kappa.value, varpi=varpi.value,

@@ -112,6 +112,24 @@ int orc_fitness(int D, int n, int k, const int *adj_off, const int *adj,
     return 0;
 }
 
+/* k-partitioning fitness (Section 7): M_d replaced by \bar M_d = J - M_d,
+ * f(S_d) = 1/2 sum(A (.) \bar M_d) = edges whose ends lie in different
+ * groups (cut edges), counted here directly from the adjacency lists. */
+int orc_cut(int D, int n, const int *adj_off, const int *adj, const int *colors, long long *cut)
+{
+    if (D < 0 || n < 0 || !colors || !cut)
+        return ORC_EBADARG;
+    for (int d = 0; d < D; ++d) {
+        long long twice = 0;
+        const int *c = colors + (size_t)d * n;
+        for (int i = 0; i < n; ++i)
+            for (int e = adj_off[i]; e < adj_off[i + 1]; ++e)
+                twice += (c[adj[e]] != c[i]);
+        cut[d] = twice / 2;
+    }
+    return 0;
+}
+
 /* Equity fitness (eq. 3) and its gradient (eq. 14). */
 int orc_equity(int D, int n, int k, const int *colors,
                int *sizes, long long *f_eq, int *E)
@@ -154,6 +172,23 @@ int orc_mtilde(int D, int n, const int *colors, int *Mt)
             for (int d = 0; d < D; ++d)
                 s += (colors[(size_t)d * n + i] == colors[(size_t)d * n + m]);
             Mt[(size_t)i * n + m] = s;
+        }
+    return 0;
+}
+
+/* The k-partitioning counterpart of eq. 4 (Section 7: M replaced by
+ * \bar M = J - M): Mb[i*n+m] = sum_d (1 - m_{d,i,m}) = #{d : c_d(i) != c_d(m)};
+ * Mb[i*n+i] = 0. */
+int orc_mbar(int D, int n, const int *colors, int *Mb)
+{
+    if (D < 0 || n < 0 || !colors || !Mb)
+        return ORC_EBADARG;
+    for (int i = 0; i < n; ++i)
+        for (int m = 0; m < n; ++m) {
+            int s = 0;
+            for (int d = 0; d < D; ++d)
+                s += (colors[(size_t)d * n + i] != colors[(size_t)d * n + m]);
+            Mb[(size_t)i * n + m] = s;
         }
     return 0;
 }
@@ -211,13 +246,19 @@ int orc_penalty_bonus(int n, const int *adj_off, const int *adj, const int *Mt,
 }
 
 /* eq. 13: grad_S L = A.S + nu t grad f_eq + 2 alpha lambda t (A (.) Mt^(alpha-1)).S
- *                    - 2 beta mu t (\bar A (.) Mt^(beta-1)).S                     */
+ *                    - 2 beta mu t (\bar A (.) Mt^(beta-1)).S
+ * k-partitioning (problem 2 or 3, Section 7): every M_d of eq. 7 becomes
+ * J - M_d, so Mt here is \bar M~ = sum_d (J - M_d) (orc_mbar) and, since
+ * d(J - M_d)/dS_d = -dM_d/dS_d, every term but the equity one changes sign:
+ * grad_S L = -A.S + nu t grad f_eq - 2 alpha lambda t (A (.) Mt^(alpha-1)).S
+ *            + 2 beta mu t (\bar A (.) Mt^(beta-1)).S                           */
 int orc_grad_S(int D, int n, int k, const int *adj_off, const int *adj,
                const int *colors, const int *Mt, const int *E,
                const orc_params *p, long long t, double *G)
 {
     if (D < 0 || n < 0 || k < 1 || !colors || !Mt || !p || !G)
         return ORC_EBADARG;
+    const double sg = (p->problem == 2 || p->problem == 3) ? -1.0 : 1.0;
     const double tt = (double)t;
     const double cpen = 2.0 * p->alpha * p->lambda_ * tt;
     const double cbon = 2.0 * p->beta * p->mu * tt;
@@ -252,7 +293,7 @@ int orc_grad_S(int D, int n, int k, const int *adj_off, const int *adj,
                 g[j] = 0.0;
             /* (A . S_d)[i, j]: one count per neighbour of colour j */
             for (int e = adj_off[i]; e < adj_off[i + 1]; ++e)
-                g[c[adj[e]]] += 1.0;
+                g[c[adj[e]]] += sg;
             /* nu t d f_eq / d s_{d,i,j} (eq. 14), the same for every vertex */
             if (E && ceq != 0.0)
                 for (int j = 0; j < k; ++j)
@@ -263,10 +304,10 @@ int orc_grad_S(int D, int n, int k, const int *adj_off, const int *adj,
                 int mt = Mt[(size_t)i * n + m];
                 if (mark[m]) {
                     if (cpen != 0.0)
-                        g[c[m]] += ca[mt];
+                        g[c[m]] += sg * ca[mt];
                 } else if (m != i || p->bonus_diag) {
                     if (cbon != 0.0)
-                        g[c[m]] -= cb[mt];
+                        g[c[m]] -= sg * cb[mt];
                 }
             }
         }
@@ -321,21 +362,24 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
              const orc_params *p, long long t, int stop_on_legal,
              double *W,
              int *colors, int *gamma_own, long long *f_color, long long *f_eq,
-             int *Mt, double *G, double *gW,
+             long long *f_cut, int *Mt, double *G, double *gW,
              double *loss, double *kappa, double *varpi,
              long long *f_min, int *d_star, int *updated)
 {
-    if (D < 1 || n < 0 || k < 1 || !p || !W)
+    if (D < 1 || n < 0 || k < 1 || !p || !W || p->problem < 0 || p->problem > 3)
         return ORC_EBADARG;
+    const int part = p->problem == 2 || p->problem == 3; /* k-partitioning */
     const size_t Dn = (size_t)D * n, Dk = (size_t)D * k, nn = (size_t)n * n;
     int rc = 0;
     int *c = colors ? colors : (int *)malloc(sizeof(int) * (Dn ? Dn : 1));
     long long *fc = f_color ? f_color : (long long *)malloc(sizeof(long long) * D);
     long long *fe = f_eq ? f_eq : (long long *)malloc(sizeof(long long) * D);
+    long long *fx = f_cut ? f_cut : (long long *)malloc(sizeof(long long) * D);
     int *E = (int *)malloc(sizeof(int) * (Dk ? Dk : 1));
     int *M = Mt ? Mt : (int *)malloc(sizeof(int) * (nn ? nn : 1));
+    int *Mb = part ? (int *)malloc(sizeof(int) * (nn ? nn : 1)) : NULL;
     double *Gr = G ? G : (double *)malloc(sizeof(double) * (Dn * k > 0 ? Dn * k : 1));
-    if (!c || !fc || !fe || !E || !M || !Gr) {
+    if (!c || !fc || !fe || !fx || !E || !M || (part && !Mb) || !Gr) {
         rc = ORC_ENOMEM;
         goto out;
     }
@@ -343,11 +387,16 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
     orc_assign(D, n, k, W, c);
     /* Step 2 */
     orc_fitness(D, n, k, adj_off, adj, c, gamma_own, fc);
+    orc_cut(D, n, adj_off, adj, c, fx);
     orc_equity(D, n, k, c, NULL, fe, E);
+    /* the fitness each problem minimises: f_color (k-COL), f_color + f_eq
+     * (ECP), cut edges (k-partitioning), cut edges + f_eq (balanced) */
+    long long *fobj = part ? fx : fc;
+    const int with_eq = p->problem == 1 || p->problem == 3;
     long long fmin = -1;
     int dstar = 0;
     for (int d = 0; d < D; ++d) {
-        long long f = fc[d] + (p->problem == 1 ? fe[d] : 0);
+        long long f = fobj[d] + (with_eq ? fe[d] : 0);
         if (fmin < 0 || f < fmin) {
             fmin = f;
             dstar = d;
@@ -357,14 +406,17 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
         *f_min = fmin;
     if (d_star)
         *d_star = dstar;
-    /* Step 3 */
+    /* Step 3 (the partitioning terms use \bar M~ in place of M~) */
     orc_mtilde(D, n, c, M);
+    if (part)
+        orc_mbar(D, n, c, Mb);
+    const int *X = part ? Mb : M;
     double ks = 0.0, vs = 0.0;
-    orc_penalty_bonus(n, adj_off, adj, M, p->alpha, p->beta, p->bonus_diag, &ks, &vs);
+    orc_penalty_bonus(n, adj_off, adj, X, p->alpha, p->beta, p->bonus_diag, &ks, &vs);
     {
         double sc = 0.0, se = 0.0;
         for (int d = 0; d < D; ++d) {
-            sc += (double)fc[d];
+            sc += (double)fobj[d];
             se += (double)fe[d];
         }
         const double tt = (double)t;
@@ -375,7 +427,7 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
         if (varpi)
             *varpi = vs;
     }
-    orc_grad_S(D, n, k, adj_off, adj, c, M, E, p, t, Gr);
+    orc_grad_S(D, n, k, adj_off, adj, c, X, E, p, t, Gr);
     /* Step 4 unless the population already holds a legal solution */
     if (stop_on_legal && fmin == 0) {
         if (updated)
@@ -391,6 +443,8 @@ out:
     if (c != colors) free(c);
     if (fc != f_color) free(fc);
     if (fe != f_eq) free(fe);
+    if (fx != f_cut) free(fx);
+    free(Mb);
     free(E);
     if (M != Mt) free(M);
     if (Gr != G) free(Gr);
@@ -413,7 +467,7 @@ long long orc_run(int D, int n, int k, const int *adj_off, const int *adj,
         long long fmin = 0;
         int dstar = 0, upd = 0;
         int rc = orc_step(D, n, k, adj_off, adj, p, *t, stop_on_legal, W, c,
-                          NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
+                          NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
                           &fmin, &dstar, &upd);
         if (rc) {
             free(c);

@@ -24,7 +24,8 @@ extern "C" {
 #endif
 
 typedef struct {
-    int problem;        /* 0 = k-COL (GCP), 1 = ECP                         */
+    int problem;        /* 0 = k-COL (GCP), 1 = ECP, 2 = k-partitioning,
+                           3 = balanced k-partitioning (Section 7)          */
     double sigma0;      /* std of the N(0, sigma0) initial weights (Table 2) */
     double eta;         /* learning rate                                      */
     double alpha;       /* penalisation exponent  (eq. 5)                     */
@@ -54,6 +55,10 @@ int orc_gamma(int D, int n, int k, const int *adj_off, const int *adj,
 int orc_fitness(int D, int n, int k, const int *adj_off, const int *adj,
                 const int *colors, int *gamma_own, long long *f_color);
 
+/* k-partitioning fitness (Section 7): cut[d] = edges whose ends lie in
+ * different groups of individual d, 1/2 sum(A (.) (J - M_d)). */
+int orc_cut(int D, int n, const int *adj_off, const int *adj, const int *colors, long long *cut);
+
 /* Equity (eq. 3, eq. 14): sizes[d*k+j] = #V_{d,j}; f_eq[d]; E[d*k+j] in
  * {-1,0,+1} = d f_eq / d s_{d,i,j}.  c1 = floor(n/k), c2 = ceil(n/k). */
 int orc_equity(int D, int n, int k, const int *colors,
@@ -62,6 +67,10 @@ int orc_equity(int D, int n, int k, const int *colors,
 /* Step 3-i (eq. 4): Mt[i*n+m] = #{d : c_d(i) == c_d(m)}; Mt[i*n+i] = D. */
 int orc_mtilde(int D, int n, const int *colors, int *Mt);
 
+/* k-partitioning counterpart of eq. 4 (Section 7, M -> J - M):
+ * Mb[i*n+m] = #{d : c_d(i) != c_d(m)}; Mb[i*n+i] = 0. */
+int orc_mbar(int D, int n, const int *colors, int *Mb);
+
 /* eq. 5 and eq. 6 over ordered pairs (i, m):
  * kappa = sum a_im Mt^alpha, varpi = sum (1 - a_im) Mt^beta
  * (diagonal of \bar A included iff bonus_diag). */
@@ -69,7 +78,10 @@ int orc_penalty_bonus(int n, const int *adj_off, const int *adj, const int *Mt,
                       double alpha, double beta, int bonus_diag,
                       double *kappa, double *varpi);
 
-/* eq. 13: grad_S L for the one-hot population at iteration t, D*n*k. */
+/* eq. 13: grad_S L for the one-hot population at iteration t, D*n*k.  For
+ * the k-partitioning problems (2, 3) Mt must be \bar M~ (orc_mbar) and the
+ * A.S, penalty and bonus terms change sign (derivative of eq. 7 with every
+ * M_d replaced by J - M_d); the equity term keeps its sign. */
 int orc_grad_S(int D, int n, int k, const int *adj_off, const int *adj,
                const int *colors, const int *Mt, const int *E,
                const orc_params *p, long long t, double *G);
@@ -81,15 +93,19 @@ int orc_update(int D, int n, int k, const orc_params *p, long long t,
                const double *G, double *W, double *gW);
 
 /* One full iteration at counter t on W (in/out).  Every output may be NULL.
- * loss = f_color(S) + nu t f_eq(S) + lambda t kappa - mu t varpi  (eq. 7).
- * f[d] = f_color + (problem == ECP ? f_eq : 0); *f_min, *d_star = lowest
- * d attaining it.  If stop_on_legal and f_min == 0 the weights are left
- * untouched and *updated = 0 (Algorithm 1 stop rule), else *updated = 1. */
+ * loss = f(S) + nu t f_eq(S) + lambda t kappa - mu t varpi  (eq. 7), with
+ * f = f_color (problems 0, 1) or the cut edges f_cut (problems 2, 3, whose
+ * kappa and varpi are taken over \bar M~).  The fitness minimised per
+ * individual is f_color (k-COL), f_color + f_eq (ECP), f_cut
+ * (k-partitioning) or f_cut + f_eq (balanced); *f_min, *d_star = lowest d
+ * attaining it.  Mt always receives M~ (eq. 4).  If stop_on_legal and
+ * f_min == 0 the weights are left untouched and *updated = 0 (Algorithm 1
+ * stop rule), else *updated = 1. */
 int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
              const orc_params *p, long long t, int stop_on_legal,
              double *W,
              int *colors, int *gamma_own, long long *f_color, long long *f_eq,
-             int *Mt, double *G, double *gW,
+             long long *f_cut, int *Mt, double *G, double *gW,
              double *loss, double *kappa, double *varpi,
              long long *f_min, int *d_star, int *updated);
 
