@@ -120,6 +120,37 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def fp8_library_tflops(dev, N=8192):
+    """Dense FP8 throughput of the vendor library on this GPU: torch._scaled_mm
+    (cuBLASLt) on E4M3 N x N x N with tensor-wise scales, best of 10 launches
+    timed with CUDA events after 3 warm-ups (2 N^3 flops each)."""
+    import torch
+    try:
+        g = torch.Generator(device=dev).manual_seed(0)
+        a = torch.randn(N, N, device=dev, generator=g).to(torch.float8_e4m3fn)
+        b = torch.randn(N, N, device=dev, generator=g).to(torch.float8_e4m3fn).t()  # column-major operand
+        one = torch.ones((), device=dev, dtype=torch.float32)
+
+        def mm():
+            return torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+
+        for _ in range(3):
+            mm()
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mm()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return {"tflops": 2.0 * N ** 3 / (best * 1e-3) / 1e12, "ms": best,
+                "how": f"torch._scaled_mm e4m3 {N}^3, tensor-wise scales, bf16 out, best of 10"}
+    except Exception as e:  # the library may lack an FP8 kernel for this GPU
+        return {"tflops": None, "error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -343,6 +374,10 @@ def run_ours(args):
                                    "mtilde_tflops": fl_m / (us_m * 1e-6) / 1e12,
                                    "peak_source": ("measured bf16 x 2 (fp8/bf16 nominal ratio)"
                                                    if peaks else "fallback")}
+                    lib8 = fp8_library_tflops(dev)
+                    tensor_roof["fp8_library"] = lib8
+                    if lib8.get("tflops"):
+                        tensor_roof["frac_of_fp8_library"] = ach / lib8["tflops"]
         ctx.tc_set_params(p)
         forms["chosen"] = max((f for f in forms if f != "chosen"), key=lambda f: forms[f]["value"])
 

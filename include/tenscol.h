@@ -52,6 +52,14 @@ extern "C" {
 /* ---- problems and step forms -------------------------------------------- */
 #define TC_KCOL 0 /* k-colouring, GCP by k-descent (Section 3.5: f = f_color) */
 #define TC_ECP 1  /* equitable colouring (eq. 3: f = f_color + f_eq)          */
+/* k-partitioning (Section 7): Algorithm 1 with every M_d = S_d S_d^T of
+ * eq. 1-7 replaced by J - M_d.  The fitness is the number of cut edges
+ * (edges between different groups), the penalty and bonus of eq. 5-6 are
+ * taken over sum_d (J - M_d) = D J - M~, and eq. 13's A.S, penalty and bonus
+ * terms change sign.  The balanced variant adds f_eq of eq. 3 to the
+ * fitness (and nu t grad f_eq to the gradient, as for the ECP). */
+#define TC_KPART 2     /* f = cut edges                                      */
+#define TC_KPART_BAL 3 /* f = cut edges + f_eq                               */
 
 /* How steps 2-3 and the products of eq. 13 are computed.  All forms give
  * identical colours, conflicts and fitness and the same W step to FP32
@@ -67,7 +75,7 @@ extern "C" {
 
 /* Parameters of Table 2 of the paper plus the run policy. */
 typedef struct {
-    int problem;     /* TC_KCOL or TC_ECP                                    */
+    int problem;     /* TC_KCOL, TC_ECP, TC_KPART or TC_KPART_BAL            */
     float sigma0;    /* std of the N(0, sigma0) initial weights (Section 3.2)*/
     float eta;       /* learning rate (Section 3.7)                          */
     float alpha;     /* penalisation exponent, > 1 (eq. 5)                   */
@@ -86,7 +94,9 @@ typedef struct tc_ctx tc_ctx; /* opaque: one graph + one population */
 
 /* Fills *p with Table 2's column for `problem` (GCP: mu = 1e-6, nu = 0;
  * ECP: mu = 0, nu = 1e-5), rho = 100, stop_on_legal = 1, bonus_diag = 1,
- * form = TC_FORM_ONEHOT.  Returns TC_ERR_ARG for a NULL p or bad problem. */
+ * form = TC_FORM_ONEHOT.  The paper gives no parameters for partitioning:
+ * TC_KPART takes the GCP column, TC_KPART_BAL the GCP column with the ECP's
+ * nu = 1e-5.  Returns TC_ERR_ARG for a NULL p or bad problem. */
 int tc_params_default(tc_params *p, int problem);
 
 /* Creates a context on CUDA device `device` with its own stream.
@@ -128,11 +138,13 @@ int tc_set_params(tc_ctx *ctx, const tc_params *p);
  * individual is tracked on the device at every evaluated iteration. */
 int tc_step(tc_ctx *ctx, int64_t n_iters, int64_t *iters_done);
 
-/* Best-so-far individual over all evaluated iterations (lowest d among
- * ties, first iteration reaching the value): coloring[n] (caller-owned),
- * its f_color and f_eq, the individual index and the iteration t at which it
- * was seen.  Any output pointer may be NULL.  TC_ERR_STATE if no iteration
- * has been evaluated yet. */
+/* Best-so-far individual over all evaluated iterations (lowest fitness f
+ * of the problem, lowest d among ties, first iteration reaching the value):
+ * coloring[n] (caller-owned), its f_color (monochromatic edges; for the
+ * partitioning problems the cut edges are |E| - f_color) and f_eq, the
+ * individual index and the iteration t at which it was seen.  Any output
+ * pointer may be NULL.  TC_ERR_STATE if no iteration has been evaluated
+ * yet. */
 int tc_best(tc_ctx *ctx, int32_t *coloring, int64_t *conflicts, int64_t *equity,
             int32_t *individual, int64_t *iteration);
 
@@ -197,7 +209,8 @@ int tc_st_grad_dev(tc_ctx *ctx, float *gradW_dev, float *loss_dev);
  * (nu ignored): loss_dev[4] = L, kappa, varpi, f_color; gradW_dev = dL/dW
  * (eq. 13 through the softmax Jacobian).  Device pointers of D*n*k floats;
  * uses the graph and parameters of the context, k <= 128.  Allocates and
- * frees its own temporaries; the population is not touched. */
+ * frees its own temporaries; the population is not touched.  TC_ERR_ARG for
+ * the partitioning problems. */
 int tc_relaxed_dev(tc_ctx *ctx, const float *W_dev, float tau, int64_t t, float *loss_dev,
                    float *gradW_dev);
 
@@ -240,27 +253,33 @@ int tc_set_graph_chunk(tc_ctx *ctx, int chunk);
  * Algorithm 1 with stop_on_legal for at most max_iters iterations; a legal
  * colouring (f_color = 0, and f_eq = 0 for the ECP) moves on to k - 1, the
  * first k without one within the budget ends the descent.  *p as for
- * tc_init_population (NULL: Table 2 for TC_KCOL); stop_on_legal is forced
- * on.  Outputs (any may be NULL): *k_best the smallest k solved (-1 if
- * none), coloring[n] its legal colouring, *iters_total the iterations run.
- * The context keeps the population of the last k tried. */
+ * tc_init_population (NULL: Table 2 for TC_KCOL; TC_ERR_ARG for the
+ * partitioning problems); stop_on_legal is forced on.  Outputs (any may be
+ * NULL): *k_best the smallest k solved (-1 if none), coloring[n] its legal
+ * colouring, *iters_total the iterations run.  The context keeps the
+ * population of the last k tried. */
 int tc_kdescent(tc_ctx *ctx, uint64_t seed, int D, int k_start, int k_min, int64_t max_iters,
                 const tc_params *p, int32_t *k_best, int32_t *coloring, int64_t *iters_total);
 
 /* The plan the autotuner chose for the dense contractions of this context
  * (tc_init_population / tc_set_params time every candidate on the context's
- * own operands and keep the fastest; the FP32 form keeps one fixed plan):
- *   plan[0] Gamma column tile (128 or 256)   plan[1] Gamma cluster size
- *   plan[2] M~ column tile                    plan[3] M~ cluster size
- *   plan[4] M~ K splits                       plan[5] candidates timed
+ * own operands and keep the fastest; the FP32 form keeps one fixed plan).
+ * `plan` has 8 entries:
+ *   plan[0] Gamma unit rows: 128 (one CTA per unit) or 256 (a CTA pair
+ *           running 256-row cta_group::2 MMAs)
+ *   plan[1] Gamma column tile (128 or 256)   plan[2] Gamma cluster size
+ *   plan[3..5] the same for M~               plan[6] M~ K splits
+ *   plan[7] candidates timed
  *   us[0], us[1]: best times of Gamma and M~ in microseconds (0 for FP32).
  * TC_ERR_STATE when the context has no dense form. */
 int tc_dense_plan(tc_ctx *ctx, int32_t *plan, float *us);
 
-/* Pins the plan of the dense contractions: plan[0..4] as above (the FP8
- * form accepts column tiles 128 / 256, Gamma clusters 1 / 2 / 4 dividing
- * the row tiles, M~ clusters 1 / 2 (2 with 256-wide tiles), K splits
- * 1 .. D k / 128; the FP32 form only 256, 1, 256, 1, s).  TC_ERR_ARG for a
+/* Pins the plan of the dense contractions: plan[0..6] as above.  The FP8
+ * form accepts, per contraction, unit rows 128 with column tile 128 / 256
+ * and clusters sharing the B tile (Gamma: 1 / 2 / 4 dividing the 128-row
+ * tiles; M~: 1, or 2 with 256-wide tiles), or unit rows 256 with column tile
+ * 128 / 256 and cluster 2 (the pair); K splits 1 .. D k / 128.  The FP32
+ * form takes only 128, 256, 1 for both and any K split.  TC_ERR_ARG for a
  * plan outside these, TC_ERR_STATE without a dense form.  Kept until the
  * next tc_init_population or form change, which tune again. */
 int tc_dense_set_plan(tc_ctx *ctx, const int32_t *plan);

@@ -7,21 +7,25 @@
 // FP8 E4M3 represents exactly; FP32 accumulation is exact below 2^24, so the
 // results are the exact integer counts.
 //
-//   k_gemm_tc    tcgen05.mma (kind::f8f6f4, M = 128, N = 256, K = 32) on the
-//                5th-generation tensor cores: persistent CTA per SM, warp 0
-//                streams 128B-swizzled K-major tiles with TMA into a 4-stage
-//                shared-memory ring, warp 1 issues the MMAs into one of two
-//                TMEM accumulators (2 x 256 columns), warps 2-5 drain the other
-//                accumulator (tcgen05.ld) and store it.
+//   k_gemm_tc    tcgen05.mma (kind::f8f6f4, K = 32) on the 5th-generation
+//                tensor cores: persistent CTA per SM, warp 0 streams
+//                128B-swizzled K-major tiles with TMA into a shared-memory
+//                ring of ~192 KB, warp 1 issues the MMAs into one of two TMEM
+//                accumulators, warps 2-5 drain the other (tcgen05.ld) into
+//                shared memory and warp 6 stores it with TMA.  Units of 128
+//                rows run on one CTA (M = 128, N = 128 / 256, clusters
+//                sharing the B tile by multicast) or units of 256 rows on a
+//                CTA pair (cta_group::2, M = 256: each CTA loads half of the
+//                B tile, so a CTA moves a third fewer operand bytes per MMA).
 //   k_gemm_simt  the same contraction with FP32 FFMA on the CUDA cores (the
 //                plain FP32 comparator), same work units and epilogues.
 //
 // Work is a host-built list of units (tile row, tile column, first and last
 // K block); the M~ units cover only tiles touching the upper triangle and may
-// split K, their partial sums being added with FP32 atomics (exact: integer
-// values).  Every mbarrier wait is bounded by one second of wall time; on
-// expiry the kernel records TC_ERR_TIMEOUT, drains its MMAs, frees TMEM and
-// returns.
+// split K, their partial sums being added in L2 by TMA reduce-adds (FP32
+// atomics in the comparator; exact either way: integer values).  Every mbarrier wait is bounded by one second of wall
+// time; on expiry the kernel records TC_ERR_TIMEOUT, drains its MMAs, frees
+// TMEM and returns.
 #include <cuda_fp8.h>
 #include <stdint.h>
 
@@ -31,19 +35,32 @@ namespace {
 
 constexpr int BM = 128, BK = 128;  // BK in bytes = FP8 elements
 constexpr int BN = 256;            // column tile of the FP32 comparator and the padding unit
-constexpr int TC_THREADS = 224;  // producer, MMA, four epilogue warps, output warp
+constexpr int TC_THREADS = 192;  // producer, MMA, four epilogue warps
+// Output staging of the tensor-core epilogue: 32 KB after the operand ring,
+// 8 KB per epilogue warp, which stages and sends its own 32 rows without
+// waiting for the other warps: four 2 KB buffers of [32 columns][32 rows]
+// uint16 for Gamma (one TMA store each), or two 4 KB buffers of [32 rows][32
+// floats], 128-byte swizzled, for M~ (one TMA reduce-add each: the split-K
+// partial sums add up in L2).
+constexpr int STG_BYTES = 32768;
+constexpr int STG_WARP = STG_BYTES / 4;
 
 // Tile shapes of the tensor-core GEMM (the column tile BN_ is tuned per
-// context): the stage ring keeps about 192 KB of operands in flight.
-template <int BN_>
+// context).  PAIR: the two CTAs of a cluster pair run one 256-row MMA
+// (cta_group::2): each holds its 128 rows of A and half of the B tile, and
+// its 128 rows of the accumulator.  The stage ring keeps about 192 KB of
+// operands in flight.
+template <int BN_, bool PAIR = false>
 struct TcShape {
-    static constexpr int STAGES = BN_ == 256 ? 4 : 6;
-    static constexpr int A_BYTES = BM * BK, B_BYTES = BN_ * BK, STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int TMEM_COLS = 2 * BN_;  // two BN_-column FP32 accumulators
-    // instruction descriptor: D = F32, A = B = E4M3, both K-major, M = BM, N = BN_
+    static constexpr int B_ROWS = PAIR ? BN_ / 2 : BN_;  // B rows held per CTA
+    static constexpr int A_BYTES = BM * BK, B_BYTES = B_ROWS * BK, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGES = 196608 / STAGE_BYTES;
+    static constexpr int TM = PAIR ? 2 * BM : BM;  // output rows of a unit
+    static constexpr int TMEM_COLS = 2 * BN_;      // two BN_-column FP32 accumulators
+    // instruction descriptor: D = F32, A = B = E4M3, both K-major, M = TM, N = BN_
     static constexpr uint32_t IDESC =
-        (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 32768 + 1024;  // + output staging, alignment
+        (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN_ >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + 1024;  // + output staging, alignment
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -127,6 +144,28 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// Shared::cluster address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+    return r;
+}
+
+// TMA load into this CTA's shared memory whose bytes complete on a barrier
+// of either CTA of the pair (`bar`: shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Arrive on a barrier of another CTA of the cluster (shared::cluster address).
+__device__ __forceinline__ void bar_arrive_remote(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
 // with 128-byte swizzling: rows of 128 bytes, 8-row atoms 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -139,29 +178,70 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// One MMA of the CTA (PAIR = false) or of the CTA pair (PAIR = true, issued
+// by the even CTA; the descriptors name the same offsets in both CTAs).
+template <bool PAIR>
 __device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        int accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (PAIR)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
 }
 
 // Arrives on the barrier at the same offset in every CTA of `mask` once the
 // MMAs issued so far have completed.
+template <bool PAIR>
 __device__ __forceinline__ void mma_commit_mc(uint64_t* b, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            su32(b)),
-        "h"(mask)
-        : "memory");
+    if constexpr (PAIR)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                su32(b)),
+            "h"(mask)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                su32(b)),
+            "h"(mask)
+            : "memory");
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     su32(b))
-                 : "memory");
+    if constexpr (PAIR)
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                     : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                     : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
+    if constexpr (PAIR) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t cols) {
+    if constexpr (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols));
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols));
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -171,6 +251,9 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// 32 lanes x 32 columns of FP32 from TMEM into v (asynchronous: the values
+// are valid after tmem_wait, which names the registers so that no use of
+// them moves above it).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
@@ -182,7 +265,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
           "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
           "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait(uint32_t* v) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]),
+                   "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]),
+                   "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]),
+                   "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
 }
 
 // Gamma entry (row i, column d k + j) in the transposed layout: column-major
@@ -190,12 +283,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
 __device__ __forceinline__ uint16_t* gamma_at(const tc_gemm_args& g, int row, int col) {
     return reinterpret_cast<uint16_t*>(g.C) + (size_t)col * g.rows_alloc + row;
 }
-
-// Output staging of the tensor-core epilogue: 32 KB after the operand ring,
-// four 8 KB buffers of [32 columns][128 rows] uint16 for Gamma (one TMA store
-// each), or two 16 KB buffers of [128 rows][32 floats], 128-byte swizzled, for
-// M~ (one TMA reduce-add each: the split-K partial sums add up in L2).
-constexpr int STG_BYTES = 32768;
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
@@ -213,10 +300,6 @@ __device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, int x,
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ void bulk_wait_read_all() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void st_shared_u16(uint32_t a, uint16_t v) {
@@ -227,20 +310,25 @@ __device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y,
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 
-// CL > 1: the CL CTAs of a cluster take CL units that share the column tile
-// and K range (consecutive in the unit list); each loads 1/CL of the B tile
-// and multicasts it to all, so B crosses L2 once per cluster.
-template <int BN_, int CL>
+// PAIR = false, CL > 1: the CL CTAs of a cluster take CL units that share the
+// column tile and K range (consecutive in the unit list); each loads 1/CL of
+// the B tile and multicasts it to all, so B crosses L2 once per cluster.
+// PAIR = true (CL = 2): the CTA pair takes one 256-row unit; the even CTA
+// waits for both CTAs' operand bytes on its own barriers and issues the
+// cta_group::2 MMAs, whose completion is multicast to the barriers of both;
+// each CTA drains and stores its own 128 rows.
+template <int BN_, int CL, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
               const __grid_constant__ CUtensorMap tmC, tc_gemm_args g) {
-    using Sh = TcShape<BN_>;
+    static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
+    using Sh = TcShape<BN_, PAIR>;
     constexpr int STAGES = Sh::STAGES, A_BYTES = Sh::A_BYTES, B_BYTES = Sh::B_BYTES,
-                  STAGE_BYTES = Sh::STAGE_BYTES, TMEM_COLS = Sh::TMEM_COLS;
+                  STAGE_BYTES = Sh::STAGE_BYTES, TMEM_COLS = Sh::TMEM_COLS, TM = Sh::TM;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 128-byte swizzled tiles need 1024-byte aligned bases
     uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain, sfull[4], sempty[4];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -248,29 +336,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
     const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
     const int group = blockIdx.x / CL, ngroups = gridDim.x / CL;
+    // units of this CTA: PAIR, one per cluster; else one per CTA
+    const int u_first = PAIR ? group : group * CL + (int)crank, u_step = PAIR ? ngroups : ngroups * CL;
+    const bool leader = !PAIR || crank == 0u;
+    const int row_half = PAIR ? (int)crank * BM : 0;  // this CTA's rows inside a unit
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             bar_init(&full[s], 1);
-            bar_init(&empty[s], CL);  // one MMA commit from every CTA of the cluster
+            bar_init(&empty[s], PAIR ? 1 : CL);  // one MMA commit from every CTA issuing into the stage
         }
         for (int a = 0; a < 2; ++a) {
             bar_init(&tfull[a], 1);
-            bar_init(&tempty[a], 4);
-        }
-        for (int b = 0; b < 4; ++b) {
-            bar_init(&sfull[b], 4);   // the four epilogue warps staged their rows
-            bar_init(&sempty[b], 1);  // the TMA store / reduce has read the buffer
+            bar_init(&tempty[a], PAIR ? 8 : 4);  // the epilogue warps of every CTA holding the accumulator
         }
         bar_init(&drain, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
+    if (warp == 1) tmem_alloc<PAIR>(&tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     if (CL > 1) cluster_sync_all();  // peers' barriers initialised before any multicast
@@ -281,28 +365,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {  // TMA producer
             unsigned gk = 0;
             bool ok = true;
-            for (int u = group * CL + (int)crank; u < g.n_units && ok; u += ngroups * CL) {
+            for (int u = u_first; u < g.n_units && ok; u += u_step) {
                 const int4 w = g.units[u];
                 for (int kb = w.z; kb < w.w; ++kb, ++gk) {
                     const int s = gk % STAGES;
                     const unsigned r = gk / STAGES;
                     if (!(ok = bar_wait(&empty[s], (r & 1u) ^ 1u, &abort_flag, g.err))) break;
                     uint8_t* sa = smem + s * STAGE_BYTES;
-                    bar_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(sa, &tmX, kb * BK, w.x * BM, &full[s]);
-                    if (CL == 1)
-                        tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN_, &full[s]);
-                    else  // my slice of the shared B tile, to every CTA of the cluster
-                        tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), &tmY, kb * BK,
-                                       w.y * BN_ + (int)crank * (BN_ / CL), &full[s], cmask);
+                    if constexpr (PAIR) {
+                        // both CTAs' bytes complete on the even CTA's barrier
+                        const uint32_t fb = peer_addr(&full[s], 0u);
+                        if (leader) bar_expect_tx(&full[s], 2 * STAGE_BYTES);
+                        tma_load_2d_pair(sa, &tmX, kb * BK, w.x * TM + row_half, fb);
+                        tma_load_2d_pair(sa + A_BYTES, &tmY, kb * BK, w.y * BN_ + (int)crank * (BN_ / 2), fb);
+                    } else {
+                        bar_expect_tx(&full[s], STAGE_BYTES);
+                        tma_load_2d(sa, &tmX, kb * BK, w.x * BM, &full[s]);
+                        if (CL == 1)
+                            tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN_, &full[s]);
+                        else  // my slice of the shared B tile, to every CTA of the cluster
+                            tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), &tmY, kb * BK,
+                                           w.y * BN_ + (int)crank * (BN_ / CL), &full[s], cmask);
+                    }
                 }
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {  // MMA issuer
+        if (lane == 0 && leader) {  // MMA issuer
             unsigned gk = 0, ui = 0;
             bool ok = true;
-            for (int u = group * CL + (int)crank; u < g.n_units && ok; u += ngroups * CL, ++ui) {
+            for (int u = u_first; u < g.n_units && ok; u += u_step, ++ui) {
                 const int4 w = g.units[u];
                 const int a = ui & 1;
                 const unsigned ua = ui >> 1;
@@ -318,16 +410,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < BK / 32; ++kk)  // +32 bytes = +2 in the address field
-                        mma_f8(dt, ad + 2 * kk, bd + 2 * kk, Sh::IDESC, (kb > w.z || kk > 0) ? 1 : 0);
+                        mma_f8<PAIR>(dt, ad + 2 * kk, bd + 2 * kk, Sh::IDESC, (kb > w.z || kk > 0) ? 1 : 0);
                     if (CL == 1)
-                        mma_commit(&empty[s]);  // stage s is free once these MMAs finish
+                        mma_commit<PAIR>(&empty[s]);  // stage s is free once these MMAs finish
                     else
-                        mma_commit_mc(&empty[s], cmask);  // ... in every CTA it was multicast to
+                        mma_commit_mc<PAIR>(&empty[s], cmask);  // ... in every CTA that holds part of it
                 }
-                if (ok) mma_commit(&tfull[a]);
+                if (ok) {
+                    if (PAIR)
+                        mma_commit_mc<PAIR>(&tfull[a], cmask);  // both CTAs hold rows of the accumulator
+                    else
+                        mma_commit<PAIR>(&tfull[a]);
+                }
             }
             // drain: every issued MMA completes before TMEM is released
-            mma_commit(&drain);
+            mma_commit<PAIR>(&drain);
             const unsigned long long t0 = gns();
             while (!bar_try(&drain, 0)) {
                 if (gns() - t0 > 1000000000ull) {
@@ -336,88 +433,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         }
-    } else if (warp < 6) {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ...
-        // Each 32-column chunk goes through a shared-memory buffer: every warp
-        // writes its 32 rows, then the output warp sends the 128-row block
-        // with one TMA store (Gamma) or reduce-add (M~).
+    } else {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ... 32 (warp % 4) + 31
+        // Each warp drains its 32 rows of the accumulator 32 columns at a
+        // time (the next chunk's TMEM load in flight while the current one is
+        // staged) and sends every chunk with its own TMA store (Gamma) or
+        // reduce-add (M~) from a private buffer: no warp waits for another.
+        // A buffer is reused once the bulk group that read it is done (bulk
+        // groups are per thread: lane 0 issues and waits for them all).
         const int q = warp & 3;
-        const int row_in_tile = 32 * q + lane;
         const bool gamma = g.mode == TC_GEMM_GAMMA;
-        const int nb = gamma ? 4 : 2;
-        const uint32_t bytes_b = gamma ? 8192u : 16384u;
-        const uint32_t stg = su32(smem + STAGES * STAGE_BYTES);
+        const unsigned nb = gamma ? 4u : 2u;              // buffers per warp
+        const uint32_t bytes_b = gamma ? 2048u : 4096u;   // [32 cols][32 rows] u16 | [32 rows][32 f32]
+        const uint32_t stg = su32(smem + STAGES * STAGE_BYTES) + (uint32_t)q * STG_WARP;
+        uint8_t* stg_gen = smem + STAGES * STAGE_BYTES + q * STG_WARP;
         unsigned ui = 0, gc = 0;  // unit and chunk counters
-        for (int u = group * CL + (int)crank; u < g.n_units; u += ngroups * CL, ++ui) {
+        constexpr int NCH = BN_ / 32;
+        for (int u = u_first; u < g.n_units; u += u_step, ++ui) {
+            const int4 w = g.units[u];
             const int a = ui & 1;
             const unsigned ua = ui >> 1;
             if (!bar_wait(&tfull[a], ua & 1u, &abort_flag, g.err)) break;
             tc_fence_after();
-#pragma unroll 1
-            for (int c = 0; c < BN_ / 32; ++c, ++gc) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN_ + 32 * c), v);
-                const int b = (int)(gc % (unsigned)nb);
-                const unsigned use = gc / (unsigned)nb;
-                // the buffer is free once the output warp's TMA operation read it
-                bar_wait(&sempty[b], (use & 1u) ^ 1u, &abort_flag, g.err);
-                if (gamma) {  // [32 columns][128 rows] uint16
-                    const uint32_t base = stg + (uint32_t)b * bytes_b + 2u * (uint32_t)row_in_tile;
+            const int row0 = w.x * TM + row_half + 32 * q;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * BN_);
+            // stage chunk c from v into its buffer and send it
+            auto emit = [&](const uint32_t* v, int c) {
+                const uint32_t b = gc % nb;
+                if (gc >= nb) {  // the group that last read buffer b is nb chunks back
+                    if (lane == 0) {
+                        if (gamma)
+                            asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+                        else
+                            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    }
+                    __syncwarp();
+                }
+                if (gamma) {  // element (column e, row lane) at 2 (32 e + lane)
+                    const uint32_t base = stg + b * bytes_b + 2u * (uint32_t)lane;
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
-                        st_shared_u16(base + 256u * (uint32_t)e, (uint16_t)__float2uint_rn(__uint_as_float(v[e])));
-                } else {  // [128 rows][32 floats], 16-byte chunks swizzled by row mod 8
-                    const uint32_t base = stg + (uint32_t)b * bytes_b + 128u * (uint32_t)row_in_tile;
+                        st_shared_u16(base + 64u * (uint32_t)e, (uint16_t)__float2uint_rn(__uint_as_float(v[e])));
+                } else {  // row lane: 128 bytes, 16-byte chunks swizzled by row mod 8
+                    const uint32_t base = stg + b * bytes_b + 128u * (uint32_t)lane;
 #pragma unroll
                     for (int h = 0; h < 8; ++h)
-                        st_shared_v4(base + 16u * (uint32_t)(h ^ (row_in_tile & 7)), v[4 * h], v[4 * h + 1],
-                                     v[4 * h + 2], v[4 * h + 3]);
+                        st_shared_v4(base + 16u * (uint32_t)(h ^ (lane & 7)), v[4 * h], v[4 * h + 1], v[4 * h + 2],
+                                     v[4 * h + 3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the TMA unit
                 __syncwarp();
-                if (lane == 0) bar_arrive(&sfull[b]);
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) bar_arrive(&tempty[a]);
-        }
-    } else if (lane == 0) {  // output warp: TMA store / reduce of each staged chunk
-        const bool gamma = g.mode == TC_GEMM_GAMMA;
-        const int nb = gamma ? 4 : 2;
-        const int bytes_b = gamma ? 8192 : 16384;
-        uint8_t* stg = smem + STAGES * STAGE_BYTES;
-        unsigned gc = 0;
-        bool ok = true;
-        for (int u = group * CL + (int)crank; u < g.n_units && ok; u += ngroups * CL) {
-            const int4 w = g.units[u];
-            for (int c = 0; c < BN_ / 32; ++c, ++gc) {
-                const int b = (int)(gc % (unsigned)nb);
-                if (!(ok = bar_wait(&sfull[b], (gc / (unsigned)nb) & 1u, &abort_flag, g.err))) break;
-                const int col0 = w.y * BN_ + 32 * c;
-                if (gamma) {
-                    if (col0 < g.cols_alloc)  // columns past D k are padding: not stored
-                        tma_store_2d(&tmC, w.x * BM, col0, stg + b * bytes_b);
+                if (lane == 0) {
+                    const int col0 = w.y * BN_ + 32 * c;
+                    if (!gamma)
+                        tma_reduce_add_2d(&tmC, col0, row0, stg_gen + b * bytes_b);
+                    else if (col0 < g.cols_alloc)  // columns past D k are padding: not stored
+                        tma_store_2d(&tmC, row0, col0, stg_gen + b * bytes_b);
                     else
                         asm volatile("cp.async.bulk.commit_group;" ::: "memory");  // an empty group keeps the count
-                } else {
-                    tma_reduce_add_2d(&tmC, col0, w.x * BM, stg + b * bytes_b);
                 }
-                // every group but the newest nb - 1 has read its buffer: the
-                // chunk nb - 1 back may be overwritten
-                if (gamma)
-                    asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+                __syncwarp();  // converged for the next tcgen05.ld / wait
+                ++gc;
+            };
+            uint32_t v0[32], v1[32];
+            tmem_ld32(tbase, v0);
+#pragma unroll 1
+            for (int c = 0; c < NCH; c += 2) {
+                tmem_wait(v0);
+                tmem_ld32(tbase + (uint32_t)(32 * (c + 1)), v1);  // NCH is even
+                emit(v0, c);
+                tmem_wait(v1);
+                if (c + 2 < NCH) tmem_ld32(tbase + (uint32_t)(32 * (c + 2)), v0);
+                emit(v1, c + 1);
+            }
+            // every TMEM load of this accumulator has completed (waited above)
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (PAIR)  // the accumulator is free once both CTAs drained it
+                    bar_arrive_remote(peer_addr(&tempty[a], 0u));
                 else
-                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-                if (gc + 1 >= (unsigned)nb) bar_arrive(&sempty[(gc + 1 - (unsigned)nb) % (unsigned)nb]);
+                    bar_arrive(&tempty[a]);
             }
         }
-        bulk_wait_all();  // the output is in global memory before the CTA exits
+        if (lane == 0) bulk_wait_all();  // the output is in global memory before the CTA exits
     }
     tc_fence_before();
     __syncthreads();
     if (CL > 1) cluster_sync_all();  // no CTA leaves while peers may still write into it
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        tmem_free<PAIR>(tmem, TMEM_COLS);
     }
 }
 
@@ -536,12 +641,12 @@ int tc_gemm_tile_m() { return BM; }
 int tc_gemm_tile_n() { return BN; }
 int tc_gemm_tile_k() { return BK; }
 
-template <int BN_, int CL>
+template <int BN_, int CL, bool PAIR>
 static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(groups * CL);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = TcShape<BN_>::SMEM;
+    cfg.dynamicSmemBytes = TcShape<BN_, PAIR>::SMEM;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
@@ -552,73 +657,92 @@ static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttrib
     return cfg;
 }
 
-template <int BN_, int CL>
-static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
-                             const tc_gemm_args& g, int slots, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN_, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcShape<BN_>::SMEM);
-    if (e != cudaSuccess) return e;
-    int groups = slots < g.n_units / CL ? slots : g.n_units / CL;
-    if (groups < 1) groups = 1;
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tc_config<BN_, CL>(groups, s, attr);
-    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL>, tmX, tmY, tmC, g);
+// The shared-memory opt-in of a kernel variant, set once per device (a host
+// call per launch would sit between the launches of a step).
+template <int BN_, int CL, bool PAIR>
+static cudaError_t smem_opt_in() {
+    static int done_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev == done_dev) return e;
+    e = cudaFuncSetAttribute(k_gemm_tc<BN_, CL, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcShape<BN_, PAIR>::SMEM);
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
 }
 
-template <int BN_, int CL>
+template <int BN_, int CL, bool PAIR>
+static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                             const tc_gemm_args& g, int slots, cudaStream_t s) {
+    cudaError_t e = smem_opt_in<BN_, CL, PAIR>();
+    if (e != cudaSuccess) return e;
+    const int per_cluster = PAIR ? 1 : CL;  // units a cluster takes per round
+    int groups = slots < g.n_units / per_cluster ? slots : g.n_units / per_cluster;
+    if (groups < 1) groups = 1;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(groups, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL, PAIR>, tmX, tmY, tmC, g);
+}
+
+template <int BN_, int CL, bool PAIR>
 static int slots_tc(int num_sms) {
     // clusters must sit inside one GPC, so fewer than num_sms / CL of them
     // may be resident at once: a grid sized past that runs a second wave
-    if (cudaFuncSetAttribute(k_gemm_tc<BN_, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TcShape<BN_>::SMEM) != cudaSuccess) {
+    if (smem_opt_in<BN_, CL, PAIR>() != cudaSuccess) {
         (void)cudaGetLastError();
         return num_sms / CL;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tc_config<BN_, CL>(num_sms / CL, nullptr, attr);
+    cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(num_sms / CL, nullptr, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<BN_, CL>, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<BN_, CL, PAIR>, &cfg) != cudaSuccess || n < 1) {
         (void)cudaGetLastError();
         return num_sms / CL;
     }
     return n < num_sms / CL ? n : num_sms / CL;
 }
 
-int tc_gemm_cluster_slots(int cluster, int bn, int num_sms) {
+int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms) {
+    if (tm == 2 * BM) return bn == 128 ? slots_tc<128, 2, true>(num_sms) : slots_tc<256, 2, true>(num_sms);
     if (bn == 128) {
         switch (cluster) {
-            case 4: return slots_tc<128, 4>(num_sms);
-            case 2: return slots_tc<128, 2>(num_sms);
-            default: return slots_tc<128, 1>(num_sms);
+            case 4: return slots_tc<128, 4, false>(num_sms);
+            case 2: return slots_tc<128, 2, false>(num_sms);
+            default: return slots_tc<128, 1, false>(num_sms);
         }
     }
     switch (cluster) {
-        case 4: return slots_tc<256, 4>(num_sms);
-        case 2: return slots_tc<256, 2>(num_sms);
-        default: return slots_tc<256, 1>(num_sms);
+        case 4: return slots_tc<256, 4, false>(num_sms);
+        case 2: return slots_tc<256, 2, false>(num_sms);
+        default: return slots_tc<256, 1, false>(num_sms);
     }
 }
 
-// `cluster`: CTAs sharing each B tile (1, 2 or 4); the unit list must come
-// in groups of that many units with equal column tile and K range, and tmY's
-// box must hold bn / cluster rows.  `bn`: the column tile (128 or 256) the
-// units were cut with.  `slots`: clusters launched at most (one wave, from
-// tc_gemm_cluster_slots).  tmC: the output, Gamma transposed [D k][n_pad]
-// uint16 with 128 x 32 boxes, or M~ [n_pad][n_pad] f32 with 32 x 128 boxes,
-// 128-byte swizzled.
+// `tm`: rows of a unit, 128 (one CTA per unit) or 256 (a CTA pair per unit,
+// cta_group::2 MMAs; cluster 2).  `cluster` (tm = 128): CTAs sharing each B
+// tile (1, 2 or 4); the unit list must come in groups of that many units
+// with equal column tile and K range.  tmY's box holds bn / cluster rows
+// (tm = 128) or bn / 2 rows (tm = 256).  `bn`: the column tile (128 or 256)
+// the units were cut with.  `slots`: clusters launched at most (one wave,
+// from tc_gemm_cluster_slots).  tmC: the output, Gamma transposed
+// [D k][n_pad] uint16, or M~ [n_pad][n_pad] f32 128-byte swizzled, both with
+// 32 x 32 boxes (one warp's rows of one 32-column chunk).
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
-                              const tc_gemm_args& g, int slots, int cluster, int bn, cudaStream_t s) {
+                              const tc_gemm_args& g, int slots, int tm, int cluster, int bn, cudaStream_t s) {
+    if (tm == 2 * BM)
+        return bn == 128 ? launch_tc<128, 2, true>(tmX, tmY, tmC, g, slots, s)
+                         : launch_tc<256, 2, true>(tmX, tmY, tmC, g, slots, s);
     if (bn == 128) {
         switch (cluster) {
-            case 4: return launch_tc<128, 4>(tmX, tmY, tmC, g, slots, s);
-            case 2: return launch_tc<128, 2>(tmX, tmY, tmC, g, slots, s);
-            default: return launch_tc<128, 1>(tmX, tmY, tmC, g, slots, s);
+            case 4: return launch_tc<128, 4, false>(tmX, tmY, tmC, g, slots, s);
+            case 2: return launch_tc<128, 2, false>(tmX, tmY, tmC, g, slots, s);
+            default: return launch_tc<128, 1, false>(tmX, tmY, tmC, g, slots, s);
         }
     }
     switch (cluster) {
-        case 4: return launch_tc<256, 4>(tmX, tmY, tmC, g, slots, s);
-        case 2: return launch_tc<256, 2>(tmX, tmY, tmC, g, slots, s);
-        default: return launch_tc<256, 1>(tmX, tmY, tmC, g, slots, s);
+        case 4: return launch_tc<256, 4, false>(tmX, tmY, tmC, g, slots, s);
+        case 2: return launch_tc<256, 2, false>(tmX, tmY, tmC, g, slots, s);
+        default: return launch_tc<256, 1, false>(tmX, tmY, tmC, g, slots, s);
     }
 }
 

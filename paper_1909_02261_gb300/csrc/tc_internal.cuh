@@ -28,6 +28,13 @@ struct tc_dev_state {
     int pad;
 };
 
+// Problems whose Algorithm 1 uses J - M_d in place of M_d (Section 7), and
+// those whose fitness includes f_eq (eq. 3).
+__host__ __device__ inline bool tc_is_partition(int problem) {
+    return problem == TC_KPART || problem == TC_KPART_BAL;
+}
+__host__ __device__ inline bool tc_has_equity(int problem) { return problem == TC_ECP || problem == TC_KPART_BAL; }
+
 // Everything a kernel of the step needs, passed by value.
 struct tc_kparams {
     int n, D, k;
@@ -35,6 +42,7 @@ struct tc_kparams {
     int ct_bytes;     // bytes per colour in cT: 1 when k <= 255, else 2
     int adj_words;    // 32-bit words per adjacency-bitmask row
     int problem, nb_iter, bonus_diag, stop_on_legal, commit;
+    long long n_edges;  // |E| (the partitioning fitness is |E| - f_color)
     int csr_walk;     // grad_S L by adjacency lists (mu = 0, sparse graph)
     float eta, rho, lambda_, mu, nu, alpha, beta;
     float* W;                 // weights, tile-transposed (tc_w_index)
@@ -56,10 +64,12 @@ struct tc_kparams {
     float* loss_part;         // 2 x n_pair_blocks partial kappa / varpi
     int n_pair_blocks;
     const int2* pair_tiles;   // upper-triangular 32x32 tile list
-    const float* lutA;        // [0..D]: 2 alpha v^(alpha-1)
-    const float* lutB;        // [0..D]: 2 beta v^(beta-1)
-    const float* powA;        // [0..D]: v^alpha
-    const float* powB;        // [0..D]: v^beta
+    // tables over v = m~ in [0..D], with x = v for the colouring problems and
+    // x = D - v (the entry of sum_d (J - M_d)) for the partitioning problems
+    const float* lutA;        // 2 alpha x^(alpha-1)
+    const float* lutB;        // 2 beta x^(beta-1)
+    const float* powA;        // x^alpha
+    const float* powB;        // x^beta
     tc_dev_state* st;
     uint16_t* best;           // n best-so-far colours
     // dense forms (NULL in the one-hot form)
@@ -147,12 +157,18 @@ struct tc_gemm_args {
     int rows_alloc, cols_alloc;
     int* err;
 };
+// Shape of one contraction's work: rows of a unit (128 on one CTA, 256 on a
+// CTA pair), column tile, CTAs per cluster (sharing the B tile, or the pair).
+struct tc_gemm_shape {
+    int tm = 128, bn = 256, cl = 1;
+    bool operator==(const tc_gemm_shape& o) const { return tm == o.tm && bn == o.bn && cl == o.cl; }
+};
 int tc_gemm_tile_m();
 int tc_gemm_tile_n();
 int tc_gemm_tile_k();
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
-                              const tc_gemm_args& g, int slots, int cluster, int bn, cudaStream_t s);
-int tc_gemm_cluster_slots(int cluster, int bn, int num_sms);
+                              const tc_gemm_args& g, int slots, int tm, int cluster, int bn, cudaStream_t s);
+int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);
 cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s);

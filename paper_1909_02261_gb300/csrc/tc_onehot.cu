@@ -218,10 +218,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
                                       : acc[a][b];
     }
 
-    // pair coefficient of eq. 13 and loss terms of eq. 5-6
+    // pair coefficient of eq. 13 and loss terms of eq. 5-6; the partitioning
+    // problems (M_d -> J - M_d, tables over D - m~) negate every term
     const long long t = P.st->t;
     const float cA = (float)((double)P.lambda_ * (double)t);
     const float cB = (float)((double)P.mu * (double)t);
+    const float sg = tc_is_partition(P.problem) ? -1.0f : 1.0f;
     const int pad = P.Dp - D;  // padded colour slots always compare equal
     float kap = 0.f, var = 0.f;
     __syncthreads();  // s_a / s_b are reused as transpose tiles
@@ -238,19 +240,20 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
             if (i < n && m < n && (I < M || ml >= il)) {
                 mt = from_gemm ? __float2int_rn(P.M32[(size_t)i * P.ldm + m])
                                : (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
+                mt = min(max(mt, 0), D);  // a count of individuals: the tables hold D + 1 entries
                 const bool edge = (P.adj[(size_t)i * P.adj_words + (m >> 5)] >> (m & 31)) & 1u;
                 if (m == i) {
                     mt = D;
                     if (P.bonus_diag) {
-                        bb = -cB * P.lutB[D];
+                        bb = -sg * (cB * P.lutB[D]);
                         var += P.powB[D];
                     }
                 } else if (edge) {
                     // the A.S term enters through B only in the one-hot form
-                    bb = from_gemm ? cA * P.lutA[mt] : fmaf(cA, P.lutA[mt], 1.0f);
+                    bb = sg * (from_gemm ? cA * P.lutA[mt] : fmaf(cA, P.lutA[mt], 1.0f));
                     kap += 2.0f * P.powA[mt];
                 } else {
-                    bb = -cB * P.lutB[mt];
+                    bb = -sg * (cB * P.lutB[mt]);
                     var += 2.0f * P.powB[mt];
                 }
                 P.B[(size_t)i * P.ldb + m] = bb;
@@ -326,13 +329,17 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
     long long fc = 0, fe = 0;
     unsigned long long key = ~0ull;
     float ka = 0.f, va = 0.f;
+    const bool part = tc_is_partition(P.problem), with_eq = tc_has_equity(P.problem);
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         // k_gsum summed gamma_d(i) over the vertices: each conflict twice
         const int a = __ldcg(P.fcolor + d) / 2, b = __ldcg(P.feq + d);
         P.fcolor[d] = a;
         fc += a;
         fe += b;
-        const unsigned long long f = (unsigned long long)(a + (P.problem == TC_ECP ? b : 0));
+        // the fitness of the problem: monochromatic or (partitioning) cut edges,
+        // plus f_eq for the ECP and the balanced partitioning
+        const long long fobj = part ? P.n_edges - a : (long long)a;
+        const unsigned long long f = (unsigned long long)(fobj + (with_eq ? b : 0));
         const unsigned long long kk = (f << 32) | (unsigned)d;
         key = kk < key ? kk : key;
     }
@@ -371,7 +378,8 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
         const int fmin = (int)(key >> 32), dstar = (int)(key & 0xffffffffu);
         const long long t = st->t;
         const double tt = (double)t;
-        st->loss = (float)fc + (float)((double)P.nu * tt) * (float)fe +
+        const long long fsum = part ? (long long)D * P.n_edges - fc : fc;  // the fitness term of eq. 7
+        st->loss = (float)fsum + (float)((double)P.nu * tt) * (float)fe +
                    (float)((double)P.lambda_ * tt) * ka - (float)((double)P.mu * tt) * va;
         st->kappa = ka;
         st->varpi = va;
@@ -616,11 +624,12 @@ __device__ __forceinline__ void fence_proxy_async() {
 // shared panel), else `bstride`.  STG: pm, of and xs (= nu t E_dj) are the
 // warp's shared-memory copies; else pm, of in global memory and xs unused
 // (Ed, nut give the equity term).  Gout[j * 32] receives the class sum + nu t
-// E_dj (+ the gamma-matrix entry in the dense forms).
+// E_dj (+ gs times the gamma-matrix entry in the dense forms: gs = -1 for the
+// partitioning problems, whose A.S term changes sign).
 template <int BS, bool STG>
 __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const float* xs, const int8_t* Ed,
-                                           const uint16_t* grow, int gstride, const float* Bl, int bstride,
-                                           float nut, int k, int jb, int je, float* Gout) {
+                                           const uint16_t* grow, float gs, int gstride, const float* Bl,
+                                           int bstride, float nut, int k, int jb, int je, float* Gout) {
     const int bs = BS > 0 ? BS : bstride;
     if (jb >= je) return;
     int s = STG ? of[jb] : __ldg(of + jb);
@@ -644,7 +653,7 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
             extra = nut * (float)__ldg(Ed + j);
         }
         if (grow) {
-            extra += (float)g0;
+            extra += gs * (float)g0;
             g0 = g1;
             g1 = g2;
             g2 = g3;
@@ -682,8 +691,8 @@ __device__ __forceinline__ uint4 lds_u32x4(uint32_t a) {
 // lists both in shared memory), on 32-bit shared addresses: the B entry of
 // vertex v for this lane sits at bl + 128 v.
 __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, const float* xs,
-                                                  const uint16_t* grow, int gstride, uint32_t bl, int k, int jb,
-                                                  int je, float* Gout) {
+                                                  const uint16_t* grow, float gs, int gstride, uint32_t bl, int k,
+                                                  int jb, int je, float* Gout) {
     if (jb >= je) return;
     uint32_t p = pm + 4u * (uint32_t)of[jb];
     uint32_t e = pm + 4u * (uint32_t)of[jb + 1];
@@ -698,7 +707,7 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
         const uint32_t e_next = pm + 4u * (uint32_t)of[j + 2 <= k ? j + 2 : k];
         float extra = xs[j];
         if (grow) {
-            extra += (float)g0;
+            extra += gs * (float)g0;
             g0 = g1;
             g1 = g2;
             g2 = g3;
@@ -725,11 +734,12 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
 // additions per iteration instead of D n^2.  Accumulates in Gs[j * 32].
 // Also counts gamma_d(i) (eq. 1): the neighbours sharing i's colour.
 __device__ __forceinline__ int neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
-                                              const int8_t* Ed, const uint16_t* grow, int gstride, const float* Bl,
-                                              int bstride, float nut, int k, float* Gs, int i, bool valid) {
+                                              const int8_t* Ed, const uint16_t* grow, float gs, int gstride,
+                                              const float* Bl, int bstride, float nut, int k, float* Gs, int i,
+                                              bool valid) {
     for (int j = 0; j < k; ++j) {
         float g0 = nut * (float)__ldg(Ed + j);
-        if (grow) g0 += (float)__ldg(grow + (size_t)j * gstride);
+        if (grow) g0 += gs * (float)__ldg(grow + (size_t)j * gstride);
         Gs[j * 32] = g0;
     }
     if (!valid) return 0;
@@ -758,17 +768,18 @@ __device__ __forceinline__ int neighbour_sums(const int* rowptr, const int* coli
 
 // gamma_d(i) (eq. 1) from the individual's class lists: the members of i's
 // own class that are adjacent to i.  In the one-hot form the pair matrix
-// tells them apart exactly: B_im >= 1 on edges (1 + lambda t (...) >= 1) and
-// B_im <= 0 off them (-mu t (...) <= 0, the diagonal, the padding row).
+// tells them apart exactly: sg B_im >= 1 on edges (1 + lambda t (...) >= 1)
+// and sg B_im <= 0 off them (-mu t (...) <= 0, the diagonal, the padding
+// row), sg = -1 for the partitioning problems (whose B is negated), else 1.
 template <bool STG>
 __device__ __forceinline__ int own_class_conflicts(const uint32_t* pm, const int* of, int ci, const float* Bl,
-                                                   int bstride) {
+                                                   int bstride, float sg) {
     const int s = STG ? of[ci] : __ldg(of + ci), e = STG ? of[ci + 1] : __ldg(of + ci + 1);
     int conf = 0;
     for (int p = s; p < e; p += 4) {  // padded class: whole 4-wide chunks
         const uint4 v = STG ? *reinterpret_cast<const uint4*>(pm + p) : __ldg(reinterpret_cast<const uint4*>(pm + p));
-        conf += (Bl[(int)v.x * bstride] >= 0.5f) + (Bl[(int)v.y * bstride] >= 0.5f) +
-                (Bl[(int)v.z * bstride] >= 0.5f) + (Bl[(int)v.w * bstride] >= 0.5f);
+        conf += (sg * Bl[(int)v.x * bstride] >= 0.5f) + (sg * Bl[(int)v.y * bstride] >= 0.5f) +
+                (sg * Bl[(int)v.z * bstride] >= 0.5f) + (sg * Bl[(int)v.w * bstride] >= 0.5f);
     }
     return conf;
 }
@@ -876,6 +887,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             // the item's gamma entries: colour j of row i0 + lane at grow[j * gstride]
             const uint16_t* grow = P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad, k) : nullptr;
             const int gstride = P.n_pad;
+            const float gs = tc_is_partition(P.problem) ? -1.0f : 1.0f;  // sign of the A.S term
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
             const bool live = lane < rows;
             const int bstride = BTS ? 32 : P.ldb;
@@ -883,8 +895,8 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
             if (CSR) {
-                conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, gstride, Bl, bstride, nut, k,
-                                      Gw + lane, i0 + lane, live);
+                conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, gs, gstride, Bl,
+                                      bstride, nut, k, Gw + lane, i0 + lane, live);
                 __syncwarp();
                 for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
                 __syncwarp();
@@ -893,13 +905,13 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 const int kh = min(k, (k + 4) >> 1), jb = STG ? h * kh : 0, je = STG ? (h ? k : kh) : k;
                 if (STG) {
                     if (BTS)
-                        class_sums_shared(smem_u32(ps), os, xs, grow, gstride, smem_u32(Bl), k, jb, je, Gout);
+                        class_sums_shared(smem_u32(ps), os, xs, grow, gs, gstride, smem_u32(Bl), k, jb, je, Gout);
                     else
-                        class_sums<0, true>(ps, os, xs, Ed, grow, gstride, Bl, P.ldb, nut, k, jb, je, Gout);
+                        class_sums<0, true>(ps, os, xs, Ed, grow, gs, gstride, Bl, P.ldb, nut, k, jb, je, Gout);
                 } else if (BTS) {
-                    class_sums<32, false>(pm, of, nullptr, Ed, grow, gstride, Bl, 32, nut, k, 0, k, Gout);
+                    class_sums<32, false>(pm, of, nullptr, Ed, grow, gs, gstride, Bl, 32, nut, k, 0, k, Gout);
                 } else {
-                    class_sums<0, false>(pm, of, nullptr, Ed, grow, gstride, Bl, P.ldb, nut, k, 0, k, Gout);
+                    class_sums<0, false>(pm, of, nullptr, Ed, grow, gs, gstride, Bl, P.ldb, nut, k, 0, k, Gout);
                 }
                 if (counter) {
                     conf = 0;
@@ -907,9 +919,9 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                         if (P.G16)
                             conf = __ldg(grow + (size_t)ci * gstride);  // the gamma matrix of the dense forms
                         else if (STG)
-                            conf = own_class_conflicts<true>(ps, os, ci, Bl, bstride);
+                            conf = own_class_conflicts<true>(ps, os, ci, Bl, bstride, gs);
                         else
-                            conf = own_class_conflicts<false>(pm, of, ci, Bl, bstride);
+                            conf = own_class_conflicts<false>(pm, of, ci, Bl, bstride, gs);
                     }
                 }
             }

@@ -66,8 +66,7 @@ struct tc_ctx {
     int4* d_units_g = nullptr;
     int4* d_units_m = nullptr;
     int n_units_g = 0, n_units_m = 0;
-    int cl_g = 1, cl_m = 1;      // cluster sizes sharing B tiles (Gamma, M~)
-    int bn_g = 256, bn_m = 256;  // column tiles of the two contractions
+    tc_gemm_shape sh_g, sh_m;    // tiles and clusters of the two contractions (Gamma, M~)
     int split_m = 1;             // K splits of M~
     int slots_g = 0, slots_m = 0;  // clusters of those sizes resident at once
     int tune_candidates = 0;       // configurations timed by the autotuner
@@ -200,7 +199,7 @@ void free_graph(tc_ctx* c) {
 }
 
 int check_params(const tc_params* p) {
-    if (p->problem != TC_KCOL && p->problem != TC_ECP) return TC_ERR_ARG;
+    if (p->problem < TC_KCOL || p->problem > TC_KPART_BAL) return TC_ERR_ARG;
     if (!(p->eta >= 0.f) || !(p->rho >= 1.f) || p->nb_iter < 1) return TC_ERR_ARG;
     if (!(p->alpha > 1.f) || !(p->beta > 1.f)) return TC_ERR_ARG;
     if (!(p->lambda_ >= 0.f) || !(p->mu >= 0.f) || !(p->nu >= 0.f) || !(p->sigma0 >= 0.f))
@@ -220,6 +219,7 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.ct_bytes = c->k <= 255 ? 1 : 2;
     P.adj_words = c->adj_words;
     P.problem = c->p.problem;
+    P.n_edges = c->nnz / 2;
     P.nb_iter = c->p.nb_iter;
     P.bonus_diag = c->p.bonus_diag;
     P.stop_on_legal = c->p.stop_on_legal;
@@ -281,16 +281,16 @@ std::vector<int4> units_gamma(int mt, int nt, int kblocks) {
     return u;
 }
 
-// Work units of M~ = S_cat . S_cat^T: the (row, column) tiles touching the
-// upper triangle, each K range split `split` ways (partial sums added with
-// atomics).  With bn = 2 BM every column holds an even number of such row
-// tiles, so row pairs share the column tile (clusters of 2).
-std::vector<int4> units_mtilde(int mt, int bn, int ntm, int kblocks, int split) {
-    const int BMt = tc_gemm_tile_m();
+// Work units of M~ = S_cat . S_cat^T: the (row, column) tiles of tm x bn
+// touching the upper triangle, each K range split `split` ways (partial sums
+// added in L2 by the TMA reduce).  With tm = 128 and bn = 256 every column
+// holds an even number of such row tiles, so row pairs share the column tile
+// (clusters of 2).
+std::vector<int4> units_mtilde(int mt, int tm, int bn, int ntm, int kblocks, int split) {
     std::vector<int2> tri;
     for (int c = 0; c < ntm; ++c)
         for (int bm = 0; bm < mt; ++bm)
-            if ((long long)c * bn + bn - 1 >= (long long)bm * BMt) tri.push_back(make_int2(bm, c));
+            if ((long long)c * bn + bn - 1 >= (long long)bm * tm) tri.push_back(make_int2(bm, c));
     std::vector<int4> u;
     for (int sidx = 0; sidx < split; ++sidx)
         for (auto& tt : tri) {
@@ -306,96 +306,119 @@ int upload_units(tc_ctx* c, int4* dst, const std::vector<int4>& u) {
 }
 
 // Whether a plan suits the context's dense form and sizes.
-bool plan_valid(const tc_ctx* c, int bn_g, int cl_g, int bn_m, int cl_m, int split) {
-    const int mt = c->n_pad / tc_gemm_tile_m(), km = c->ldg / tc_gemm_tile_k();
-    if (c->p.form == TC_FORM_DENSE_FP32)  // the CUDA-core comparator: 128 x 256 tiles
-        return bn_g == 256 && cl_g == 1 && bn_m == 256 && cl_m == 1 && split >= 1 && split <= km;
-    if ((bn_g != 128 && bn_g != 256) || (bn_m != 128 && bn_m != 256)) return false;
-    if ((cl_g != 1 && cl_g != 2 && cl_g != 4) || mt % cl_g) return false;
-    if ((cl_m != 1 && cl_m != 2) || (cl_m == 2 && bn_m != 256)) return false;
-    return split >= 1 && split <= km;
+bool shape_valid(const tc_ctx* c, const tc_gemm_shape& q, bool mtilde) {
+    const int BMt = tc_gemm_tile_m();
+    if (q.bn != 128 && q.bn != 256) return false;
+    if (q.tm == 2 * BMt) return q.cl == 2 && c->n_pad % q.tm == 0;  // a CTA pair per unit
+    if (q.tm != BMt) return false;
+    if (mtilde) return q.cl == 1 || (q.cl == 2 && q.bn == 256);
+    return (q.cl == 1 || q.cl == 2 || q.cl == 4) && (c->n_pad / BMt) % q.cl == 0;
 }
 
-// Makes a plan current: unit lists, the multicast operands' tensor maps,
-// resident cluster counts.
-int apply_plan(tc_ctx* c, int bn_g, int cl_g, int bn_m, int cl_m, int split) {
+bool plan_valid(const tc_ctx* c, const tc_gemm_shape& g, const tc_gemm_shape& m, int split) {
+    const int km = c->ldg / tc_gemm_tile_k();
+    if (split < 1 || split > km) return false;
+    if (c->p.form == TC_FORM_DENSE_FP32) {  // the CUDA-core comparator: 128 x 256 tiles
+        const tc_gemm_shape f;
+        return g == f && m == f;
+    }
+    return shape_valid(c, g, false) && shape_valid(c, m, true);
+}
+
+// Box rows of the B operand each CTA loads: its slice of the shared tile
+// (cluster multicast) or its half of the pair's tile.
+int b_box_rows(const tc_gemm_shape& q) { return q.tm == 2 * tc_gemm_tile_m() ? q.bn / 2 : q.bn / q.cl; }
+
+std::vector<int4> plan_units_gamma(const tc_ctx* c, const tc_gemm_shape& q) {
+    return units_gamma(c->n_pad / q.tm, (int)(c->ldg / q.bn), c->n_pad / tc_gemm_tile_k());
+}
+
+std::vector<int4> plan_units_mtilde(const tc_ctx* c, const tc_gemm_shape& q, int kblocks, int split) {
+    return units_mtilde(c->n_pad / q.tm, q.tm, q.bn, c->n_pad / q.bn, kblocks, split);
+}
+
+// Makes a plan current: unit lists, the B operands' tensor maps, resident
+// cluster counts.
+int apply_plan(tc_ctx* c, const tc_gemm_shape& sg, const tc_gemm_shape& sm, int split) {
     const int BKt = tc_gemm_tile_k();
-    const int n_pad = c->n_pad, mt = n_pad / tc_gemm_tile_m();
+    const int n_pad = c->n_pad;
     const long long ldg = c->ldg;
     const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
-    const std::vector<int4> ug = units_gamma(mt, (int)(ldg / bn_g), n_pad / BKt);
-    const std::vector<int4> um = units_mtilde(mt, bn_m, n_pad / bn_m, (int)(ldg / BKt), split);
+    const std::vector<int4> ug = plan_units_gamma(c, sg);
+    const std::vector<int4> um = plan_units_mtilde(c, sm, (int)(ldg / BKt), split);
     int rc;
     if ((rc = upload_units(c, c->d_units_g, ug)) || (rc = upload_units(c, c->d_units_m, um))) return rc;
-    if ((rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, bn_g / cl_g, sw)) ||
-        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, bn_m / cl_m, sw)))
+    if ((rc = tc_encode_tmap_2d(&c->tmS8T, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, b_box_rows(sg), sw)) ||
+        (rc = tc_encode_tmap_2d(&c->tmS8y, u8, c->d_S8, ldg, n_pad, ldg, BKt, b_box_rows(sm), sw)))
         return rc;
     c->n_units_g = (int)ug.size();
     c->n_units_m = (int)um.size();
-    c->bn_g = bn_g;
-    c->cl_g = cl_g;
-    c->bn_m = bn_m;
-    c->cl_m = cl_m;
+    c->sh_g = sg;
+    c->sh_m = sm;
     c->split_m = split;
-    c->slots_g = tc_gemm_cluster_slots(cl_g, bn_g, c->num_sms);
-    c->slots_m = tc_gemm_cluster_slots(cl_m, bn_m, c->num_sms);
+    c->slots_g = tc_gemm_cluster_slots(sg.tm, sg.cl, sg.bn, c->num_sms);
+    c->slots_m = tc_gemm_cluster_slots(sm.tm, sm.cl, sm.bn, c->num_sms);
     TC_CHECK(cudaStreamSynchronize(c->stream));
     return TC_OK;
 }
 
 // Autotuner of the FP8 tensor-core contractions: times every candidate
-// (column tile 128 or 256, cluster size sharing the B tile, K splits of M~)
-// on the context's own operands, one warm-up and three timed launches each,
-// and keeps the fastest (the shapes differ from instance to instance).  The
-// FP32 comparator keeps the 128 x 256 tiles.
+// (128-row units on one CTA with column tile 128 or 256 and clusters
+// sharing the B tile, or 256-row units on a CTA pair; K splits of M~) on the
+// context's own operands, one warm-up and three timed launches each, and
+// keeps the fastest (the shapes differ from instance to instance).  The FP32
+// comparator keeps the 128 x 256 tiles.
 int plan_dense(tc_ctx* c) {
     const int BMt = tc_gemm_tile_m(), BKt = tc_gemm_tile_k();
     const int n_pad = c->n_pad;
     const long long ldg = c->ldg;
-    const int mt = n_pad / BMt, kg = n_pad / BKt, km = (int)(ldg / BKt);
+    const int km = (int)(ldg / BKt);
     const CUtensorMapDataType u8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
     int rc;
     if ((rc = tc_encode_tmap_2d(&c->tmA8, u8, c->d_A8, n_pad, n_pad, n_pad, BKt, BMt, sw)) ||
         (rc = tc_encode_tmap_2d(&c->tmS8x, u8, c->d_S8, ldg, n_pad, ldg, BKt, BMt, sw)) ||
-        // outputs: Gamma transposed [D k][n_pad] uint16 in 128-row x 32-column
-        // boxes, M~ [n_pad][n_pad] f32 in 32-column x 128-row swizzled boxes
+        // outputs: Gamma transposed [D k][n_pad] uint16 and M~ [n_pad][n_pad]
+        // f32 (128-byte swizzled), each in boxes of 32 rows x 32 columns
         (rc = tc_encode_tmap_2d(&c->tmG16, CU_TENSOR_MAP_DATA_TYPE_UINT16, c->d_G16, n_pad,
-                                (uint64_t)c->D * c->k, 2ull * n_pad, 128, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) ||
+                                (uint64_t)c->D * c->k, 2ull * n_pad, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) ||
         (rc = tc_encode_tmap_2d(&c->tmM32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c->d_M32, n_pad, n_pad, 4ull * n_pad, 32,
-                                128, sw)))
+                                32, sw)))
         return rc;
-    auto split_for = [&](int bn, int cl, int slots) {
-        const int tri = (int)units_mtilde(mt, bn, n_pad / bn, 1, 1).size();
-        return std::max(1, std::min((slots * cl + tri - 1) / tri, km));
-    };
+    // CTAs resident at once for a shape, and the triangle's tile count
+    auto ctas = [&](const tc_gemm_shape& q) { return tc_gemm_cluster_slots(q.tm, q.cl, q.bn, c->num_sms) * q.cl; };
+    auto tri_tiles = [&](const tc_gemm_shape& q) { return (int)plan_units_mtilde(c, q, 1, 1).size(); };
     struct Cand {
-        int bn, cl, split;
+        tc_gemm_shape q;
+        int split;
     };
     std::vector<Cand> cg, cm;
     const bool tc = c->p.form == TC_FORM_DENSE_FP8;
     if (tc) {
-        for (int bn : {256, 128})
-            for (int cl : {1, 2, 4})
-                if (mt % cl == 0) cg.push_back({bn, cl, 1});
-        for (int bn : {256, 128})
-            for (int cl : {1, 2}) {
-                if (cl == 2 && bn != 256) continue;
-                // splits around the one that fills the resident CTAs: those
-                // that give one or two full waves, and fewer (less reduction)
-                const int slots = tc_gemm_cluster_slots(cl, bn, c->num_sms) * cl;
-                const int tri = (int)units_mtilde(mt, bn, n_pad / bn, 1, 1).size();
-                std::vector<int> sps = {std::max(1, slots / tri), std::max(1, 2 * slots / tri),
-                                        split_for(bn, cl, slots / cl), std::max(1, slots / tri / 2)};
-                std::sort(sps.begin(), sps.end());
-                sps.erase(std::unique(sps.begin(), sps.end()), sps.end());
-                for (int sp : sps)
-                    if (sp <= km) cm.push_back({bn, cl, sp});
-            }
+        std::vector<tc_gemm_shape> shapes;
+        for (int bn : {256, 128}) {
+            for (int cl : {1, 2, 4}) shapes.push_back({BMt, bn, cl});
+            shapes.push_back({2 * BMt, bn, 2});
+        }
+        for (const tc_gemm_shape& q : shapes)
+            if (shape_valid(c, q, false)) cg.push_back({q, 1});
+        for (const tc_gemm_shape& q : shapes) {
+            if (!shape_valid(c, q, true)) continue;
+            // splits around the one that fills the resident CTAs: those that
+            // give one or two full waves of units, and fewer (less reduction)
+            const int slots = ctas(q) / (q.tm == 2 * BMt ? 2 : 1), tri = tri_tiles(q);
+            std::vector<int> sps = {slots / tri, 2 * slots / tri, (slots + tri - 1) / tri, slots / tri / 2};
+            for (int& sp : sps) sp = std::max(1, std::min(sp, km));  // 1 .. K blocks
+            std::sort(sps.begin(), sps.end());
+            sps.erase(std::unique(sps.begin(), sps.end()), sps.end());
+            for (int sp : sps) cm.push_back({q, sp});
+        }
+        if (cg.empty() || cm.empty()) return TC_ERR_UNSUPPORTED;  // no shape fits (n_pad is a multiple of 256)
     } else {
-        cg.push_back({256, 1, 1});
-        cm.push_back({256, 1, split_for(256, 1, c->num_sms)});
+        const tc_gemm_shape f;
+        cg.push_back({f, 1});
+        cm.push_back({f, std::max(1, std::min((c->num_sms + tri_tiles(f) - 1) / tri_tiles(f), km))});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     TC_CHECK(cudaEventCreate(&e0));
@@ -430,16 +453,16 @@ int plan_dense(tc_ctx* c) {
     rc = TC_OK;
     for (const Cand& q : cg) {
         if (!tc) break;
-        const std::vector<int4> u = units_gamma(mt, (int)(ldg / q.bn), kg);
+        const std::vector<int4> u = plan_units_gamma(c, q.q);
         CUtensorMap tmY;
-        const int slots = tc_gemm_cluster_slots(q.cl, q.bn, c->num_sms);
-        if ((rc = tc_encode_tmap_2d(&tmY, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, q.bn / q.cl, sw)) ||
+        const int slots = tc_gemm_cluster_slots(q.q.tm, q.q.cl, q.q.bn, c->num_sms);
+        if ((rc = tc_encode_tmap_2d(&tmY, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, b_box_rows(q.q), sw)) ||
             (rc = upload_units(c, c->d_units_g, u)))
             break;
         tc_gemm_args g = {c->d_units_g, (int)u.size(), TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
                           &c->d_st->err};
-        const float ms =
-            time_it([&] { return tc_launch_gemm_tc(c->tmA8, tmY, c->tmG16, g, slots, q.cl, q.bn, c->stream); });
+        const float ms = time_it(
+            [&] { return tc_launch_gemm_tc(c->tmA8, tmY, c->tmG16, g, slots, q.q.tm, q.q.cl, q.q.bn, c->stream); });
         ++timed;
         if (ms >= 0.f && ms < best_g) {
             best_g = ms;
@@ -448,16 +471,16 @@ int plan_dense(tc_ctx* c) {
     }
     for (const Cand& q : cm) {
         if (!tc || rc) break;
-        const std::vector<int4> u = units_mtilde(mt, q.bn, n_pad / q.bn, km, q.split);
+        const std::vector<int4> u = plan_units_mtilde(c, q.q, km, q.split);
         CUtensorMap tmY;
-        const int slots = tc_gemm_cluster_slots(q.cl, q.bn, c->num_sms);
-        if ((rc = tc_encode_tmap_2d(&tmY, u8, c->d_S8, ldg, n_pad, ldg, BKt, q.bn / q.cl, sw)) ||
+        const int slots = tc_gemm_cluster_slots(q.q.tm, q.q.cl, q.q.bn, c->num_sms);
+        if ((rc = tc_encode_tmap_2d(&tmY, u8, c->d_S8, ldg, n_pad, ldg, BKt, b_box_rows(q.q), sw)) ||
             (rc = upload_units(c, c->d_units_m, u)))
             break;
         tc_gemm_args g = {c->d_units_m, (int)u.size(), TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
                           &c->d_st->err};
-        const float ms =
-            time_it([&] { return tc_launch_gemm_tc(c->tmS8x, tmY, c->tmM32, g, slots, q.cl, q.bn, c->stream); });
+        const float ms = time_it(
+            [&] { return tc_launch_gemm_tc(c->tmS8x, tmY, c->tmM32, g, slots, q.q.tm, q.q.cl, q.q.bn, c->stream); });
         ++timed;
         if (ms >= 0.f && ms < best_m) {
             best_m = ms;
@@ -468,7 +491,7 @@ int plan_dense(tc_ctx* c) {
     cudaEventDestroy(e1);
     if (rc) return rc;
     if (tc && (best_g >= 1e30f || best_m >= 1e30f)) return TC_ERR_CUDA;  // no configuration ran
-    if ((rc = apply_plan(c, pick_g.bn, pick_g.cl, pick_m.bn, pick_m.cl, pick_m.split))) return rc;
+    if ((rc = apply_plan(c, pick_g.q, pick_m.q, pick_m.split))) return rc;
     c->tune_candidates = timed;
     c->tune_us_g = tc ? 1e3f * best_g : 0.f;
     c->tune_us_m = tc ? 1e3f * best_m : 0.f;
@@ -536,8 +559,10 @@ int upload_luts(tc_ctx* c) {
     const int D1 = c->D + 1;
     std::vector<float> h(4 * (size_t)D1);
     const double a = c->p.alpha, b = c->p.beta;
+    const bool part = tc_is_partition(c->p.problem);
     for (int v = 0; v < D1; ++v) {
-        const double x = (double)v;
+        // v = m~; the partitioning problems weigh sum_d (J - M_d) = D - m~
+        const double x = part ? (double)(c->D - v) : (double)v;
         h[v] = (float)(2.0 * a * pow(x, a - 1.0));
         h[D1 + v] = (float)(2.0 * b * pow(x, b - 1.0));
         h[2 * D1 + v] = (float)pow(x, a);
@@ -623,12 +648,14 @@ int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
     if (which == 0) {
         TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, s));
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, c->tmM32, gm, c->slots_m, c->cl_m, c->bn_m, s)
+            return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, c->tmM32, gm, c->slots_m, c->sh_m.tm, c->sh_m.cl,
+                                          c->sh_m.bn, s)
                       : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, s);
         }, s));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
-            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, c->tmG16, gg, c->slots_g, c->cl_g, c->bn_g, s)
+            return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, c->tmG16, gg, c->slots_g, c->sh_g.tm, c->sh_g.cl,
+                                          c->sh_g.bn, s)
                       : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, s);
         }, s));
     }
@@ -820,7 +847,7 @@ const char* tc_strerror(int code) {
 }
 
 int tc_params_default(tc_params* p, int problem) {
-    if (!p || (problem != TC_KCOL && problem != TC_ECP)) return TC_ERR_ARG;
+    if (!p || problem < TC_KCOL || problem > TC_KPART_BAL) return TC_ERR_ARG;
     memset(p, 0, sizeof(*p));
     p->problem = problem;
     p->sigma0 = 0.01f;
@@ -829,7 +856,7 @@ int tc_params_default(tc_params* p, int problem) {
     p->lambda_ = 1e-5f;
     p->beta = 1.2f;
     p->mu = problem == TC_ECP ? 0.0f : 1e-6f;
-    p->nu = problem == TC_ECP ? 1e-5f : 0.0f;
+    p->nu = tc_has_equity(problem) ? 1e-5f : 0.0f;
     p->rho = 100.0f;
     p->nb_iter = 5;
     p->stop_on_legal = 1;
@@ -1364,6 +1391,7 @@ int tc_st_grad_dev(tc_ctx* c, float* gradW_dev, float* loss_dev) {
 int tc_relaxed_dev(tc_ctx* c, const float* W_dev, float tau, int64_t t, float* loss_dev, float* gradW_dev) {
     if (!c || !W_dev || !loss_dev || !gradW_dev || !(tau > 0.f) || t < 0) return TC_ERR_ARG;
     if (!c->pop) return TC_ERR_STATE;
+    if (tc_is_partition(c->p.problem)) return TC_ERR_ARG;  // the relaxation covers the GCP terms
     if (c->k > 128) return TC_ERR_UNSUPPORTED;
     DeviceGuard g(c->device);
     const int n = c->n;
@@ -1409,6 +1437,7 @@ int tc_kdescent(tc_ctx* c, uint64_t seed, int D, int k_start, int k_min, int64_t
     p.stop_on_legal = 1;
     int rc = check_params(&p);
     if (rc) return rc;
+    if (tc_is_partition(p.problem)) return TC_ERR_ARG;  // k-descent is for the colouring problems
     std::vector<int32_t> col(c->n);
     long long total = 0;
     for (int k = k_start; k >= k_min; --k) {
@@ -1430,12 +1459,9 @@ int tc_kdescent(tc_ctx* c, uint64_t seed, int D, int k_start, int k_min, int64_t
 int tc_dense_plan(tc_ctx* c, int32_t* plan, float* us) {
     if (!c || !plan) return TC_ERR_ARG;
     if (!c->pop || !c->d_M32) return TC_ERR_STATE;
-    plan[0] = c->bn_g;
-    plan[1] = c->cl_g;
-    plan[2] = c->bn_m;
-    plan[3] = c->cl_m;
-    plan[4] = c->split_m;
-    plan[5] = c->tune_candidates;
+    const int v[8] = {c->sh_g.tm, c->sh_g.bn, c->sh_g.cl, c->sh_m.tm, c->sh_m.bn, c->sh_m.cl, c->split_m,
+                      c->tune_candidates};
+    memcpy(plan, v, sizeof(v));
     if (us) {
         us[0] = c->tune_us_g;
         us[1] = c->tune_us_m;
@@ -1446,14 +1472,16 @@ int tc_dense_plan(tc_ctx* c, int32_t* plan, float* us) {
 int tc_dense_set_plan(tc_ctx* c, const int32_t* plan) {
     if (!c || !plan) return TC_ERR_ARG;
     if (!c->pop || !c->d_M32) return TC_ERR_STATE;
-    if (!plan_valid(c, plan[0], plan[1], plan[2], plan[3], plan[4])) return TC_ERR_ARG;
+    const tc_gemm_shape sg{plan[0], plan[1], plan[2]}, sm{plan[3], plan[4], plan[5]};
+    if (!plan_valid(c, sg, sm, plan[6])) return TC_ERR_ARG;
     DeviceGuard g(c->device);
     TC_CHECK(cudaStreamSynchronize(c->stream));
-    const int old[5] = {c->bn_g, c->cl_g, c->bn_m, c->cl_m, c->split_m};
-    int rc = apply_plan(c, plan[0], plan[1], plan[2], plan[3], plan[4]);
+    const tc_gemm_shape og = c->sh_g, om = c->sh_m;
+    const int osplit = c->split_m;
+    int rc = apply_plan(c, sg, sm, plan[6]);
     if (rc) {
         (void)cudaGetLastError();
-        apply_plan(c, old[0], old[1], old[2], old[3], old[4]);
+        apply_plan(c, og, om, osplit);
         return rc;
     }
     drop_graph_exec(c);

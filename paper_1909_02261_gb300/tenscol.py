@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 TC_OK = 0
-TC_KCOL, TC_ECP = 0, 1
+TC_KCOL, TC_ECP, TC_KPART, TC_KPART_BAL = 0, 1, 2, 3  # problems (tenscol.h)
 TC_FORM_ONEHOT, TC_FORM_DENSE_FP8, TC_FORM_DENSE_FP32 = 0, 1, 2
 TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE, TC_KID_GEMM_M, TC_KID_GEMM_G, TC_KID_GSUM = range(6)
 KERNEL_NAMES = {TC_KID_PAIRS: "k_pairs", TC_KID_CLASSES: "k_classes", TC_KID_UPDATE: "k_update",
@@ -277,15 +277,18 @@ class TensCol:
 
     def tc_dense_plan(self):
         """The autotuned plan of the dense contractions (see tenscol.h)."""
-        plan = np.zeros(6, np.int32)
+        plan = np.zeros(8, np.int32)
         us = np.zeros(2, np.float32)
         _ck(self._L.tc_dense_plan(self.h, _ptr(plan), _ptr(us)), "tc_dense_plan")
-        return dict(gamma_tile_n=int(plan[0]), gamma_cluster=int(plan[1]), mtilde_tile_n=int(plan[2]),
-                    mtilde_cluster=int(plan[3]), mtilde_splits=int(plan[4]), candidates=int(plan[5]),
-                    gamma_us=float(us[0]), mtilde_us=float(us[1]))
+        return dict(gamma_tile_m=int(plan[0]), gamma_tile_n=int(plan[1]), gamma_cluster=int(plan[2]),
+                    mtilde_tile_m=int(plan[3]), mtilde_tile_n=int(plan[4]), mtilde_cluster=int(plan[5]),
+                    mtilde_splits=int(plan[6]), candidates=int(plan[7]), gamma_us=float(us[0]),
+                    mtilde_us=float(us[1]))
 
-    def tc_dense_set_plan(self, gamma_tile_n, gamma_cluster, mtilde_tile_n, mtilde_cluster, mtilde_splits):
-        plan = np.array([gamma_tile_n, gamma_cluster, mtilde_tile_n, mtilde_cluster, mtilde_splits], np.int32)
+    def tc_dense_set_plan(self, gamma, mtilde, mtilde_splits):
+        """Pins the plan: `gamma` and `mtilde` are (unit rows, column tile,
+        cluster) triples, e.g. (128, 256, 4) or (256, 256, 2) for a CTA pair."""
+        plan = np.array([*gamma, *mtilde, mtilde_splits], np.int32)
         _ck(self._L.tc_dense_set_plan(self.h, _ptr(plan)), "tc_dense_set_plan")
 
     def tc_launch_count(self) -> int:

@@ -38,12 +38,14 @@ def g_rel_error(G_gpu, G_ref):
 
 
 def loss_close(gpu_loss, ref, po, t, rtol=1e-5):
-    """loss[0..3] = L, kappa, varpi, sum f_color against the oracle."""
+    """loss[0..3] = L, kappa, varpi, sum f_color against the oracle (the
+    fitness term of L is the cut edges for the partitioning problems)."""
     L, kap, var, fsum = [float(x) for x in gpu_loss]
     assert fsum == float(ref["f_color"].sum())
     assert kap == _approx(ref["kappa"], rtol)
     assert var == _approx(ref["varpi"], rtol)
-    scale = abs(ref["f_color"].sum()) + po.nu * t * abs(ref["f_eq"].sum()) + \
+    fit = ref["f_cut"] if po.problem in (2, 3) else ref["f_color"]
+    scale = abs(fit.sum()) + po.nu * t * abs(ref["f_eq"].sum()) + \
         po.lambda_ * t * abs(ref["kappa"]) + po.mu * t * abs(ref["varpi"])
     assert abs(L - ref["loss"]) <= rtol * max(scale, 1.0), (L, ref["loss"])
 

@@ -96,35 +96,43 @@ def test_switch_form_on_live_population():
             check_iteration(ctx, rp, ci, p, t)
 
 
-PLANS = [  # Gamma tile, Gamma cluster, M~ tile, M~ cluster, M~ K splits
-    (256, 1, 256, 1, 1), (256, 2, 256, 2, 3), (256, 4, 256, 1, 7), (128, 1, 128, 1, 1),
-    (128, 2, 128, 1, 4), (128, 4, 256, 2, 2)]
+# (Gamma unit rows, column tile, cluster), (M~ unit rows, column tile,
+# cluster), M~ K splits; 256-row units run on a CTA pair (cta_group::2)
+PLANS = [
+    ((128, 256, 1), (128, 256, 1), 1), ((128, 256, 2), (128, 256, 2), 3), ((128, 256, 4), (128, 256, 1), 4),
+    ((128, 128, 1), (128, 128, 1), 1), ((128, 128, 2), (128, 128, 1), 4), ((128, 128, 4), (128, 256, 2), 2),
+    ((256, 256, 2), (256, 256, 2), 3), ((256, 128, 2), (256, 128, 2), 4), ((256, 256, 2), (128, 256, 2), 1),
+    ((128, 256, 1), (256, 256, 2), 2)]
+
+
+def plan_of(got):
+    return ((got["gamma_tile_m"], got["gamma_tile_n"], got["gamma_cluster"]),
+            (got["mtilde_tile_m"], got["mtilde_tile_n"], got["mtilde_cluster"]), got["mtilde_splits"])
 
 
 @pytest.mark.parametrize("plan", PLANS)
 def test_every_tensor_core_plan_is_exact(plan):
     """Each tile / cluster / split-K variant the autotuner may pick, pinned,
-    on a graph spanning several row tiles (n_pad = 768: 6 of 128) and column
-    tiles, against the oracle element by element."""
+    on a graph spanning several row tiles (n_pad = 768: 6 of 128, 3 of 256)
+    and column tiles, against the oracle element by element."""
     n, D, k = 700, 11, 37
     rp, ci = inputs.gnp(n, 0.5, seed=21)
     W = inputs.init_weights(D, n, k, 0.02, seed=22)
     p = params(TC_KCOL, stop_on_legal=0, lambda_=1e-3, mu=1e-4, form=TC_FORM_DENSE_FP8)
     with make_ctx(rp, ci, D, k, p, W, 7) as ctx:
-        if plan[1] == 4:  # clusters of 4 need the row tiles to come in fours
+        if plan[0][2] == 4:  # clusters of 4 need the 128-row tiles to come in fours
             with pytest.raises(TensColError):
                 ctx.tc_dense_set_plan(*plan)
             return
         ctx.tc_dense_set_plan(*plan)
-        got = ctx.tc_dense_plan()
-        assert (got["gamma_tile_n"], got["gamma_cluster"], got["mtilde_tile_n"], got["mtilde_cluster"],
-                got["mtilde_splits"]) == plan
+        assert plan_of(ctx.tc_dense_plan()) == plan
         check_iteration(ctx, rp, ci, p, 7)
 
 
-@pytest.mark.parametrize("plan", [(256, 4, 256, 2, 5), (128, 4, 128, 1, 9)])
-def test_cluster_of_four_plans_are_exact(plan):
-    n, D, k = 1000, 30, 41  # n_pad = 1024: 8 row tiles; D k = 1230: 10 K blocks
+@pytest.mark.parametrize("plan", [((128, 256, 4), (128, 256, 2), 5), ((128, 128, 4), (128, 128, 1), 9),
+                                  ((256, 256, 2), (256, 256, 2), 10), ((256, 128, 2), (256, 256, 2), 7)])
+def test_workload_sized_plans_are_exact(plan):
+    n, D, k = 1000, 30, 41  # n_pad = 1024: 8 row tiles of 128; D k = 1230: 10 K blocks
     rp, ci = inputs.gnp(n, 0.5, seed=23)
     W = inputs.init_weights(D, n, k, 0.02, seed=24)
     p = params(TC_KCOL, stop_on_legal=0, lambda_=1e-3, mu=1e-4, form=TC_FORM_DENSE_FP8)
@@ -139,7 +147,10 @@ def test_autotuner_times_candidates_and_rejects_bad_plans():
     with make_ctx(rp, ci, 5, 20, params(TC_KCOL, form=TC_FORM_DENSE_FP8), W, 0) as ctx:
         got = ctx.tc_dense_plan()
         assert got["candidates"] >= 4 and got["gamma_us"] > 0 and got["mtilde_us"] > 0
-        for bad in [(64, 1, 256, 1, 1), (256, 3, 256, 1, 1), (128, 1, 128, 2, 1), (256, 1, 256, 1, 0)]:
+        for bad in [((128, 64, 1), (128, 256, 1), 1), ((128, 256, 3), (128, 256, 1), 1),
+                    ((128, 128, 1), (128, 128, 2), 1), ((128, 256, 1), (128, 256, 1), 0),
+                    ((256, 256, 1), (128, 256, 1), 1), ((128, 256, 1), (256, 256, 4), 1),
+                    ((512, 256, 2), (128, 256, 1), 1)]:
             with pytest.raises(TensColError):
                 ctx.tc_dense_set_plan(*bad)
         assert ctx.tc_dense_plan() == got  # unchanged by the refused plans
