@@ -11,8 +11,9 @@
 //                tensor cores: persistent CTA per SM, warp 0 streams
 //                128B-swizzled K-major tiles with TMA into a shared-memory
 //                ring of ~192 KB, warp 1 issues the MMAs into one of two TMEM
-//                accumulators, warps 2-5 drain the other (tcgen05.ld) into
-//                shared memory and warp 6 stores it with TMA.  Units of 128
+//                accumulators, eight epilogue warps drain the other
+//                (tcgen05.ld) and store it with TMA, each its own 32 rows of
+//                half the columns, without handshakes.  Units of 128
 //                rows run on one CTA (M = 128, N = 128 / 256, clusters
 //                sharing the B tile by multicast) or units of 256 rows on a
 //                CTA pair (cta_group::2, M = 256: each CTA loads half of the
@@ -35,15 +36,19 @@ namespace {
 
 constexpr int BM = 128, BK = 128;  // BK in bytes = FP8 elements
 constexpr int BN = 256;            // column tile of the FP32 comparator and the padding unit
-constexpr int TC_THREADS = 192;  // producer, MMA, four epilogue warps
+// Epilogue warps: two per TMEM lane quarter, each draining half of the
+// accumulator's columns (one warp per quarter could not keep up with the
+// MMAs of the short-K Gamma tiles).
+constexpr int EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (2 + EPI_WARPS);  // producer, MMA, epilogue warps
 // Output staging of the tensor-core epilogue: 32 KB after the operand ring,
-// 8 KB per epilogue warp, which stages and sends its own 32 rows without
-// waiting for the other warps: four 2 KB buffers of [32 columns][32 rows]
-// uint16 for Gamma (one TMA store each), or two 4 KB buffers of [32 rows][32
+// 4 KB per epilogue warp, which stages and sends its own 32 rows without
+// waiting for the other warps: two 2 KB buffers of [32 columns][32 rows]
+// uint16 for Gamma (one TMA store each), or one 4 KB buffer of [32 rows][32
 // floats], 128-byte swizzled, for M~ (one TMA reduce-add each: the split-K
 // partial sums add up in L2).
 constexpr int STG_BYTES = 32768;
-constexpr int STG_WARP = STG_BYTES / 4;
+constexpr int STG_WARP = STG_BYTES / EPI_WARPS;
 
 // Tile shapes of the tensor-core GEMM (the column tile BN_ is tuned per
 // context).  PAIR: the two CTAs of a cluster pair run one 256-row MMA
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             bar_init(&tfull[a], 1);
-            bar_init(&tempty[a], PAIR ? 8 : 4);  // the epilogue warps of every CTA holding the accumulator
+            bar_init(&tempty[a], PAIR ? 2 * EPI_WARPS : EPI_WARPS);  // the epilogue warps of every CTA holding it
         }
         bar_init(&drain, 1);
         abort_flag = 0;
@@ -360,6 +365,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (CL > 1) cluster_sync_all();  // peers' barriers initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    // launched as a programmatic dependent of the previous kernel of the
+    // step: the set-up above overlaps its tail; the operands it wrote (and
+    // the outputs it read) are only touched after it has completed
+    pdl_trigger();
+    pdl_wait();
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
@@ -433,21 +443,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         }
-    } else {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ... 32 (warp % 4) + 31
-        // Each warp drains its 32 rows of the accumulator 32 columns at a
-        // time (the next chunk's TMEM load in flight while the current one is
-        // staged) and sends every chunk with its own TMA store (Gamma) or
-        // reduce-add (M~) from a private buffer: no warp waits for another.
-        // A buffer is reused once the bulk group that read it is done (bulk
-        // groups are per thread: lane 0 issues and waits for them all).
-        const int q = warp & 3;
+    } else {  // epilogue warps: TMEM lanes 32 (warp % 4) ... 32 (warp % 4) + 31
+        // Each warp drains its 32 rows of the accumulator, in its share of
+        // the columns, 32 columns at a time (the next chunk's TMEM load in
+        // flight while the current one is staged) and sends every chunk with
+        // its own TMA store (Gamma) or reduce-add (M~) from a private buffer:
+        // no warp waits for another.  A buffer is reused once the bulk group
+        // that read it is done (bulk groups are per thread: lane 0 issues and
+        // waits for them all).
+        const int q = warp & 3, ew = warp - 2;
         const bool gamma = g.mode == TC_GEMM_GAMMA;
-        const unsigned nb = gamma ? 4u : 2u;              // buffers per warp
         const uint32_t bytes_b = gamma ? 2048u : 4096u;   // [32 cols][32 rows] u16 | [32 rows][32 f32]
-        const uint32_t stg = su32(smem + STAGES * STAGE_BYTES) + (uint32_t)q * STG_WARP;
-        uint8_t* stg_gen = smem + STAGES * STAGE_BYTES + q * STG_WARP;
+        const unsigned nb = STG_WARP / bytes_b;            // buffers per warp (1, 2 or 4)
+        const uint32_t stg = su32(smem + STAGES * STAGE_BYTES) + (uint32_t)ew * STG_WARP;
+        uint8_t* stg_gen = smem + STAGES * STAGE_BYTES + ew * STG_WARP;
         unsigned ui = 0, gc = 0;  // unit and chunk counters
-        constexpr int NCH = BN_ / 32;
+        constexpr int NCH = BN_ / 32 / (EPI_WARPS / 4);  // chunks per warp per unit (even)
+        static_assert(NCH >= 2 && NCH % 2 == 0, "each epilogue warp takes an even number of chunks");
+        const int cbase = (ew >> 2) * NCH;                 // its first chunk
         for (int u = u_first; u < g.n_units; u += u_step, ++ui) {
             const int4 w = g.units[u];
             const int a = ui & 1;
@@ -461,10 +474,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t b = gc % nb;
                 if (gc >= nb) {  // the group that last read buffer b is nb chunks back
                     if (lane == 0) {
-                        if (gamma)
+                        if (nb >= 4)
                             asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
-                        else
+                        else if (nb == 2)
                             asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        else
+                            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                     }
                     __syncwarp();
                 }
@@ -495,14 +510,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ++gc;
             };
             uint32_t v0[32], v1[32];
-            tmem_ld32(tbase, v0);
+            tmem_ld32(tbase + (uint32_t)(32 * cbase), v0);
 #pragma unroll 1
-            for (int c = 0; c < NCH; c += 2) {
+            for (int c = cbase; c < cbase + NCH; c += 2) {
                 tmem_wait(v0);
                 tmem_ld32(tbase + (uint32_t)(32 * (c + 1)), v1);  // NCH is even
                 emit(v0, c);
                 tmem_wait(v1);
-                if (c + 2 < NCH) tmem_ld32(tbase + (uint32_t)(32 * (c + 2)), v0);
+                if (c + 2 < cbase + NCH) tmem_ld32(tbase + (uint32_t)(32 * (c + 2)), v0);
                 emit(v1, c + 1);
             }
             // every TMEM load of this accumulator has completed (waited above)
@@ -642,7 +657,7 @@ int tc_gemm_tile_n() { return BN; }
 int tc_gemm_tile_k() { return BK; }
 
 template <int BN_, int CL, bool PAIR>
-static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttribute* attr) {
+static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttribute* attr, bool pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(groups * CL);
     cfg.blockDim = dim3(TC_THREADS);
@@ -652,8 +667,10 @@ static cudaLaunchConfig_t tc_config(int groups, cudaStream_t s, cudaLaunchAttrib
     attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     return cfg;
 }
 
@@ -673,14 +690,14 @@ static cudaError_t smem_opt_in() {
 
 template <int BN_, int CL, bool PAIR>
 static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
-                             const tc_gemm_args& g, int slots, cudaStream_t s) {
+                             const tc_gemm_args& g, int slots, bool pdl, cudaStream_t s) {
     cudaError_t e = smem_opt_in<BN_, CL, PAIR>();
     if (e != cudaSuccess) return e;
     const int per_cluster = PAIR ? 1 : CL;  // units a cluster takes per round
     int groups = slots < g.n_units / per_cluster ? slots : g.n_units / per_cluster;
     if (groups < 1) groups = 1;
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(groups, s, attr);
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(groups, s, attr, pdl);
     return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL, PAIR>, tmX, tmY, tmC, g);
 }
 
@@ -692,8 +709,8 @@ static int slots_tc(int num_sms) {
         (void)cudaGetLastError();
         return num_sms / CL;
     }
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(num_sms / CL, nullptr, attr);
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(num_sms / CL, nullptr, attr, false);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<BN_, CL, PAIR>, &cfg) != cudaSuccess || n < 1) {
         (void)cudaGetLastError();
@@ -726,23 +743,25 @@ int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms) {
 // the units were cut with.  `slots`: clusters launched at most (one wave,
 // from tc_gemm_cluster_slots).  tmC: the output, Gamma transposed
 // [D k][n_pad] uint16, or M~ [n_pad][n_pad] f32 128-byte swizzled, both with
-// 32 x 32 boxes (one warp's rows of one 32-column chunk).
+// 32 x 32 boxes (one warp's rows of one 32-column chunk).  `pdl`: launched as
+// a programmatic dependent of the stream's previous kernel.
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
-                              const tc_gemm_args& g, int slots, int tm, int cluster, int bn, cudaStream_t s) {
+                              const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
+                              cudaStream_t s) {
     if (tm == 2 * BM)
-        return bn == 128 ? launch_tc<128, 2, true>(tmX, tmY, tmC, g, slots, s)
-                         : launch_tc<256, 2, true>(tmX, tmY, tmC, g, slots, s);
+        return bn == 128 ? launch_tc<128, 2, true>(tmX, tmY, tmC, g, slots, pdl, s)
+                         : launch_tc<256, 2, true>(tmX, tmY, tmC, g, slots, pdl, s);
     if (bn == 128) {
         switch (cluster) {
-            case 4: return launch_tc<128, 4, false>(tmX, tmY, tmC, g, slots, s);
-            case 2: return launch_tc<128, 2, false>(tmX, tmY, tmC, g, slots, s);
-            default: return launch_tc<128, 1, false>(tmX, tmY, tmC, g, slots, s);
+            case 4: return launch_tc<128, 4, false>(tmX, tmY, tmC, g, slots, pdl, s);
+            case 2: return launch_tc<128, 2, false>(tmX, tmY, tmC, g, slots, pdl, s);
+            default: return launch_tc<128, 1, false>(tmX, tmY, tmC, g, slots, pdl, s);
         }
     }
     switch (cluster) {
-        case 4: return launch_tc<256, 4, false>(tmX, tmY, tmC, g, slots, s);
-        case 2: return launch_tc<256, 2, false>(tmX, tmY, tmC, g, slots, s);
-        default: return launch_tc<256, 1, false>(tmX, tmY, tmC, g, slots, s);
+        case 4: return launch_tc<256, 4, false>(tmX, tmY, tmC, g, slots, pdl, s);
+        case 2: return launch_tc<256, 2, false>(tmX, tmY, tmC, g, slots, pdl, s);
+        default: return launch_tc<256, 1, false>(tmX, tmY, tmC, g, slots, pdl, s);
     }
 }
 

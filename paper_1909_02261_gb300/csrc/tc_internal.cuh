@@ -73,7 +73,7 @@ struct tc_kparams {
     tc_dev_state* st;
     uint16_t* best;           // n best-so-far colours
     // dense forms (NULL in the one-hot form)
-    const float* M32;         // n_pad x n_pad group concentration from a GEMM
+    float* M32;               // n_pad x n_pad group concentration from a GEMM (k_pairs zeroes it)
     int ldm;
     const uint16_t* G16;      // n_pad x ldg gamma matrix A.S_cat from a GEMM
     int ldg;
@@ -167,7 +167,8 @@ int tc_gemm_tile_m();
 int tc_gemm_tile_n();
 int tc_gemm_tile_k();
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
-                              const tc_gemm_args& g, int slots, int tm, int cluster, int bn, cudaStream_t s);
+                              const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
+                              cudaStream_t s);
 int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);

@@ -156,8 +156,21 @@ __global__ void k_assign(tc_kparams P) {
 template <int CB>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     pdl_trigger();
-    pdl_wait();  // colours from the previous k_update
-    if (P.commit && P.st->stop) return;
+    pdl_wait();  // colours from the previous k_update (dense forms: M~ from the GEMM)
+    const int2 tile = P.pair_tiles[blockIdx.x];
+    if (P.commit && P.st->stop) {
+        // the dense forms' M~ accumulates by reduce-adds: every block leaves
+        // its entries zero for the next GEMM, also when it has nothing to do
+        if (P.M32)
+            for (int e = threadIdx.x; e < PT * PT; e += PAIR_THREADS) {
+                const int i = tile.x * PT + e / PT, m = tile.y * PT + e % PT;
+                if (i < P.n && m < P.n) {
+                    P.M32[(size_t)i * P.ldm + m] = 0.f;
+                    P.M32[(size_t)m * P.ldm + i] = 0.f;
+                }
+            }
+        return;
+    }
     __shared__ uint32_t s_a[PT][PAIR_CW + 1];
     __shared__ uint32_t s_b[PT][PAIR_CW + 1];
     __shared__ float s_red[2][PAIR_THREADS / 32];
@@ -166,7 +179,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     constexpr int SH = CB == 1 ? 7 : 15;
 
     const int n = P.n, D = P.D;
-    const int2 tile = P.pair_tiles[blockIdx.x];
     const int I = tile.x, M = tile.y;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int Dw = P.Dp * CB / 4;
@@ -229,6 +241,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     __syncthreads();  // s_a / s_b are reused as transpose tiles
     float(*s_t)[PT + 1] = reinterpret_cast<float(*)[PT + 1]>(&s_a[0][0]);
     int(*s_m)[PT + 1] = reinterpret_cast<int(*)[PT + 1]>(&s_b[0][0]);
+    // dense forms: this thread's M~ entries, all loaded before any store (the
+    // entries are zeroed after use for the next iteration's reduce-adds)
+    int mg[PP][PP];
+    if (from_gemm) {
+#pragma unroll
+        for (int a = 0; a < PP; ++a)
+#pragma unroll
+            for (int b = 0; b < PP; ++b) {
+                const int il = ty + 16 * a, ml = tx + 16 * b, i = I * PT + il, m = M * PT + ml;
+                mg[a][b] = (i < n && m < n && (I < M || ml >= il)) ? __float2int_rn(__ldcg(P.M32 + (size_t)i * P.ldm + m))
+                                                                   : 0;
+            }
+    }
 #pragma unroll
     for (int a = 0; a < PP; ++a) {
         const int il = ty + 16 * a, i = I * PT + il;
@@ -238,8 +263,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
             float bb = 0.f;
             int mt = 0;
             if (i < n && m < n && (I < M || ml >= il)) {
-                mt = from_gemm ? __float2int_rn(P.M32[(size_t)i * P.ldm + m])
-                               : (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
+                if (from_gemm) {
+                    mt = mg[a][b];
+                    P.M32[(size_t)i * P.ldm + m] = 0.f;
+                } else {
+                    mt = (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
+                }
                 mt = min(max(mt, 0), D);  // a count of individuals: the tables hold D + 1 entries
                 const bool edge = (P.adj[(size_t)i * P.adj_words + (m >> 5)] >> (m & 31)) & 1u;
                 if (m == i) {
@@ -270,6 +299,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
         const int mm = M * PT + ml, ii = I * PT + il;
         if (mm < n && ii < n && (I < M || il < ml)) {
             P.B[(size_t)mm * P.ldb + ii] = s_t[ml][il];
+            if (from_gemm) P.M32[(size_t)mm * P.ldm + ii] = 0.f;  // the GEMM's tiles reach below the diagonal
             if (P.dbg_Mt) P.dbg_Mt[(size_t)mm * n + ii] = s_m[ml][il];
         }
     }

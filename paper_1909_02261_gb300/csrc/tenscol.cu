@@ -462,7 +462,7 @@ int plan_dense(tc_ctx* c) {
         tc_gemm_args g = {c->d_units_g, (int)u.size(), TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
                           &c->d_st->err};
         const float ms = time_it(
-            [&] { return tc_launch_gemm_tc(c->tmA8, tmY, c->tmG16, g, slots, q.q.tm, q.q.cl, q.q.bn, c->stream); });
+            [&] { return tc_launch_gemm_tc(c->tmA8, tmY, c->tmG16, g, slots, q.q.tm, q.q.cl, q.q.bn, false, c->stream); });
         ++timed;
         if (ms >= 0.f && ms < best_g) {
             best_g = ms;
@@ -480,7 +480,7 @@ int plan_dense(tc_ctx* c) {
         tc_gemm_args g = {c->d_units_m, (int)u.size(), TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
                           &c->d_st->err};
         const float ms = time_it(
-            [&] { return tc_launch_gemm_tc(c->tmS8x, tmY, c->tmM32, g, slots, q.q.tm, q.q.cl, q.q.bn, c->stream); });
+            [&] { return tc_launch_gemm_tc(c->tmS8x, tmY, c->tmM32, g, slots, q.q.tm, q.q.cl, q.q.bn, false, c->stream); });
         ++timed;
         if (ms >= 0.f && ms < best_m) {
             best_m = ms;
@@ -491,6 +491,9 @@ int plan_dense(tc_ctx* c) {
     cudaEventDestroy(e1);
     if (rc) return rc;
     if (tc && (best_g >= 1e30f || best_m >= 1e30f)) return TC_ERR_CUDA;  // no configuration ran
+    // the timed M~ launches left sums behind; the iteration expects zeros
+    // (k_pairs zeroes M~ after reading it)
+    TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)n_pad * n_pad, c->stream));
     if ((rc = apply_plan(c, pick_g.q, pick_m.q, pick_m.split))) return rc;
     c->tune_candidates = timed;
     c->tune_us_g = tc ? 1e3f * best_g : 0.f;
@@ -645,17 +648,16 @@ int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
     tc_gemm_args gg = {c->d_units_g, c->n_units_g, TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
                        &c->d_st->err};
     const bool tc = c->p.form == TC_FORM_DENSE_FP8;
-    if (which == 0) {
-        TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)c->n_pad * c->n_pad, s));
+    if (which == 0) {  // M~ is zero here: k_pairs zeroes it after reading it
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
             return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, c->tmM32, gm, c->slots_m, c->sh_m.tm, c->sh_m.cl,
-                                          c->sh_m.bn, s)
+                                          c->sh_m.bn, true, s)
                       : tc_launch_gemm_simt(c->d_S8, c->d_S8, c->ldg, gm, c->num_sms, s);
         }, s));
     } else {
         TC_CHECK(timed(c, TC_KID_GEMM_G, [&] {
             return tc ? tc_launch_gemm_tc(c->tmA8, c->tmS8T, c->tmG16, gg, c->slots_g, c->sh_g.tm, c->sh_g.cl,
-                                          c->sh_g.bn, s)
+                                          c->sh_g.bn, true, s)
                       : tc_launch_gemm_simt(c->d_A8, c->d_S8T, c->n_pad, gg, c->num_sms, s);
         }, s));
     }
