@@ -42,6 +42,7 @@ class Params(C.Structure):
         ("rho", C.c_double),
         ("nb_iter", C.c_int),
         ("bonus_diag", C.c_int),
+        ("zcost", C.c_void_p),
     ]
 
 
@@ -80,12 +81,13 @@ def _declare(L):
     L.orc_equity.argtypes = [_i, _i, _i, _p, _p, _p, _p]
     L.orc_mtilde.argtypes = [_i, _i, _p, _p]
     L.orc_cut.argtypes = [_i, _i, _p, _p, _p, _p]
+    L.orc_mscp.argtypes = [_i, _i, _i, _p, _p, _p]
     L.orc_mbar.argtypes = [_i, _i, _p, _p]
     L.orc_penalty_bonus.argtypes = [_i, _p, _p, _p, C.c_double, C.c_double, _i, _p, _p]
     L.orc_grad_S.argtypes = [_i, _i, _i, _p, _p, _p, _p, _p, C.POINTER(Params), _ll, _p]
     L.orc_update.argtypes = [_i, _i, _i, C.POINTER(Params), _ll, _p, _p, _p]
     L.orc_step.argtypes = [_i, _i, _i, _p, _p, C.POINTER(Params), _ll, _i, _p,
-                           _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
+                           _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
     L.orc_run.restype = _ll
     L.orc_run.argtypes = [_i, _i, _i, _p, _p, C.POINTER(Params), C.POINTER(_ll), _ll,
                           _i, _p, _p, C.POINTER(_ll), C.POINTER(_ll)]
@@ -111,13 +113,20 @@ def _f64(a):
 
 def make_params(**kw) -> Params:
     """Parameter block; defaults are the GCP column of Table 2 (rho = 100).
-    problem: 0 k-COL, 1 ECP, 2 k-partitioning, 3 balanced k-partitioning."""
+    problem: 0 k-COL, 1 ECP, 2 k-partitioning, 3 balanced k-partitioning,
+    4 minimum sum colouring; zcost: the colour costs z_l of problem 4 (None:
+    z_l = l + 1)."""
     d = dict(problem=0, sigma0=0.01, eta=1e-3, alpha=2.5, lambda_=1e-5,
              beta=1.2, mu=1e-6, nu=0.0, rho=100.0, nb_iter=5, bonus_diag=1)
     if "lambda" in kw:
         kw["lambda_"] = kw.pop("lambda")
+    z = kw.pop("zcost", None)
     d.update(kw)
-    return Params(**d)
+    p = Params(**d)
+    if z is not None:
+        p._z = _i32(z)  # kept alive with the block
+        p.zcost = p._z.ctypes.data
+    return p
 
 
 def _check(rc, what):
@@ -172,6 +181,17 @@ def cut(rowptr, colidx, colors):
     D, n = colors.shape
     f = np.empty((D,), np.int64)
     _check(lib().orc_cut(D, n, _ptr(rowptr), _ptr(colidx), _ptr(colors), _ptr(f)), "cut")
+    return f
+
+
+def mscp(colors, zcost=None):
+    """Total colour cost per individual (minimum sum colouring, Section 7)."""
+    colors = _i32(colors)
+    D, n = colors.shape
+    k = int(colors.max()) + 1 if zcost is None else len(zcost)
+    z = None if zcost is None else _i32(zcost)
+    f = np.empty((D,), np.int64)
+    _check(lib().orc_mscp(D, n, k, _ptr(colors), _ptr(z), _ptr(f)), "mscp")
     return f
 
 
@@ -239,7 +259,7 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
     out = dict(
         colors=np.empty((D, n), np.int32), gamma_own=np.empty((D, n), np.int32),
         f_color=np.empty((D,), np.int64), f_eq=np.empty((D,), np.int64),
-        f_cut=np.empty((D,), np.int64), Mt=np.empty((n, n), np.int32),
+        f_cut=np.empty((D,), np.int64), f_mscp=np.empty((D,), np.int64), Mt=np.empty((n, n), np.int32),
         G=np.empty((D, n, k), np.float64) if want_G else None,
         gW=np.empty((D, n, k), np.float64) if want_G else None)
     loss, kappa, varpi = C.c_double(), C.c_double(), C.c_double()
@@ -247,7 +267,7 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
     _check(lib().orc_step(D, n, k, _ptr(rowptr), _ptr(colidx), C.byref(params), t,
                           int(stop_on_legal), _ptr(W),
                           _ptr(out["colors"]), _ptr(out["gamma_own"]), _ptr(out["f_color"]),
-                          _ptr(out["f_eq"]), _ptr(out["f_cut"]), _ptr(out["Mt"]), _ptr(out["G"]),
+                          _ptr(out["f_eq"]), _ptr(out["f_cut"]), _ptr(out["f_mscp"]), _ptr(out["Mt"]), _ptr(out["G"]),
                           _ptr(out["gW"]),
                           C.byref(loss), C.byref(kappa), C.byref(varpi),
                           C.byref(fmin), C.byref(dstar), C.byref(upd)), "step")

@@ -130,6 +130,23 @@ int orc_cut(int D, int n, const int *adj_off, const int *adj, const int *colors,
     return 0;
 }
 
+/* Minimum sum colouring (Section 7): the additive fitness sums the cost of
+ * the colour each vertex takes, f_mscp(S_d) = sum_i sum_l s_{d,i,l} z_l. */
+int orc_mscp(int D, int n, int k, const int *colors, const int *z, long long *f_mscp)
+{
+    if (D < 0 || n < 0 || k < 1 || !colors || !f_mscp)
+        return ORC_EBADARG;
+    for (int d = 0; d < D; ++d) {
+        long long f = 0;
+        for (int i = 0; i < n; ++i) {
+            const int l = colors[(size_t)d * n + i];
+            f += z ? (long long)z[l] : (long long)(l + 1);
+        }
+        f_mscp[d] = f;
+    }
+    return 0;
+}
+
 /* Equity fitness (eq. 3) and its gradient (eq. 14). */
 int orc_equity(int D, int n, int k, const int *colors,
                int *sizes, long long *f_eq, int *E)
@@ -362,12 +379,17 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
              const orc_params *p, long long t, int stop_on_legal,
              double *W,
              int *colors, int *gamma_own, long long *f_color, long long *f_eq,
-             long long *f_cut, int *Mt, double *G, double *gW,
+             long long *f_cut, long long *f_mscp, int *Mt, double *G, double *gW,
              double *loss, double *kappa, double *varpi,
              long long *f_min, int *d_star, int *updated)
 {
-    if (D < 1 || n < 0 || k < 1 || !p || !W || p->problem < 0 || p->problem > 3)
+    if (D < 1 || n < 0 || k < 1 || !p || !W || p->problem < 0 || p->problem > 4)
         return ORC_EBADARG;
+    if (p->zcost)
+        for (int l = 0; l < k; ++l)
+            if (p->zcost[l] < 0)
+                return ORC_EBADARG;
+    const int mscp = p->problem == 4; /* minimum sum colouring */
     const int part = p->problem == 2 || p->problem == 3; /* k-partitioning */
     const size_t Dn = (size_t)D * n, Dk = (size_t)D * k, nn = (size_t)n * n;
     int rc = 0;
@@ -375,11 +397,12 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
     long long *fc = f_color ? f_color : (long long *)malloc(sizeof(long long) * D);
     long long *fe = f_eq ? f_eq : (long long *)malloc(sizeof(long long) * D);
     long long *fx = f_cut ? f_cut : (long long *)malloc(sizeof(long long) * D);
+    long long *fm = f_mscp ? f_mscp : (long long *)malloc(sizeof(long long) * D);
     int *E = (int *)malloc(sizeof(int) * (Dk ? Dk : 1));
     int *M = Mt ? Mt : (int *)malloc(sizeof(int) * (nn ? nn : 1));
     int *Mb = part ? (int *)malloc(sizeof(int) * (nn ? nn : 1)) : NULL;
     double *Gr = G ? G : (double *)malloc(sizeof(double) * (Dn * k > 0 ? Dn * k : 1));
-    if (!c || !fc || !fe || !fx || !E || !M || (part && !Mb) || !Gr) {
+    if (!c || !fc || !fe || !fx || !fm || !E || !M || (part && !Mb) || !Gr) {
         rc = ORC_ENOMEM;
         goto out;
     }
@@ -389,14 +412,21 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
     orc_fitness(D, n, k, adj_off, adj, c, gamma_own, fc);
     orc_cut(D, n, adj_off, adj, c, fx);
     orc_equity(D, n, k, c, NULL, fe, E);
+    orc_mscp(D, n, k, c, p->zcost, fm);
+    if (mscp) /* f_mscp replaces f_eq: its gradient z_l stands in for eq. 14 */
+        for (int d = 0; d < D; ++d)
+            for (int j = 0; j < k; ++j)
+                E[(size_t)d * k + j] = p->zcost ? p->zcost[j] : j + 1;
     /* the fitness each problem minimises: f_color (k-COL), f_color + f_eq
-     * (ECP), cut edges (k-partitioning), cut edges + f_eq (balanced) */
+     * (ECP), cut edges (k-partitioning), cut edges + f_eq (balanced),
+     * f_color + f_mscp (minimum sum colouring) */
     long long *fobj = part ? fx : fc;
-    const int with_eq = p->problem == 1 || p->problem == 3;
+    long long *fadd = mscp ? fm : fe; /* the additive term of the fitness and of eq. 7 */
+    const int with_add = p->problem == 1 || p->problem == 3 || mscp;
     long long fmin = -1;
     int dstar = 0;
     for (int d = 0; d < D; ++d) {
-        long long f = fobj[d] + (with_eq ? fe[d] : 0);
+        long long f = fobj[d] + (with_add ? fadd[d] : 0);
         if (fmin < 0 || f < fmin) {
             fmin = f;
             dstar = d;
@@ -417,7 +447,7 @@ int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
         double sc = 0.0, se = 0.0;
         for (int d = 0; d < D; ++d) {
             sc += (double)fobj[d];
-            se += (double)fe[d];
+            se += (double)fadd[d];
         }
         const double tt = (double)t;
         if (loss)
@@ -444,6 +474,7 @@ out:
     if (fc != f_color) free(fc);
     if (fe != f_eq) free(fe);
     if (fx != f_cut) free(fx);
+    if (fm != f_mscp) free(fm);
     free(Mb);
     free(E);
     if (M != Mt) free(M);
@@ -467,7 +498,7 @@ long long orc_run(int D, int n, int k, const int *adj_off, const int *adj,
         long long fmin = 0;
         int dstar = 0, upd = 0;
         int rc = orc_step(D, n, k, adj_off, adj, p, *t, stop_on_legal, W, c,
-                          NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
+                          NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
                           &fmin, &dstar, &upd);
         if (rc) {
             free(c);

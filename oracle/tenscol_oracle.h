@@ -25,7 +25,8 @@ extern "C" {
 
 typedef struct {
     int problem;        /* 0 = k-COL (GCP), 1 = ECP, 2 = k-partitioning,
-                           3 = balanced k-partitioning (Section 7)          */
+                           3 = balanced k-partitioning, 4 = minimum sum
+                           colouring (Section 7)                            */
     double sigma0;      /* std of the N(0, sigma0) initial weights (Table 2) */
     double eta;         /* learning rate                                      */
     double alpha;       /* penalisation exponent  (eq. 5)                     */
@@ -36,6 +37,8 @@ typedef struct {
     double rho;         /* smoothing divisor      (eq. 8)                     */
     int nb_iter;        /* smoothing period       (Step 4-iv)                 */
     int bonus_diag;     /* 1: \bar A = J - A keeps its diagonal (Section 3.6.2)*/
+    const int *zcost;   /* problem 4: cost z_l >= 0 of colour l (k entries);
+                           NULL: z_l = l + 1 (colours numbered 1..k)        */
 } orc_params;
 
 /* Structural check of the adjacency lists: ids in range, no self loop,
@@ -67,6 +70,10 @@ int orc_equity(int D, int n, int k, const int *colors,
 /* Step 3-i (eq. 4): Mt[i*n+m] = #{d : c_d(i) == c_d(m)}; Mt[i*n+i] = D. */
 int orc_mtilde(int D, int n, const int *colors, int *Mt);
 
+/* Minimum sum colouring (Section 7): f_mscp[d] = sum_i sum_l s_{d,i,l} z_l =
+ * the total cost of the colours individual d uses (z = NULL: z_l = l + 1). */
+int orc_mscp(int D, int n, int k, const int *colors, const int *z, long long *f_mscp);
+
 /* k-partitioning counterpart of eq. 4 (Section 7, M -> J - M):
  * Mb[i*n+m] = #{d : c_d(i) != c_d(m)}; Mb[i*n+i] = 0. */
 int orc_mbar(int D, int n, const int *colors, int *Mb);
@@ -94,18 +101,20 @@ int orc_update(int D, int n, int k, const orc_params *p, long long t,
 
 /* One full iteration at counter t on W (in/out).  Every output may be NULL.
  * loss = f(S) + nu t f_eq(S) + lambda t kappa - mu t varpi  (eq. 7), with
- * f = f_color (problems 0, 1) or the cut edges f_cut (problems 2, 3, whose
- * kappa and varpi are taken over \bar M~).  The fitness minimised per
- * individual is f_color (k-COL), f_color + f_eq (ECP), f_cut
- * (k-partitioning) or f_cut + f_eq (balanced); *f_min, *d_star = lowest d
- * attaining it.  Mt always receives M~ (eq. 4).  If stop_on_legal and
+ * f = f_color (problems 0, 1, 4) or the cut edges f_cut (problems 2, 3,
+ * whose kappa and varpi are taken over \bar M~); for problem 4 the additive
+ * fitness f_mscp takes the place of f_eq in the loss and the gradient (the
+ * derivative of nu t f_mscp by s_{d,i,l} is nu t z_l).  The fitness
+ * minimised per individual is f_color (k-COL), f_color + f_eq (ECP), f_cut
+ * (k-partitioning), f_cut + f_eq (balanced) or f_color + f_mscp (minimum
+ * sum colouring); *f_min, *d_star = lowest d attaining it.  Mt always receives M~ (eq. 4).  If stop_on_legal and
  * f_min == 0 the weights are left untouched and *updated = 0 (Algorithm 1
  * stop rule), else *updated = 1. */
 int orc_step(int D, int n, int k, const int *adj_off, const int *adj,
              const orc_params *p, long long t, int stop_on_legal,
              double *W,
              int *colors, int *gamma_own, long long *f_color, long long *f_eq,
-             long long *f_cut, int *Mt, double *G, double *gW,
+             long long *f_cut, long long *f_mscp, int *Mt, double *G, double *gW,
              double *loss, double *kappa, double *varpi,
              long long *f_min, int *d_star, int *updated);
 
