@@ -83,6 +83,9 @@ def _declare(L):
     L.orc_cut.argtypes = [_i, _i, _p, _p, _p, _p]
     L.orc_mscp.argtypes = [_i, _i, _i, _p, _p, _p]
     L.orc_mbar.argtypes = [_i, _i, _p, _p]
+    L.orc_assign_multi.argtypes = [_i, _i, _i, _p, _p, _p]
+    L.orc_step_multi.argtypes = [_i, _i, _i, _p, _p, _p, C.POINTER(Params), _ll, _i, _p,
+                                 _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
     L.orc_penalty_bonus.argtypes = [_i, _p, _p, _p, C.c_double, C.c_double, _i, _p, _p]
     L.orc_grad_S.argtypes = [_i, _i, _i, _p, _p, _p, _p, _p, C.POINTER(Params), _ll, _p]
     L.orc_update.argtypes = [_i, _i, _i, C.POINTER(Params), _ll, _p, _p, _p]
@@ -273,6 +276,38 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
                           C.byref(fmin), C.byref(dstar), C.byref(upd)), "step")
     out.update(W=W, loss=loss.value, kappa=kappa.value, varpi=varpi.value,
                f_min=fmin.value, d_star=dstar.value, updated=bool(upd.value))
+    return out
+
+
+def assign_multi(W, demand):
+    """Multicolouring Step 1 (Section 7): the dense 0/1 tensor S (D x n x k)."""
+    W = _f64(W)
+    D, n, k = W.shape
+    demand = _i32(demand)
+    S = np.empty((D, n, k), np.float64)
+    _check(lib().orc_assign_multi(D, n, k, _ptr(W), _ptr(demand), _ptr(S)), "assign_multi")
+    return S
+
+
+def step_multi(rowptr, colidx, W, demand, params: Params, t: int, stop_on_legal: bool = False):
+    """One multicolouring iteration on a copy of W; every intermediate."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    W = _f64(W).copy()
+    D, n, k = W.shape
+    _check_graph_size(rowptr, n)
+    demand = _i32(demand)
+    out = dict(S=np.empty((D, n, k), np.float64), f_color=np.empty((D,), np.int64),
+               Mt=np.empty((n, n), np.int32), G=np.empty((D, n, k), np.float64),
+               gW=np.empty((D, n, k), np.float64))
+    loss, kappa, varpi = C.c_double(), C.c_double(), C.c_double()
+    fmin, dstar, upd = C.c_longlong(), C.c_int(), C.c_int()
+    _check(lib().orc_step_multi(D, n, k, _ptr(rowptr), _ptr(colidx), _ptr(demand), C.byref(params), t,
+                                int(stop_on_legal), _ptr(W), _ptr(out["S"]), _ptr(out["f_color"]),
+                                _ptr(out["Mt"]), _ptr(out["G"]), _ptr(out["gW"]), C.byref(loss),
+                                C.byref(kappa), C.byref(varpi), C.byref(fmin), C.byref(dstar),
+                                C.byref(upd)), "step_multi")
+    out.update(W=W, loss=loss.value, kappa=kappa.value, varpi=varpi.value, f_min=fmin.value,
+               d_star=dstar.value, updated=bool(upd.value))
     return out
 
 

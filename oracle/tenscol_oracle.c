@@ -617,6 +617,148 @@ int orc_relaxed(int D, int n, int k, const int *adj_off, const int *adj,
     return 0;
 }
 
+/* Multicolouring, Step 1 (Section 7): the demand[i] largest weights of w_{d,i},
+ * picked one at a time as the largest not yet taken (lowest index on ties). */
+int orc_assign_multi(int D, int n, int k, const double *W, const int *demand, double *S)
+{
+    if (D < 0 || n < 0 || k < 1 || !W || !demand || !S)
+        return ORC_EBADARG;
+    for (int i = 0; i < n; ++i)
+        if (demand[i] < 1 || demand[i] > k)
+            return ORC_EBADARG;
+    memset(S, 0, sizeof(double) * (size_t)D * n * k);
+    for (size_t r = 0; r < (size_t)D * n; ++r) {
+        const double *w = W + r * k;
+        double *s = S + r * k;
+        const int c = demand[r % (size_t)n];
+        for (int q = 0; q < c; ++q) {
+            int best = -1;
+            for (int l = 0; l < k; ++l)
+                if (s[l] == 0.0 && (best < 0 || w[l] > w[best]))
+                    best = l;
+            s[best] = 1.0;
+        }
+    }
+    return 0;
+}
+
+int orc_step_multi(int D, int n, int k, const int *adj_off, const int *adj, const int *demand,
+                   const orc_params *p, long long t, int stop_on_legal, double *W,
+                   double *S, long long *f_color, int *Mt, double *G, double *gW,
+                   double *loss, double *kappa, double *varpi,
+                   long long *f_min, int *d_star, int *updated)
+{
+    if (D < 1 || n < 0 || k < 1 || !p || !W || !demand || p->problem != 0)
+        return ORC_EBADARG;
+    const size_t Dn = (size_t)D * n, nn = (size_t)n * n;
+    int rc = 0;
+    double *Sx = S ? S : (double *)malloc(sizeof(double) * (Dn * k > 0 ? Dn * k : 1));
+    double *A = (double *)calloc(nn ? nn : 1, sizeof(double));
+    double *Md = (double *)malloc(sizeof(double) * (nn ? nn : 1)); /* M_d of one individual */
+    double *Mtd = (double *)calloc(nn ? nn : 1, sizeof(double));  /* M~ */
+    long long *fc = f_color ? f_color : (long long *)malloc(sizeof(long long) * D);
+    double *Gr = G ? G : (double *)malloc(sizeof(double) * (Dn * k > 0 ? Dn * k : 1));
+    if (!Sx || !A || !Md || !Mtd || !fc || !Gr) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    if ((rc = orc_assign_multi(D, n, k, W, demand, Sx)))
+        goto out;
+    for (int i = 0; i < n; ++i)
+        for (int e = adj_off[i]; e < adj_off[i + 1]; ++e)
+            A[(size_t)i * n + adj[e]] = 1.0;
+    /* Step 2: M_d = S_d S_d^T, f_color = 1/2 sum(A (.) M_d); Step 3-i: M~ */
+    for (int d = 0; d < D; ++d) {
+        const double *Sd = Sx + (size_t)d * n * k;
+        double twice = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int m = 0; m < n; ++m) {
+                double v = 0.0;
+                for (int l = 0; l < k; ++l)
+                    v += Sd[(size_t)i * k + l] * Sd[(size_t)m * k + l];
+                Md[(size_t)i * n + m] = v;
+                twice += A[(size_t)i * n + m] * v;
+                Mtd[(size_t)i * n + m] += v;
+            }
+        fc[d] = (long long)(twice / 2.0 + 0.5);
+    }
+    long long fmin = -1;
+    int dstar = 0;
+    for (int d = 0; d < D; ++d)
+        if (fmin < 0 || fc[d] < fmin) {
+            fmin = fc[d];
+            dstar = d;
+        }
+    if (f_min)
+        *f_min = fmin;
+    if (d_star)
+        *d_star = dstar;
+    if (Mt)
+        for (size_t q = 0; q < nn; ++q)
+            Mt[q] = (int)(Mtd[q] + 0.5);
+    /* eq. 5-7 */
+    const double tt = (double)t;
+    double ks = 0.0, vs = 0.0, sc = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int m = 0; m < n; ++m) {
+            const double a = A[(size_t)i * n + m], x = Mtd[(size_t)i * n + m];
+            const double abar = (m == i && !p->bonus_diag) ? 0.0 : 1.0 - a;
+            ks += a * pow(x, p->alpha);
+            vs += abar * pow(x, p->beta);
+        }
+    for (int d = 0; d < D; ++d)
+        sc += (double)fc[d];
+    if (loss)
+        *loss = sc + p->lambda_ * tt * ks - p->mu * tt * vs;
+    if (kappa)
+        *kappa = ks;
+    if (varpi)
+        *varpi = vs;
+    /* eq. 13, row by row: G_d[i,j] = sum_m C_im S_d[m,j] with the pair
+     * coefficient C_im = a_im (1 + 2 alpha lambda t m~^(alpha-1))
+     *                   - abar_im 2 beta mu t m~^(beta-1) */
+    for (int d = 0; d < D; ++d) {
+        const double *Sd = Sx + (size_t)d * n * k;
+        for (int i = 0; i < n; ++i) {
+            double *g = Gr + ((size_t)d * n + i) * k;
+            for (int j = 0; j < k; ++j)
+                g[j] = 0.0;
+            for (int m = 0; m < n; ++m) {
+                const double a = A[(size_t)i * n + m], x = Mtd[(size_t)i * n + m];
+                const double abar = (m == i && !p->bonus_diag) ? 0.0 : 1.0 - a;
+                double cim = a;
+                if (a != 0.0)
+                    cim += 2.0 * p->alpha * p->lambda_ * tt * pow(x, p->alpha - 1.0);
+                if (abar != 0.0)
+                    cim -= 2.0 * p->beta * p->mu * tt * pow(x, p->beta - 1.0);
+                if (cim == 0.0)
+                    continue;
+                for (int j = 0; j < k; ++j)
+                    g[j] += cim * Sd[(size_t)m * k + j];
+            }
+        }
+    }
+    /* Step 4 unless the population already holds a legal multicolouring */
+    if (stop_on_legal && fmin == 0) {
+        if (updated)
+            *updated = 0;
+        if (gW)
+            memset(gW, 0, sizeof(double) * Dn * k);
+    } else {
+        rc = orc_update(D, n, k, p, t, Gr, W, gW);
+        if (updated)
+            *updated = 1;
+    }
+out:
+    if (Sx != S) free(Sx);
+    if (fc != f_color) free(fc);
+    if (Gr != G) free(Gr);
+    free(A);
+    free(Md);
+    free(Mtd);
+    return rc;
+}
+
 long long orc_check_conflicts(long long n_edges, const int *u, const int *v,
                               const int *coloring)
 {

@@ -137,6 +137,27 @@ int orc_relaxed(int D, int n, int k, const int *adj_off, const int *adj,
                 const orc_params *p, long long t, double tau, const double *W,
                 double *loss, double *gradW, double *Mt);
 
+/* Multicolouring (Section 7): vertex i must take demand[i] >= 1 colours.
+ * Step 1 becomes: S_{d,i,l} = 1 for the demand[i] colours l with the largest
+ * w_{d,i,l} (the lower index first among equal weights), else 0.  S is the
+ * dense D*n*k 0/1 tensor, index (d*n + i)*k + l. */
+int orc_assign_multi(int D, int n, int k, const double *W, const int *demand, double *S);
+
+/* One iteration of Algorithm 1 for multicolouring (problem 0 only; the
+ * equity term is not used), every quantity from its definition on the dense
+ * tensor S of orc_assign_multi: M_d = S_d S_d^T, f_color(S_d) = 1/2
+ * sum(A (.) M_d) (eq. 1-2), M~ = sum_d M_d (eq. 4), kappa and varpi (eq. 5-6
+ * over ordered pairs, the diagonal of \bar A iff bonus_diag), L (eq. 7),
+ * grad_S L = A S_d + 2 alpha lambda t (A (.) M~^(alpha-1)) S_d
+ *            - 2 beta mu t (\bar A (.) M~^(beta-1)) S_d  (eq. 13),
+ * then Step 4 (orc_update).  Outputs as for orc_step (any may be NULL); S
+ * receives the assignment of this iteration. */
+int orc_step_multi(int D, int n, int k, const int *adj_off, const int *adj, const int *demand,
+                   const orc_params *p, long long t, int stop_on_legal, double *W,
+                   double *S, long long *f_color, int *Mt, double *G, double *gW,
+                   double *loss, double *kappa, double *varpi,
+                   long long *f_min, int *d_star, int *updated);
+
 /* Checker: recount conflicts edge by edge from an edge list (u[e], v[e]),
  * and the equity deviation of a single colouring. */
 long long orc_check_conflicts(long long n_edges, const int *u, const int *v,
