@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-baseline-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--dense-plan", default=None,
+                    help="pin the FP8 form's GEMM plan after tuning (reproducible profiles): seven integers "
+                         "gamma_rows,gamma_cols,gamma_cluster,mtilde_rows,mtilde_cols,mtilde_cluster,mtilde_splits")
     return ap.parse_args()
 
 
@@ -349,6 +352,9 @@ def run_ours(args):
                                   ("dense_fp32", T.TC_FORM_DENSE_FP32, min(args.steps, 60))):
             pf = T.params(T.TC_KCOL, stop_on_legal=0, form=form)
             ctx.tc_set_params(pf)
+            if form == T.TC_FORM_DENSE_FP8 and args.dense_plan:
+                v = [int(x) for x in args.dense_plan.split(",")]
+                ctx.tc_dense_set_plan(tuple(v[0:3]), tuple(v[3:6]), v[6])
             tms, _, _, _, _, _ = time_steps(steps, 3, False, False)
             _, fk, fc, _, _, _ = time_steps(steps, 3, False, True)
             rec = {"value": D * steps / (tms / 1e3), "ms_per_step": tms / steps,

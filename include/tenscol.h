@@ -60,6 +60,12 @@ extern "C" {
  * fitness (and nu t grad f_eq to the gradient, as for the ECP). */
 #define TC_KPART 2     /* f = cut edges                                      */
 #define TC_KPART_BAL 3 /* f = cut edges + f_eq                               */
+/* Minimum sum colouring (Section 7): colour l costs z_l >= 0
+ * (tc_set_color_costs; z_l = l + 1 by default) and the additive fitness
+ * f_mscp(S_d) = sum_i z_{c_d(i)} takes the place of f_eq: f = f_color +
+ * f_mscp, nu t f_mscp in eq. 7 and nu t z_l in eq. 13.  With positive costs
+ * f never reaches 0: the run goes on and tc_best keeps the lowest f. */
+#define TC_MSCP 4
 
 /* How steps 2-3 and the products of eq. 13 are computed.  All forms give
  * identical colours, conflicts and fitness and the same W step to FP32
@@ -75,7 +81,7 @@ extern "C" {
 
 /* Parameters of Table 2 of the paper plus the run policy. */
 typedef struct {
-    int problem;     /* TC_KCOL, TC_ECP, TC_KPART or TC_KPART_BAL            */
+    int problem;     /* TC_KCOL, TC_ECP, TC_KPART, TC_KPART_BAL or TC_MSCP   */
     float sigma0;    /* std of the N(0, sigma0) initial weights (Section 3.2)*/
     float eta;       /* learning rate (Section 3.7)                          */
     float alpha;     /* penalisation exponent, > 1 (eq. 5)                   */
@@ -96,7 +102,8 @@ typedef struct tc_ctx tc_ctx; /* opaque: one graph + one population */
  * ECP: mu = 0, nu = 1e-5), rho = 100, stop_on_legal = 1, bonus_diag = 1,
  * form = TC_FORM_ONEHOT.  The paper gives no parameters for partitioning:
  * TC_KPART takes the GCP column, TC_KPART_BAL the GCP column with the ECP's
- * nu = 1e-5.  Returns TC_ERR_ARG for a NULL p or bad problem. */
+ * nu = 1e-5; so does TC_MSCP (nu weighs the colour costs).  Returns
+ * TC_ERR_ARG for a NULL p or bad problem. */
 int tc_params_default(tc_params *p, int problem);
 
 /* Creates a context on CUDA device `device` with its own stream.
@@ -141,7 +148,8 @@ int tc_step(tc_ctx *ctx, int64_t n_iters, int64_t *iters_done);
 /* Best-so-far individual over all evaluated iterations (lowest fitness f
  * of the problem, lowest d among ties, first iteration reaching the value):
  * coloring[n] (caller-owned), its f_color (monochromatic edges; for the
- * partitioning problems the cut edges are |E| - f_color) and f_eq, the
+ * partitioning problems the cut edges are |E| - f_color) and its additive
+ * term in `equity` (f_eq, or f_mscp for TC_MSCP), the
  * individual index and the iteration t at which it was seen.  Any output
  * pointer may be NULL.  TC_ERR_STATE if no iteration has been evaluated
  * yet. */
@@ -164,7 +172,7 @@ int tc_set_state_dev(tc_ctx *ctx, const float *W_dev);
  *   colors[D*n]    c_d(i) = argmax_j w_{d,i,j}, lowest j on ties (Section 3.4)
  *   gamma_own[D*n] conflicting neighbours of i in individual d (eq. 1)
  *   f_color[D]     monochromatic edges of individual d (eq. 1)
- *   f_eq[D]        equity fitness (eq. 3)
+ *   f_eq[D]        equity fitness (eq. 3); f_mscp for TC_MSCP
  *   Mtilde[n*n]    group concentration matrix (eq. 4)
  *   G[D*n*k]       grad_S L at iteration t (eq. 13)
  *   loss[4]        L (eq. 7), kappa (eq. 5), varpi (eq. 6), sum_d f_color */
@@ -210,7 +218,7 @@ int tc_st_grad_dev(tc_ctx *ctx, float *gradW_dev, float *loss_dev);
  * (eq. 13 through the softmax Jacobian).  Device pointers of D*n*k floats;
  * uses the graph and parameters of the context, k <= 128.  Allocates and
  * frees its own temporaries; the population is not touched.  TC_ERR_ARG for
- * the partitioning problems. */
+ * the partitioning problems and TC_MSCP. */
 int tc_relaxed_dev(tc_ctx *ctx, const float *W_dev, float tau, int64_t t, float *loss_dev,
                    float *gradW_dev);
 
@@ -254,7 +262,7 @@ int tc_set_graph_chunk(tc_ctx *ctx, int chunk);
  * colouring (f_color = 0, and f_eq = 0 for the ECP) moves on to k - 1, the
  * first k without one within the budget ends the descent.  *p as for
  * tc_init_population (NULL: Table 2 for TC_KCOL; TC_ERR_ARG for the
- * partitioning problems); stop_on_legal is forced on.  Outputs (any may be
+ * partitioning problems and TC_MSCP); stop_on_legal is forced on.  Outputs (any may be
  * NULL): *k_best the smallest k solved (-1 if none), coloring[n] its legal
  * colouring, *iters_total the iterations run.  The context keeps the
  * population of the last k tried. */
@@ -273,6 +281,44 @@ int tc_kdescent(tc_ctx *ctx, uint64_t seed, int D, int k_start, int k_min, int64
  *   us[0], us[1]: best times of Gamma and M~ in microseconds (0 for FP32).
  * TC_ERR_STATE when the context has no dense form. */
 int tc_dense_plan(tc_ctx *ctx, int32_t *plan, float *us);
+
+/* Colour costs z[0..k-1] >= 0 of the minimum sum colouring (TC_MSCP,
+ * Section 7), copied; k must be the population's k.  Every population
+ * starts with z_l = l + 1.  TC_ERR_ARG for a negative cost or another k,
+ * TC_ERR_STATE without a population, TC_ERR_UNSUPPORTED when n max(z) + |E|
+ * reaches 2^31 (the fitness is reduced in 32 bits).  Takes effect from the
+ * next iteration, also inside captured CUDA graphs. */
+int tc_set_color_costs(tc_ctx *ctx, const int32_t *z, int k);
+
+/* Multicolouring (Section 7): vertex i must take demand[i] colours, no
+ * colour shared across an edge.  Step 1 then selects the demand[i] colours
+ * of largest weight in w_{d,i} (the lower colour first among equal weights)
+ * and every other step of Algorithm 1 keeps its formula on the multi-hot S:
+ * f_color counts, per edge, the colours its ends share; m~_im the colours i
+ * and m share summed over the population (m~_ii = D demand[i]).  Needs the
+ * k-COL problem in a dense form (FP8 or FP32: the GEMMs compute A.S and
+ * S S^T of the multi-hot S); 1 <= demand[i] <= min(k, 8); n must be the
+ * graph's n.  Re-derives the population's colours from W and clears the
+ * best-so-far; all demands 1 returns to one colour per vertex.  A new
+ * population (tc_init_population) starts with demands 1.  TC_ERR_ARG for a
+ * bad demand or n, TC_ERR_STATE without a population, TC_ERR_UNSUPPORTED in
+ * the one-hot form, for another problem, or for D max(demand) >= 2^24;
+ * tc_set_params refuses to leave the dense forms or k-COL while demands are
+ * set.  tc_best reports the best individual's colour of largest weight;
+ * tc_best_multi its colour sets. */
+int tc_set_demands(tc_ctx *ctx, const int32_t *demand, int n);
+
+/* Best-so-far individual of the multicolouring: colors[i * stride + q] for
+ * q < demand[i] its colours of vertex i in increasing order, -1 up to
+ * stride (>= the largest demand); *conflicts the colours shared across
+ * edges; individual index and iteration as for tc_best.  Any output may be
+ * NULL.  TC_ERR_STATE without demands set or before the first iteration. */
+int tc_best_multi(tc_ctx *ctx, int32_t *colors, int stride, int64_t *conflicts, int32_t *individual,
+                  int64_t *iteration);
+
+/* The current colour sets of the whole population, colors[(d * n + i) *
+ * stride + q] as in tc_best_multi (D * n * stride entries, caller-owned). */
+int tc_get_multicolors(tc_ctx *ctx, int32_t *colors, int stride);
 
 /* Pins the plan of the dense contractions: plan[0..6] as above.  The FP8
  * form accepts, per contraction, unit rows 128 with column tile 128 / 256

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libtenscol.so")
-SOURCES = ["tenscol.cu", "tc_onehot.cu", "tc_dense.cu", "tc_relaxed.cu", "tc_noalloc.cu"]
+SOURCES = ["tenscol.cu", "tc_onehot.cu", "tc_dense.cu", "tc_relaxed.cu", "tc_noalloc.cu", "tc_multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -33,7 +33,11 @@ struct tc_dev_state {
 __host__ __device__ inline bool tc_is_partition(int problem) {
     return problem == TC_KPART || problem == TC_KPART_BAL;
 }
-__host__ __device__ inline bool tc_has_equity(int problem) { return problem == TC_ECP || problem == TC_KPART_BAL; }
+// Problems whose fitness adds a per-individual term: f_eq (eq. 3) for the ECP
+// and the balanced partitioning, f_mscp for the minimum sum colouring.
+__host__ __device__ inline bool tc_has_additive(int problem) {
+    return problem == TC_ECP || problem == TC_KPART_BAL || problem == TC_MSCP;
+}
 
 // Everything a kernel of the step needs, passed by value.
 struct tc_kparams {
@@ -58,9 +62,11 @@ struct tc_kparams {
                               // class padded to a multiple of 4 with vertex n
     int perm_stride;          // n + 3k rounded up to a multiple of 8
     int* off;                 // D x (k + 1) padded colour-class offsets into perm
-    int8_t* E;                // D x k equity gradient signs (eq. 14)
+    float* E;                 // D x k gradient factor of the additive fitness term by s_{d,i,j}:
+                              // the equity sign (eq. 14), or the colour cost z_j (minimum sum colouring)
+    const int* zcost;         // k colour costs of the minimum sum colouring
     int* fcolor;              // D conflicts (eq. 1)
-    int* feq;                 // D equity fitness (eq. 3)
+    int* feq;                 // D additive fitness: f_eq (eq. 3), or f_mscp (minimum sum colouring)
     float* loss_part;         // 2 x n_pair_blocks partial kappa / varpi
     int n_pair_blocks;
     const int2* pair_tiles;   // upper-triangular 32x32 tile list
@@ -72,6 +78,12 @@ struct tc_kparams {
     const float* powB;        // x^beta
     tc_dev_state* st;
     uint16_t* best;           // n best-so-far colours
+    // multicolouring (Section 7; dense forms only), NULL / 0 otherwise
+    const int* dem;           // n demands c_i in [1, TC_MAX_DEMAND]
+    uint16_t* cm;             // D x n x cmax colour sets, increasing, 0xFFFF past c_i
+    uint16_t* best_m;         // n x cmax colour sets of the best-so-far individual
+    int cmax;                 // largest demand
+    int mt_max;               // largest value of m~: D, or D cmax in the multicolouring
     // dense forms (NULL in the one-hot form)
     float* M32;               // n_pad x n_pad group concentration from a GEMM (k_pairs zeroes it)
     int ldm;
@@ -92,6 +104,7 @@ struct tc_kparams {
 // the 32 rows of one colour are one 128-byte line.  Rows n .. 32 nT - 1 of
 // the last tile are padding (zero, never read).
 constexpr int TC_WT = 32;
+constexpr int TC_MAX_DEMAND = 8;  // colours a vertex may take in the multicolouring
 __host__ __device__ inline size_t tc_w_index(int d, int i, int j, int nT, int k) {
     return (((size_t)d * nT + i / TC_WT) * k + j) * TC_WT + (i % TC_WT);
 }
@@ -172,6 +185,8 @@ cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, co
 int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);
+cudaError_t tc_launch_assign_multi(const tc_kparams& P, int clear_old, cudaStream_t s);
+cudaError_t tc_launch_classes_multi(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_onehot_build(const tc_kparams& P, cudaStream_t s);
 
 int tc_relaxed_run(const tc_kparams& P, const float* W, float tau, long long t, float* loss, float* gradW,

@@ -269,13 +269,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
                 } else {
                     mt = (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
                 }
-                mt = min(max(mt, 0), D);  // a count of individuals: the tables hold D + 1 entries
+                // a count of shared colours: the tables hold mt_max + 1 entries
+                mt = min(max(mt, 0), P.mt_max);
                 const bool edge = (P.adj[(size_t)i * P.adj_words + (m >> 5)] >> (m & 31)) & 1u;
                 if (m == i) {
-                    mt = D;
+                    // m~_ii: D (one colour per vertex), from the GEMM D c_i in the multicolouring
+                    if (!from_gemm) mt = D;
                     if (P.bonus_diag) {
-                        bb = -sg * (cB * P.lutB[D]);
-                        var += P.powB[D];
+                        bb = -sg * (cB * P.lutB[mt]);
+                        var += P.powB[mt];
                     }
                 } else if (edge) {
                     // the A.S term enters through B only in the one-hot form
@@ -359,7 +361,7 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
     long long fc = 0, fe = 0;
     unsigned long long key = ~0ull;
     float ka = 0.f, va = 0.f;
-    const bool part = tc_is_partition(P.problem), with_eq = tc_has_equity(P.problem);
+    const bool part = tc_is_partition(P.problem), with_eq = tc_has_additive(P.problem);
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
         // k_gsum summed gamma_d(i) over the vertices: each conflict twice
         const int a = __ldcg(P.fcolor + d) / 2, b = __ldcg(P.feq + d);
@@ -367,7 +369,8 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
         fc += a;
         fe += b;
         // the fitness of the problem: monochromatic or (partitioning) cut edges,
-        // plus f_eq for the ECP and the balanced partitioning
+        // plus f_eq for the ECP and the balanced partitioning, or f_mscp for
+        // the minimum sum colouring
         const long long fobj = part ? P.n_edges - a : (long long)a;
         const unsigned long long f = (unsigned long long)(fobj + (with_eq ? b : 0));
         const unsigned long long kk = (f << 32) | (unsigned)d;
@@ -433,9 +436,13 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
         s_better = better;
     }
     __syncthreads();
-    if (s_better)
+    if (s_better) {
         for (int i = threadIdx.x; i < P.n; i += blockDim.x)
             P.best[i] = P.c[(size_t)s_dstar * P.n + i];
+        if (P.cm)  // multicolouring: the colour sets too
+            for (size_t e = threadIdx.x; e < (size_t)P.n * P.cmax; e += blockDim.x)
+                P.best_m[e] = P.cm[(size_t)s_dstar * P.n * P.cmax + e];
+    }
     if (threadIdx.x == 0) st->done_gsum = 0u;
 }
 
@@ -506,13 +513,22 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
         run += ph;
     }
     if (threadIdx.x == CLS_THREADS - 1) od[k] = s_scan[32 + nwp - 1];
-    // equity fitness (eq. 3) and its gradient sign (eq. 14)
+    // the additive fitness term and its gradient factor: equity (eq. 3)
+    // with the sign of eq. 14, or for the minimum sum colouring the colour
+    // costs f_mscp = sum_j #V_{d,j} z_j, whose gradient is z_j (Section 7)
     const int c1 = n / k, c2 = (n + k - 1) / k;
+    const bool mscp = P.problem == TC_MSCP;
     long long fe = 0;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const int h = s_hist[j];
-        fe += min(abs(h - c1), abs(h - c2));
-        P.E[(size_t)d * k + j] = (int8_t)(h > c2 ? 1 : (h < c1 ? -1 : 0));
+        if (mscp) {
+            const int z = __ldg(P.zcost + j);
+            fe += (long long)h * z;
+            P.E[(size_t)d * k + j] = (float)z;
+        } else {
+            fe += min(abs(h - c1), abs(h - c2));
+            P.E[(size_t)d * k + j] = h > c2 ? 1.0f : (h < c1 ? -1.0f : 0.0f);
+        }
     }
     fe = block_sum<long long>(fe, sh_ll);
     if (threadIdx.x == 0) P.feq[d] = (int)fe;
@@ -653,11 +669,11 @@ __device__ __forceinline__ void fence_proxy_async() {
 // and four independent loads of B.  BS > 0: B rows BS floats apart (the
 // shared panel), else `bstride`.  STG: pm, of and xs (= nu t E_dj) are the
 // warp's shared-memory copies; else pm, of in global memory and xs unused
-// (Ed, nut give the equity term).  Gout[j * 32] receives the class sum + nu t
-// E_dj (+ gs times the gamma-matrix entry in the dense forms: gs = -1 for the
-// partitioning problems, whose A.S term changes sign).
+// (Ed, nut give the additive term).  Gout[j * 32] receives the class sum +
+// nu t E_dj (+ gs times the gamma-matrix entry in the dense forms: gs = -1 for
+// the partitioning problems, whose A.S term changes sign).
 template <int BS, bool STG>
-__device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const float* xs, const int8_t* Ed,
+__device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, const float* xs, const float* Ed,
                                            const uint16_t* grow, float gs, int gstride, const float* Bl,
                                            int bstride, float nut, int k, int jb, int je, float* Gout) {
     const int bs = BS > 0 ? BS : bstride;
@@ -680,7 +696,7 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
             extra = xs[j];
         } else {
             e_next = (j + 2 <= k) ? __ldg(of + j + 2) : 0;  // next bound, ahead of use
-            extra = nut * (float)__ldg(Ed + j);
+            extra = nut * __ldg(Ed + j);
         }
         if (grow) {
             extra += gs * (float)g0;
@@ -764,11 +780,11 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
 // additions per iteration instead of D n^2.  Accumulates in Gs[j * 32].
 // Also counts gamma_d(i) (eq. 1): the neighbours sharing i's colour.
 __device__ __forceinline__ int neighbour_sums(const int* rowptr, const int* colidx, const uint16_t* cd,
-                                              const int8_t* Ed, const uint16_t* grow, float gs, int gstride,
+                                              const float* Ed, const uint16_t* grow, float gs, int gstride,
                                               const float* Bl, int bstride, float nut, int k, float* Gs, int i,
                                               bool valid) {
     for (int j = 0; j < k; ++j) {
-        float g0 = nut * (float)__ldg(Ed + j);
+        float g0 = nut * __ldg(Ed + j);
         if (grow) g0 += gs * (float)__ldg(grow + (size_t)j * gstride);
         Gs[j * 32] = g0;
     }
@@ -816,9 +832,9 @@ __device__ __forceinline__ int own_class_conflicts(const uint32_t* pm, const int
 
 // One 128-byte line per lane: the item's sorted vertices, class offsets and
 // equity signs arrive in L1 in parallel instead of one L2 round trip per line.
-__device__ __forceinline__ void prefetch_item(const uint32_t* pm, int plen, const int* of, int k, const int8_t* Ed,
+__device__ __forceinline__ void prefetch_item(const uint32_t* pm, int plen, const int* of, int k, const float* Ed,
                                               int lane) {
-    const int lp = (4 * plen + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (k + 127) / 128;
+    const int lp = (4 * plen + 127) / 128, lo = (4 * (k + 1) + 127) / 128, le = (4 * k + 127) / 128;
     for (int l = lane; l < lp + lo + le; l += 32) {
         const char* a = l < lp ? (const char*)pm + 128 * l
                                : (l < lp + lo ? (const char*)of + 128 * (l - lp)
@@ -899,7 +915,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const int d = (int)(qq - (long long)T * D);
             const uint32_t* pm = P.perm + (size_t)d * P.perm_stride;
             const int* of = P.off + (size_t)d * (k + 1);
-            const int8_t* Ed = P.E + (size_t)d * k;
+            const float* Ed = P.E + (size_t)d * k;
             if (STG) {
                 pair_sync(unit);  // the pair's reads of the previous item are done
                 const uint4* src = reinterpret_cast<const uint4*>(pm);
@@ -908,7 +924,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
 #pragma unroll 4
                 for (int l = t64; l < P.perm_stride / 4; l += 64) dst[l] = __ldg(src + l);
                 for (int j = t64; j <= k; j += 64) os[j] = __ldg(of + j);
-                for (int j = t64; j < k; j += 64) xs[j] = nut * (float)__ldg(Ed + j);
+                for (int j = t64; j < k; j += 64) xs[j] = nut * __ldg(Ed + j);
                 pair_sync(unit);
             } else if (!CSR) {
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
@@ -946,7 +962,11 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 if (counter) {
                     conf = 0;
                     if (live) {
-                        if (P.G16)
+                        if (P.cm) {  // multicolouring: shared colours with the neighbours, over i's colours
+                            const uint16_t* set = P.cm + ((size_t)d * n + i0 + lane) * P.cmax;
+                            const int ci_n = __ldg(P.dem + i0 + lane);
+                            for (int qq = 0; qq < ci_n; ++qq) conf += __ldg(grow + (size_t)set[qq] * gstride);
+                        } else if (P.G16)
                             conf = __ldg(grow + (size_t)ci * gstride);  // the gamma matrix of the dense forms
                         else if (STG)
                             conf = own_class_conflicts<true>(ps, os, ci, Bl, bstride, gs);
@@ -1101,7 +1121,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     if (h != 0) return;
     // lower half wins ties: it holds the lower colours
     if (xb[64 + lane] > xb[lane]) newc = __float_as_int(xb[96 + lane]);
-    if (live) {
+    if (live && !P.cm) {  // (the multicolouring's next assignment is k_assign_multi)
         const int i = i0 + lane;
         if (P.S8 && cur != newc) {  // dense forms: move the one-hot entry of (d, i) in both operands
             const size_t co = (size_t)d * k + cur, cn = (size_t)d * k + newc;
@@ -1257,6 +1277,7 @@ cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
 }
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
+    if (P.cm) return tc_launch_classes_multi(P, s);  // multicolouring: a vertex in several classes
     const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // per-warp colour counts
     const int smem = (int)(counts + 16ll * ((P.n + 7) / 8));  // + the individual's colours
     cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

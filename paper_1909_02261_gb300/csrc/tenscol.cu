@@ -46,7 +46,14 @@ struct tc_ctx {
     float* d_Gbuf = nullptr;  // grad_S L tiles between k_gsum and k_update
     uint32_t* d_perm = nullptr;
     int* d_off = nullptr;
-    int8_t* d_E = nullptr;
+    float* d_E = nullptr;
+    int* d_z = nullptr;         // k colour costs (minimum sum colouring), z_j = j + 1 unless set
+    // multicolouring (tc_set_demands; dense forms): demands, colour sets
+    int cmax = 0;                // largest demand; 0: one colour per vertex
+    long long dem_sum = 0;       // sum of the demands
+    int* d_dem = nullptr;
+    uint16_t* d_cm = nullptr;
+    uint16_t* d_best_m = nullptr;
     int* d_fcolor = nullptr;
     int* d_feq = nullptr;
     float* d_loss_part = nullptr;
@@ -178,12 +185,18 @@ void free_population(tc_ctx* c) {
     dfree(c->d_perm);
     dfree(c->d_off);
     dfree(c->d_E);
+    dfree(c->d_z);
     dfree(c->d_fcolor);
     dfree(c->d_feq);
     dfree(c->d_loss_part);
     dfree(c->d_lut);
     dfree(c->d_st);
     dfree(c->d_best);
+    dfree(c->d_dem);
+    dfree(c->d_cm);
+    dfree(c->d_best_m);
+    c->cmax = 0;
+    c->dem_sum = 0;
     c->pop = false;
     c->D = c->k = c->Dp = 0;
 }
@@ -199,7 +212,7 @@ void free_graph(tc_ctx* c) {
 }
 
 int check_params(const tc_params* p) {
-    if (p->problem < TC_KCOL || p->problem > TC_KPART_BAL) return TC_ERR_ARG;
+    if (p->problem < TC_KCOL || p->problem > TC_MSCP) return TC_ERR_ARG;
     if (!(p->eta >= 0.f) || !(p->rho >= 1.f) || p->nb_iter < 1) return TC_ERR_ARG;
     if (!(p->alpha > 1.f) || !(p->beta > 1.f)) return TC_ERR_ARG;
     if (!(p->lambda_ >= 0.f) || !(p->mu >= 0.f) || !(p->nu >= 0.f) || !(p->sigma0 >= 0.f))
@@ -208,6 +221,17 @@ int check_params(const tc_params* p) {
         return TC_ERR_UNSUPPORTED;
     return TC_OK;
 }
+
+// Entries per individual of the colour-class lists (each vertex once per
+// colour it takes, each class padded to a multiple of 4) and the largest
+// value of m~ (the tables of k_pairs hold that many + 1 entries).
+int perm_stride_for(int n, int k, int cmax, long long dem_sum) {
+    const long long entries = cmax > 0 ? dem_sum : n;
+    return (int)((entries + 3ll * k + 7) & ~7ll);
+}
+int mt_max_for(int D, int cmax) { return D * (cmax > 0 ? cmax : 1); }
+int perm_stride(const tc_ctx* c) { return perm_stride_for(c->n, c->k, c->cmax, c->dem_sum); }
+int mt_max(const tc_ctx* c) { return mt_max_for(c->D, c->cmax); }
 
 tc_kparams make_kparams(tc_ctx* c, int commit) {
     tc_kparams P;
@@ -242,15 +266,17 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.Gbuf = c->d_Gbuf;
     P.ldb = c->ldb;
     P.perm = c->d_perm;
-    P.perm_stride = (c->n + 3 * c->k + 7) & ~7;
+    P.perm_stride = perm_stride(c);
     P.off = c->d_off;
     P.E = c->d_E;
+    P.zcost = c->d_z;
     P.fcolor = c->d_fcolor;
     P.feq = c->d_feq;
     P.loss_part = c->d_loss_part;
     P.n_pair_blocks = c->n_tiles;
     P.pair_tiles = c->d_tiles;
-    const int D1 = c->D + 1;
+    P.mt_max = mt_max(c);
+    const int D1 = P.mt_max + 1;
     P.lutA = c->d_lut;
     P.lutB = c->d_lut + D1;
     P.powA = c->d_lut + 2 * D1;
@@ -259,7 +285,13 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.best = c->d_best;
     // with mu = 0 the pair matrix vanishes off the edges; below a density of
     // 1/8 walking the adjacency lists beats walking all n vertices per class
-    P.csr_walk = c->p.mu == 0.0f && c->nnz * 8 < (long long)c->n * c->n;
+    P.csr_walk = c->p.mu == 0.0f && c->nnz * 8 < (long long)c->n * c->n && c->cmax == 0;
+    if (c->cmax > 0) {  // multicolouring
+        P.dem = c->d_dem;
+        P.cm = c->d_cm;
+        P.best_m = c->d_best_m;
+        P.cmax = c->cmax;
+    }
     if (c->p.form != TC_FORM_ONEHOT && c->d_M32) {
         P.M32 = c->d_M32;
         P.ldm = c->n_pad;
@@ -551,7 +583,9 @@ cudaError_t rebuild_onehot(tc_ctx* c) {
     if (!c->d_S8) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(c->d_S8, 0, (size_t)c->n_pad * c->ldg, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_S8T, 0, (size_t)c->ldg * c->n_pad, c->stream);
-    if (e == cudaSuccess) e = tc_launch_onehot_build(make_kparams(c, 0), c->stream);
+    if (e == cudaSuccess)  // multicolouring: the colour sets of Step 1 from W (they replace c)
+        e = c->cmax > 0 ? tc_launch_assign_multi(make_kparams(c, 0), 0, c->stream)
+                        : tc_launch_onehot_build(make_kparams(c, 0), c->stream);
     c->launches += 1;
     return e;
 }
@@ -559,7 +593,7 @@ cudaError_t rebuild_onehot(tc_ctx* c) {
 // The LUTs of the pair terms over the integer values v = 0..D of m~ (eq. 5,
 // 6, 13), computed once in double precision on the host.
 int upload_luts(tc_ctx* c) {
-    const int D1 = c->D + 1;
+    const int D1 = mt_max(c) + 1;
     std::vector<float> h(4 * (size_t)D1);
     const double a = c->p.alpha, b = c->p.beta;
     const bool part = tc_is_partition(c->p.problem);
@@ -668,7 +702,10 @@ int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
 cudaError_t launch_grad_update(tc_ctx* c, const tc_kparams& P, int debug_only) {
     cudaError_t e = timed(c, TC_KID_GSUM, [&] { return tc_launch_gsum(P, c->tmB, c->num_sms, c->stream); });
     if (e != cudaSuccess) return e;
-    return timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->num_sms, c->stream, debug_only); });
+    e = timed(c, TC_KID_UPDATE, [&] { return tc_launch_update(P, c->num_sms, c->stream, debug_only); });
+    // multicolouring: Step 1 of the next iteration (top-c_i sets, FP8 operands)
+    if (e == cudaSuccess && P.cm && debug_only == 0) e = tc_launch_assign_multi(P, 1, c->stream);
+    return e;
 }
 
 int launch_iteration(tc_ctx* c) {
@@ -687,7 +724,9 @@ int launch_iteration(tc_ctx* c) {
     return TC_OK;
 }
 
-int launches_per_iteration(const tc_ctx* c) { return c->p.form == TC_FORM_ONEHOT ? 4 : 6; }
+int launches_per_iteration(const tc_ctx* c) {
+    return (c->p.form == TC_FORM_ONEHOT ? 4 : 6) + (c->cmax > 0 ? 1 : 0);
+}
 
 int read_state(tc_ctx* c, tc_dev_state* h) {
     TC_CHECK(cudaMemcpyAsync(h, c->d_st, sizeof(*h), cudaMemcpyDeviceToHost, c->stream));
@@ -849,7 +888,7 @@ const char* tc_strerror(int code) {
 }
 
 int tc_params_default(tc_params* p, int problem) {
-    if (!p || problem < TC_KCOL || problem > TC_KPART_BAL) return TC_ERR_ARG;
+    if (!p || problem < TC_KCOL || problem > TC_MSCP) return TC_ERR_ARG;
     memset(p, 0, sizeof(*p));
     p->problem = problem;
     p->sigma0 = 0.01f;
@@ -858,7 +897,7 @@ int tc_params_default(tc_params* p, int problem) {
     p->lambda_ = 1e-5f;
     p->beta = 1.2f;
     p->mu = problem == TC_ECP ? 0.0f : 1e-6f;
-    p->nu = tc_has_equity(problem) ? 1e-5f : 0.0f;
+    p->nu = tc_has_additive(problem) ? 1e-5f : 0.0f;
     p->rho = 100.0f;
     p->nb_iter = 5;
     p->stop_on_legal = 1;
@@ -1028,7 +1067,7 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
         (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
         (rc = dalloc(&c->d_Gbuf, (size_t)D * ((n + 31) / 32) * 32 * k)) ||
         (rc = dalloc(&c->d_perm, (size_t)D * ((n + 3 * k + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
-        (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_fcolor, D)) ||
+        (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_z, (size_t)k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
         (rc = dalloc(&c->d_lut, 4 * (size_t)(D + 1))) || (rc = dalloc(&c->d_st, 1)) ||
         (rc = dalloc(&c->d_best, n))) {
@@ -1057,6 +1096,10 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
         e = cudaMemsetAsync(c->d_B, 0, sizeof(float) * (size_t)(n + 1) * ((n + 3) & ~3), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * D, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_best, 0, sizeof(uint16_t) * n, c->stream);
+    std::vector<int> zdef(k);
+    for (int j = 0; j < k; ++j) zdef[j] = j + 1;  // colours numbered 1..k
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_z, zdef.data(), sizeof(int) * k, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)  // padding rows of the last vertex tile stay zero
@@ -1087,6 +1130,8 @@ int tc_set_params(tc_ctx* c, const tc_params* p) {
     if (!c->pop) return TC_ERR_STATE;
     int rc = check_params(p);
     if (rc) return rc;
+    if (c->cmax > 0 && (p->form == TC_FORM_ONEHOT || p->problem != TC_KCOL))
+        return TC_ERR_UNSUPPORTED;  // the multicolouring runs the k-COL problem in a dense form
     DeviceGuard g(c->device);
     TC_CHECK(cudaStreamSynchronize(c->stream));
     tc_params old = c->p;
@@ -1393,7 +1438,7 @@ int tc_st_grad_dev(tc_ctx* c, float* gradW_dev, float* loss_dev) {
 int tc_relaxed_dev(tc_ctx* c, const float* W_dev, float tau, int64_t t, float* loss_dev, float* gradW_dev) {
     if (!c || !W_dev || !loss_dev || !gradW_dev || !(tau > 0.f) || t < 0) return TC_ERR_ARG;
     if (!c->pop) return TC_ERR_STATE;
-    if (tc_is_partition(c->p.problem)) return TC_ERR_ARG;  // the relaxation covers the GCP terms
+    if (tc_is_partition(c->p.problem) || c->p.problem == TC_MSCP) return TC_ERR_ARG;  // the GCP terms only
     if (c->k > 128) return TC_ERR_UNSUPPORTED;
     DeviceGuard g(c->device);
     const int n = c->n;
@@ -1439,7 +1484,8 @@ int tc_kdescent(tc_ctx* c, uint64_t seed, int D, int k_start, int k_min, int64_t
     p.stop_on_legal = 1;
     int rc = check_params(&p);
     if (rc) return rc;
-    if (tc_is_partition(p.problem)) return TC_ERR_ARG;  // k-descent is for the colouring problems
+    // k-descent is for the problems whose fitness reaches 0 on a solution
+    if (tc_is_partition(p.problem) || p.problem == TC_MSCP) return TC_ERR_ARG;
     std::vector<int32_t> col(c->n);
     long long total = 0;
     for (int k = k_start; k >= k_min; --k) {
@@ -1455,6 +1501,130 @@ int tc_kdescent(tc_ctx* c, uint64_t seed, int D, int k_start, int k_min, int64_t
         if (k_best) *k_best = k;
         if (coloring) memcpy(coloring, col.data(), sizeof(int32_t) * (size_t)c->n);
     }
+    return TC_OK;
+}
+
+int tc_set_color_costs(tc_ctx* c, const int32_t* z, int k) {
+    if (!c || !z) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    if (k != c->k) return TC_ERR_ARG;
+    long long zmax = 0;
+    for (int j = 0; j < k; ++j) {
+        if (z[j] < 0) return TC_ERR_ARG;
+        zmax = std::max(zmax, (long long)z[j]);
+    }
+    // the reduction keeps f = f_color + f_mscp in 31 bits
+    if (zmax * c->n + c->nnz / 2 >= (1ll << 31)) return TC_ERR_UNSUPPORTED;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaMemcpyAsync(c->d_z, z, sizeof(int) * (size_t)k, cudaMemcpyHostToDevice, c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+int tc_set_demands(tc_ctx* c, const int32_t* demand, int n) {
+    if (!c || !demand) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    if (n != c->n) return TC_ERR_ARG;
+    if (c->p.form == TC_FORM_ONEHOT || c->p.problem != TC_KCOL) return TC_ERR_UNSUPPORTED;
+    int cmax = 1;
+    long long sum = 0;
+    for (int i = 0; i < n; ++i) {
+        if (demand[i] < 1 || demand[i] > std::min(c->k, TC_MAX_DEMAND)) return TC_ERR_ARG;
+        cmax = std::max(cmax, (int)demand[i]);
+        sum += demand[i];
+    }
+    if ((long long)c->D * cmax >= (1ll << 24)) return TC_ERR_UNSUPPORTED;  // M~ exact in FP32
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    const int new_cmax = cmax > 1 ? cmax : 0;  // all demands 1: one colour per vertex
+    const long long new_sum = cmax > 1 ? sum : 0;
+    // new buffers first: a failed allocation leaves the context as it was
+    uint32_t* perm = nullptr;
+    float* lut = nullptr;
+    int* dem = nullptr;
+    uint16_t *cm = nullptr, *best_m = nullptr;
+    int rc;
+    if ((rc = dalloc(&perm, (size_t)c->D * perm_stride_for(c->n, c->k, new_cmax, new_sum))) ||
+        (rc = dalloc(&lut, 4 * (size_t)(mt_max_for(c->D, new_cmax) + 1))) ||
+        (new_cmax > 0 && ((rc = dalloc(&dem, (size_t)n)) || (rc = dalloc(&cm, (size_t)c->D * n * new_cmax)) ||
+                          (rc = dalloc(&best_m, (size_t)n * new_cmax))))) {
+        dfree(perm);
+        dfree(lut);
+        dfree(dem);
+        dfree(cm);
+        dfree(best_m);
+        return rc;
+    }
+    dfree(c->d_perm);
+    dfree(c->d_lut);
+    dfree(c->d_dem);
+    dfree(c->d_cm);
+    dfree(c->d_best_m);
+    c->d_perm = perm;
+    c->d_lut = lut;
+    c->d_dem = dem;
+    c->d_cm = cm;
+    c->d_best_m = best_m;
+    c->cmax = new_cmax;
+    c->dem_sum = new_sum;
+    if (dem) TC_CHECK(cudaMemcpyAsync(dem, demand, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = upload_luts(c))) return rc;
+    // Step 1 again under the new demands, and a fresh best-so-far
+    TC_CHECK(tc_launch_assign(make_kparams(c, 0), c->stream));
+    TC_CHECK(rebuild_onehot(c));
+    c->launches += 1;
+    tc_dev_state h;
+    if ((rc = read_state(c, &h))) return rc;
+    h.best_f = -1;
+    h.best_d = -1;
+    h.best_t = -1;
+    h.stop = 0;
+    TC_CHECK(cudaMemcpyAsync(c->d_st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    drop_graph_exec(c);
+    return TC_OK;
+}
+
+int tc_best_multi(tc_ctx* c, int32_t* colors, int stride, int64_t* conflicts, int32_t* individual,
+                  int64_t* iteration) {
+    if (!c) return TC_ERR_ARG;
+    if (!c->pop || c->cmax == 0) return TC_ERR_STATE;
+    if (colors && stride < c->cmax) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    tc_dev_state h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    if (h.best_f < 0) return TC_ERR_STATE;
+    if (colors) {
+        std::vector<uint16_t> b((size_t)c->n * c->cmax);
+        TC_CHECK(cudaMemcpyAsync(b.data(), c->d_best_m, sizeof(uint16_t) * b.size(), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        TC_CHECK(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < c->n; ++i)
+            for (int q = 0; q < stride; ++q) {
+                const int v = q < c->cmax ? b[(size_t)i * c->cmax + q] : 0xFFFF;
+                colors[(size_t)i * stride + q] = v == 0xFFFF ? -1 : v;
+            }
+    }
+    if (conflicts) *conflicts = h.best_fcolor;
+    if (individual) *individual = h.best_d;
+    if (iteration) *iteration = h.best_t;
+    return TC_OK;
+}
+
+int tc_get_multicolors(tc_ctx* c, int32_t* colors, int stride) {
+    if (!c || !colors) return TC_ERR_ARG;
+    if (!c->pop || c->cmax == 0) return TC_ERR_STATE;
+    if (stride < c->cmax) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    std::vector<uint16_t> b((size_t)c->D * c->n * c->cmax);
+    TC_CHECK(cudaMemcpyAsync(b.data(), c->d_cm, sizeof(uint16_t) * b.size(), cudaMemcpyDeviceToHost, c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    for (size_t r = 0; r < (size_t)c->D * c->n; ++r)
+        for (int q = 0; q < stride; ++q) {
+            const int v = q < c->cmax ? b[r * c->cmax + q] : 0xFFFF;
+            colors[r * stride + q] = v == 0xFFFF ? -1 : v;
+        }
     return TC_OK;
 }
 

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 TC_OK = 0
-TC_KCOL, TC_ECP, TC_KPART, TC_KPART_BAL = 0, 1, 2, 3  # problems (tenscol.h)
+TC_KCOL, TC_ECP, TC_KPART, TC_KPART_BAL, TC_MSCP = 0, 1, 2, 3, 4  # problems (tenscol.h)
 TC_FORM_ONEHOT, TC_FORM_DENSE_FP8, TC_FORM_DENSE_FP32 = 0, 1, 2
 TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE, TC_KID_GEMM_M, TC_KID_GEMM_G, TC_KID_GSUM = range(6)
 KERNEL_NAMES = {TC_KID_PAIRS: "k_pairs", TC_KID_CLASSES: "k_classes", TC_KID_UPDATE: "k_update",
@@ -96,6 +96,10 @@ def load(build_if_missing: bool = True):
                                   P(i64)]),
         "tc_dense_plan": (C.c_int, [vp, vp, vp]),
         "tc_dense_set_plan": (C.c_int, [vp, vp]),
+        "tc_set_color_costs": (C.c_int, [vp, vp, C.c_int]),
+        "tc_set_demands": (C.c_int, [vp, vp, C.c_int]),
+        "tc_best_multi": (C.c_int, [vp, vp, C.c_int, vp, vp, vp]),
+        "tc_get_multicolors": (C.c_int, [vp, vp, C.c_int]),
         "tc_batch_create": (C.c_int, [P(vp), C.c_int]),
         "tc_batch_add": (C.c_int, [vp, vp]),
         "tc_batch_step": (C.c_int, [vp, i64, C.c_int]),
@@ -290,6 +294,34 @@ class TensCol:
         cluster) triples, e.g. (128, 256, 4) or (256, 256, 2) for a CTA pair."""
         plan = np.array([*gamma, *mtilde, mtilde_splits], np.int32)
         _ck(self._L.tc_dense_set_plan(self.h, _ptr(plan)), "tc_dense_set_plan")
+
+    def tc_set_color_costs(self, z):
+        """Colour costs z_l of the minimum sum colouring (TC_MSCP), one per colour."""
+        z = np.ascontiguousarray(z, np.int32)
+        _ck(self._L.tc_set_color_costs(self.h, _ptr(z), int(z.size)), "tc_set_color_costs")
+
+    def tc_set_demands(self, demand):
+        """Multicolouring: vertex i takes demand[i] colours (dense forms, k-COL)."""
+        dm = np.ascontiguousarray(demand, np.int32)
+        _ck(self._L.tc_set_demands(self.h, _ptr(dm), int(dm.size)), "tc_set_demands")
+        self.cmax = int(dm.max()) if dm.size else 1
+
+    def tc_best_multi(self):
+        """Best-so-far multicolouring: colour sets (n x cmax, -1 padded) and counts."""
+        stride = max(1, getattr(self, "cmax", 1))
+        col = np.empty((self.n, stride), np.int32)
+        fc, t = C.c_int64(), C.c_int64()
+        d = C.c_int32()
+        _ck(self._L.tc_best_multi(self.h, _ptr(col), stride, C.byref(fc), C.byref(d), C.byref(t)),
+            "tc_best_multi")
+        return dict(colors=col, conflicts=fc.value, individual=d.value, iteration=t.value)
+
+    def tc_get_multicolors(self):
+        """Current colour sets of the population: D x n x cmax, -1 padded."""
+        stride = max(1, getattr(self, "cmax", 1))
+        col = np.empty((self.D, self.n, stride), np.int32)
+        _ck(self._L.tc_get_multicolors(self.h, _ptr(col), stride), "tc_get_multicolors")
+        return col
 
     def tc_launch_count(self) -> int:
         c = C.c_int64()

@@ -14,12 +14,18 @@ def f32(x):
     return float(np.float32(x))
 
 
-def oracle_params(p):
-    """Oracle parameter block holding exactly the FP32 values the library uses."""
+def oracle_params(p, zcost=None):
+    """Oracle parameter block holding exactly the FP32 values the library uses
+    (zcost: the colour costs of the minimum sum colouring, None = l + 1)."""
     return O.make_params(problem=int(p.problem), sigma0=f32(p.sigma0), eta=f32(p.eta),
                          alpha=f32(p.alpha), lambda_=f32(p.lambda_), beta=f32(p.beta),
                          mu=f32(p.mu), nu=f32(p.nu), rho=f32(p.rho), nb_iter=int(p.nb_iter),
-                         bonus_diag=int(p.bonus_diag))
+                         bonus_diag=int(p.bonus_diag), zcost=zcost)
+
+
+def additive(ref, po):
+    """The oracle's additive fitness term: f_mscp (minimum sum colouring) or f_eq."""
+    return ref["f_mscp"] if po.problem == 4 else ref["f_eq"]
 
 
 def w_step_rel_error(W_gpu, ref, po, t):
@@ -45,7 +51,7 @@ def loss_close(gpu_loss, ref, po, t, rtol=1e-5):
     assert kap == _approx(ref["kappa"], rtol)
     assert var == _approx(ref["varpi"], rtol)
     fit = ref["f_cut"] if po.problem in (2, 3) else ref["f_color"]
-    scale = abs(fit.sum()) + po.nu * t * abs(ref["f_eq"].sum()) + \
+    scale = abs(fit.sum()) + po.nu * t * abs(additive(ref, po).sum()) + \
         po.lambda_ * t * abs(ref["kappa"]) + po.mu * t * abs(ref["varpi"])
     assert abs(L - ref["loss"]) <= rtol * max(scale, 1.0), (L, ref["loss"])
 
@@ -55,18 +61,19 @@ def _approx(x, rtol):
     return pytest.approx(x, rel=rtol, abs=1e-30)
 
 
-def check_iteration(ctx, rp, ci, p, t, want_G=True):
+def check_iteration(ctx, rp, ci, p, t, want_G=True, zcost=None):
     """Evaluate + one step on the GPU vs one oracle step from the GPU's own
-    weights: exact colours / conflicts / equity / M~, G and W within W_RTOL."""
+    weights: exact colours / conflicts / equity (or colour costs) / M~, G and
+    W within W_RTOL."""
     W0, t0 = ctx.tc_get_state()
     assert t0 == t
-    po = oracle_params(p)
+    po = oracle_params(p, zcost)
     ev = ctx.tc_evaluate(want_G=want_G)
     ref = O.step(rp, ci, W0, po, t, stop_on_legal=False)
     assert np.array_equal(ev["colors"], ref["colors"])
     assert np.array_equal(ev["gamma_own"], ref["gamma_own"])
     assert np.array_equal(ev["f_color"], ref["f_color"])
-    assert np.array_equal(ev["f_eq"], ref["f_eq"])
+    assert np.array_equal(ev["f_eq"], additive(ref, po))
     assert np.array_equal(ev["Mt"], ref["Mt"])
     loss_close(ev["loss"], ref, po, t)
     if want_G:
