@@ -157,3 +157,16 @@ def test_autotuner_times_candidates_and_rejects_bad_plans():
     with make_ctx(rp, ci, 5, 20, params(TC_KCOL, form=TC_FORM_ONEHOT), W, 0) as ctx:
         with pytest.raises(TensColError):
             ctx.tc_dense_plan()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_full_size_workload_one_step(form):
+    """The benchmark workload G(1000, 0.5), k = 90, D = 200 in the dense forms,
+    on the plan the autotuner picks (as the benchmark runs it), compared in
+    full on one iteration: every Gamma-derived conflict count and every M~
+    entry exactly, grad_S L and the W step within the step tolerance."""
+    rp, ci = inputs.gnp(1000, 0.5, seed=2)
+    W = inputs.init_weights(200, 1000, 90, 0.01, seed=2)
+    p = params(TC_KCOL, stop_on_legal=0, form=form)
+    with make_ctx(rp, ci, 200, 90, p, W, 777) as ctx:
+        check_iteration(ctx, rp, ci, p, 777, want_G=True)

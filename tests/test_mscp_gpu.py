@@ -74,3 +74,13 @@ def test_color_costs_are_checked():
                 ctx.tc_set_color_costs(bad)
         with pytest.raises(TensColError):
             ctx.tc_kdescent(1, 3, 5, 3, 10, params(TC_MSCP))
+
+
+def test_mscp_at_workload_shape():
+    """Minimum sum colouring on the benchmark's graph shape (G(1000, 0.5),
+    k = 90), default costs, one-hot form, one iteration compared in full."""
+    rp, ci = inputs.gnp(1000, 0.5, seed=2)
+    W = inputs.init_weights(40, 1000, 90, 0.01, seed=2)
+    p = params(TC_MSCP, stop_on_legal=0, lambda_=1e-4, mu=1e-5, nu=1e-5)
+    with make_ctx(rp, ci, 40, 90, p, W, 321) as ctx:
+        check_iteration(ctx, rp, ci, p, 321)

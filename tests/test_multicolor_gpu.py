@@ -149,3 +149,15 @@ def test_multicolor_refusals():
         ctx.tc_set_state(W, 0)
         ctx.tc_step(2)  # still runs as a multicolouring
         assert ctx.tc_get_multicolors().shape == (D, n, 2)
+
+
+def test_multicolor_at_workload_shape():
+    """Multicolouring on the benchmark's graph shape (G(1000, 0.5), k = 90)
+    with demands 1..3, FP8 tensor-core form, one iteration compared in full."""
+    n, D, k = 1000, 24, 90
+    rp, ci = inputs.gnp(n, 0.5, seed=2)
+    W = inputs.init_weights(D, n, k, 0.01, seed=2)
+    demand = np.random.default_rng(2).integers(1, 4, n).astype(np.int32)
+    p = params(TC_KCOL, stop_on_legal=0, lambda_=1e-4, mu=1e-5, form=TC_FORM_DENSE_FP8)
+    with make_ctx(rp, ci, D, k, p, W, 321, demand) as ctx:
+        check_multi_iteration(ctx, rp, ci, p, 321, demand)

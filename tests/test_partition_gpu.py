@@ -105,3 +105,13 @@ def test_partition_rejected_where_undefined():
         ctx.tc_init_graph(50, rp, ci)
         with pytest.raises(TensColError):
             ctx.tc_kdescent(1, 4, 6, 3, 10, params(TC_KPART))
+
+
+def test_partition_at_workload_shape():
+    """Balanced k-partitioning on the benchmark's graph shape (G(1000, 0.5),
+    k = 90) in the one-hot form, one iteration compared in full."""
+    rp, ci = inputs.gnp(1000, 0.5, seed=2)
+    W = inputs.init_weights(40, 1000, 90, 0.01, seed=2)
+    p = params(TC_KPART_BAL, stop_on_legal=0, lambda_=1e-4, mu=1e-5, nu=1e-4)
+    with make_ctx(rp, ci, 40, 90, p, W, 321) as ctx:
+        check_iteration(ctx, rp, ci, p, 321)
