@@ -192,6 +192,7 @@ int tc_step_async(tc_ctx *ctx, int64_t n_iters);
 #define TC_KID_GEMM_M 3  /* dense forms: M~ = S S^T GEMM                     */
 #define TC_KID_GEMM_G 4  /* dense forms: Gamma = A S GEMM                    */
 #define TC_KID_GSUM 5    /* grad_S L tiles (class sums of the pair matrix)   */
+#define TC_KID_GEMM_F 6  /* dense FP8 form: M~ and Gamma in one launch       */
 #define TC_NUM_KID 8
 
 /* Per-kernel device timing with CUDA events recorded around every launch
@@ -272,13 +273,15 @@ int tc_kdescent(tc_ctx *ctx, uint64_t seed, int D, int k_start, int k_min, int64
 /* The plan the autotuner chose for the dense contractions of this context
  * (tc_init_population / tc_set_params time every candidate on the context's
  * own operands and keep the fastest; the FP32 form keeps one fixed plan).
- * `plan` has 8 entries:
+ * `plan` has 9 entries:
  *   plan[0] Gamma unit rows: 128 (one CTA per unit) or 256 (a CTA pair
  *           running 256-row cta_group::2 MMAs)
  *   plan[1] Gamma column tile (128 or 256)   plan[2] Gamma cluster size
  *   plan[3..5] the same for M~               plan[6] M~ K splits
- *   plan[7] candidates timed
- *   us[0], us[1]: best times of Gamma and M~ in microseconds (0 for FP32).
+ *   plan[7] 1: both contractions in one launch (M~ units first)
+ *   plan[8] candidates timed
+ *   us[0..2] (us may be NULL; else 3 floats): best times of Gamma, M~ and
+ *   the single launch of both in microseconds (0 when not timed, or FP32).
  * TC_ERR_STATE when the context has no dense form. */
 int tc_dense_plan(tc_ctx *ctx, int32_t *plan, float *us);
 
@@ -320,7 +323,9 @@ int tc_best_multi(tc_ctx *ctx, int32_t *colors, int stride, int64_t *conflicts, 
  * stride + q] as in tc_best_multi (D * n * stride entries, caller-owned). */
 int tc_get_multicolors(tc_ctx *ctx, int32_t *colors, int stride);
 
-/* Pins the plan of the dense contractions: plan[0..6] as above.  The FP8
+/* Pins the plan of the dense contractions: plan[0..7] as above (plan[7] = 1
+ * needs one shape for both, 128-row units and clusters of 1, or 2 with
+ * 256-wide tiles; the FP8 form only).  The FP8
  * form accepts, per contraction, unit rows 128 with column tile 128 / 256
  * and clusters sharing the B tile (Gamma: 1 / 2 / 4 dividing the 128-row
  * tiles; M~: 1, or 2 with 256-wide tiles), or unit rows 256 with column tile

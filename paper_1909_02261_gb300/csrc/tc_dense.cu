@@ -325,7 +325,8 @@ __device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y,
 template <int BN_, int CL, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-              const __grid_constant__ CUtensorMap tmC, tc_gemm_args g) {
+              const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmX2,
+              const __grid_constant__ CUtensorMap tmY2, const __grid_constant__ CUtensorMap tmC2, tc_gemm_args g) {
     static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
     using Sh = TcShape<BN_, PAIR>;
     constexpr int STAGES = Sh::STAGES, A_BYTES = Sh::A_BYTES, B_BYTES = Sh::B_BYTES,
@@ -376,7 +377,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             unsigned gk = 0;
             bool ok = true;
             for (int u = u_first; u < g.n_units && ok; u += u_step) {
-                const int4 w = g.units[u];
+                int4 w = g.units[u];
+                const bool second = (w.y & TC_UNIT_SECOND) != 0;  // a unit of the other contraction
+                w.y &= ~TC_UNIT_SECOND;
+                const CUtensorMap* mX = second ? &tmX2 : &tmX;
+                const CUtensorMap* mY = second ? &tmY2 : &tmY;
                 for (int kb = w.z; kb < w.w; ++kb, ++gk) {
                     const int s = gk % STAGES;
                     const unsigned r = gk / STAGES;
@@ -386,15 +391,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         // both CTAs' bytes complete on the even CTA's barrier
                         const uint32_t fb = peer_addr(&full[s], 0u);
                         if (leader) bar_expect_tx(&full[s], 2 * STAGE_BYTES);
-                        tma_load_2d_pair(sa, &tmX, kb * BK, w.x * TM + row_half, fb);
-                        tma_load_2d_pair(sa + A_BYTES, &tmY, kb * BK, w.y * BN_ + (int)crank * (BN_ / 2), fb);
+                        tma_load_2d_pair(sa, mX, kb * BK, w.x * TM + row_half, fb);
+                        tma_load_2d_pair(sa + A_BYTES, mY, kb * BK, w.y * BN_ + (int)crank * (BN_ / 2), fb);
                     } else {
                         bar_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(sa, &tmX, kb * BK, w.x * BM, &full[s]);
+                        tma_load_2d(sa, mX, kb * BK, w.x * BM, &full[s]);
                         if (CL == 1)
-                            tma_load_2d(sa + A_BYTES, &tmY, kb * BK, w.y * BN_, &full[s]);
+                            tma_load_2d(sa + A_BYTES, mY, kb * BK, w.y * BN_, &full[s]);
                         else  // my slice of the shared B tile, to every CTA of the cluster
-                            tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), &tmY, kb * BK,
+                            tma_load_2d_mc(sa + A_BYTES + crank * (B_BYTES / CL), mY, kb * BK,
                                            w.y * BN_ + (int)crank * (BN_ / CL), &full[s], cmask);
                     }
                 }
@@ -452,8 +457,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // that read it is done (bulk groups are per thread: lane 0 issues and
         // waits for them all).
         const int q = warp & 3, ew = warp - 2;
-        const bool gamma = g.mode == TC_GEMM_GAMMA;
-        const uint32_t bytes_b = gamma ? 2048u : 4096u;   // [32 cols][32 rows] u16 | [32 rows][32 f32]
+        // [32 cols][32 rows] u16 (2 KB, Gamma) | [32 rows][32 f32] (4 KB, M~); a
+        // launch of both contractions gives every chunk the 4 KB buffer
+        const uint32_t bytes_b = (g.fused || g.mode != TC_GEMM_GAMMA) ? 4096u : 2048u;
         const unsigned nb = STG_WARP / bytes_b;            // buffers per warp (1, 2 or 4)
         const uint32_t stg = su32(smem + STAGES * STAGE_BYTES) + (uint32_t)ew * STG_WARP;
         uint8_t* stg_gen = smem + STAGES * STAGE_BYTES + ew * STG_WARP;
@@ -462,7 +468,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         static_assert(NCH >= 2 && NCH % 2 == 0, "each epilogue warp takes an even number of chunks");
         const int cbase = (ew >> 2) * NCH;                 // its first chunk
         for (int u = u_first; u < g.n_units; u += u_step, ++ui) {
-            const int4 w = g.units[u];
+            int4 w = g.units[u];
+            const bool second = (w.y & TC_UNIT_SECOND) != 0;
+            w.y &= ~TC_UNIT_SECOND;
+            const bool gamma = (second ? g.mode2 : g.mode) == TC_GEMM_GAMMA;
+            const CUtensorMap* mC = second ? &tmC2 : &tmC;
+            const int cols_alloc = second ? g.cols_alloc2 : g.cols_alloc;
             const int a = ui & 1;
             const unsigned ua = ui >> 1;
             if (!bar_wait(&tfull[a], ua & 1u, &abort_flag, g.err)) break;
@@ -500,9 +511,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) {
                     const int col0 = w.y * BN_ + 32 * c;
                     if (!gamma)
-                        tma_reduce_add_2d(&tmC, col0, row0, stg_gen + b * bytes_b);
-                    else if (col0 < g.cols_alloc)  // columns past D k are padding: not stored
-                        tma_store_2d(&tmC, row0, col0, stg_gen + b * bytes_b);
+                        tma_reduce_add_2d(mC, col0, row0, stg_gen + b * bytes_b);
+                    else if (col0 < cols_alloc)  // columns past D k are padding: not stored
+                        tma_store_2d(mC, row0, col0, stg_gen + b * bytes_b);
                     else
                         asm volatile("cp.async.bulk.commit_group;" ::: "memory");  // an empty group keeps the count
                 }
@@ -690,6 +701,7 @@ static cudaError_t smem_opt_in() {
 
 template <int BN_, int CL, bool PAIR>
 static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                             const CUtensorMap& tmX2, const CUtensorMap& tmY2, const CUtensorMap& tmC2,
                              const tc_gemm_args& g, int slots, bool pdl, cudaStream_t s) {
     cudaError_t e = smem_opt_in<BN_, CL, PAIR>();
     if (e != cudaSuccess) return e;
@@ -698,7 +710,7 @@ static cudaError_t launch_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, con
     if (groups < 1) groups = 1;
     cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = tc_config<BN_, CL, PAIR>(groups, s, attr, pdl);
-    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL, PAIR>, tmX, tmY, tmC, g);
+    return cudaLaunchKernelEx(&cfg, k_gemm_tc<BN_, CL, PAIR>, tmX, tmY, tmC, tmX2, tmY2, tmC2, g);
 }
 
 template <int BN_, int CL, bool PAIR>
@@ -748,20 +760,27 @@ int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms) {
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
                               const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
                               cudaStream_t s) {
+    return tc_launch_gemm_tc2(tmX, tmY, tmC, tmX, tmY, tmC, g, slots, tm, cluster, bn, pdl, s);
+}
+
+cudaError_t tc_launch_gemm_tc2(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                               const CUtensorMap& tmX2, const CUtensorMap& tmY2, const CUtensorMap& tmC2,
+                               const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
+                               cudaStream_t s) {
     if (tm == 2 * BM)
-        return bn == 128 ? launch_tc<128, 2, true>(tmX, tmY, tmC, g, slots, pdl, s)
-                         : launch_tc<256, 2, true>(tmX, tmY, tmC, g, slots, pdl, s);
+        return bn == 128 ? launch_tc<128, 2, true>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s)
+                         : launch_tc<256, 2, true>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
     if (bn == 128) {
         switch (cluster) {
-            case 4: return launch_tc<128, 4, false>(tmX, tmY, tmC, g, slots, pdl, s);
-            case 2: return launch_tc<128, 2, false>(tmX, tmY, tmC, g, slots, pdl, s);
-            default: return launch_tc<128, 1, false>(tmX, tmY, tmC, g, slots, pdl, s);
+            case 4: return launch_tc<128, 4, false>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
+            case 2: return launch_tc<128, 2, false>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
+            default: return launch_tc<128, 1, false>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
         }
     }
     switch (cluster) {
-        case 4: return launch_tc<256, 4, false>(tmX, tmY, tmC, g, slots, pdl, s);
-        case 2: return launch_tc<256, 2, false>(tmX, tmY, tmC, g, slots, pdl, s);
-        default: return launch_tc<256, 1, false>(tmX, tmY, tmC, g, slots, pdl, s);
+        case 4: return launch_tc<256, 4, false>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
+        case 2: return launch_tc<256, 2, false>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
+        default: return launch_tc<256, 1, false>(tmX, tmY, tmC, tmX2, tmY2, tmC2, g, slots, pdl, s);
     }
 }
 

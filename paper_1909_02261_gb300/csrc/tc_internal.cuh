@@ -162,14 +162,19 @@ constexpr int TC_BT_BOX_ROWS = 128;  // rows per TMA box of the B column panel
 #define TC_GEMM_GAMMA 0  /* C uint16 transposed (tc_gamma_index); ldc = k, cols_alloc = D k */
 #define TC_GEMM_MTILDE 1 /* C float, atomic adds (K may be split)       */
 struct tc_gemm_args {
-    const int4* units;  // (tile row, tile column, first K block, end K block)
+    const int4* units;  // (tile row, tile column, first K block, end K block); bit 30
+                        // of the column marks a unit of the second contraction
     int n_units;
     int mode;
     void* C;
     int ldc;
     int rows_alloc, cols_alloc;
     int* err;
+    // one launch for both contractions: the marked units use the second set
+    // of tensor maps, this mode and column bound (fused = 0: no marked units)
+    int fused, mode2, cols_alloc2;
 };
+constexpr int TC_UNIT_SECOND = 1 << 30;
 // Shape of one contraction's work: rows of a unit (128 on one CTA, 256 on a
 // CTA pair), column tile, CTAs per cluster (sharing the B tile, or the pair).
 struct tc_gemm_shape {
@@ -182,6 +187,12 @@ int tc_gemm_tile_k();
 cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
                               const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
                               cudaStream_t s);
+// Both contractions in one launch: the units marked TC_UNIT_SECOND use tmX2,
+// tmY2, tmC2, g.mode2 and g.cols_alloc2 (g.fused = 1); 128-row units only.
+cudaError_t tc_launch_gemm_tc2(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
+                               const CUtensorMap& tmX2, const CUtensorMap& tmY2, const CUtensorMap& tmC2,
+                               const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
+                               cudaStream_t s);
 int tc_gemm_cluster_slots(int tm, int cluster, int bn, int num_sms);
 cudaError_t tc_launch_gemm_simt(const uint8_t* X, const uint8_t* Y, int ldk, const tc_gemm_args& g,
                                 int num_sms, cudaStream_t s);

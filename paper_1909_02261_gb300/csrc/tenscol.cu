@@ -74,10 +74,14 @@ struct tc_ctx {
     int4* d_units_m = nullptr;
     int n_units_g = 0, n_units_m = 0;
     tc_gemm_shape sh_g, sh_m;    // tiles and clusters of the two contractions (Gamma, M~)
+    bool fused = false;          // both contractions in one launch (same shape; M~ units first)
+    int4* d_units_f = nullptr;
+    int n_units_f = 0;
     int split_m = 1;             // K splits of M~
     int slots_g = 0, slots_m = 0;  // clusters of those sizes resident at once
     int tune_candidates = 0;       // configurations timed by the autotuner
     float tune_us_g = 0.f, tune_us_m = 0.f;  // their best times
+    float tune_us_f = 0.f;                   // best time of one launch for both (0: none timed)
     alignas(64) CUtensorMap tmA8;
     alignas(64) CUtensorMap tmS8T;
     alignas(64) CUtensorMap tmS8x;
@@ -169,7 +173,9 @@ void free_dense(tc_ctx* c) {
     dfree(c->d_M32);
     dfree(c->d_units_g);
     dfree(c->d_units_m);
-    c->n_units_g = c->n_units_m = 0;
+    dfree(c->d_units_f);
+    c->n_units_g = c->n_units_m = c->n_units_f = 0;
+    c->fused = false;
     c->n_pad = c->ldg = 0;
 }
 
@@ -369,9 +375,30 @@ std::vector<int4> plan_units_mtilde(const tc_ctx* c, const tc_gemm_shape& q, int
     return units_mtilde(c->n_pad / q.tm, q.tm, q.bn, c->n_pad / q.bn, kblocks, split);
 }
 
+// The unit list of one launch for both contractions: the M~ units (long K
+// ranges) first, then the Gamma units marked as the second contraction; the
+// persistent CTAs take units round robin, so the long ones start first.
+std::vector<int4> plan_units_fused(const tc_ctx* c, const tc_gemm_shape& q, int split) {
+    std::vector<int4> u = plan_units_mtilde(c, q, (int)(c->ldg / tc_gemm_tile_k()), split);
+    for (int4 w : plan_units_gamma(c, q)) {
+        w.y |= TC_UNIT_SECOND;
+        u.push_back(w);
+    }
+    return u;
+}
+
+// Whether both contractions can share a launch: one shape, 128-row units,
+// clusters of 1 or 2 (a cluster's units must share the column tile in both
+// lists: the M~ list comes in such pairs when bn = 2 x 128).
+bool fusable(const tc_ctx* c, const tc_gemm_shape& g, const tc_gemm_shape& m) {
+    return c->p.form == TC_FORM_DENSE_FP8 && g == m && g.tm == tc_gemm_tile_m() &&
+           (g.cl == 1 || (g.cl == 2 && g.bn == 256));
+}
+
 // Makes a plan current: unit lists, the B operands' tensor maps, resident
 // cluster counts.
-int apply_plan(tc_ctx* c, const tc_gemm_shape& sg, const tc_gemm_shape& sm, int split) {
+int apply_plan(tc_ctx* c, const tc_gemm_shape& sg, const tc_gemm_shape& sm, int split, bool fused) {
+    if (fused && !fusable(c, sg, sm)) return TC_ERR_ARG;
     const int BKt = tc_gemm_tile_k();
     const int n_pad = c->n_pad;
     const long long ldg = c->ldg;
@@ -386,6 +413,13 @@ int apply_plan(tc_ctx* c, const tc_gemm_shape& sg, const tc_gemm_shape& sm, int 
         return rc;
     c->n_units_g = (int)ug.size();
     c->n_units_m = (int)um.size();
+    c->fused = fused;
+    c->n_units_f = 0;
+    if (fused) {
+        const std::vector<int4> uf = plan_units_fused(c, sg, split);
+        if ((rc = upload_units(c, c->d_units_f, uf))) return rc;
+        c->n_units_f = (int)uf.size();
+    }
     c->sh_g = sg;
     c->sh_m = sm;
     c->split_m = split;
@@ -519,6 +553,33 @@ int plan_dense(tc_ctx* c) {
             pick_m = q;
         }
     }
+    // one launch for both contractions (M~ units first, then Gamma's): every
+    // M~ candidate whose shape both can share, kept if it beats the two
+    // best separate launches together
+    float best_f = 1e30f;
+    Cand pick_f = pick_m;
+    for (const Cand& q : cm) {
+        if (!tc || rc) break;
+        if (!fusable(c, q.q, q.q)) continue;
+        const std::vector<int4> u = plan_units_fused(c, q.q, q.split);
+        CUtensorMap tmYm, tmYg;
+        const int slots = tc_gemm_cluster_slots(q.q.tm, q.q.cl, q.q.bn, c->num_sms);
+        if ((rc = tc_encode_tmap_2d(&tmYm, u8, c->d_S8, ldg, n_pad, ldg, BKt, b_box_rows(q.q), sw)) ||
+            (rc = tc_encode_tmap_2d(&tmYg, u8, c->d_S8T, n_pad, ldg, n_pad, BKt, b_box_rows(q.q), sw)) ||
+            (rc = upload_units(c, c->d_units_f, u)))
+            break;
+        tc_gemm_args g = {c->d_units_f, (int)u.size(), TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
+                          &c->d_st->err, 1, TC_GEMM_GAMMA, c->D * c->k};
+        const float ms = time_it([&] {
+            return tc_launch_gemm_tc2(c->tmS8x, tmYm, c->tmM32, c->tmA8, tmYg, c->tmG16, g, slots, q.q.tm, q.q.cl,
+                                      q.q.bn, false, c->stream);
+        });
+        ++timed;
+        if (ms >= 0.f && ms < best_f) {
+            best_f = ms;
+            pick_f = q;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
@@ -526,10 +587,14 @@ int plan_dense(tc_ctx* c) {
     // the timed M~ launches left sums behind; the iteration expects zeros
     // (k_pairs zeroes M~ after reading it)
     TC_CHECK(cudaMemsetAsync(c->d_M32, 0, sizeof(float) * (size_t)n_pad * n_pad, c->stream));
-    if ((rc = apply_plan(c, pick_g.q, pick_m.q, pick_m.split))) return rc;
+    const bool fuse = tc && best_f < best_g + best_m;
+    if ((rc = fuse ? apply_plan(c, pick_f.q, pick_f.q, pick_f.split, true)
+                   : apply_plan(c, pick_g.q, pick_m.q, pick_m.split, false)))
+        return rc;
     c->tune_candidates = timed;
     c->tune_us_g = tc ? 1e3f * best_g : 0.f;
     c->tune_us_m = tc ? 1e3f * best_m : 0.f;
+    c->tune_us_f = tc && best_f < 1e30f ? 1e3f * best_f : 0.f;
     return TC_OK;
 }
 
@@ -553,7 +618,7 @@ int setup_dense(tc_ctx* c) {
     if ((rc = dalloc(&c->d_A8, (size_t)n_pad * n_pad)) || (rc = dalloc(&c->d_S8, (size_t)n_pad * ldg)) ||
         (rc = dalloc(&c->d_S8T, (size_t)ldg * n_pad)) || (rc = dalloc(&c->d_G16, (size_t)n_pad * ldg)) ||
         (rc = dalloc(&c->d_M32, (size_t)n_pad * n_pad)) || (rc = dalloc(&c->d_units_g, max_ug)) ||
-        (rc = dalloc(&c->d_units_m, max_um))) {
+        (rc = dalloc(&c->d_units_m, max_um)) || (rc = dalloc(&c->d_units_f, max_ug + max_um))) {
         free_dense(c);
         return rc;
     }
@@ -682,6 +747,16 @@ int launch_dense_gemms(tc_ctx* c, int which, cudaStream_t s) {
     tc_gemm_args gg = {c->d_units_g, c->n_units_g, TC_GEMM_GAMMA, c->d_G16, c->k, c->n_pad, c->D * c->k,
                        &c->d_st->err};
     const bool tc = c->p.form == TC_FORM_DENSE_FP8;
+    if (tc && c->fused) {  // both contractions in the first launch (M~ is zero: k_pairs zeroes it)
+        if (which != 0) return TC_OK;
+        tc_gemm_args gf = {c->d_units_f, c->n_units_f, TC_GEMM_MTILDE, c->d_M32, c->n_pad, c->n_pad, c->n_pad,
+                           &c->d_st->err, 1, TC_GEMM_GAMMA, c->D * c->k};
+        TC_CHECK(timed(c, TC_KID_GEMM_F, [&] {
+            return tc_launch_gemm_tc2(c->tmS8x, c->tmS8y, c->tmM32, c->tmA8, c->tmS8T, c->tmG16, gf, c->slots_m,
+                                      c->sh_m.tm, c->sh_m.cl, c->sh_m.bn, true, s);
+        }, s));
+        return TC_OK;
+    }
     if (which == 0) {  // M~ is zero here: k_pairs zeroes it after reading it
         TC_CHECK(timed(c, TC_KID_GEMM_M, [&] {
             return tc ? tc_launch_gemm_tc(c->tmS8x, c->tmS8y, c->tmM32, gm, c->slots_m, c->sh_m.tm, c->sh_m.cl,
@@ -725,7 +800,8 @@ int launch_iteration(tc_ctx* c) {
 }
 
 int launches_per_iteration(const tc_ctx* c) {
-    return (c->p.form == TC_FORM_ONEHOT ? 4 : 6) + (c->cmax > 0 ? 1 : 0);
+    const int gemms = c->p.form == TC_FORM_ONEHOT ? 0 : (c->fused ? 1 : 2);
+    return 4 + gemms + (c->cmax > 0 ? 1 : 0);
 }
 
 int read_state(tc_ctx* c, tc_dev_state* h) {
@@ -1631,12 +1707,13 @@ int tc_get_multicolors(tc_ctx* c, int32_t* colors, int stride) {
 int tc_dense_plan(tc_ctx* c, int32_t* plan, float* us) {
     if (!c || !plan) return TC_ERR_ARG;
     if (!c->pop || !c->d_M32) return TC_ERR_STATE;
-    const int v[8] = {c->sh_g.tm, c->sh_g.bn, c->sh_g.cl, c->sh_m.tm, c->sh_m.bn, c->sh_m.cl, c->split_m,
-                      c->tune_candidates};
+    const int v[9] = {c->sh_g.tm, c->sh_g.bn, c->sh_g.cl, c->sh_m.tm,      c->sh_m.bn,
+                      c->sh_m.cl, c->split_m, c->fused ? 1 : 0, c->tune_candidates};
     memcpy(plan, v, sizeof(v));
     if (us) {
         us[0] = c->tune_us_g;
         us[1] = c->tune_us_m;
+        us[2] = c->tune_us_f;
     }
     return TC_OK;
 }
@@ -1645,15 +1722,17 @@ int tc_dense_set_plan(tc_ctx* c, const int32_t* plan) {
     if (!c || !plan) return TC_ERR_ARG;
     if (!c->pop || !c->d_M32) return TC_ERR_STATE;
     const tc_gemm_shape sg{plan[0], plan[1], plan[2]}, sm{plan[3], plan[4], plan[5]};
-    if (!plan_valid(c, sg, sm, plan[6])) return TC_ERR_ARG;
+    if (!plan_valid(c, sg, sm, plan[6]) || (plan[7] != 0 && plan[7] != 1)) return TC_ERR_ARG;
+    if (plan[7] == 1 && !fusable(c, sg, sm)) return TC_ERR_ARG;
     DeviceGuard g(c->device);
     TC_CHECK(cudaStreamSynchronize(c->stream));
     const tc_gemm_shape og = c->sh_g, om = c->sh_m;
     const int osplit = c->split_m;
-    int rc = apply_plan(c, sg, sm, plan[6]);
+    const bool ofused = c->fused;
+    int rc = apply_plan(c, sg, sm, plan[6], plan[7] == 1);
     if (rc) {
         (void)cudaGetLastError();
-        apply_plan(c, og, om, osplit);
+        apply_plan(c, og, om, osplit, ofused);
         return rc;
     }
     drop_graph_exec(c);

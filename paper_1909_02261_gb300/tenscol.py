@@ -18,9 +18,10 @@ from . import build as _build
 TC_OK = 0
 TC_KCOL, TC_ECP, TC_KPART, TC_KPART_BAL, TC_MSCP = 0, 1, 2, 3, 4  # problems (tenscol.h)
 TC_FORM_ONEHOT, TC_FORM_DENSE_FP8, TC_FORM_DENSE_FP32 = 0, 1, 2
-TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE, TC_KID_GEMM_M, TC_KID_GEMM_G, TC_KID_GSUM = range(6)
+TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE, TC_KID_GEMM_M, TC_KID_GEMM_G, TC_KID_GSUM, TC_KID_GEMM_F = range(7)
 KERNEL_NAMES = {TC_KID_PAIRS: "k_pairs", TC_KID_CLASSES: "k_classes", TC_KID_UPDATE: "k_update",
-                TC_KID_GEMM_M: "gemm_mtilde", TC_KID_GEMM_G: "gemm_gamma", TC_KID_GSUM: "k_gsum"}
+                TC_KID_GEMM_M: "gemm_mtilde", TC_KID_GEMM_G: "gemm_gamma", TC_KID_GSUM: "k_gsum",
+                TC_KID_GEMM_F: "gemm_fused"}
 HEADER = os.path.join(_build.INCLUDE, "tenscol.h")
 
 
@@ -281,18 +282,19 @@ class TensCol:
 
     def tc_dense_plan(self):
         """The autotuned plan of the dense contractions (see tenscol.h)."""
-        plan = np.zeros(8, np.int32)
-        us = np.zeros(2, np.float32)
+        plan = np.zeros(9, np.int32)
+        us = np.zeros(3, np.float32)
         _ck(self._L.tc_dense_plan(self.h, _ptr(plan), _ptr(us)), "tc_dense_plan")
         return dict(gamma_tile_m=int(plan[0]), gamma_tile_n=int(plan[1]), gamma_cluster=int(plan[2]),
                     mtilde_tile_m=int(plan[3]), mtilde_tile_n=int(plan[4]), mtilde_cluster=int(plan[5]),
-                    mtilde_splits=int(plan[6]), candidates=int(plan[7]), gamma_us=float(us[0]),
-                    mtilde_us=float(us[1]))
+                    mtilde_splits=int(plan[6]), fused=bool(plan[7]), candidates=int(plan[8]),
+                    gamma_us=float(us[0]), mtilde_us=float(us[1]), fused_us=float(us[2]))
 
-    def tc_dense_set_plan(self, gamma, mtilde, mtilde_splits):
+    def tc_dense_set_plan(self, gamma, mtilde, mtilde_splits, fused=False):
         """Pins the plan: `gamma` and `mtilde` are (unit rows, column tile,
-        cluster) triples, e.g. (128, 256, 4) or (256, 256, 2) for a CTA pair."""
-        plan = np.array([*gamma, *mtilde, mtilde_splits], np.int32)
+        cluster) triples, e.g. (128, 256, 4) or (256, 256, 2) for a CTA pair;
+        fused: both contractions in one launch (one shape for both)."""
+        plan = np.array([*gamma, *mtilde, mtilde_splits, int(fused)], np.int32)
         _ck(self._L.tc_dense_set_plan(self.h, _ptr(plan)), "tc_dense_set_plan")
 
     def tc_set_color_costs(self, z):

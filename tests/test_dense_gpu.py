@@ -97,17 +97,24 @@ def test_switch_form_on_live_population():
 
 
 # (Gamma unit rows, column tile, cluster), (M~ unit rows, column tile,
-# cluster), M~ K splits; 256-row units run on a CTA pair (cta_group::2)
+# cluster), M~ K splits[, one launch for both]; 256-row units run on a CTA
+# pair (cta_group::2)
 PLANS = [
     ((128, 256, 1), (128, 256, 1), 1), ((128, 256, 2), (128, 256, 2), 3), ((128, 256, 4), (128, 256, 1), 4),
     ((128, 128, 1), (128, 128, 1), 1), ((128, 128, 2), (128, 128, 1), 4), ((128, 128, 4), (128, 256, 2), 2),
     ((256, 256, 2), (256, 256, 2), 3), ((256, 128, 2), (256, 128, 2), 4), ((256, 256, 2), (128, 256, 2), 1),
-    ((128, 256, 1), (256, 256, 2), 2)]
+    ((128, 256, 1), (256, 256, 2), 2), ((128, 256, 1), (128, 256, 1), 3, True),
+    ((128, 256, 2), (128, 256, 2), 2, True), ((128, 128, 1), (128, 128, 1), 4, True)]
 
 
 def plan_of(got):
     return ((got["gamma_tile_m"], got["gamma_tile_n"], got["gamma_cluster"]),
-            (got["mtilde_tile_m"], got["mtilde_tile_n"], got["mtilde_cluster"]), got["mtilde_splits"])
+            (got["mtilde_tile_m"], got["mtilde_tile_n"], got["mtilde_cluster"]), got["mtilde_splits"],
+            got["fused"])
+
+
+def full(plan):
+    return plan if len(plan) == 4 else (*plan, False)
 
 
 @pytest.mark.parametrize("plan", PLANS)
@@ -125,12 +132,13 @@ def test_every_tensor_core_plan_is_exact(plan):
                 ctx.tc_dense_set_plan(*plan)
             return
         ctx.tc_dense_set_plan(*plan)
-        assert plan_of(ctx.tc_dense_plan()) == plan
+        assert plan_of(ctx.tc_dense_plan()) == full(plan)
         check_iteration(ctx, rp, ci, p, 7)
 
 
 @pytest.mark.parametrize("plan", [((128, 256, 4), (128, 256, 2), 5), ((128, 128, 4), (128, 128, 1), 9),
-                                  ((256, 256, 2), (256, 256, 2), 10), ((256, 128, 2), (256, 256, 2), 7)])
+                                  ((256, 256, 2), (256, 256, 2), 10), ((256, 128, 2), (256, 256, 2), 7),
+                                  ((128, 256, 2), (128, 256, 2), 7, True), ((128, 256, 1), (128, 256, 1), 10, True)])
 def test_workload_sized_plans_are_exact(plan):
     n, D, k = 1000, 30, 41  # n_pad = 1024: 8 row tiles of 128; D k = 1230: 10 K blocks
     rp, ci = inputs.gnp(n, 0.5, seed=23)
@@ -150,7 +158,8 @@ def test_autotuner_times_candidates_and_rejects_bad_plans():
         for bad in [((128, 64, 1), (128, 256, 1), 1), ((128, 256, 3), (128, 256, 1), 1),
                     ((128, 128, 1), (128, 128, 2), 1), ((128, 256, 1), (128, 256, 1), 0),
                     ((256, 256, 1), (128, 256, 1), 1), ((128, 256, 1), (256, 256, 4), 1),
-                    ((512, 256, 2), (128, 256, 1), 1)]:
+                    ((512, 256, 2), (128, 256, 1), 1), ((128, 256, 1), (128, 128, 1), 1, True),
+                    ((256, 256, 2), (256, 256, 2), 1, True), ((128, 256, 4), (128, 256, 4), 1, True)]:
             with pytest.raises(TensColError):
                 ctx.tc_dense_set_plan(*bad)
         assert ctx.tc_dense_plan() == got  # unchanged by the refused plans
