@@ -324,8 +324,8 @@ int tc_best_multi(tc_ctx *ctx, int32_t *colors, int stride, int64_t *conflicts, 
 int tc_get_multicolors(tc_ctx *ctx, int32_t *colors, int stride);
 
 /* Pins the plan of the dense contractions: plan[0..7] as above (plan[7] = 1
- * needs one shape for both, 128-row units and clusters of 1, or 2 with
- * 256-wide tiles; the FP8 form only).  The FP8
+ * needs one shape for both: 128-row units in clusters of 1, or 2 with
+ * 256-wide tiles, or 256-row units on CTA pairs; the FP8 form only).  The FP8
  * form accepts, per contraction, unit rows 128 with column tile 128 / 256
  * and clusters sharing the B tile (Gamma: 1 / 2 / 4 dividing the 128-row
  * tiles; M~: 1, or 2 with 256-wide tiles), or unit rows 256 with column tile

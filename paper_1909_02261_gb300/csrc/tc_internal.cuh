@@ -188,7 +188,7 @@ cudaError_t tc_launch_gemm_tc(const CUtensorMap& tmX, const CUtensorMap& tmY, co
                               const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,
                               cudaStream_t s);
 // Both contractions in one launch: the units marked TC_UNIT_SECOND use tmX2,
-// tmY2, tmC2, g.mode2 and g.cols_alloc2 (g.fused = 1); 128-row units only.
+// tmY2, tmC2, g.mode2 and g.cols_alloc2 (g.fused = 1).
 cudaError_t tc_launch_gemm_tc2(const CUtensorMap& tmX, const CUtensorMap& tmY, const CUtensorMap& tmC,
                                const CUtensorMap& tmX2, const CUtensorMap& tmY2, const CUtensorMap& tmC2,
                                const tc_gemm_args& g, int slots, int tm, int cluster, int bn, bool pdl,

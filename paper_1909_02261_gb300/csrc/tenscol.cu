@@ -387,12 +387,14 @@ std::vector<int4> plan_units_fused(const tc_ctx* c, const tc_gemm_shape& q, int 
     return u;
 }
 
-// Whether both contractions can share a launch: one shape, 128-row units,
-// clusters of 1 or 2 (a cluster's units must share the column tile in both
-// lists: the M~ list comes in such pairs when bn = 2 x 128).
+// Whether both contractions can share a launch: one shape for both, either
+// 128-row units in clusters of 1 or 2 (a cluster's units must share the
+// column tile in both lists: the M~ list comes in such pairs when bn = 2 x
+// 128) or 256-row units on CTA pairs (a unit per pair).
 bool fusable(const tc_ctx* c, const tc_gemm_shape& g, const tc_gemm_shape& m) {
-    return c->p.form == TC_FORM_DENSE_FP8 && g == m && g.tm == tc_gemm_tile_m() &&
-           (g.cl == 1 || (g.cl == 2 && g.bn == 256));
+    if (c->p.form != TC_FORM_DENSE_FP8 || !(g == m)) return false;
+    if (g.tm == 2 * tc_gemm_tile_m()) return g.cl == 2;
+    return g.tm == tc_gemm_tile_m() && (g.cl == 1 || (g.cl == 2 && g.bn == 256));
 }
 
 // Makes a plan current: unit lists, the B operands' tensor maps, resident

@@ -104,7 +104,8 @@ PLANS = [
     ((128, 128, 1), (128, 128, 1), 1), ((128, 128, 2), (128, 128, 1), 4), ((128, 128, 4), (128, 256, 2), 2),
     ((256, 256, 2), (256, 256, 2), 3), ((256, 128, 2), (256, 128, 2), 4), ((256, 256, 2), (128, 256, 2), 1),
     ((128, 256, 1), (256, 256, 2), 2), ((128, 256, 1), (128, 256, 1), 3, True),
-    ((128, 256, 2), (128, 256, 2), 2, True), ((128, 128, 1), (128, 128, 1), 4, True)]
+    ((128, 256, 2), (128, 256, 2), 2, True), ((128, 128, 1), (128, 128, 1), 4, True),
+    ((256, 256, 2), (256, 256, 2), 3, True), ((256, 128, 2), (256, 128, 2), 2, True)]
 
 
 def plan_of(got):
@@ -138,7 +139,8 @@ def test_every_tensor_core_plan_is_exact(plan):
 
 @pytest.mark.parametrize("plan", [((128, 256, 4), (128, 256, 2), 5), ((128, 128, 4), (128, 128, 1), 9),
                                   ((256, 256, 2), (256, 256, 2), 10), ((256, 128, 2), (256, 256, 2), 7),
-                                  ((128, 256, 2), (128, 256, 2), 7, True), ((128, 256, 1), (128, 256, 1), 10, True)])
+                                  ((128, 256, 2), (128, 256, 2), 7, True), ((128, 256, 1), (128, 256, 1), 10, True),
+                                  ((256, 256, 2), (256, 256, 2), 8, True)])
 def test_workload_sized_plans_are_exact(plan):
     n, D, k = 1000, 30, 41  # n_pad = 1024: 8 row tiles of 128; D k = 1230: 10 K blocks
     rp, ci = inputs.gnp(n, 0.5, seed=23)
@@ -159,7 +161,7 @@ def test_autotuner_times_candidates_and_rejects_bad_plans():
                     ((128, 128, 1), (128, 128, 2), 1), ((128, 256, 1), (128, 256, 1), 0),
                     ((256, 256, 1), (128, 256, 1), 1), ((128, 256, 1), (256, 256, 4), 1),
                     ((512, 256, 2), (128, 256, 1), 1), ((128, 256, 1), (128, 128, 1), 1, True),
-                    ((256, 256, 2), (256, 256, 2), 1, True), ((128, 256, 4), (128, 256, 4), 1, True)]:
+                    ((256, 256, 2), (128, 256, 2), 1, True), ((128, 256, 4), (128, 256, 4), 1, True)]:
             with pytest.raises(TensColError):
                 ctx.tc_dense_set_plan(*bad)
         assert ctx.tc_dense_plan() == got  # unchanged by the refused plans
