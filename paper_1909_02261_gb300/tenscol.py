@@ -192,6 +192,7 @@ class TensCol:
         _ck(self._L.tc_init_population(self.h, seed, D, k, None if p is None else C.byref(p)),
             "tc_init_population")
         self.D, self.k = D, k
+        self.cmax = 1  # a new population takes one colour per vertex
 
     def tc_set_params(self, p: tc_params):
         _ck(self._L.tc_set_params(self.h, C.byref(p)), "tc_set_params")
@@ -278,6 +279,7 @@ class TensCol:
         # the context keeps the population of the last k tried
         last = k_min if kb.value == k_min else (kb.value - 1 if kb.value > 0 else k_start)
         self.D, self.k = D, last
+        self.cmax = 1
         return kb.value, (col if kb.value > 0 else None), it.value
 
     def tc_dense_plan(self):
