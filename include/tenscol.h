@@ -308,7 +308,9 @@ int tc_set_color_costs(tc_ctx *ctx, const int32_t *z, int k);
  * the one-hot form, for another problem, or for D max(demand) >= 2^24;
  * tc_set_params refuses to leave the dense forms or k-COL while demands are
  * set.  tc_best reports the best individual's colour of largest weight;
- * tc_best_multi its colour sets. */
+ * tc_best_multi its colour sets.  A failed allocation (TC_ERR_OOM) leaves
+ * the context as it was; a CUDA error after that point (TC_ERR_CUDA) leaves
+ * it to be re-initialised with tc_init_population. */
 int tc_set_demands(tc_ctx *ctx, const int32_t *demand, int n);
 
 /* Best-so-far individual of the multicolouring: colors[i * stride + q] for
