@@ -285,6 +285,32 @@ int tc_kdescent(tc_ctx *ctx, uint64_t seed, int D, int k_start, int k_min, int64
  * TC_ERR_STATE when the context has no dense form. */
 int tc_dense_plan(tc_ctx *ctx, int32_t *plan, float *us);
 
+/* One record of the iteration trace (tc_set_trace). */
+typedef struct {
+    int64_t t;          /* iteration of Algorithm 1                          */
+    int32_t f_min;      /* min_d f(S_d) of the problem (the stop test)       */
+    int32_t individual; /* lowest d attaining it                             */
+    int32_t f_color;    /* its f_color (eq. 1)                               */
+    int32_t f_add;      /* its additive term: f_eq (eq. 3), or f_mscp        */
+    float loss;         /* L(t) of the population (eq. 7)                    */
+    float kappa;        /* eq. 5                                             */
+    float varpi;        /* eq. 6                                             */
+    int32_t pad;
+} tc_trace_entry;
+
+/* Iteration trace (the loss and fitness evolution the paper follows in
+ * Section 5): every `every` iterations t (t % every == 0) of tc_step /
+ * tc_step_async / batches, the population reduction writes one record into
+ * a device ring of `capacity` records; capacity 0 turns the trace off.
+ * Clears the ring.  TC_ERR_ARG for capacity < 0 or every < 1, TC_ERR_STATE
+ * without a population; a new population turns the trace off. */
+int tc_set_trace(tc_ctx *ctx, int capacity, int every);
+
+/* Copies the retained records, oldest first, up to `max` of them into out
+ * (caller-owned; may be NULL to count only); *count receives how many are
+ * retained (at most the capacity).  Synchronises the context's stream. */
+int tc_get_trace(tc_ctx *ctx, tc_trace_entry *out, int max, int *count);
+
 /* Colour costs z[0..k-1] >= 0 of the minimum sum colouring (TC_MSCP,
  * Section 7), copied; k must be the population's k.  Every population
  * starts with z_l = l + 1.  TC_ERR_ARG for a negative cost or another k,

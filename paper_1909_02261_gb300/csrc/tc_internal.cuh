@@ -26,6 +26,7 @@ struct tc_dev_state {
     unsigned int done_update;
     float loss, kappa, varpi;
     int pad;
+    long long trace_n;    // trace records written so far
 };
 
 // Problems whose Algorithm 1 uses J - M_d in place of M_d (Section 7), and
@@ -84,6 +85,9 @@ struct tc_kparams {
     uint16_t* best_m;         // n x cmax colour sets of the best-so-far individual
     int cmax;                 // largest demand
     int mt_max;               // largest value of m~: D, or D cmax in the multicolouring
+    // iteration trace (NULL: off): ring of trace_cap records, one every trace_every t
+    tc_trace_entry* trace;
+    int trace_cap, trace_every;
     // dense forms (NULL in the one-hot form)
     float* M32;               // n_pad x n_pad group concentration from a GEMM (k_pairs zeroes it)
     int ldm;

@@ -419,6 +419,20 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
         st->fcolor_sum = fc;
         st->last_fmin = fmin;
         st->last_dstar = dstar;
+        if (P.trace && P.commit && t % P.trace_every == 0) {  // the iteration trace
+            tc_trace_entry e;
+            e.t = t;
+            e.f_min = fmin;
+            e.individual = dstar;
+            e.f_color = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
+            e.f_add = __ldcg(P.feq + dstar);
+            e.loss = st->loss;
+            e.kappa = ka;
+            e.varpi = va;
+            e.pad = 0;
+            P.trace[st->trace_n % P.trace_cap] = e;
+            st->trace_n += 1;
+        }
         int better = 0;
         if (P.commit) {
             st->evaluated += 1;

@@ -54,6 +54,9 @@ struct tc_ctx {
     int* d_dem = nullptr;
     uint16_t* d_cm = nullptr;
     uint16_t* d_best_m = nullptr;
+    // iteration trace (tc_set_trace)
+    tc_trace_entry* d_trace = nullptr;
+    int trace_cap = 0, trace_every = 1;
     int* d_fcolor = nullptr;
     int* d_feq = nullptr;
     float* d_loss_part = nullptr;
@@ -201,6 +204,8 @@ void free_population(tc_ctx* c) {
     dfree(c->d_dem);
     dfree(c->d_cm);
     dfree(c->d_best_m);
+    dfree(c->d_trace);
+    c->trace_cap = 0;
     c->cmax = 0;
     c->dem_sum = 0;
     c->pop = false;
@@ -292,6 +297,11 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     // with mu = 0 the pair matrix vanishes off the edges; below a density of
     // 1/8 walking the adjacency lists beats walking all n vertices per class
     P.csr_walk = c->p.mu == 0.0f && c->nnz * 8 < (long long)c->n * c->n && c->cmax == 0;
+    if (c->trace_cap > 0) {
+        P.trace = c->d_trace;
+        P.trace_cap = c->trace_cap;
+        P.trace_every = c->trace_every;
+    }
     if (c->cmax > 0) {  // multicolouring
         P.dem = c->d_dem;
         P.cm = c->d_cm;
@@ -1596,6 +1606,46 @@ int tc_set_color_costs(tc_ctx* c, const int32_t* z, int k) {
     DeviceGuard g(c->device);
     TC_CHECK(cudaMemcpyAsync(c->d_z, z, sizeof(int) * (size_t)k, cudaMemcpyHostToDevice, c->stream));
     TC_CHECK(cudaStreamSynchronize(c->stream));
+    return TC_OK;
+}
+
+int tc_set_trace(tc_ctx* c, int capacity, int every) {
+    if (!c || capacity < 0 || every < 1) return TC_ERR_ARG;
+    if (!c->pop) return TC_ERR_STATE;
+    DeviceGuard g(c->device);
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    tc_trace_entry* ring = nullptr;
+    int rc;
+    if (capacity > 0 && (rc = dalloc(&ring, (size_t)capacity))) return rc;
+    dfree(c->d_trace);
+    c->d_trace = ring;
+    c->trace_cap = capacity;
+    c->trace_every = every;
+    const long long zero = 0;
+    TC_CHECK(cudaMemcpyAsync(&c->d_st->trace_n, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    drop_graph_exec(c);  // captured launches carry the old ring
+    return TC_OK;
+}
+
+int tc_get_trace(tc_ctx* c, tc_trace_entry* out, int max, int* count) {
+    if (!c || max < 0) return TC_ERR_ARG;
+    if (count) *count = 0;
+    if (!c->pop) return TC_ERR_STATE;
+    if (c->trace_cap == 0) return TC_OK;
+    DeviceGuard g(c->device);
+    tc_dev_state h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    const long long kept = std::min<long long>(h.trace_n, c->trace_cap);
+    if (count) *count = (int)kept;
+    if (!out || max == 0 || kept == 0) return TC_OK;
+    std::vector<tc_trace_entry> ring((size_t)c->trace_cap);
+    TC_CHECK(cudaMemcpyAsync(ring.data(), c->d_trace, sizeof(tc_trace_entry) * ring.size(), cudaMemcpyDeviceToHost,
+                             c->stream));
+    TC_CHECK(cudaStreamSynchronize(c->stream));
+    const long long first = h.trace_n - kept;  // oldest retained record
+    for (long long r = 0; r < kept && r < max; ++r) out[r] = ring[(size_t)((first + r) % c->trace_cap)];
     return TC_OK;
 }
 

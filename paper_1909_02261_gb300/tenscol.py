@@ -43,6 +43,12 @@ class tc_params(C.Structure):
     ]
 
 
+class tc_trace_entry(C.Structure):
+    _fields_ = [("t", C.c_int64), ("f_min", C.c_int32), ("individual", C.c_int32), ("f_color", C.c_int32),
+                ("f_add", C.c_int32), ("loss", C.c_float), ("kappa", C.c_float), ("varpi", C.c_float),
+                ("pad", C.c_int32)]
+
+
 class TensColError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -99,6 +105,8 @@ def load(build_if_missing: bool = True):
         "tc_dense_set_plan": (C.c_int, [vp, vp]),
         "tc_set_color_costs": (C.c_int, [vp, vp, C.c_int]),
         "tc_set_demands": (C.c_int, [vp, vp, C.c_int]),
+        "tc_set_trace": (C.c_int, [vp, C.c_int, C.c_int]),
+        "tc_get_trace": (C.c_int, [vp, vp, C.c_int, P(C.c_int)]),
         "tc_best_multi": (C.c_int, [vp, vp, C.c_int, vp, vp, vp]),
         "tc_get_multicolors": (C.c_int, [vp, vp, C.c_int]),
         "tc_batch_create": (C.c_int, [P(vp), C.c_int]),
@@ -303,6 +311,19 @@ class TensCol:
         """Colour costs z_l of the minimum sum colouring (TC_MSCP), one per colour."""
         z = np.ascontiguousarray(z, np.int32)
         _ck(self._L.tc_set_color_costs(self.h, _ptr(z), int(z.size)), "tc_set_color_costs")
+
+    def tc_set_trace(self, capacity: int, every: int = 1):
+        """Record (t, min f, argmin, its f_color and additive term, L, kappa,
+        varpi) every `every` iterations in a device ring of `capacity`."""
+        _ck(self._L.tc_set_trace(self.h, int(capacity), int(every)), "tc_set_trace")
+
+    def tc_get_trace(self):
+        """The retained trace records, oldest first, as a list of dicts."""
+        n = C.c_int()
+        _ck(self._L.tc_get_trace(self.h, None, 0, C.byref(n)), "tc_get_trace")
+        buf = (tc_trace_entry * max(1, n.value))()
+        _ck(self._L.tc_get_trace(self.h, buf, n.value, C.byref(n)), "tc_get_trace")
+        return [{f: getattr(buf[r], f) for f, _ in tc_trace_entry._fields_ if f != "pad"} for r in range(n.value)]
 
     def tc_set_demands(self, demand):
         """Multicolouring: vertex i takes demand[i] colours (dense forms, k-COL)."""
