@@ -871,9 +871,19 @@ __host__ __device__ inline int gsum_stage_words(int perm_stride, int k) {
     return perm_stride + ((k + 1 + 3) & ~3) + ((k + 3) & ~3);
 }
 
+// Items (32-vertex tile T, individual d) run tile-major; each tile's D
+// items form ceil(D / units) chunks of about one item per unit (a warp, or a
+// warp pair when staged), and every block takes a contiguous run of whole
+// chunks.  A block whose run crosses a tile boundary reloads the B panel
+// between two barriers; with whole chunks on both sides its units still
+// need no more rounds than a block inside one tile.
+__host__ __device__ inline long long gsum_chunk_item(long long c, int cpt, int D) {
+    return (c / cpt) * D + ((c % cpt) * D) / cpt;
+}
+
 template <bool BTS, bool CSR, bool STG>
 __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
-    k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int items_per_block) {
+    k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB) {
     pdl_trigger();
     pdl_wait();  // B from k_pairs, the class lists from k_classes
     tc_dev_state* st = P.st;
@@ -900,9 +910,10 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     const long long t = st->t;
     const float nut = (float)((double)P.nu * (double)t);
     const int nT = (n + 31) / 32;
-    const long long Q = (long long)nT * D;
-    long long q = (long long)blockIdx.x * items_per_block;
-    const long long qend = min(Q, q + items_per_block);
+    const int cpt = (D + nunits - 1) / nunits;  // chunks per tile
+    const long long C = (long long)nT * cpt;
+    long long q = gsum_chunk_item(C * blockIdx.x / gridDim.x, cpt, D);
+    const long long qend = gsum_chunk_item(C * (blockIdx.x + 1) / gridDim.x, cpt, D);
     while (q < qend) {
         const int T = (int)(q / D);
         const long long seg_end = min(qend, (long long)(T + 1) * D);
@@ -1300,12 +1311,15 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
 }
 
 template <bool BTS, bool CSR, bool STG>
-static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int blocks, int warps, int smem,
-                                 int per_block, cudaStream_t s) {
+static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, int warps, int smem,
+                                 cudaStream_t s) {
     auto fn = k_gsum<BTS, CSR, STG>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return tc_launch_pdl(fn, dim3(blocks), dim3(warps * 32), smem, s, P, tmB, per_block);
+    const int units = STG ? warps / 2 : warps;
+    const long long chunks = (long long)((P.n + 31) / 32) * ((P.D + units - 1) / units);
+    const int blocks = (int)std::max(1ll, std::min<long long>(num_sms, chunks));
+    return tc_launch_pdl(fn, dim3(blocks), dim3(warps * 32), smem, s, P, tmB);
 }
 
 // grad_S L tiles (k_gsum) into P.Gbuf: the B panel in shared memory when it
@@ -1330,18 +1344,14 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
     }
     if (warps < 1) return cudaErrorInvalidValue;
     const int smem = (int)std::max(smem_ll, 2048ll);  // the population reduction's scratch at least
-    const long long items = (long long)((P.n + 31) / 32) * P.D;
-    long long blocks = std::min<long long>(num_sms, items);
-    if (blocks < 1) blocks = 1;
-    const int per_block = (int)((items + blocks - 1) / blocks);
     if (P.csr_walk)
-        return bts ? launch_gsum_t<true, true, false>(P, tmB, (int)blocks, warps, smem, per_block, s)
-                   : launch_gsum_t<false, true, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
+        return bts ? launch_gsum_t<true, true, false>(P, tmB, num_sms, warps, smem, s)
+                   : launch_gsum_t<false, true, false>(P, tmB, num_sms, warps, smem, s);
     if (stg)
-        return bts ? launch_gsum_t<true, false, true>(P, tmB, (int)blocks, warps, smem, per_block, s)
-                   : launch_gsum_t<false, false, true>(P, tmB, (int)blocks, warps, smem, per_block, s);
-    return bts ? launch_gsum_t<true, false, false>(P, tmB, (int)blocks, warps, smem, per_block, s)
-               : launch_gsum_t<false, false, false>(P, tmB, (int)blocks, warps, smem, per_block, s);
+        return bts ? launch_gsum_t<true, false, true>(P, tmB, num_sms, warps, smem, s)
+                   : launch_gsum_t<false, false, true>(P, tmB, num_sms, warps, smem, s);
+    return bts ? launch_gsum_t<true, false, false>(P, tmB, num_sms, warps, smem, s)
+               : launch_gsum_t<false, false, false>(P, tmB, num_sms, warps, smem, s);
 }
 
 // k_update: as many stages as fit (at most 16), two fewer consumer pairs
