@@ -34,7 +34,8 @@ constexpr int PP = PT / 16;         // pairs per thread along each tile edge
 constexpr int PAIR_THREADS = 256;   // 16 x 16 threads, PP x PP pairs each
 constexpr int PAIR_CW = 64;         // colour words per chunk (< 256: lane counters)
 constexpr int CLS_THREADS = 256;
-constexpr int UPD_MAX_WARPS = 15;  // a producer warp and 7 pairs
+constexpr int UPD_GW = 4;          // k_update: warps per item, each a quarter of the colours
+constexpr int UPD_MAX_WARPS = 21;  // a producer warp and 5 groups
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -1037,20 +1038,26 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
 // ---------------------------------------------------------------------------
 // k_update is warp-specialised.  Warp 0 streams the block's items through a
 // ring of S stages (grad_S tile and weight tile, each k x 32 floats and
-// contiguous in the tiled layouts) with bulk copies.  P pairs of warps take
-// the items in turn (latency, not issue, bounds one lane walking a whole
-// row): warp h of a pair updates the colours [jb, je) of all 32 rows in
-// place, lane r owning row r, and the two halves meet twice through shared
-// memory (softmax sums, then argmax); the producer writes each updated
-// weight tile back with a bulk store before its stage is refilled.
+// contiguous in the tiled layouts) with bulk copies.  P groups of UPD_GW
+// warps take the items in turn (latency, not issue, bounds one lane walking
+// a whole row): warp h of a group updates the colours [jb, je) (a quarter)
+// of all 32 rows in place, lane r owning row r, and the quarters meet twice
+// through shared memory (softmax sums, then argmax); the producer writes
+// each updated weight tile back with a bulk store before its stage is
+// refilled.  A group holds its stage while it computes, so the quarters
+// (half the time per item of halves) leave more of the ring loading.
 // Shared memory: full[S], done[S] mbarriers, S stages of 64 k floats
-// ([Gs | Ws], 16-byte aligned), P exchange slots of 256 floats (xa [2][2][32]:
-// Z, num per half; xb [2][2][32]: best value, colour per half).
-constexpr int UPD_MAX_PAIRS = (UPD_MAX_WARPS - 1) / 2;
+// ([Gs | Ws], 16-byte aligned), P exchange slots of 512 floats (xa [4][2][32]:
+// Z, num per quarter; xb [4][2][32]: best value, colour per quarter).
+constexpr int UPD_MAX_GROUPS = (UPD_MAX_WARPS - 1) / UPD_GW;
 constexpr int UPD_MAX_STAGES = 16;
 
 __host__ __device__ constexpr long long upd_smem_bytes(int k, int S, int P) {
-    return 16ll * S + 256ll * k * S + 1024ll * P;
+    return 16ll * S + 256ll * k * S + 2048ll * P;
+}
+
+__device__ __forceinline__ void group_sync(int grp) {  // the UPD_GW warps of group grp (named barrier grp + 1)
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "n"(UPD_GW * 32) : "memory");
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {  // 2^x, PTX ex2.approx
@@ -1063,23 +1070,26 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One item (32-row tile T of individual d) by warp h of pair `pair`, its
-// tiles already in Gs, Ws.  Returns with both warps done with the stage.
+// One item (32-row tile T of individual d) by warp h (a quarter of the
+// colours) of group `grp`, its tiles already in Gs, Ws.  xa, xb: the group's
+// exchange slots of 256 floats each.  Returns with all the group's warps
+// done with the stage.
 __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, float* xa, float* xb,
-                                            int pair, int h, int T, int d, int cur, bool smooth,
+                                            int grp, int h, int T, int d, int cur, bool smooth,
                                             int debug_only) {
+    static_assert(UPD_GW == 4, "the sums below combine four quarters");
     const int n = P.n, k = P.k;
     const int lane = threadIdx.x & 31;
     const int i0 = T * 32;
     const int rows = min(32, n - i0);
-    const int kh = (k + 1) >> 1, jb = h * kh, je = min(k, jb + kh);
+    const int kq = (k + UPD_GW - 1) / UPD_GW, jb = min(k, h * kq), je = min(k, jb + kq);
     const bool live = lane < rows;
     if (debug_only == 1) {
         if (live) {
             float* g = P.dbg_G + ((size_t)d * n + i0 + lane) * k;
             for (int jj = jb; jj < je; ++jj) g[jj] = Gs[jj * 32 + lane];
         }
-        pair_sync(pair);
+        group_sync(grp);
         return;
     }
     float* wr = Ws + lane;
@@ -1088,7 +1098,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     // the row maximum is the weight of the row's current colour: the colours
     // are the argmax of W, kept in step with it by every update
     const float nml = live ? -wr[cur * 32] * kL2E : 0.f;
-    // softmax sums of this half: e_j = 2^(w_j log2 e - max log2 e)
+    // softmax sums of this quarter: e_j = 2^(w_j log2 e - max log2 e)
     float z4[4] = {0.f, 0.f, 0.f, 0.f}, n4[4] = {0.f, 0.f, 0.f, 0.f};
     if (live) {
         int j = jb;
@@ -1107,9 +1117,10 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     }
     xa[h * 64 + lane] = (z4[0] + z4[1]) + (z4[2] + z4[3]);
     xa[h * 64 + 32 + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
-    pair_sync(pair);
-    const float Z = xa[lane] + xa[64 + lane];  // same order in both warps
-    const float num = xa[32 + lane] + xa[96 + lane];
+    group_sync(grp);
+    // same order in every warp of the group
+    const float Z = (xa[lane] + xa[64 + lane]) + (xa[128 + lane] + xa[192 + lane]);
+    const float num = (xa[32 + lane] + xa[96 + lane]) + (xa[160 + lane] + xa[224 + lane]);
     const float invZ = 1.0f / Z;
     const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
     float bestv = -INFINITY;
@@ -1136,16 +1147,22 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
         }
     }
     if (debug_only == 2) {
-        pair_sync(pair);
+        group_sync(grp);
         return;
     }
     xb[h * 64 + lane] = bestv;
     xb[h * 64 + 32 + lane] = __int_as_float(newc);
     fence_proxy_async();  // this lane's writes of Ws, before the producer's bulk store
-    pair_sync(pair);
+    group_sync(grp);
     if (h != 0) return;
-    // lower half wins ties: it holds the lower colours
-    if (xb[64 + lane] > xb[lane]) newc = __float_as_int(xb[96 + lane]);
+    // the lowest quarter wins ties: it holds the lower colours
+    bestv = xb[lane];
+#pragma unroll
+    for (int q = 1; q < UPD_GW; ++q)
+        if (xb[q * 64 + lane] > bestv) {
+            bestv = xb[q * 64 + lane];
+            newc = __float_as_int(xb[q * 64 + 32 + lane]);
+        }
     if (live && !P.cm) {  // (the multicolouring's next assignment is k_assign_multi)
         const int i = i0 + lane;
         if (P.S8 && cur != newc) {  // dense forms: move the one-hot entry of (d, i) in both operands
@@ -1167,7 +1184,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     if (!debug_only && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
     const int n = P.n, D = P.D, k = P.k;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, npairs = ((int)(blockDim.x >> 5) - 1) >> 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, ngroups = ((int)(blockDim.x >> 5) - 1) / UPD_GW;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
     uint64_t* done = full + S;
     float* stages = sm + 4 * S;  // after 2 S mbarriers (16 S bytes)
@@ -1194,56 +1211,56 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
         return ((size_t)(qq - (long long)T * D) * nT + T) * k * 32;
     };
     if (warp == 0) {
-        if (lane == 0) {  // producer: loads of item r, write-back of item r - S
-            for (int r = 0; r < R + S; ++r) {
+        if (lane == 0) {  // producer: item r into stage r % S once its previous use is released
+            for (int r = 0; r < R; ++r) {
                 const int s = r % S, u = r / S;
                 float* Gs = stages + (size_t)s * 64 * k;
-                if (u > 0 && r - S < R) {
-                    mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
-                    if (debug_only == 0) {
-                        bulk_store(P.W + tile_of(r - S), Gs + 32 * k, bytes);
-                        bulk_wait_read();  // the stage may be refilled once the store has read it
-                    }
-                }
-                if (r < R) {
-                    const size_t tile = tile_of(r);
-                    mbar_expect_tx(full + s, debug_only == 1 ? bytes : 2 * bytes);
-                    bulk_load(Gs, P.Gbuf + tile, bytes, full + s);
-                    if (debug_only != 1) bulk_load(Gs + 32 * k, P.W + tile, bytes, full + s);
-                }
+                if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
+                const size_t tile = tile_of(r);
+                mbar_expect_tx(full + s, debug_only == 1 ? bytes : 2 * bytes);
+                bulk_load(Gs, P.Gbuf + tile, bytes, full + s);
+                if (debug_only != 1) bulk_load(Gs + 32 * k, P.W + tile, bytes, full + s);
             }
-            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
         }
         __syncwarp();
-    } else {  // consumer pairs
-        const int pair = (warp - 1) >> 1, h = (warp - 1) & 1;
-        float* xa = xch + (size_t)pair * 256;
-        float* xb = xa + 128;
+    } else {  // consumer groups
+        const int grp = (warp - 1) / UPD_GW, h = (warp - 1) % UPD_GW;
+        float* xa = xch + (size_t)grp * 512;
+        float* xb = xa + 256;
         // the rows' current colours, one item ahead (an L2 round trip)
         auto colour_of = [&](int r) {
             const long long qq = q0 + r;
             const int T = (int)(qq / D), d = (int)(qq - (long long)T * D), i = T * 32 + lane;
             return i < n ? (int)__ldg(P.c + (size_t)d * n + i) : 0;
         };
-        int cur_next = pair < R ? colour_of(pair) : 0;
-        for (int r = pair; r < R; r += npairs) {
+        int cur_next = grp < R ? colour_of(grp) : 0;
+        for (int r = grp; r < R; r += ngroups) {
             const long long qq = q0 + r;
             const int T = (int)(qq / D), d = (int)(qq - (long long)T * D);
             const int s = r % S, u = r / S;
             const int cur = cur_next;
-            if (r + npairs < R) cur_next = colour_of(r + npairs);
+            if (r + ngroups < R) cur_next = colour_of(r + ngroups);
             // A parity wait is only sound within one phase of the barrier.
-            // Another pair may still hold use u - 1 of this stage (the loads
-            // of use u - 1 were issued, since this pair's previous item,
+            // Another group may still hold use u - 1 of this stage (the loads
+            // of use u - 1 were issued, since this group's previous item,
             // loaded later, was; their bytes may not have landed): wait for
             // that use to be released first, then for use u's bytes.
             if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
             mbar_wait_bounded(full + s, (unsigned)u & 1u, &st->err);
             float* Gs = stages + (size_t)s * 64 * k;
-            update_item(P, Gs, Gs + 32 * k, xa, xb, pair, h, T, d, cur, smooth, debug_only);
-            // both warps are past the pair's last barrier of the item
-            if (h == 0 && lane == 0) mbar_arrive(done + s);
+            update_item(P, Gs, Gs + 32 * k, xa, xb, grp, h, T, d, cur, smooth, debug_only);
+            // all the group's warps are past its last barrier of the item (their
+            // writes of the weight tile fenced for the async proxy): one lane
+            // writes the tile back and frees the stage once the store has read it
+            if (h == 0 && lane == 0) {
+                if (debug_only == 0) {
+                    bulk_store(P.W + tile_of(r), Gs + 32 * k, bytes);
+                    bulk_wait_read();
+                }
+                mbar_arrive(done + s);
+            }
         }
+        if (h == 0 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
     }
     if (!debug_only) {
         __syncthreads();
@@ -1354,15 +1371,15 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
                : launch_gsum_t<false, false, false>(P, tmB, num_sms, warps, smem, s);
 }
 
-// k_update: as many stages as fit (at most 16), two fewer consumer pairs
-// (at most 7) so that loads run ahead of the updates; one block per SM.
+// k_update: as many stages as fit (at most 16), at most 5 consumer groups,
+// three stages fewer; one block per SM.
 cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only) {
     const long long per_stage = 16ll + 256ll * P.k;
     int S = (int)std::min<long long>(UPD_MAX_STAGES, (kSmemOptin - 1024ll) / per_stage);
     if (S < 1) return cudaErrorInvalidValue;
-    // two stages loading ahead of the pairs (fewer pairs measured slower:
-    // the update arithmetic is latency-bound per pair)
-    int pairs = S >= 4 ? std::min(UPD_MAX_PAIRS, S - 2) : std::max(1, S - 1);
+    // groups of UPD_GW warps, three stages loading ahead of them (at the
+    // benchmark shape 9 stages: 3, 4, 5 groups measured 50.9, 43.5, 42.6 us)
+    int pairs = S >= 4 ? std::min(UPD_MAX_GROUPS, S - 3) : 1;
     while (S > 1 && upd_smem_bytes(P.k, S, pairs) > kSmemOptin) --S;
     if (upd_smem_bytes(P.k, S, pairs) > kSmemOptin) return cudaErrorInvalidValue;
     const int smem = (int)upd_smem_bytes(P.k, S, pairs);
@@ -1372,6 +1389,6 @@ cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, i
     const int per_block = (int)((items + blocks - 1) / blocks);
     cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return tc_launch_pdl(k_update, dim3((unsigned)blocks), dim3((1 + 2 * pairs) * 32), smem, s, P, per_block, S,
-                         debug_only);
+    return tc_launch_pdl(k_update, dim3((unsigned)blocks), dim3((1 + UPD_GW * pairs) * 32), smem, s, P, per_block,
+                         S, debug_only);
 }
