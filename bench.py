@@ -418,6 +418,21 @@ def run_ours(args):
     kernels = {T.KERNEL_NAMES.get(q, f"kid{q}"): {"launches": int(kcnt[q]),
                                                    "avg_us": 1e3 * kms[q] / max(1, kcnt[q])}
                for q in range(len(kms)) if kcnt[q] > 0}
+    # k_gsum's own ceiling: every addition of the one-hot gather (D n^2 per
+    # launch) needs one 4-byte shared-memory load of B, and an SM serves one
+    # 128-byte wavefront (a warp's 32 loads) per clock: 32 additions per SM
+    # per clock at the highest SM clock seen
+    gsum_roof = None
+    if kcnt[T.TC_KID_GSUM] > 0:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        adds = float(D) * n * n
+        us = 1e3 * kms[T.TC_KID_GSUM] / kcnt[T.TC_KID_GSUM]
+        ach = adds / (us * 1e-6) / 1e9
+        peak_lds = sms * 32 * mhz * 1e6 / 1e9
+        gsum_roof = {"bound": "alu", "kernel": "k_gsum", "achieved": ach, "peak": peak_lds,
+                     "unit": "Gadd/s", "frac": ach / peak_lds, "work_per_launch": adds,
+                     "peak_source": f"{sms} SMs x 32 shared-memory loads per clock x {mhz:.0f} MHz"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "individual-steps/s", "n_gpus": world,
@@ -430,6 +445,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}"},
         "roofline": roof,
         "roofline_tensor": tensor_roof,
+        "roofline_gsum": gsum_roof,
         "forms": forms,
         "kernels": kernels,
         "gpu_launches": int(launches),
