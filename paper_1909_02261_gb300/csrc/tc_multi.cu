@@ -85,8 +85,10 @@ __device__ __forceinline__ bool has_colour(const uint16_t* set, int c, int j) {
 // One block per individual: class sizes, padded offsets, class lists; the
 // additive term is absent (multicolouring is a k-COL variant): E = 0, f_eq = 0.
 __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P) {
-    pdl_trigger();
+    // k_gsum reads the pair matrix of k_pairs before its own wait: it may
+    // start only once this kernel's predecessors are complete
     pdl_wait();
+    pdl_trigger();
     if (P.commit && P.st->stop) return;
     __shared__ int s_hist[TC_MAX_K];
     __shared__ int s_off[TC_MAX_K + 1];

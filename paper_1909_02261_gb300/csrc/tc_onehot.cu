@@ -469,8 +469,10 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
 // the per-warp colour counts of the sort.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
-    pdl_trigger();
+    // k_gsum reads the pair matrix of k_pairs before its own wait: it may
+    // start only once this kernel's predecessors are complete
     pdl_wait();
+    pdl_trigger();
     if (P.commit && P.st->stop) return;
     __shared__ int s_hist[TC_MAX_K];
     __shared__ int s_cur[TC_MAX_K];
@@ -775,7 +777,10 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
             g3 = j + 4 < je ? __ldg(grow + (size_t)(j + 4) * gstride) : (uint16_t)0;
         }
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 2
+        // not unrolled: classes are ~3 chunks long, and the remainder handling
+        // of an unrolled loop cost more than it saved (56.1 M against 59.1 M
+        // warp instructions per launch; 60.4 M unrolled by 4)
+#pragma unroll 1
         for (; p < e; p += 16) {
             const uint4 v = lds_u32x4(p);
             a0 += lds_f32(bl + 128u * v.x);
@@ -886,9 +891,15 @@ template <bool BTS, bool CSR, bool STG>
 __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB) {
     pdl_trigger();
-    pdl_wait();  // B from k_pairs, the class lists from k_classes
+    // k_classes lets this kernel start only after its own predecessors (k_pairs
+    // and, in the dense forms, the GEMMs) are complete: the stop flag of the
+    // previous iteration and B can be read now, and the first panel of B is
+    // loaded while k_classes finishes; its class lists need the wait below
     tc_dev_state* st = P.st;
-    if (P.commit && st->stop) return;
+    if (P.commit && st->stop) {
+        pdl_wait();
+        return;
+    }
     extern __shared__ __align__(1024) float sm[];
     __shared__ __align__(8) uint64_t s_bbar;
     const int n = P.n, D = P.D, k = P.k;
@@ -915,24 +926,30 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     const long long C = (long long)nT * cpt;
     long long q = gsum_chunk_item(C * blockIdx.x / gridDim.x, cpt, D);
     const long long qend = gsum_chunk_item(C * (blockIdx.x + 1) / gridDim.x, cpt, D);
+    // B[0..n] x [32 T, 32 T + 32) -> Bt by 2-D TMA boxes, zero filled past
+    // the matrix edge; B is symmetric, so these are its columns
+    auto load_panel = [&](int T) {
+        fence_proxy_async();
+        mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
+        for (int b = 0; b < nbox; ++b)
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
+                "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS), "r"(smem_u32(&s_bbar))
+                : "memory");
+    };
+    if (BTS && threadIdx.x == 0 && q < qend) load_panel((int)(q / D));
+    pdl_wait();  // the class lists (and equity terms) from k_classes
+    bool first = true;
     while (q < qend) {
         const int T = (int)(q / D);
         const long long seg_end = min(qend, (long long)(T + 1) * D);
         if (BTS) {
-            // B[0..n] x [32 T, 32 T + 32) -> Bt by 2-D TMA boxes, zero filled
-            // past the matrix edge; B is symmetric, so these are its columns
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(&s_bbar, (unsigned)(nbox * TC_BT_BOX_ROWS * 32 * 4));
-                for (int b = 0; b < nbox; ++b)
-                    asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(Bt + (size_t)b * TC_BT_BOX_ROWS * 32)),
-                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(T * 32), "r"(b * TC_BT_BOX_ROWS),
-                        "r"(smem_u32(&s_bbar))
-                        : "memory");
+            if (!first) {
+                __syncthreads();  // every pair is done with the previous panel
+                if (threadIdx.x == 0) load_panel(T);
             }
+            first = false;
             mbar_wait_bounded(&s_bbar, bphase, &st->err);
             bphase ^= 1u;
         }
