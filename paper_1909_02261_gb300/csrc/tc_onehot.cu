@@ -1196,9 +1196,9 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
 __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
     k_update(tc_kparams P, int items_per_block, int S, int debug_only) {
     pdl_trigger();
-    pdl_wait();  // the grad_S tiles from k_gsum
+    // Before the wait for k_gsum: only what earlier kernels wrote (the weight
+    // tiles, t) is read; the stop flag and the grad_S tiles come after it.
     tc_dev_state* st = P.st;
-    if (!debug_only && st->stop) return;
     extern __shared__ __align__(1024) float sm[];
     const int n = P.n, D = P.D, k = P.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, ngroups = ((int)(blockDim.x >> 5) - 1) / UPD_GW;
@@ -1227,13 +1227,33 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
         const int T = (int)(qq / D);
         return ((size_t)(qq - (long long)T * D) * nT + T) * k * 32;
     };
+    // the weight tiles of the first stages load while k_gsum finishes
+    const int pre = debug_only == 1 ? 0 : min(S, R);
+    if (warp == 0 && lane == 0)
+        for (int r = 0; r < pre; ++r) {
+            mbar_expect_tx(full + r, 2 * bytes);
+            bulk_load(stages + (size_t)r * 64 * k + 32 * k, P.W + tile_of(r), bytes, full + r);
+        }
+    pdl_wait();  // the grad_S tiles and the stop flag from k_gsum
+    if (!debug_only && st->stop) {
+        if (warp == 0 && lane == 0) {  // no copy may still be landing when the block exits
+            for (int r = 0; r < pre; ++r)
+                bulk_load(stages + (size_t)r * 64 * k, P.Gbuf + tile_of(r), bytes, full + r);
+            for (int r = 0; r < pre; ++r) mbar_wait_bounded(full + r, 0u, &st->err);
+        }
+        return;
+    }
     if (warp == 0) {
         if (lane == 0) {  // producer: item r into stage r % S once its previous use is released
             for (int r = 0; r < R; ++r) {
                 const int s = r % S, u = r / S;
                 float* Gs = stages + (size_t)s * 64 * k;
-                if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
                 const size_t tile = tile_of(r);
+                if (r < pre) {  // its weight tile is on the way
+                    bulk_load(Gs, P.Gbuf + tile, bytes, full + s);
+                    continue;
+                }
+                if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
                 mbar_expect_tx(full + s, debug_only == 1 ? bytes : 2 * bytes);
                 bulk_load(Gs, P.Gbuf + tile, bytes, full + s);
                 if (debug_only != 1) bulk_load(Gs + 32 * k, P.W + tile, bytes, full + s);
