@@ -156,8 +156,10 @@ __global__ void k_assign(tc_kparams P) {
 // ---------------------------------------------------------------------------
 template <int CB>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
-    pdl_trigger();
     pdl_wait();  // colours from the previous k_update (dense forms: M~ from the GEMM)
+    // k_classes reads the colours before its own wait: it may start only
+    // once this kernel's predecessors are complete
+    pdl_trigger();
     const int2 tile = P.pair_tiles[blockIdx.x];
     if (P.commit && P.st->stop) {
         // the dense forms' M~ accumulates by reduce-adds: every block leaves
@@ -469,11 +471,15 @@ __device__ void finalize_population(const tc_kparams& P, void* scratch) {
 // the per-warp colour counts of the sort.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
-    // k_gsum reads the pair matrix of k_pairs before its own wait: it may
-    // start only once this kernel's predecessors are complete
-    pdl_wait();
-    pdl_trigger();
-    if (P.commit && P.st->stop) return;
+    // Launched once k_pairs has passed its own wait, so the colours of the
+    // previous update (and the stop flag) are final: the class lists need
+    // nothing from k_pairs and are built while it runs.  The wait for k_pairs
+    // comes at the end, before this kernel lets k_gsum start (k_gsum reads
+    // the pair matrix of k_pairs before its own wait).
+    if (P.commit && P.st->stop) {
+        pdl_wait();
+        return;
+    }
     __shared__ int s_hist[TC_MAX_K];
     __shared__ int s_cur[TC_MAX_K];
     __shared__ int s_scan[64];
@@ -592,6 +598,8 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     }
     // conflicts (eq. 1) are counted by k_gsum, which walks these class lists
     if (threadIdx.x == 0) P.fcolor[d] = 0;
+    pdl_wait();
+    pdl_trigger();
 }
 
 

@@ -800,9 +800,9 @@ int launch_iteration(tc_ctx* c) {
     tc_kparams P = make_kparams(c, 1);
     const bool dense = P.M32 != nullptr;
     int rc;
-    // k_pairs and k_classes share only the completion ticket (the last block
-    // of either reduces the population); one stream: run side by side they
-    // stretch the latency-bound k_classes more than they overlap
+    // k_pairs and k_classes share no data: k_classes builds its class lists
+    // while k_pairs runs (it is launched once k_pairs has passed its wait)
+    // and waits for k_pairs only before it lets k_gsum start
     if (dense && (rc = launch_dense_gemms(c, 0, c->stream))) return rc;
     TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
     if (dense && (rc = launch_dense_gemms(c, 1, c->stream))) return rc;
