@@ -952,14 +952,21 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     while (q < qend) {
         const int T = (int)(q / D);
         const long long seg_end = min(qend, (long long)(T + 1) * D);
+        // Each warp waits for the segment's panel just before its first walk,
+        // so that the staging of its first item overlaps the panel's load.
+        // Every segment holds an item, so some warp has waited for the
+        // previous panel before the barrier below lets the next one start.
+        bool panel_pending = false;
+        unsigned seg_phase = 0;
         if (BTS) {
             if (!first) {
                 __syncthreads();  // every pair is done with the previous panel
                 if (threadIdx.x == 0) load_panel(T);
             }
             first = false;
-            mbar_wait_bounded(&s_bbar, bphase, &st->err);
+            seg_phase = bphase;
             bphase ^= 1u;
+            panel_pending = true;
         }
         const int i0 = T * 32, rows = min(32, n - i0);
         for (long long qq = q + unit; qq < seg_end; qq += nunits) {
@@ -979,6 +986,10 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 pair_sync(unit);
             } else if (!CSR) {
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
+            }
+            if (BTS && panel_pending) {
+                mbar_wait_bounded(&s_bbar, seg_phase, &st->err);
+                panel_pending = false;
             }
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
             // the item's gamma entries: colour j of row i0 + lane at grow[j * gstride]
