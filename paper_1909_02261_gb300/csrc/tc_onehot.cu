@@ -679,6 +679,18 @@ __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async_16(uint32_t smem_dst, const void* gsrc) {  // both 16-byte aligned
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_dst), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_4(uint32_t smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_dst), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {  // this thread's copies have landed
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void pair_sync(int pair) {  // warps 2 pair, 2 pair + 1 (named barrier pair + 1)
     asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
 }
@@ -692,9 +704,9 @@ __device__ __forceinline__ void fence_proxy_async() {
 // colour-sorted vertices (length a multiple of 4; padding is vertex n, a zero
 // row of B), so a class is a loop of 4-wide chunks: one 16-byte index load
 // and four independent loads of B.  BS > 0: B rows BS floats apart (the
-// shared panel), else `bstride`.  STG: pm, of and xs (= nu t E_dj) are the
+// shared panel), else `bstride`.  STG: pm, of and xs (= E_dj) are the
 // warp's shared-memory copies; else pm, of in global memory and xs unused
-// (Ed, nut give the additive term).  Gout[j * 32] receives the class sum +
+// (Ed gives E).  Gout[j * 32] receives the class sum +
 // nu t E_dj (+ gs times the gamma-matrix entry in the dense forms: gs = -1 for
 // the partitioning problems, whose A.S term changes sign).
 template <int BS, bool STG>
@@ -718,7 +730,7 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
         float extra;
         if (STG) {
             e_next = of[j + 2 <= k ? j + 2 : k];
-            extra = xs[j];
+            extra = nut * xs[j];
         } else {
             e_next = (j + 2 <= k) ? __ldg(of + j + 2) : 0;  // next bound, ahead of use
             extra = nut * __ldg(Ed + j);
@@ -761,7 +773,7 @@ __device__ __forceinline__ uint4 lds_u32x4(uint32_t a) {
 // class_sums for the hot configuration (the tile's B columns and the item's
 // lists both in shared memory), on 32-bit shared addresses: the B entry of
 // vertex v for this lane sits at bl + 128 v.
-__device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, const float* xs,
+__device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, const float* xs, float nut,
                                                   const uint16_t* grow, float gs, int gstride, uint32_t bl, int k,
                                                   int jb, int je, float* Gout) {
     if (jb >= je) return;
@@ -776,7 +788,7 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
     }
     for (int j = jb; j < je; ++j) {
         const uint32_t e_next = pm + 4u * (uint32_t)of[j + 2 <= k ? j + 2 : k];
-        float extra = xs[j];
+        float extra = nut * xs[j];
         if (grow) {
             extra += gs * (float)g0;
             g0 = g1;
@@ -976,13 +988,13 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const float* Ed = P.E + (size_t)d * k;
             if (STG) {
                 pair_sync(unit);  // the pair's reads of the previous item are done
+                // asynchronous copies (cp.async), all in flight at once
                 const uint4* src = reinterpret_cast<const uint4*>(pm);
-                uint4* dst = reinterpret_cast<uint4*>(ps);
                 const int t64 = h * 32 + lane;
-#pragma unroll 4
-                for (int l = t64; l < P.perm_stride / 4; l += 64) dst[l] = __ldg(src + l);
-                for (int j = t64; j <= k; j += 64) os[j] = __ldg(of + j);
-                for (int j = t64; j < k; j += 64) xs[j] = nut * __ldg(Ed + j);
+                for (int l = t64; l < P.perm_stride / 4; l += 64) cp_async_16(smem_u32(ps) + 16u * l, src + l);
+                for (int j = t64; j <= k; j += 64) cp_async_4(smem_u32(os + j), of + j);
+                for (int j = t64; j < k; j += 64) cp_async_4(smem_u32(xs + j), Ed + j);
+                cp_async_wait_all();
                 pair_sync(unit);
             } else if (!CSR) {
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
@@ -1013,7 +1025,8 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 const int kh = min(k, (k + 4) >> 1), jb = STG ? h * kh : 0, je = STG ? (h ? k : kh) : k;
                 if (STG) {
                     if (BTS)
-                        class_sums_shared(smem_u32(ps), os, xs, grow, gs, gstride, smem_u32(Bl), k, jb, je, Gout);
+                        class_sums_shared(smem_u32(ps), os, xs, nut, grow, gs, gstride, smem_u32(Bl), k, jb, je,
+                                          Gout);
                     else
                         class_sums<0, true>(ps, os, xs, Ed, grow, gs, gstride, Bl, P.ldb, nut, k, jb, je, Gout);
                 } else if (BTS) {
