@@ -391,6 +391,34 @@ def run_ours(args):
         ctx.tc_set_params(p)
         forms["chosen"] = max((f for f in forms if f != "chosen"), key=lambda f: forms[f]["value"])
 
+    # the problem variants of Section 7 on the same graph, k and D (throughput
+    # shapes; the same timing rules): equitable colouring, k-partitioning
+    # (plain and balanced), minimum sum colouring (costs z_j = j + 1) in the
+    # one-hot form, multicolouring (demands 1..3) in the FP8 dense form
+    variants = None
+    if not args.no_forms and world == 1:
+        variants = {}
+        vsteps = min(args.steps, 500)
+        cases = (("ecp", T.params(T.TC_ECP, stop_on_legal=0, mu=0.0, nu=1e-5), None),
+                 ("kpart", T.params(T.TC_KPART, stop_on_legal=0), None),
+                 ("kpart_balanced", T.params(T.TC_KPART_BAL, stop_on_legal=0, nu=1e-5), None),
+                 ("mscp", T.params(T.TC_MSCP, stop_on_legal=0), None),
+                 ("multicolor_dense_fp8", T.params(T.TC_KCOL, stop_on_legal=0, form=T.TC_FORM_DENSE_FP8),
+                  np.random.default_rng(w["graph_seed"]).integers(1, 4, n).astype(np.int32)))
+        for name, pv, demand in cases:
+            ctx.tc_set_params(pv)
+            if demand is not None:
+                ctx.tc_set_demands(demand)
+            vms, _, _, _, _, _ = time_steps(vsteps, 3, False, False)
+            _, vk, vc, _, _, _ = time_steps(min(vsteps, 200), 3, False, True)
+            variants[name] = {"value": D * vsteps / (vms / 1e3), "unit": "individual-steps/s",
+                              "ms_per_step": vms / vsteps, "steps": vsteps,
+                              "kernels_us": {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * vk[q] / max(1, vc[q])
+                                             for q in range(len(vk)) if vc[q] > 0}}
+            if demand is not None:
+                ctx.tc_set_demands(np.ones(n, np.int32))
+        ctx.tc_set_params(p)
+
     # roofline of the dominant stage: the gradient + update stage (k_update,
     # preceded by k_gsum when the gradient tiles are computed separately)
     kid = int(np.argmax(kms))
@@ -447,6 +475,7 @@ def run_ours(args):
         "roofline_tensor": tensor_roof,
         "roofline_gsum": gsum_roof,
         "forms": forms,
+        "variants": variants,
         "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clocks,
