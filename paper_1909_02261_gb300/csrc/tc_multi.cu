@@ -84,7 +84,11 @@ __device__ __forceinline__ bool has_colour(const uint16_t* set, int c, int j) {
 
 // One block per individual: class sizes, padded offsets, class lists; the
 // additive term is absent (multicolouring is a k-COL variant): E = 0, f_eq = 0.
-__global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P) {
+// masks (k x adj_words words of dynamic shared memory, or 0): the class
+// membership bitmasks, from which a warp writes a class's members in vertex
+// order with a popcount scan over n / 32 words; without them it tests every
+// vertex for the class.
+__global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P, int masks) {
     // k_gsum reads the pair matrix of k_pairs before its own wait: it may
     // start only once this kernel's predecessors are complete
     pdl_wait();
@@ -99,10 +103,18 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P) {
         s_hist[j] = 0;
         P.E[(size_t)d * k + j] = 0.0f;
     }
+    extern __shared__ uint32_t mk[];  // masks: bit b of mk[j aw + w]: vertex 32 w + b has colour j
+    const int aw = P.adj_words;
+    if (masks)
+        for (int e = threadIdx.x; e < k * aw; e += blockDim.x) mk[e] = 0u;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int c = P.dem[i];
-        for (int q = 0; q < c; ++q) atomicAdd(&s_hist[cmd[(size_t)i * cmax + q]], 1);
+        for (int q = 0; q < c; ++q) {
+            const int col = cmd[(size_t)i * cmax + q];
+            atomicAdd(&s_hist[col], 1);
+            if (masks) atomicOr(&mk[col * aw + (i >> 5)], 1u << (i & 31));
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {  // padded exclusive scan (k <= TC_MAX_K, once per individual)
@@ -119,15 +131,32 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P) {
     int* od = P.off + (size_t)d * (k + 1);
     uint32_t* pd = P.perm + (size_t)d * P.perm_stride;
     for (int j = threadIdx.x; j <= k; j += blockDim.x) od[j] = s_off[j];
-    // a warp per class: vertices in order, members compacted by ballot
+    // a warp per class, members in vertex order
     for (int j = warp; j < k; j += nwp) {
         int pos = s_off[j];
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + lane;
-            const bool in = i < n && has_colour(cmd + (size_t)i * cmax, P.dem[i], j);
-            const unsigned m = __ballot_sync(0xffffffffu, in);
-            if (in) pd[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
-            pos += __popc(m);
+        if (masks) {  // lane w: the members in word w, after those of the lower words
+            for (int w0 = 0; w0 < aw; w0 += 32) {
+                const int w = w0 + lane;
+                uint32_t bits = w < aw ? mk[j * aw + w] : 0u;
+                const int cnt = __popc(bits);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                for (int q = pos + incl - cnt; bits; bits &= bits - 1u, ++q)
+                    pd[q] = (uint32_t)(32 * w + __ffs(bits) - 1);
+                pos += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        } else {  // vertices in order, members compacted by ballot
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + lane;
+                const bool in = i < n && has_colour(cmd + (size_t)i * cmax, P.dem[i], j);
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) pd[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+                pos += __popc(m);
+            }
         }
         for (int q = pos + lane; q < s_off[j + 1]; q += 32) pd[q] = (uint32_t)n;  // padding entries
     }
@@ -143,5 +172,12 @@ cudaError_t tc_launch_assign_multi(const tc_kparams& P, int clear_old, cudaStrea
 }
 
 cudaError_t tc_launch_classes_multi(const tc_kparams& P, cudaStream_t s) {
-    return tc_launch_pdl(k_classes_multi, dim3(P.D), dim3(MC_THREADS), 0, s, P);
+    const long long mask_bytes = 4ll * P.k * P.adj_words;
+    const int masks = mask_bytes <= 96 * 1024 ? 1 : 0;
+    const int smem = masks ? (int)mask_bytes : 0;
+    if (masks) {
+        cudaError_t e = cudaFuncSetAttribute(k_classes_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    return tc_launch_pdl(k_classes_multi, dim3(P.D), dim3(MC_THREADS), smem, s, P, masks);
 }
