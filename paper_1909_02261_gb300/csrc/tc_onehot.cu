@@ -612,10 +612,10 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
 //             of B in shared memory (2-D TMA boxes); each warp sums B over the
 //             individual's colour classes, one vertex per lane.
 //   k_update  streams the item's grad_S tile and its 32 x k weight rows into
-//             shared memory with bulk async copies, each lane updates its own
-//             row (softmax, straight-through gradient of eq. 12, descent step,
-//             smoothing of eq. 8, the next argmax) and the rows go back with a
-//             bulk async store.
+//             shared memory with bulk async copies, lane r of four warps
+//             updates row r (softmax, straight-through gradient of eq. 12,
+//             descent step, smoothing of eq. 8, the next argmax) and the rows
+//             go back with a bulk async store.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -1079,9 +1079,9 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
 // ---------------------------------------------------------------------------
 // k_update: per item, bulk copies bring the grad_S tile and the weight tile
 // (both [k][32], contiguous: the tile-transposed weight layout) into shared
-// memory; lane r of each warp of a pair updates its half of row r with loops
-// uniform across the warp and free of bank conflicts, and the tile goes back
-// with a bulk store.
+// memory; lane r of each warp of a group of four updates its quarter of row
+// r with loops uniform across the warp and free of bank conflicts, and the
+// tile goes back with a bulk store.
 // debug_only: 1 = copy grad_S L to P.dbg_G; 2 = write grad_W L to P.dbg_G
 // instead of updating W.
 // ---------------------------------------------------------------------------
