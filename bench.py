@@ -406,17 +406,23 @@ def run_ours(args):
                  ("multicolor_dense_fp8", T.params(T.TC_KCOL, stop_on_legal=0, form=T.TC_FORM_DENSE_FP8),
                   np.random.default_rng(w["graph_seed"]).integers(1, 4, n).astype(np.int32)))
         for name, pv, demand in cases:
-            ctx.tc_set_params(pv)
-            if demand is not None:
-                ctx.tc_set_demands(demand)
-            vms, _, _, _, _, _ = time_steps(vsteps, 3, False, False)
-            _, vk, vc, _, _, _ = time_steps(min(vsteps, 200), 3, False, True)
-            variants[name] = {"value": D * vsteps / (vms / 1e3), "unit": "individual-steps/s",
-                              "ms_per_step": vms / vsteps, "steps": vsteps,
-                              "kernels_us": {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * vk[q] / max(1, vc[q])
-                                             for q in range(len(vk)) if vc[q] > 0}}
-            if demand is not None:
-                ctx.tc_set_demands(np.ones(n, np.int32))
+            demanded = False
+            try:  # a variant that fails is reported, not fatal to the headline line
+                ctx.tc_set_params(pv)
+                if demand is not None:
+                    ctx.tc_set_demands(demand)
+                    demanded = True
+                vms, _, _, _, _, _ = time_steps(vsteps, 3, False, False)
+                _, vk, vc, _, _, _ = time_steps(min(vsteps, 200), 3, False, True)
+                variants[name] = {"value": D * vsteps / (vms / 1e3), "unit": "individual-steps/s",
+                                  "ms_per_step": vms / vsteps, "steps": vsteps,
+                                  "kernels_us": {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * vk[q] / max(1, vc[q])
+                                                 for q in range(len(vk)) if vc[q] > 0}}
+            except T.TensColError as exc:
+                variants[name] = {"error": str(exc)}
+            finally:
+                if demanded:
+                    ctx.tc_set_demands(np.ones(n, np.int32))
         ctx.tc_set_params(p)
 
     # roofline of the dominant stage: the gradient + update stage (k_update,
