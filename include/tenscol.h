@@ -308,7 +308,9 @@ int tc_set_trace(tc_ctx *ctx, int capacity, int every);
 
 /* Copies the retained records, oldest first, up to `max` of them into out
  * (caller-owned; may be NULL to count only); *count receives how many are
- * retained (at most the capacity).  Synchronises the context's stream. */
+ * retained (at most the capacity; 0 with the trace off).  Synchronises the
+ * context's stream.  TC_ERR_ARG for max < 0, TC_ERR_STATE without a
+ * population, a CUDA error code if the copy fails. */
 int tc_get_trace(tc_ctx *ctx, tc_trace_entry *out, int max, int *count);
 
 /* Colour costs z[0..k-1] >= 0 of the minimum sum colouring (TC_MSCP,
