@@ -151,8 +151,9 @@ __global__ void k_assign(tc_kparams P) {
 // k_pairs: one 32x32 tile (I <= M) of vertex pairs per block, 2x2 pairs per
 // thread.  Colours are packed 4 (8-bit, k <= 255) or 2 (16-bit) to a word of
 // cT; equal colours are counted without branches: x = a ^ b has a zero lane
-// exactly where the colours agree, and ~(((x & 0x7f..) + 0x7f..) | x) sets
-// the top bit of precisely those lanes (no carry crosses a lane).
+// exactly where the colours agree, ~(((x & 0x7f..) + 0x7f..) | x) sets the
+// top bit of precisely those lanes (no carry crosses a lane), and a dp4a
+// with 0x01010101 adds the marked bytes: 128 per equal colour.
 // ---------------------------------------------------------------------------
 template <int CB>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
@@ -179,7 +180,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     __shared__ float s_red[2][PAIR_THREADS / 32];
     constexpr uint32_t LOW = CB == 1 ? 0x7F7F7F7Fu : 0x7FFF7FFFu;
     constexpr uint32_t HIGH = CB == 1 ? 0x80808080u : 0x80008000u;
-    constexpr int SH = CB == 1 ? 7 : 15;
 
     const int n = P.n, D = P.D;
     const int I = tile.x, M = tile.y;
@@ -203,11 +203,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
             s_b[r][w] = mm < n ? cTw[(size_t)mm * Dw + w0 + w] : 0u;
         }
         __syncthreads();
-        uint32_t acc[PP][PP];
-#pragma unroll
-        for (int a = 0; a < PP; ++a)
-#pragma unroll
-            for (int b = 0; b < PP; ++b) acc[a][b] = 0u;
         for (int w = 0; w < cw; ++w) {
             uint32_t av[PP], bv[PP];
 #pragma unroll
@@ -221,16 +216,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
                 for (int b = 0; b < PP; ++b) {
                     const uint32_t x = av[a] ^ bv[b];
                     const uint32_t y = (x & LOW) + LOW;
-                    acc[a][b] += (~(y | x) & HIGH) >> SH;
+                    // the byte sum of the marks (0x80 per equal colour): 128
+                    // per equal colour, one dp4a instead of a shift and an add
+                    wide[a][b] = __dp4a(~(y | x) & HIGH, 0x01010101u, wide[a][b]);
                 }
         }
-        // fold the per-lane chunk counters (< 256) into two 16-bit lanes
-#pragma unroll
-        for (int a = 0; a < PP; ++a)
-#pragma unroll
-            for (int b = 0; b < PP; ++b)
-                wide[a][b] += CB == 1 ? (acc[a][b] & 0x00FF00FFu) + ((acc[a][b] >> 8) & 0x00FF00FFu)
-                                      : acc[a][b];
     }
 
     // pair coefficient of eq. 13 and loss terms of eq. 5-6; the partitioning
@@ -270,7 +260,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
                     mt = mg[a][b];
                     P.M32[(size_t)i * P.ldm + m] = 0.f;
                 } else {
-                    mt = (int)((wide[a][b] & 0xFFFFu) + (wide[a][b] >> 16)) - pad;
+                    mt = (int)(wide[a][b] >> 7) - pad;
                 }
                 // a count of shared colours: the tables hold mt_max + 1 entries
                 mt = min(max(mt, 0), P.mt_max);
