@@ -153,10 +153,14 @@ __global__ void k_assign(tc_kparams P) {
 // cT; equal colours are counted without branches: x = a ^ b has a zero lane
 // exactly where the colours agree, ~(((x & 0x7f..) + 0x7f..) | x) sets the
 // top bit of precisely those lanes (no carry crosses a lane), and a dp4a
-// with 0x01010101 adds the marked bytes: 128 per equal colour.
+// with 0x01010101 adds the marked bytes: 128 per equal colour.  C7 (8-bit
+// lanes, k <= 128): colours fit in 7 bits and the padding slots (all ones)
+// cancel in x, so no lane of x has its top bit set, x & 0x7f.. is x and the
+// mark is ~(x + 0x7f..) & 0x80.. (one operation fewer per word).
 // ---------------------------------------------------------------------------
-template <int CB>
+template <int CB, bool C7>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
+    static_assert(!C7 || CB == 1, "7-bit colours are packed in bytes");
     pdl_wait();  // colours from the previous k_update (dense forms: M~ from the GEMM)
     // k_classes reads the colours before its own wait: it may start only
     // once this kernel's predecessors are complete
@@ -215,10 +219,10 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
 #pragma unroll
                 for (int b = 0; b < PP; ++b) {
                     const uint32_t x = av[a] ^ bv[b];
-                    const uint32_t y = (x & LOW) + LOW;
+                    const uint32_t mark = C7 ? ~(x + LOW) & HIGH : ~(((x & LOW) + LOW) | x) & HIGH;
                     // the byte sum of the marks (0x80 per equal colour): 128
                     // per equal colour, one dp4a instead of a shift and an add
-                    wide[a][b] = __dp4a(~(y | x) & HIGH, 0x01010101u, wide[a][b]);
+                    wide[a][b] = __dp4a(mark, 0x01010101u, wide[a][b]);
                 }
         }
     }
@@ -1380,8 +1384,9 @@ cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s) {
 
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
     if (P.ct_bytes == 1)
-        return tc_launch_pdl(k_pairs<1>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
-    return tc_launch_pdl(k_pairs<2>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
+        return P.k <= 128 ? tc_launch_pdl(k_pairs<1, true>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P)
+                          : tc_launch_pdl(k_pairs<1, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
+    return tc_launch_pdl(k_pairs<2, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
 }
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
