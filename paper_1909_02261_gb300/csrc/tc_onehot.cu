@@ -907,7 +907,9 @@ __host__ __device__ inline long long gsum_chunk_item(long long c, int cpt, int D
     return (c / cpt) * D + ((c % cpt) * D) / cpt;
 }
 
-template <bool BTS, bool CSR, bool STG>
+// DN: the dense forms' gamma matrix (and the multicolouring's colour sets)
+// may be present; without it their code is compiled out of the one-hot walk.
+template <bool BTS, bool CSR, bool STG, bool DN>
 __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB) {
     pdl_trigger();
@@ -1005,7 +1007,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             }
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
             // the item's gamma entries: colour j of row i0 + lane at grow[j * gstride]
-            const uint16_t* grow = P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad, k) : nullptr;
+            const uint16_t* grow = DN && P.G16 ? P.G16 + tc_gamma_index(d, i0 + lane, 0, P.n_pad, k) : nullptr;
             const int gstride = P.n_pad;
             const float gs = tc_is_partition(P.problem) ? -1.0f : 1.0f;  // sign of the A.S term
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
@@ -1037,11 +1039,11 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 if (counter) {
                     conf = 0;
                     if (live) {
-                        if (P.cm) {  // multicolouring: shared colours with the neighbours, over i's colours
+                        if (DN && P.cm) {  // multicolouring: shared colours with the neighbours, over i's colours
                             const uint16_t* set = P.cm + ((size_t)d * n + i0 + lane) * P.cmax;
                             const int ci_n = __ldg(P.dem + i0 + lane);
                             for (int qq = 0; qq < ci_n; ++qq) conf += __ldg(grow + (size_t)set[qq] * gstride);
-                        } else if (P.G16)
+                        } else if (DN && P.G16)
                             conf = __ldg(grow + (size_t)ci * gstride);  // the gamma matrix of the dense forms
                         else if (STG)
                             conf = own_class_conflicts<true>(ps, os, ci, Bl, bstride, gs);
@@ -1401,7 +1403,7 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
 template <bool BTS, bool CSR, bool STG>
 static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, int warps, int smem,
                                  cudaStream_t s) {
-    auto fn = k_gsum<BTS, CSR, STG>;
+    auto fn = (P.G16 || P.cm) ? k_gsum<BTS, CSR, STG, true> : k_gsum<BTS, CSR, STG, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int units = STG ? warps / 2 : warps;
