@@ -158,7 +158,7 @@ __global__ void k_assign(tc_kparams P) {
 // cancel in x, so no lane of x has its top bit set, x & 0x7f.. is x and the
 // mark is ~(x + 0x7f..) & 0x80.. (one operation fewer per word).
 // ---------------------------------------------------------------------------
-template <int CB, bool C7>
+template <int CB, bool C7, bool DN>  // DN: M~ comes from the dense forms' GEMM
 __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     static_assert(!C7 || CB == 1, "7-bit colours are packed in bytes");
     pdl_wait();  // colours from the previous k_update (dense forms: M~ from the GEMM)
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     if (P.commit && P.st->stop) {
         // the dense forms' M~ accumulates by reduce-adds: every block leaves
         // its entries zero for the next GEMM, also when it has nothing to do
-        if (P.M32)
+        if (DN)
             for (int e = threadIdx.x; e < PT * PT; e += PAIR_THREADS) {
                 const int i = tile.x * PT + e / PT, m = tile.y * PT + e % PT;
                 if (i < P.n && m < P.n) {
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
     for (int a = 0; a < PP; ++a)
 #pragma unroll
         for (int b = 0; b < PP; ++b) wide[a][b] = 0u;
-    const bool from_gemm = P.M32 != nullptr;  // dense form: M~ came from a GEMM
+    constexpr bool from_gemm = DN;  // dense form: M~ came from a GEMM
     for (int w0 = 0; w0 < (from_gemm ? 0 : Dw); w0 += PAIR_CW) {
         const int cw = min(PAIR_CW, Dw - w0);
         __syncthreads();
@@ -1127,7 +1127,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // done with the stage.
 __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, float* Ws, float* xa, float* xb,
                                             int grp, int h, int T, int d, int cur, bool smooth,
-                                            int debug_only) {
+                                            int debug_only, bool dn) {
     static_assert(UPD_GW == 4, "the sums below combine four quarters");
     const int n = P.n, k = P.k;
     const int lane = threadIdx.x & 31;
@@ -1214,9 +1214,9 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
             bestv = xb[q * 64 + lane];
             newc = __float_as_int(xb[q * 64 + 32 + lane]);
         }
-    if (live && !P.cm) {  // (the multicolouring's next assignment is k_assign_multi)
+    if (live && !(dn && P.cm)) {  // (the multicolouring's next assignment is k_assign_multi)
         const int i = i0 + lane;
-        if (P.S8 && cur != newc) {  // dense forms: move the one-hot entry of (d, i) in both operands
+        if (dn && P.S8 && cur != newc) {  // dense forms: move the one-hot entry of (d, i) in both operands
             const size_t co = (size_t)d * k + cur, cn = (size_t)d * k + newc;
             P.S8[(size_t)i * P.ldg + co] = 0;
             P.S8[(size_t)i * P.ldg + cn] = 0x38;  // E4M3 1.0
@@ -1227,8 +1227,12 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     }
 }
 
+template <int DBG, bool DN>
 __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
-    k_update(tc_kparams P, int items_per_block, int S, int debug_only) {
+    k_update(tc_kparams P, int items_per_block, int S) {
+    // DBG: the debug mode (compile time); DN: the dense forms' FP8 operands
+    // or the multicolouring may be present (else their code is compiled out)
+    constexpr int debug_only = DBG;
     pdl_trigger();
     // Before the wait for k_gsum: only what earlier kernels wrote (the weight
     // tiles, t) is read; the stop flag and the grad_S tiles come after it.
@@ -1320,7 +1324,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
             if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
             mbar_wait_bounded(full + s, (unsigned)u & 1u, &st->err);
             float* Gs = stages + (size_t)s * 64 * k;
-            update_item(P, Gs, Gs + 32 * k, xa, xb, grp, h, T, d, cur, smooth, debug_only);
+            update_item(P, Gs, Gs + 32 * k, xa, xb, grp, h, T, d, cur, smooth, debug_only, DN);
             // all the group's warps are past its last barrier of the item (their
             // writes of the weight tile fenced for the async proxy): one lane
             // writes the tile back and frees the stage once the store has read it
@@ -1385,10 +1389,13 @@ cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s) {
 }
 
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
+    if (P.M32)  // the dense forms: M~ read from the GEMM, no colour compares
+        return tc_launch_pdl(k_pairs<1, false, true>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
     if (P.ct_bytes == 1)
-        return P.k <= 128 ? tc_launch_pdl(k_pairs<1, true>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P)
-                          : tc_launch_pdl(k_pairs<1, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
-    return tc_launch_pdl(k_pairs<2, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
+        return P.k <= 128 ? tc_launch_pdl(k_pairs<1, true, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P)
+                          : tc_launch_pdl(k_pairs<1, false, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s,
+                                          P);
+    return tc_launch_pdl(k_pairs<2, false, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
 }
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
@@ -1460,8 +1467,11 @@ cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, i
     long long blocks = std::min<long long>(num_sms, items);
     if (blocks < 1) blocks = 1;
     const int per_block = (int)((items + blocks - 1) / blocks);
-    cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const bool dn = P.S8 != nullptr || P.cm != nullptr;
+    auto fn = debug_only == 1 ? (dn ? k_update<1, true> : k_update<1, false>)
+            : debug_only == 2 ? (dn ? k_update<2, true> : k_update<2, false>)
+                              : (dn ? k_update<0, true> : k_update<0, false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return tc_launch_pdl(k_update, dim3((unsigned)blocks), dim3((1 + UPD_GW * pairs) * 32), smem, s, P, per_block,
-                         S, debug_only);
+    return tc_launch_pdl(fn, dim3((unsigned)blocks), dim3((1 + UPD_GW * pairs) * 32), smem, s, P, per_block, S);
 }
