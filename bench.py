@@ -13,11 +13,12 @@ to flush the 129 MB L2 (the step's own working set, 77 MB, would otherwise
 stay cached).  Each step is bracketed by CUDA events on the stream the
 library launches on; the sum over K steps is the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus 1] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (under torchrun): N independent replicas (one population per GPU, own
-seed), weak scaling; the only collective is the timing max-reduce.
---impl reference times the CPU oracle (single thread) on the same metric.
+The path runs on one GPU (Section 5.2 runs each experiment on one GPU); a
+launch with more than one rank or --gpus above 1 is refused with an error.
+--impl reference times the CPU oracle (single thread) on the same metric;
+under torchrun only rank 0 runs it and the other ranks exit without work.
 """
 from __future__ import annotations
 
@@ -175,24 +176,6 @@ def traffic_record(kernel, src_files):
     return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == h.hexdigest() else None
 
 
-def slowest_rank(x, device):
-    """Max of x over the ranks of the process group (the slowest replica's
-    time sets the whole job's); x itself on a single process."""
-    import torch
-    import torch.distributed as dist
-    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
-        return x
-    t = torch.tensor([x], device=device, dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def whole_job_rate(world, D, steps, seconds):
-    """individual-steps/s of the whole job: every rank steps its own population
-    of D individuals `steps` times (independent replicas, weak scaling)."""
-    return world * D * steps / seconds
-
-
 def cpu_oracle_rate(rp, ci, w, iters):
     """The oracle as it stands: `iters` full iterations, single thread."""
     from oracle import oracle as O
@@ -247,17 +230,16 @@ def run_reference(args):
 
 
 def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 or args.gpus != 1:
+        # one population on one GPU; no multi-GPU path is built
+        sys.exit(f"bench.py: the TensCol step runs on one GPU; got WORLD_SIZE={world}, --gpus {args.gpus}")
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     from paper_1909_02261_gb300 import tenscol as T
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    local = 0
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -266,14 +248,10 @@ def run_ours(args):
     ctx = T.TensCol(local)
     ctx.tc_init_graph(n, rp, ci)
     p = T.params(T.TC_KCOL, stop_on_legal=0)
-    ctx.tc_init_population(w["w_seed"] + 1000 * rank, D, k, p)
+    ctx.tc_init_population(w["w_seed"], D, k, p)
     stream = torch.cuda.Stream(device=dev)
     ctx.tc_set_stream(stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
 
     def time_steps(steps, warmup, sample_clocks, kernel_timing):
         """W untimed + `steps` timed iterations, each bracketed by events on
@@ -293,7 +271,6 @@ def run_ours(args):
             if sampler:
                 sampler.start()
                 time.sleep(0.3)  # first samples before load
-            barrier()
             torch.cuda.synchronize()
             wall0 = time.perf_counter()
             for a, b in evs:
@@ -304,7 +281,6 @@ def run_ours(args):
             stream.synchronize()
             torch.cuda.synchronize()
             wall = time.perf_counter() - wall0
-            barrier()
             clocks = sampler.stop() if sampler else None
             step_ms = [a.elapsed_time(b) for a, b in evs]
             launches = ctx.tc_launch_count() - launches0
@@ -313,14 +289,13 @@ def run_ours(args):
         return float(sum(step_ms)), kms, kcnt, launches, wall, clocks
 
     total_ms, _, _, launches, wall, clocks = time_steps(args.steps, args.warmup, True, False)
-    total_ms = slowest_rank(total_ms, dev)
     # per-kernel CUDA-event times on the library's stream, same workload
     ksteps = min(args.steps, 1000)
     kernel_pass_ms, kms, kcnt, _, _, _ = time_steps(ksteps, 3, False, True)
     W_, t_now = ctx.tc_get_state()
     assert t_now == args.warmup + args.steps + 3 + ksteps, (t_now, args.warmup, args.steps)
     W_ = None
-    value = whole_job_rate(world, D, args.steps, total_ms / 1e3)
+    value = D * args.steps / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers: per step the weights go
     # host -> device, one iteration runs, the weights and the best colouring
@@ -337,8 +312,8 @@ def run_ours(args):
         best = ctx.tc_best()
         if s >= 2:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_total = slowest_rank(float(sum(e2e_times)), dev)
-    e2e_value = whole_job_rate(world, D, len(e2e_times), e2e_total) if e2e_times else None
+    e2e_total = float(sum(e2e_times))
+    e2e_value = D * len(e2e_times) / e2e_total if e2e_times else None
     h2d = Wh.nbytes
     d2h = Wh.nbytes + 4 * n + 64
 
@@ -347,7 +322,7 @@ def run_ours(args):
     # FP32 form takes ~1 ms per step)
     forms = {"onehot": {"value": value, "ms_per_step": total_ms / args.steps}}
     tensor_roof = None
-    if not args.no_forms and world == 1:
+    if not args.no_forms:
         peaks = measured_peaks()
         for name, form, steps in (("dense_fp8", T.TC_FORM_DENSE_FP8, min(args.steps, 1000)),
                                   ("dense_fp32", T.TC_FORM_DENSE_FP32, min(args.steps, 60))):
@@ -391,12 +366,12 @@ def run_ours(args):
         ctx.tc_set_params(p)
         forms["chosen"] = max((f for f in forms if f != "chosen"), key=lambda f: forms[f]["value"])
 
-    # the problem variants of Section 7 on the same graph, k and D (throughput
+    # the problem variants of Section 6 on the same graph, k and D (throughput
     # shapes; the same timing rules): equitable colouring, k-partitioning
     # (plain and balanced), minimum sum colouring (costs z_j = j + 1) in the
     # one-hot form, multicolouring (demands 1..3) in the FP8 dense form
     variants = None
-    if not args.no_forms and world == 1:
+    if not args.no_forms:
         variants = {}
         vsteps = min(args.steps, 500)
         cases = (("ecp", T.params(T.TC_ECP, stop_on_legal=0, mu=0.0, nu=1e-5), None),
@@ -469,14 +444,14 @@ def run_ours(args):
                      "peak_source": f"{sms} SMs x 32 shared-memory loads per clock x {mhz:.0f} MHz"}
 
     line = {
-        "metric": METRIC, "value": value, "unit": "individual-steps/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "individual-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "graph": "G(1000,0.5) seed 2", "n": n, "k": k, "D": D,
                    "params": "Table 2 GCP, rho=100, stop_on_legal=0", "form": "onehot",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": "single GPU"},
         "roofline": roof,
         "roofline_tensor": tensor_roof,
         "roofline_gsum": gsum_roof,
@@ -490,17 +465,14 @@ def run_ours(args):
         "wall_s_timed_region": wall,
         "best_conflicts_seen": best["conflicts"],
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(rp, ci, w, args.cpu_baseline_iters)
         line["cpu_baseline"] = {"value": rate, "unit": "individual-steps/s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"{args.cpu_baseline_iters} full oracle iterations of "
                                           f"{WORKLOAD} ({dt:.1f} s, single thread)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
 
 
 def main():

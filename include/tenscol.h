@@ -52,7 +52,7 @@ extern "C" {
 /* ---- problems and step forms -------------------------------------------- */
 #define TC_KCOL 0 /* k-colouring, GCP by k-descent (Section 3.5: f = f_color) */
 #define TC_ECP 1  /* equitable colouring (eq. 3: f = f_color + f_eq)          */
-/* k-partitioning (Section 7): Algorithm 1 with every M_d = S_d S_d^T of
+/* k-partitioning (Section 6): Algorithm 1 with every M_d = S_d S_d^T of
  * eq. 1-7 replaced by J - M_d.  The fitness is the number of cut edges
  * (edges between different groups), the penalty and bonus of eq. 5-6 are
  * taken over sum_d (J - M_d) = D J - M~, and eq. 13's A.S, penalty and bonus
@@ -60,7 +60,7 @@ extern "C" {
  * fitness (and nu t grad f_eq to the gradient, as for the ECP). */
 #define TC_KPART 2     /* f = cut edges                                      */
 #define TC_KPART_BAL 3 /* f = cut edges + f_eq                               */
-/* Minimum sum colouring (Section 7): colour l costs z_l >= 0
+/* Minimum sum colouring (Section 6): colour l costs z_l >= 0
  * (tc_set_color_costs; z_l = l + 1 by default) and the additive fitness
  * f_mscp(S_d) = sum_i z_{c_d(i)} takes the place of f_eq: f = f_color +
  * f_mscp, nu t f_mscp in eq. 7 and nu t z_l in eq. 13.  With positive costs
@@ -223,24 +223,29 @@ int tc_st_grad_dev(tc_ctx *ctx, float *gradW_dev, float *loss_dev);
 int tc_relaxed_dev(tc_ctx *ctx, const float *W_dev, float tau, int64_t t, float *loss_dev,
                    float *gradW_dev);
 
-/* For callers that cannot allocate device memory (code inside a CUDA-graph
- * capture that must not call cudaMalloc, a process sharing a device whose
- * memory pool it does not own, a fixed-budget embedding).  The paper has no
- * counterpart: this is a library service.  Computes, with no allocation of
- * any kind, the population pair terms of a population given as colours:
- * colors_dev[D*n] (device, uint16, individual-major: colour of vertex i in
- * individual d at d*n + i), adj_dev[n*n] (device, uint8 0/1, symmetric,
- * zero diagonal), and writes out_dev[0] = kappa (eq. 5) and out_dev[1] =
- * varpi (eq. 6, diagonal of bar A included iff bonus_diag) in FP32 (device).
- * Its scratch is a file-scope device array of TC_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits; n above
- * TC_NOALLOC_MAX_N is rejected with TC_ERR_ARG.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  Every call shares the one array and
- * clears its completion counter first: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller.  Runs
- * on the given stream (NULL: the legacy default stream) of the current
- * device and returns without waiting. */
+/* For callers that cannot allocate device memory: a process that shares a
+ * GPU whose memory another framework's pool manages (allocating behind the
+ * pool's back can fail or fragment it), a latency-critical loop that must
+ * not call cudaMalloc / cudaFree (they can synchronise the whole device), or
+ * an embedding whose device memory budget is fixed at start-up.  The paper
+ * has no counterpart: this is a library service.  With no allocation of any
+ * kind it computes the population pair terms of a population given as
+ * colours -- the same kappa and varpi that tc_evaluate reports in loss[1]
+ * and loss[2] -- from colors_dev[D*n] (device, uint16, individual-major:
+ * colour of vertex i in individual d at d*n + i) and adj_dev[n*n] (device,
+ * uint8 0/1, symmetric, zero diagonal), and writes out_dev[0] = kappa and
+ * out_dev[1] = varpi (the diagonal of J - A included iff bonus_diag) in FP32
+ * (device).  Its scratch is a file-scope device array of
+ * TC_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; n above TC_NOALLOC_MAX_N is rejected with TC_ERR_ARG.
+ * The first call on a device (and the first after the device's primary
+ * context was reset) looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call shares the one array and clears its completion
+ * counter first: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Runs on the given
+ * stream (NULL: the legacy default stream) of the current device and
+ * returns without waiting. */
 #define TC_NOALLOC_MAX_N 8192
 #define TC_NOALLOC_SCRATCH_BYTES 264192
 int tc_pair_terms_noalloc(int n, int D, const uint16_t *colors_dev, const uint8_t *adj_dev, float alpha,
@@ -299,7 +304,7 @@ typedef struct {
 } tc_trace_entry;
 
 /* Iteration trace (the loss and fitness evolution the paper follows in
- * Section 5): every `every` iterations t (t % every == 0) of tc_step /
+ * Section 4.3): every `every` iterations t (t % every == 0) of tc_step /
  * tc_step_async / batches, the population reduction writes one record into
  * a device ring of `capacity` records; capacity 0 turns the trace off.
  * Clears the ring.  TC_ERR_ARG for capacity < 0 or every < 1, TC_ERR_STATE
@@ -314,14 +319,14 @@ int tc_set_trace(tc_ctx *ctx, int capacity, int every);
 int tc_get_trace(tc_ctx *ctx, tc_trace_entry *out, int max, int *count);
 
 /* Colour costs z[0..k-1] >= 0 of the minimum sum colouring (TC_MSCP,
- * Section 7), copied; k must be the population's k.  Every population
+ * Section 6), copied; k must be the population's k.  Every population
  * starts with z_l = l + 1.  TC_ERR_ARG for a negative cost or another k,
  * TC_ERR_STATE without a population, TC_ERR_UNSUPPORTED when n max(z) + |E|
  * reaches 2^31 (the fitness is reduced in 32 bits).  Takes effect from the
  * next iteration, also inside captured CUDA graphs. */
 int tc_set_color_costs(tc_ctx *ctx, const int32_t *z, int k);
 
-/* Multicolouring (Section 7): vertex i must take demand[i] colours, no
+/* Multicolouring (Section 6): vertex i must take demand[i] colours, no
  * colour shared across an edge.  Step 1 then selects the demand[i] colours
  * of largest weight in w_{d,i} (the lower colour first among equal weights)
  * and every other step of Algorithm 1 keeps its formula on the multi-hot S:

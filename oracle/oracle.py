@@ -6,7 +6,7 @@ gcc on first use (into ``oracle/_build/``) and wraps each step of the
 iteration of Goudet, Duval, Hao (TensCol), Algorithm 1, with numpy arrays.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-and, for the k-partitioning problems of Section 7, by
+and, for the k-partitioning problems of Section 6, by
 ``tests/test_oracle_partition_pins.py`` (closed forms, brute force, finite
 differences, the worked kappa example of Section 3.6.1); none is "parity
 unpinned".
@@ -179,7 +179,7 @@ def equity(colors, k):
 
 
 def cut(rowptr, colidx, colors):
-    """Cut edges per individual (k-partitioning fitness, Section 7)."""
+    """Cut edges per individual (k-partitioning fitness, Section 6)."""
     rowptr, colidx, colors = _i32(rowptr), _i32(colidx), _i32(colors)
     D, n = colors.shape
     f = np.empty((D,), np.int64)
@@ -188,7 +188,7 @@ def cut(rowptr, colidx, colors):
 
 
 def mscp(colors, zcost=None):
-    """Total colour cost per individual (minimum sum colouring, Section 7)."""
+    """Total colour cost per individual (minimum sum colouring, Section 6)."""
     colors = _i32(colors)
     D, n = colors.shape
     k = int(colors.max()) + 1 if zcost is None else len(zcost)
@@ -280,7 +280,7 @@ def step(rowptr, colidx, W, params: Params, t: int, stop_on_legal: bool = False,
 
 
 def assign_multi(W, demand):
-    """Multicolouring Step 1 (Section 7): the dense 0/1 tensor S (D x n x k)."""
+    """Multicolouring Step 1 (Section 6): the dense 0/1 tensor S (D x n x k)."""
     W = _f64(W)
     D, n, k = W.shape
     demand = _i32(demand)

@@ -112,7 +112,7 @@ int orc_fitness(int D, int n, int k, const int *adj_off, const int *adj,
     return 0;
 }
 
-/* k-partitioning fitness (Section 7): M_d replaced by \bar M_d = J - M_d,
+/* k-partitioning fitness (Section 6): M_d replaced by \bar M_d = J - M_d,
  * f(S_d) = 1/2 sum(A (.) \bar M_d) = edges whose ends lie in different
  * groups (cut edges), counted here directly from the adjacency lists. */
 int orc_cut(int D, int n, const int *adj_off, const int *adj, const int *colors, long long *cut)
@@ -130,7 +130,7 @@ int orc_cut(int D, int n, const int *adj_off, const int *adj, const int *colors,
     return 0;
 }
 
-/* Minimum sum colouring (Section 7): the additive fitness sums the cost of
+/* Minimum sum colouring (Section 6): the additive fitness sums the cost of
  * the colour each vertex takes, f_mscp(S_d) = sum_i sum_l s_{d,i,l} z_l. */
 int orc_mscp(int D, int n, int k, const int *colors, const int *z, long long *f_mscp)
 {
@@ -193,7 +193,7 @@ int orc_mtilde(int D, int n, const int *colors, int *Mt)
     return 0;
 }
 
-/* The k-partitioning counterpart of eq. 4 (Section 7: M replaced by
+/* The k-partitioning counterpart of eq. 4 (Section 6: M replaced by
  * \bar M = J - M): Mb[i*n+m] = sum_d (1 - m_{d,i,m}) = #{d : c_d(i) != c_d(m)};
  * Mb[i*n+i] = 0. */
 int orc_mbar(int D, int n, const int *colors, int *Mb)
@@ -264,7 +264,7 @@ int orc_penalty_bonus(int n, const int *adj_off, const int *adj, const int *Mt,
 
 /* eq. 13: grad_S L = A.S + nu t grad f_eq + 2 alpha lambda t (A (.) Mt^(alpha-1)).S
  *                    - 2 beta mu t (\bar A (.) Mt^(beta-1)).S
- * k-partitioning (problem 2 or 3, Section 7): every M_d of eq. 7 becomes
+ * k-partitioning (problem 2 or 3, Section 6): every M_d of eq. 7 becomes
  * J - M_d, so Mt here is \bar M~ = sum_d (J - M_d) (orc_mbar) and, since
  * d(J - M_d)/dS_d = -dM_d/dS_d, every term but the equity one changes sign:
  * grad_S L = -A.S + nu t grad f_eq - 2 alpha lambda t (A (.) Mt^(alpha-1)).S
@@ -617,7 +617,7 @@ int orc_relaxed(int D, int n, int k, const int *adj_off, const int *adj,
     return 0;
 }
 
-/* Multicolouring, Step 1 (Section 7): the demand[i] largest weights of w_{d,i},
+/* Multicolouring, Step 1 (Section 6): the demand[i] largest weights of w_{d,i},
  * picked one at a time as the largest not yet taken (lowest index on ties). */
 int orc_assign_multi(int D, int n, int k, const double *W, const int *demand, double *S)
 {

@@ -26,7 +26,7 @@ extern "C" {
 typedef struct {
     int problem;        /* 0 = k-COL (GCP), 1 = ECP, 2 = k-partitioning,
                            3 = balanced k-partitioning, 4 = minimum sum
-                           colouring (Section 7)                            */
+                           colouring (Section 6)                            */
     double sigma0;      /* std of the N(0, sigma0) initial weights (Table 2) */
     double eta;         /* learning rate                                      */
     double alpha;       /* penalisation exponent  (eq. 5)                     */
@@ -58,7 +58,7 @@ int orc_gamma(int D, int n, int k, const int *adj_off, const int *adj,
 int orc_fitness(int D, int n, int k, const int *adj_off, const int *adj,
                 const int *colors, int *gamma_own, long long *f_color);
 
-/* k-partitioning fitness (Section 7): cut[d] = edges whose ends lie in
+/* k-partitioning fitness (Section 6): cut[d] = edges whose ends lie in
  * different groups of individual d, 1/2 sum(A (.) (J - M_d)). */
 int orc_cut(int D, int n, const int *adj_off, const int *adj, const int *colors, long long *cut);
 
@@ -70,11 +70,11 @@ int orc_equity(int D, int n, int k, const int *colors,
 /* Step 3-i (eq. 4): Mt[i*n+m] = #{d : c_d(i) == c_d(m)}; Mt[i*n+i] = D. */
 int orc_mtilde(int D, int n, const int *colors, int *Mt);
 
-/* Minimum sum colouring (Section 7): f_mscp[d] = sum_i sum_l s_{d,i,l} z_l =
+/* Minimum sum colouring (Section 6): f_mscp[d] = sum_i sum_l s_{d,i,l} z_l =
  * the total cost of the colours individual d uses (z = NULL: z_l = l + 1). */
 int orc_mscp(int D, int n, int k, const int *colors, const int *z, long long *f_mscp);
 
-/* k-partitioning counterpart of eq. 4 (Section 7, M -> J - M):
+/* k-partitioning counterpart of eq. 4 (Section 6, M -> J - M):
  * Mb[i*n+m] = #{d : c_d(i) != c_d(m)}; Mb[i*n+i] = 0. */
 int orc_mbar(int D, int n, const int *colors, int *Mb);
 
@@ -137,7 +137,7 @@ int orc_relaxed(int D, int n, int k, const int *adj_off, const int *adj,
                 const orc_params *p, long long t, double tau, const double *W,
                 double *loss, double *gradW, double *Mt);
 
-/* Multicolouring (Section 7): vertex i must take demand[i] >= 1 colours.
+/* Multicolouring (Section 6): vertex i must take demand[i] >= 1 colours.
  * Step 1 becomes: S_{d,i,l} = 1 for the demand[i] colours l with the largest
  * w_{d,i,l} (the lower index first among equal weights), else 0.  S is the
  * dense D*n*k 0/1 tensor, index (d*n + i)*k + l. */

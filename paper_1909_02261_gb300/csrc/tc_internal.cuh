@@ -29,7 +29,7 @@ struct tc_dev_state {
     long long trace_n;    // trace records written so far
 };
 
-// Problems whose Algorithm 1 uses J - M_d in place of M_d (Section 7), and
+// Problems whose Algorithm 1 uses J - M_d in place of M_d (Section 6), and
 // those whose fitness includes f_eq (eq. 3).
 __host__ __device__ inline bool tc_is_partition(int problem) {
     return problem == TC_KPART || problem == TC_KPART_BAL;
@@ -79,7 +79,7 @@ struct tc_kparams {
     const float* powB;        // x^beta
     tc_dev_state* st;
     uint16_t* best;           // n best-so-far colours
-    // multicolouring (Section 7; dense forms only), NULL / 0 otherwise
+    // multicolouring (Section 6; dense forms only), NULL / 0 otherwise
     const int* dem;           // n demands c_i in [1, TC_MAX_DEMAND]
     uint16_t* cm;             // D x n x cmax colour sets, increasing, 0xFFFF past c_i
     uint16_t* best_m;         // n x cmax colour sets of the best-so-far individual

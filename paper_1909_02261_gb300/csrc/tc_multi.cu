@@ -1,4 +1,4 @@
-// Multicolouring (Goudet, Duval, Hao, Section 7): vertex i must take c_i
+// Multicolouring (Goudet, Duval, Hao, Section 6): vertex i must take c_i
 // colours, no colour shared across an edge.  Step 1 of Algorithm 1 selects
 // the c_i colours of largest weight in w_{d,i}; S_d becomes a 0/1 matrix
 // with c_i ones in row i and every other step keeps its formula on it

@@ -1,9 +1,10 @@
 // Pair terms of a population without any device allocation.
 //
-// Some callers cannot allocate device memory at all: code running inside a
-// CUDA-graph capture that must not call cudaMalloc, a host process that
-// shares a device with a memory pool it does not own, or an embedding with a
-// fixed memory budget.  For them this file offers one entry point that takes
+// Some callers cannot allocate device memory at all: a host process that
+// shares a GPU whose memory another framework's pool manages, a
+// latency-critical loop that must not call cudaMalloc / cudaFree (both can
+// synchronise the whole device), or an embedding whose device memory budget
+// is fixed at start-up.  For them this file offers one entry point that takes
 // its inputs and output from the caller and keeps its scratch (the per-tile
 // partial sums and a completion ticket) in a file-scope device array.  The
 // array is part of the library image: every GPU that loads the library holds
@@ -129,7 +130,30 @@ __global__ void __launch_bounds__(NA_THREADS) k_pairs_noalloc(int n, int D, cons
 }
 
 std::mutex g_mu;
-unsigned char* g_addr[256] = {nullptr};  // device address of g_scratch per device
+// Device address of g_scratch per device, valid for the CUDA context it was
+// looked up in: a reset of the device's primary context (cudaDeviceReset)
+// makes a new context in which the array may live elsewhere.
+unsigned char* g_addr[256] = {nullptr};
+CUcontext g_addr_ctx[256] = {nullptr};
+
+// The calling thread's current driver context (cuCtxGetCurrent, reached
+// through the runtime's driver entry-point query), or nullptr on failure.
+CUcontext current_context() {
+    typedef CUresult (*get_fn)(CUcontext*);
+    static get_fn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        fn = (get_fn)p;
+    }
+    CUcontext c = nullptr;
+    return fn(&c) == CUDA_SUCCESS ? c : nullptr;
+}
 
 }  // namespace
 
@@ -145,16 +169,20 @@ extern "C" int tc_pair_terms_noalloc(int n, int D, const uint16_t* colors_dev, c
     }
     unsigned char* scratch;
     {
-        // first call on a device: look up where the array lives on it (the
-        // host-side symbol is only a stand-in, not a device address)
+        // first call on a device (or in a new context of it): look up where
+        // the array lives there (the host-side symbol is only a stand-in, not
+        // a device address); cudaGetSymbolAddress also makes the context
+        // current, so the context is read after it
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
+        const CUcontext now = current_context();
+        if (!g_addr[dev] || !now || now != g_addr_ctx[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
                 (void)cudaGetLastError();
                 return TC_ERR_CUDA;
             }
             g_addr[dev] = static_cast<unsigned char*>(p);
+            g_addr_ctx[dev] = current_context();
         }
         scratch = g_addr[dev];
     }

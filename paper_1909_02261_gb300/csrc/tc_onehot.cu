@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     if (threadIdx.x == CLS_THREADS - 1) od[k] = s_scan[32 + nwp - 1];
     // the additive fitness term and its gradient factor: equity (eq. 3)
     // with the sign of eq. 14, or for the minimum sum colouring the colour
-    // costs f_mscp = sum_j #V_{d,j} z_j, whose gradient is z_j (Section 7)
+    // costs f_mscp = sum_j #V_{d,j} z_j, whose gradient is z_j (Section 6)
     const int c1 = n / k, c2 = (n + k - 1) / k;
     const bool mscp = P.problem == TC_MSCP;
     long long fe = 0;

@@ -1,4 +1,4 @@
-"""Minimum sum colouring (Section 7: the colour-cost fitness f_mscp in place of
+"""Minimum sum colouring (Section 6: the colour-cost fitness f_mscp in place of
 f_eq) on the GPU against the oracle, in every step form:
 
 * one iteration checked element by element (colours, conflicts, colour

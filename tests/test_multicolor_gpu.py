@@ -1,4 +1,4 @@
-"""Multicolouring (Section 7: vertex i takes its c_i largest-weight colours)
+"""Multicolouring (Section 6: vertex i takes its c_i largest-weight colours)
 on the GPU against the oracle, in the two dense forms (FP8 tensor cores and
 FP32 CUDA cores), whose GEMMs compute A.S and S S^T of the multi-hot S:
 

@@ -1,4 +1,4 @@
-"""Pins of the oracle's minimum sum colouring (Section 7: Algorithm 1 with the
+"""Pins of the oracle's minimum sum colouring (Section 6: Algorithm 1 with the
 additive fitness f_mscp(S_d) = sum_i sum_l s_{d,i,l} z_l in place of f_eq)
 against closed forms, brute force and finite differences:
 

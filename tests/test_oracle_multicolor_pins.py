@@ -1,4 +1,4 @@
-"""Pins of the oracle's multicolouring (Section 7: vertex i takes the c_i
+"""Pins of the oracle's multicolouring (Section 6: vertex i takes the c_i
 colours of largest weight; everything else of Algorithm 1 on the multi-hot S)
 against closed forms, brute force, library routines and finite differences:
 

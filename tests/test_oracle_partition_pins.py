@@ -1,4 +1,4 @@
-"""Pins of the oracle's k-partitioning problems (Section 7: Algorithm 1 with
+"""Pins of the oracle's k-partitioning problems (Section 6: Algorithm 1 with
 every M_d replaced by J - M_d; fitness = cut edges, plus f_eq for the
 balanced variant) against closed forms, brute force and finite differences.
 

@@ -1,4 +1,4 @@
-"""k-partitioning and balanced k-partitioning (Section 7: Algorithm 1 with
+"""k-partitioning and balanced k-partitioning (Section 6: Algorithm 1 with
 every M_d replaced by J - M_d, fitness = cut edges, plus f_eq for the
 balanced variant) on the GPU against the oracle, in every step form:
 

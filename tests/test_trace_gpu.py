@@ -1,6 +1,6 @@
 """The iteration trace (tc_set_trace / tc_get_trace): the per-iteration
 population minimum, its individual, f_color, additive term and the loss
-terms of eq. 5-7 that the paper follows over a run (Section 5), recorded on
+terms of eq. 5-7 that the paper follows over a run (Section 4.3), recorded on
 the device.  Every record equals what tc_evaluate reports for the same
 iteration of a second context stepped one iteration at a time (the same
 kernels, so bit for bit); the ring keeps the newest records; graph replay
