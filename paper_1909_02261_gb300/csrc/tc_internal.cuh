@@ -22,7 +22,7 @@ struct tc_dev_state {
     int best_d;
     int last_fmin;
     int last_dstar;
-    unsigned int done_gsum;     // completion tickets (last-block patterns): k_gsum blocks
+    unsigned int done_classes;  // completion tickets (last-block patterns): k_classes blocks
     unsigned int done_update;
     float loss, kappa, varpi;
     int pad;
@@ -63,10 +63,14 @@ struct tc_kparams {
                               // class padded to a multiple of 4 with vertex n
     int perm_stride;          // n + 3k rounded up to a multiple of 8
     int* off;                 // D x (k + 1) padded colour-class offsets into perm
+    uint16_t* cord;           // D x cord_stride classes by decreasing padded length (k_gsum's slot walk)
+    int cord_stride;          // k rounded up to a multiple of 8
     float* E;                 // D x k gradient factor of the additive fitness term by s_{d,i,j}:
                               // the equity sign (eq. 14), or the colour cost z_j (minimum sum colouring)
     const int* zcost;         // k colour costs of the minimum sum colouring
-    int* fcolor;              // D conflicts (eq. 1)
+    int* fcolor;              // D conflicts (eq. 1), written by the population reduction
+    int* fc_acc;              // D conflicts being counted (k_pairs, or k_classes in the dense forms);
+                              // the population reduction moves them to fcolor and clears them
     int* feq;                 // D additive fitness: f_eq (eq. 3), or f_mscp (minimum sum colouring)
     float* loss_part;         // 2 x n_pair_blocks partial kappa / varpi
     int n_pair_blocks;
@@ -147,6 +151,131 @@ cudaError_t tc_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
+
+// Population reduction of one iteration, run by the last block of the
+// colour-class kernel once every individual's conflicts and additive term
+// are in: min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test),
+// the best-so-far copy, the loss of eq. 7, the stop flag and the trace.
+// `scratch`: TC_FINALIZE_SCRATCH bytes of shared memory, 8-byte aligned; any
+// block size up to 1024 threads (fixed-order sums: deterministic for a given
+// block size).
+constexpr int TC_FINALIZE_SCRATCH = 1152;
+__device__ __forceinline__ void finalize_population(const tc_kparams& P, void* scratch) {
+    // one pass: per-thread partials, warp trees, then thread 0 over the warps
+    // (fixed order: deterministic for a given block size, at most 1024)
+    long long* sh_fc = reinterpret_cast<long long*>(scratch);
+    long long* sh_fe = sh_fc + 32;
+    unsigned long long* sh_key = reinterpret_cast<unsigned long long*>(sh_fe + 32);
+    float* sh_ka = reinterpret_cast<float*>(sh_key + 32);
+    float* sh_va = sh_ka + 32;
+    int& s_dstar = *reinterpret_cast<int*>(sh_va + 32);
+    int& s_better = *(reinterpret_cast<int*>(sh_va + 32) + 1);
+    tc_dev_state* st = P.st;
+    const int D = P.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long fc = 0, fe = 0;
+    unsigned long long key = ~0ull;
+    float ka = 0.f, va = 0.f;
+    const bool part = tc_is_partition(P.problem), with_eq = tc_has_additive(P.problem);
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        // the monochromatic edges counted this iteration (k_pairs, or k_classes
+        // from the gamma matrix), cleared for the next iteration
+        const int a = __ldcg(P.fc_acc + d), b = __ldcg(P.feq + d);
+        P.fc_acc[d] = 0;
+        P.fcolor[d] = a;
+        fc += a;
+        fe += b;
+        // the fitness of the problem: monochromatic or (partitioning) cut edges,
+        // plus f_eq for the ECP and the balanced partitioning, or f_mscp for
+        // the minimum sum colouring
+        const long long fobj = part ? P.n_edges - a : (long long)a;
+        const unsigned long long f = (unsigned long long)(fobj + (with_eq ? b : 0));
+        const unsigned long long kk = (f << 32) | (unsigned)d;
+        key = kk < key ? kk : key;
+    }
+    for (int b = threadIdx.x; b < P.n_pair_blocks; b += blockDim.x) {
+        ka += __ldcg(P.loss_part + 2 * b);
+        va += __ldcg(P.loss_part + 2 * b + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fc += __shfl_xor_sync(0xffffffffu, fc, o);
+        fe += __shfl_xor_sync(0xffffffffu, fe, o);
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, key, o);
+        key = u < key ? u : key;
+        ka += __shfl_xor_sync(0xffffffffu, ka, o);
+        va += __shfl_xor_sync(0xffffffffu, va, o);
+    }
+    if (lane == 0) {
+        sh_fc[warp] = fc;
+        sh_fe[warp] = fe;
+        sh_key[warp] = key;
+        sh_ka[warp] = ka;
+        sh_va[warp] = va;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fc = fe = 0;
+        key = ~0ull;
+        ka = va = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            fc += sh_fc[w];
+            fe += sh_fe[w];
+            key = sh_key[w] < key ? sh_key[w] : key;
+            ka += sh_ka[w];
+            va += sh_va[w];
+        }
+        const int fmin = (int)(key >> 32), dstar = (int)(key & 0xffffffffu);
+        const long long t = st->t;
+        const double tt = (double)t;
+        const long long fsum = part ? (long long)D * P.n_edges - fc : fc;  // the fitness term of eq. 7
+        st->loss = (float)fsum + (float)((double)P.nu * tt) * (float)fe +
+                   (float)((double)P.lambda_ * tt) * ka - (float)((double)P.mu * tt) * va;
+        st->kappa = ka;
+        st->varpi = va;
+        st->fcolor_sum = fc;
+        st->last_fmin = fmin;
+        st->last_dstar = dstar;
+        if (P.trace && P.commit && t % P.trace_every == 0) {  // the iteration trace
+            tc_trace_entry e;
+            e.t = t;
+            e.f_min = fmin;
+            e.individual = dstar;
+            e.f_color = __ldcg(P.fcolor + dstar);  // written above (the block synced since)
+            e.f_add = __ldcg(P.feq + dstar);
+            e.loss = st->loss;
+            e.kappa = ka;
+            e.varpi = va;
+            e.pad = 0;
+            P.trace[st->trace_n % P.trace_cap] = e;
+            st->trace_n += 1;
+        }
+        int better = 0;
+        if (P.commit) {
+            st->evaluated += 1;
+            if (st->best_f < 0 || fmin < st->best_f) {
+                better = 1;
+                st->best_f = fmin;
+                st->best_fcolor = __ldcg(P.fcolor + dstar);  // written above (the block synced since)
+                st->best_feq = __ldcg(P.feq + dstar);
+                st->best_d = dstar;
+                st->best_t = t;
+            }
+            if (P.stop_on_legal && fmin == 0) st->stop = 1;
+        }
+        s_dstar = dstar;
+        s_better = better;
+    }
+    __syncthreads();
+    if (s_better) {
+        for (int i = threadIdx.x; i < P.n; i += blockDim.x)
+            P.best[i] = P.c[(size_t)s_dstar * P.n + i];
+        if (P.cm)  // multicolouring: the colour sets too
+            for (size_t e = threadIdx.x; e < (size_t)P.n * P.cmax; e += blockDim.x)
+                P.best_m[e] = P.cm[(size_t)s_dstar * P.n * P.cmax + e];
+    }
+    if (threadIdx.x == 0) st->done_classes = 0u;
+}
+
 
 // Launchers (tc_onehot.cu).  All return cudaGetLastError() of the launch.
 cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long long seed,

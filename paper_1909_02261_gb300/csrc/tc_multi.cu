@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P, int 
         }
         s_off[k] = run;
         P.feq[d] = 0;
-        P.fcolor[d] = 0;  // k_gsum counts the conflicts over these class lists
     }
     __syncthreads();
     int* od = P.off + (size_t)d * (k + 1);
@@ -159,6 +158,38 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P, int 
             }
         }
         for (int q = pos + lane; q < s_off[j + 1]; q += 32) pd[q] = (uint32_t)n;  // padding entries
+    }
+    // f_color: the colours shared across edges, from the gamma matrix (each
+    // shared colour of an edge counted from both ends)
+    __shared__ long long s_g[MC_THREADS / 32];
+    long long g = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = P.dem[i];
+        for (int q = 0; q < c; ++q)
+            g += __ldcg(P.G16 + tc_gamma_index(d, i, cmd[(size_t)i * cmax + q], P.n_pad, k));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane == 0) s_g[warp] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < nwp; ++w) t += s_g[w];
+        P.fc_acc[d] = (int)(t / 2);
+    }
+    // completion ticket: the last block reduces the population before any
+    // weight of this iteration changes
+    __shared__ int s_last;
+    __shared__ __align__(16) unsigned char s_fin[TC_FINALIZE_SCRATCH];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&P.st->done_classes, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_population(P, s_fin);
     }
 }
 

@@ -338,133 +338,17 @@ __device__ T block_sum(T v, T* sh) {
 }
 
 
-// Population reduction of one iteration, run by the last k_gsum block:
-// min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test), the
-// best-so-far copy, the loss of eq. 7 and the stop flag.
-// `scratch`: 1,104 bytes of shared memory the block no longer uses,
-// 8-byte aligned.
-__device__ void finalize_population(const tc_kparams& P, void* scratch) {
-    // one pass: per-thread partials, warp trees, then thread 0 over the warps
-    // (fixed order: deterministic for a given block size, at most 1024)
-    long long* sh_fc = reinterpret_cast<long long*>(scratch);
-    long long* sh_fe = sh_fc + 32;
-    unsigned long long* sh_key = reinterpret_cast<unsigned long long*>(sh_fe + 32);
-    float* sh_ka = reinterpret_cast<float*>(sh_key + 32);
-    float* sh_va = sh_ka + 32;
-    int& s_dstar = *reinterpret_cast<int*>(sh_va + 32);
-    int& s_better = *(reinterpret_cast<int*>(sh_va + 32) + 1);
-    tc_dev_state* st = P.st;
-    const int D = P.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    long long fc = 0, fe = 0;
-    unsigned long long key = ~0ull;
-    float ka = 0.f, va = 0.f;
-    const bool part = tc_is_partition(P.problem), with_eq = tc_has_additive(P.problem);
-    for (int d = threadIdx.x; d < D; d += blockDim.x) {
-        // k_gsum summed gamma_d(i) over the vertices: each conflict twice
-        const int a = __ldcg(P.fcolor + d) / 2, b = __ldcg(P.feq + d);
-        P.fcolor[d] = a;
-        fc += a;
-        fe += b;
-        // the fitness of the problem: monochromatic or (partitioning) cut edges,
-        // plus f_eq for the ECP and the balanced partitioning, or f_mscp for
-        // the minimum sum colouring
-        const long long fobj = part ? P.n_edges - a : (long long)a;
-        const unsigned long long f = (unsigned long long)(fobj + (with_eq ? b : 0));
-        const unsigned long long kk = (f << 32) | (unsigned)d;
-        key = kk < key ? kk : key;
-    }
-    for (int b = threadIdx.x; b < P.n_pair_blocks; b += blockDim.x) {
-        ka += __ldcg(P.loss_part + 2 * b);
-        va += __ldcg(P.loss_part + 2 * b + 1);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fc += __shfl_xor_sync(0xffffffffu, fc, o);
-        fe += __shfl_xor_sync(0xffffffffu, fe, o);
-        const unsigned long long u = __shfl_xor_sync(0xffffffffu, key, o);
-        key = u < key ? u : key;
-        ka += __shfl_xor_sync(0xffffffffu, ka, o);
-        va += __shfl_xor_sync(0xffffffffu, va, o);
-    }
-    if (lane == 0) {
-        sh_fc[warp] = fc;
-        sh_fe[warp] = fe;
-        sh_key[warp] = key;
-        sh_ka[warp] = ka;
-        sh_va[warp] = va;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        fc = fe = 0;
-        key = ~0ull;
-        ka = va = 0.f;
-        for (int w = 0; w < nw; ++w) {
-            fc += sh_fc[w];
-            fe += sh_fe[w];
-            key = sh_key[w] < key ? sh_key[w] : key;
-            ka += sh_ka[w];
-            va += sh_va[w];
-        }
-        const int fmin = (int)(key >> 32), dstar = (int)(key & 0xffffffffu);
-        const long long t = st->t;
-        const double tt = (double)t;
-        const long long fsum = part ? (long long)D * P.n_edges - fc : fc;  // the fitness term of eq. 7
-        st->loss = (float)fsum + (float)((double)P.nu * tt) * (float)fe +
-                   (float)((double)P.lambda_ * tt) * ka - (float)((double)P.mu * tt) * va;
-        st->kappa = ka;
-        st->varpi = va;
-        st->fcolor_sum = fc;
-        st->last_fmin = fmin;
-        st->last_dstar = dstar;
-        if (P.trace && P.commit && t % P.trace_every == 0) {  // the iteration trace
-            tc_trace_entry e;
-            e.t = t;
-            e.f_min = fmin;
-            e.individual = dstar;
-            e.f_color = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
-            e.f_add = __ldcg(P.feq + dstar);
-            e.loss = st->loss;
-            e.kappa = ka;
-            e.varpi = va;
-            e.pad = 0;
-            P.trace[st->trace_n % P.trace_cap] = e;
-            st->trace_n += 1;
-        }
-        int better = 0;
-        if (P.commit) {
-            st->evaluated += 1;
-            if (st->best_f < 0 || fmin < st->best_f) {
-                better = 1;
-                st->best_f = fmin;
-                st->best_fcolor = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
-                st->best_feq = __ldcg(P.feq + dstar);
-                st->best_d = dstar;
-                st->best_t = t;
-            }
-            if (P.stop_on_legal && fmin == 0) st->stop = 1;
-        }
-        s_dstar = dstar;
-        s_better = better;
-    }
-    __syncthreads();
-    if (s_better) {
-        for (int i = threadIdx.x; i < P.n; i += blockDim.x)
-            P.best[i] = P.c[(size_t)s_dstar * P.n + i];
-        if (P.cm)  // multicolouring: the colour sets too
-            for (size_t e = threadIdx.x; e < (size_t)P.n * P.cmax; e += blockDim.x)
-                P.best_m[e] = P.cm[(size_t)s_dstar * P.n * P.cmax + e];
-    }
-    if (threadIdx.x == 0) st->done_gsum = 0u;
-}
 
 // ---------------------------------------------------------------------------
 // k_classes: one individual per block.  Class sizes, equity (eq. 3, eq. 14)
 // and a stable counting sort of the vertices by colour into `perm` with every
 // class padded to a multiple of 4 entries (padding = vertex n, a zero row of
-// the pair matrix).  Dynamic shared memory: the individual's colours, then
-// the per-warp colour counts of the sort.
+// the pair matrix), the class order of k_gsum's slot walk; in the dense forms
+// the individual's conflicts from the gamma matrix.  The last block reduces
+// the population (finalize_population).  Dynamic shared memory: the
+// individual's colours, then the per-warp colour counts of the sort.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
+__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks) {
     // Launched once k_pairs has passed its own wait, so the colours of the
     // previous update (and the stop flag) are final: the class lists need
     // nothing from k_pairs and are built while it runs.  The wait for k_pairs
@@ -477,14 +361,22 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     __shared__ int s_hist[TC_MAX_K];
     __shared__ int s_cur[TC_MAX_K];
     __shared__ int s_scan[64];
+    __shared__ int s_bk[64];
     __shared__ long long sh_ll[CLS_THREADS / 32];
+    __shared__ __align__(16) unsigned char s_fin[TC_FINALIZE_SCRATCH];  // the population reduction
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int n = P.n, k = P.k, d = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
     uint16_t* cs = reinterpret_cast<uint16_t*>(s_dyn);  // n colours
     int* wcnt = reinterpret_cast<int*>(s_dyn + ((n + 7) / 8) * 4);  // after the colours: nwp x k counts
+    // after the counts (masks = 1): per colour j a bitmask of its vertices, adj_words words
+    uint32_t* mk = reinterpret_cast<uint32_t*>(wcnt + nwp * k);
+    const int aw = P.adj_words;
+    const bool onehot = P.G16 == nullptr;  // the dense forms count conflicts from the gamma matrix
     const uint16_t* cd = P.c + (size_t)d * n;
     for (int j = threadIdx.x; j < k; j += blockDim.x) s_hist[j] = 0;
+    if (onehot && masks)
+        for (int e = threadIdx.x; e < k * aw; e += blockDim.x) mk[e] = 0u;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const uint16_t c = cd[i];
         cs[i] = c;
@@ -493,8 +385,80 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
         if (P.csr_walk) P.c_snap[(size_t)d * n + i] = c;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[cs[i]], 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        atomicAdd(&s_hist[cs[i]], 1);
+        if (onehot && masks) atomicOr(&mk[cs[i] * aw + (i >> 5)], 1u << (i & 31));
+    }
+    for (int b = threadIdx.x; b < 64; b += blockDim.x) s_bk[b] = 0;
     __syncthreads();
+    // Step 2 (eq. 1), one-hot form: the individual's monochromatic edges,
+    // counted from both ends as the popcount of each vertex's adjacency row
+    // masked by its class (a warp per vertex, a lane per word); needs nothing
+    // from k_pairs, so it runs beside it
+    long long conf2 = 0;
+    if (onehot && masks) {
+        // 16-byte quads of the adjacency rows (rows are padded to 16 bytes);
+        // eight independent loads per thread in flight
+        const int wq = aw >> 2;
+        const uint4* adj4 = reinterpret_cast<const uint4*>(P.adj);
+        auto quad_conf = [&](uint4 a, int i, int q) {
+            const uint4 m = *reinterpret_cast<const uint4*>(mk + cs[i] * aw + 4 * q);
+            return __popc(a.x & m.x) + __popc(a.y & m.y) + __popc(a.z & m.z) + __popc(a.w & m.w);
+        };
+        if (wq <= 32) {  // 32 / wq vertices per warp step, a lane per quad
+            const int vpw = 32 / wq, sub = lane / wq, q = lane - sub * wq;
+            const bool act = sub < vpw;
+            const int step = nwp * vpw;
+            for (int i0 = warp * vpw + sub; i0 < n; i0 += 8 * step) {
+                uint4 a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * step;
+                    a[u] = act && i < n ? __ldg(adj4 + (size_t)i * wq + q) : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * step;
+                    if (act && i < n) conf2 += quad_conf(a[u], i, q);
+                }
+            }
+        } else {  // long rows: a warp per vertex, eight quads per lane in flight
+            for (int i = warp; i < n; i += nwp)
+                for (int q0 = lane; q0 < wq; q0 += 8 * 32) {
+                    uint4 a[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int q = q0 + 32 * u;
+                        a[u] = q < wq ? __ldg(adj4 + (size_t)i * wq + q) : make_uint4(0u, 0u, 0u, 0u);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (q0 + 32 * u < wq) conf2 += quad_conf(a[u], i, q0 + 32 * u);
+                }
+        }
+    }
+    // the class order of k_gsum's slot walk: classes by decreasing padded
+    // length (in 4-entry chunks; 63 chunks or more share the first bucket);
+    // the order within a bucket does not change any sum
+    auto bucket = [&](int j) { return 63 - min((s_hist[j] + 3) >> 2, 63); };
+    for (int j = threadIdx.x; j < k; j += blockDim.x) atomicAdd(&s_bk[bucket(j)], 1);
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the 64 bucket counts, two per lane
+        const int a0 = s_bk[2 * lane], a1 = s_bk[2 * lane + 1];
+        int incl = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        s_bk[2 * lane] = incl - a0 - a1;
+        s_bk[2 * lane + 1] = incl - a1;
+    }
+    __syncthreads();
+    {
+        uint16_t* cod = P.cord + (size_t)d * P.cord_stride;
+        for (int j = threadIdx.x; j < k; j += blockDim.x) cod[atomicAdd(&s_bk[bucket(j)], 1)] = (uint16_t)j;
+    }
     // exclusive scan of the padded class sizes: contiguous chunks per thread,
     // warp shuffles, then the warp totals
     const int per = (k + CLS_THREADS - 1) / CLS_THREADS;
@@ -590,9 +554,49 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
         }
         __syncwarp();
     }
-    // conflicts (eq. 1) are counted by k_gsum, which walks these class lists
-    if (threadIdx.x == 0) P.fcolor[d] = 0;
-    pdl_wait();
+    if (onehot) {
+        if (!masks) {
+            // the masks did not fit: walk each vertex's class list (vertex
+            // order) for its later members, both ends counted as above
+            __syncthreads();  // the class lists are written
+            const uint32_t* pdl = P.perm + (size_t)d * P.perm_stride;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int c = cs[i], b0 = s_cur[c], h = s_hist[c];
+                const uint32_t* arow = P.adj + (size_t)i * aw;
+                for (int q = h - 1; q >= 0; --q) {
+                    const int m = (int)__ldcg(pdl + b0 + q);
+                    if (m <= i) break;
+                    conf2 += 2 * ((__ldg(arow + (m >> 5)) >> (m & 31)) & 1u);
+                }
+            }
+        }
+        conf2 = block_sum<long long>(conf2, sh_ll);
+        if (threadIdx.x == 0) P.fc_acc[d] = (int)(conf2 / 2);
+    }
+    pdl_wait();  // k_pairs (and in the dense forms the GEMMs) complete
+    if (P.G16) {
+        // dense forms: gamma_d(i) = Gamma_d[i][c_d(i)] (eq. 1; the footnote
+        // to eq. 13), each monochromatic edge counted from both ends
+        long long g = 0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            g += __ldcg(P.G16 + tc_gamma_index(d, i, cs[i], P.n_pad, k));
+        g = block_sum<long long>(g, sh_ll);
+        if (threadIdx.x == 0) P.fc_acc[d] = (int)(g / 2);
+    }
+    // completion ticket: the last block reduces the population (Algorithm 1's
+    // stop test, the best-so-far copy, the loss of eq. 7) before any weight
+    // of this iteration changes
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&P.st->done_classes, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_population(P, s_fin);
+    }
     pdl_trigger();
 }
 
@@ -814,6 +818,55 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Slot walk (the one-hot form's staged walk).  The two warps of a pair split
+// into 8 lane groups of 8 lanes; lane l8 of a group covers the tile rows
+// 4 l8 .. 4 l8 + 3, so one 16-byte load of panel row m brings
+// B[m][4 l8 .. 4 l8 + 3] = B[i][m] for its four rows (B is symmetric) and a
+// group's 8 loads of one vertex are one 128-byte line.  k_classes lists each
+// individual's classes by decreasing padded length (cord); in slot s the
+// group g (0..3) of warp h of the pair sums the class at position
+// 8 s + 4 h + g of that list, so the four classes a warp walks side by side
+// have nearly equal lengths.  The warp loops to the longest of the four; a
+// group whose class is shorter reads a chunk of padding vertices (the zero
+// row n of B) instead of branching, and all four groups store their class
+// sums together at the end of the slot.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
+                                          const float* xs, const uint32_t* zchunk, float nut, const float* panel,
+                                          int k, int h, int lane, float* gtile) {
+    const int grp = lane >> 3, l8 = lane & 7;
+    const float* col = panel + 4 * l8;
+    const int nslots = (k + 7) >> 3;
+    for (int s = 0; s < nslots; ++s) {
+        const int pos = 8 * s + 4 * h + grp;
+        const int j = pos < k ? (int)cord[pos] : -1;
+        const int p0 = j >= 0 ? of[j] : 0;
+        const int len = j >= 0 ? of[j + 1] - p0 : 0;
+        int m = max(len, __shfl_xor_sync(0xffffffffu, len, 8));
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+        for (int c = 0; c < m; c += 4) {
+            const uint32_t* src = c < len ? list + p0 + c : zchunk;
+            const uint4 v = *reinterpret_cast<const uint4*>(src);
+            const float4 b0 = *reinterpret_cast<const float4*>(col + v.x * 32);
+            const float4 b1 = *reinterpret_cast<const float4*>(col + v.y * 32);
+            const float4 b2 = *reinterpret_cast<const float4*>(col + v.z * 32);
+            const float4 b3 = *reinterpret_cast<const float4*>(col + v.w * 32);
+            acc.x += (b0.x + b1.x) + (b2.x + b3.x);
+            acc.y += (b0.y + b1.y) + (b2.y + b3.y);
+            acc.z += (b0.z + b1.z) + (b2.z + b3.z);
+            acc.w += (b0.w + b1.w) + (b2.w + b3.w);
+        }
+        if (j >= 0) {
+            const float ex = nut * xs[j];
+            __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8),
+                   make_float4(acc.x + ex, acc.y + ex, acc.z + ex, acc.w + ex));
+        }
+    }
+}
+
 // Sparse form of the same sums, used when B vanishes off the edges (mu = 0:
 // no bonus term, so B_im = 0 unless a_im = 1): vertex i walks its adjacency
 // list (CSR) and adds B_im into the colour of each neighbour, D 2|E|
@@ -894,7 +947,8 @@ constexpr int GSUM_MAX_WARPS = 30;  // the staged class walk: 15 warp pairs (nam
 // share it; warp h of the pair sums the colours [h kh, min(k, (h+1) kh)),
 // kh = ceil(k / 2).
 __host__ __device__ inline int gsum_stage_words(int perm_stride, int k) {
-    return perm_stride + ((k + 1 + 3) & ~3) + ((k + 3) & ~3);
+    // + the class order of the slot walk (k uint16) and its chunk of padding vertices
+    return perm_stride + ((k + 1 + 3) & ~3) + ((k + 3) & ~3) + (((k + 1) / 2 + 3) & ~3) + 4;
 }
 
 // Items (32-vertex tile T, individual d) run tile-major; each tile's D
@@ -922,6 +976,8 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         pdl_wait();
         return;
     }
+    // the grouped walk: staged lists, the B panel in shared memory, the one-hot form
+    constexpr bool GROUPED = STG && BTS && !DN && !CSR;
     extern __shared__ __align__(1024) float sm[];
     __shared__ __align__(8) uint64_t s_bbar;
     const int n = P.n, D = P.D, k = P.k;
@@ -934,6 +990,8 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                                                (size_t)unit * gsum_stage_words(P.perm_stride, k));  // STG only
     int* os = reinterpret_cast<int*>(ps + P.perm_stride);
     float* xs = reinterpret_cast<float*>(os + ((k + 1 + 3) & ~3));
+    uint16_t* cs = reinterpret_cast<uint16_t*>(xs + ((k + 3) & ~3));  // the slot walk's class order
+    uint32_t* zc = reinterpret_cast<uint32_t*>(cs) + (((k + 1) / 2 + 3) & ~3);  // 4 padding vertices
     unsigned bphase = 0;
     if (BTS && threadIdx.x == 0) {
         mbar_init(&s_bbar, 1);
@@ -962,6 +1020,12 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     };
     if (BTS && threadIdx.x == 0 && q < qend) load_panel((int)(q / D));
     pdl_wait();  // the class lists (and equity terms) from k_classes
+    // k_classes reduced this iteration's population: a legal individual stops
+    // Algorithm 1 before Step 3 (no gradient, no weight change)
+    if (P.commit && *reinterpret_cast<volatile int*>(&st->stop)) {
+        if (BTS && threadIdx.x == 0 && q < qend) mbar_wait_bounded(&s_bbar, 0u, &st->err);  // the panel in flight
+        return;
+    }
     bool first = true;
     while (q < qend) {
         const int T = (int)(q / D);
@@ -996,6 +1060,11 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 for (int l = t64; l < P.perm_stride / 4; l += 64) cp_async_16(smem_u32(ps) + 16u * l, src + l);
                 for (int j = t64; j <= k; j += 64) cp_async_4(smem_u32(os + j), of + j);
                 for (int j = t64; j < k; j += 64) cp_async_4(smem_u32(xs + j), Ed + j);
+                if (GROUPED) {
+                    const uint32_t* co = reinterpret_cast<const uint32_t*>(P.cord + (size_t)d * P.cord_stride);
+                    for (int j = t64; j < (k + 1) / 2; j += 64) cp_async_4(smem_u32(cs) + 4u * j, co + j);
+                    if (t64 < 4) zc[t64] = (uint32_t)n;
+                }
                 cp_async_wait_all();
                 pair_sync(unit);
             } else if (!CSR) {
@@ -1013,10 +1082,18 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
             const bool live = lane < rows;
             const int bstride = BTS ? 32 : P.ldb;
-            const bool counter = !CSR && h == (STG ? 1 : 0);  // the warp that counts the conflicts
+            // per-vertex conflicts gamma_d(i) (eq. 1) are counted here only for the
+            // debug output; f_color comes from k_pairs or the gamma matrix
+            const bool counter = P.dbg_gamma && !CSR && h == (STG ? 1 : 0);
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
-            if (CSR) {
+            if (GROUPED) {
+                slot_walk(ps, os, cs, xs, zc, nut, Bt, k, h, lane, P.Gbuf + ((size_t)d * nT + T) * k * 32);
+                if (counter) {
+                    conf = 0;
+                    if (live) conf = own_class_conflicts<true>(ps, os, ci, Bt + lane, 32, gs);
+                }
+            } else if (CSR) {
                 conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, gs, gstride, Bl,
                                       bstride, nut, k, Gw + lane, i0 + lane, live);
                 __syncwarp();
@@ -1052,29 +1129,9 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                     }
                 }
             }
-            if (conf >= 0) {  // warp-uniform
-                if (P.dbg_gamma && live) P.dbg_gamma[(size_t)d * n + i0 + lane] = conf;
-                int sum = conf;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                if (lane == 0 && sum) atomicAdd(P.fcolor + d, sum);  // twice the conflicts of the item's rows
-            }
+            if (conf >= 0 && P.dbg_gamma && live) P.dbg_gamma[(size_t)d * n + i0 + lane] = conf;
         }
         q = seg_end;
-    }
-    // completion ticket: the last block reduces the population (Algorithm 1's
-    // stop test, the best-so-far copy, the loss of eq. 7) before k_update
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned ticket = atomicAdd(&st->done_gsum, 1u);
-        s_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_population(P, sm);  // the panel and staging areas are free now
     }
 }
 
@@ -1401,10 +1458,13 @@ cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     if (P.cm) return tc_launch_classes_multi(P, s);  // multicolouring: a vertex in several classes
     const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // per-warp colour counts
-    const int smem = (int)(counts + 16ll * ((P.n + 7) / 8));  // + the individual's colours
+    const long long base = counts + 16ll * ((P.n + 7) / 8);    // + the individual's colours
+    const long long mask_bytes = 4ll * P.k * P.adj_words;       // + the class bitmasks (one-hot form)
+    const int masks = P.G16 == nullptr && mask_bytes <= 64 * 1024 && base + mask_bytes <= kSmemOptin ? 1 : 0;
+    const int smem = (int)(base + (masks ? mask_bytes : 0));
     cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return tc_launch_pdl(k_classes, dim3(P.D), dim3(CLS_THREADS), smem, s, P);
+    return tc_launch_pdl(k_classes, dim3(P.D), dim3(CLS_THREADS), smem, s, P, masks);
 }
 
 template <bool BTS, bool CSR, bool STG>
