@@ -22,7 +22,7 @@ struct tc_dev_state {
     int best_d;
     int last_fmin;
     int last_dstar;
-    unsigned int done_classes;  // completion tickets (last-block patterns): k_classes blocks
+    unsigned int done_gsum;     // completion tickets (last-block patterns): k_gsum blocks
     unsigned int done_update;
     float loss, kappa, varpi;
     int pad;
@@ -59,18 +59,18 @@ struct tc_kparams {
     const int* colidx;
     float* B;                 // (n + 1) x ldb pair coefficients of eq. 13 (symmetric); row n = 0
     int ldb;                  // row stride of B: n rounded up to a multiple of 4
-    uint32_t* perm;           // D x perm_stride vertices sorted by colour (stable), every
-                              // class padded to a multiple of 4 with vertex n
-    int perm_stride;          // n + 3k rounded up to a multiple of 8
-    int* off;                 // D x (k + 1) padded colour-class offsets into perm
-    uint16_t* cord;           // D x cord_stride classes by decreasing padded length (k_gsum's slot walk)
-    int cord_stride;          // k rounded up to a multiple of 8
-    float* E;                 // D x k gradient factor of the additive fitness term by s_{d,i,j}:
-                              // the equity sign (eq. 14), or the colour cost z_j (minimum sum colouring)
+    // Per individual d, one record of rec_stride words at rec + d rec_stride
+    // (tc_rec_* below): the vertices sorted by colour (stable; every class
+    // padded to a multiple of 4 with vertex n), the padded class offsets, the
+    // gradient factor of the additive fitness term by s_{d,i,j} (the equity
+    // sign of eq. 14, or the colour cost z_j of the minimum sum colouring),
+    // the classes by decreasing padded length (k_gsum's slot walk) and a chunk
+    // of 4 padding vertices.  One record is one contiguous 16-byte-aligned copy.
+    uint32_t* rec;
+    int rec_stride;           // words per record
+    int perm_stride;          // list entries per record: n + 3k (or the demands' sum + 3k) rounded to 8
     const int* zcost;         // k colour costs of the minimum sum colouring
-    int* fcolor;              // D conflicts (eq. 1), written by the population reduction
-    int* fc_acc;              // D conflicts being counted (k_pairs, or k_classes in the dense forms);
-                              // the population reduction moves them to fcolor and clears them
+    int* fcolor;              // D conflicts (eq. 1): k_gsum adds twice each, the reduction halves them
     int* feq;                 // D additive fitness: f_eq (eq. 3), or f_mscp (minimum sum colouring)
     float* loss_part;         // 2 x n_pair_blocks partial kappa / varpi
     int n_pair_blocks;
@@ -105,6 +105,26 @@ struct tc_kparams {
     float* Gbuf;              // D x nT x k x 32 grad_S L tiles of the split update
     int* dbg_gamma;           // optional D x n conflicting-neighbour counts
 };
+
+// Layout of an individual's record (words): the colour-sorted list
+// [perm_stride], the k + 1 class offsets, the k additive-term factors, the k
+// classes by decreasing padded length (uint16), 4 padding vertices.
+__host__ __device__ inline int tc_off_words(int k) { return (k + 1 + 3) & ~3; }
+__host__ __device__ inline int tc_e_words(int k) { return (k + 3) & ~3; }
+__host__ __device__ inline int tc_cord_words(int k) { return ((k + 1) / 2 + 3) & ~3; }
+__host__ __device__ inline int tc_rec_words(int perm_stride, int k) {
+    return perm_stride + tc_off_words(k) + tc_e_words(k) + tc_cord_words(k) + 4;
+}
+__host__ __device__ inline int* tc_rec_off(uint32_t* r, int perm_stride) { return reinterpret_cast<int*>(r + perm_stride); }
+__host__ __device__ inline float* tc_rec_E(uint32_t* r, int perm_stride, int k) {
+    return reinterpret_cast<float*>(r + perm_stride + tc_off_words(k));
+}
+__host__ __device__ inline uint16_t* tc_rec_cord(uint32_t* r, int perm_stride, int k) {
+    return reinterpret_cast<uint16_t*>(r + perm_stride + tc_off_words(k) + tc_e_words(k));
+}
+__host__ __device__ inline uint32_t* tc_rec_zchunk(uint32_t* r, int perm_stride, int k) {
+    return r + perm_stride + tc_off_words(k) + tc_e_words(k) + tc_cord_words(k);
+}
 
 // The weight tensor W (D x n x k) is kept on the device tile-transposed:
 // vertex tiles of 32 rows, each stored colour-major, so that a 32-row tile
@@ -152,9 +172,9 @@ cudaError_t tc_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 
-// Population reduction of one iteration, run by the last block of the
-// colour-class kernel once every individual's conflicts and additive term
-// are in: min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test),
+// Population reduction of one iteration, run by the last block of k_gsum
+// once every individual's conflicts (counted twice, over both ends of each
+// edge) and additive term are in: min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test),
 // the best-so-far copy, the loss of eq. 7, the stop flag and the trace.
 // `scratch`: TC_FINALIZE_SCRATCH bytes of shared memory, 8-byte aligned; any
 // block size up to 1024 threads (fixed-order sums: deterministic for a given
@@ -177,10 +197,8 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
     float ka = 0.f, va = 0.f;
     const bool part = tc_is_partition(P.problem), with_eq = tc_has_additive(P.problem);
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
-        // the monochromatic edges counted this iteration (k_pairs, or k_classes
-        // from the gamma matrix), cleared for the next iteration
-        const int a = __ldcg(P.fc_acc + d), b = __ldcg(P.feq + d);
-        P.fc_acc[d] = 0;
+        // k_gsum summed gamma_d(i) over the vertices: each conflict twice
+        const int a = __ldcg(P.fcolor + d) / 2, b = __ldcg(P.feq + d);
         P.fcolor[d] = a;
         fc += a;
         fe += b;
@@ -240,7 +258,7 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
             e.t = t;
             e.f_min = fmin;
             e.individual = dstar;
-            e.f_color = __ldcg(P.fcolor + dstar);  // written above (the block synced since)
+            e.f_color = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
             e.f_add = __ldcg(P.feq + dstar);
             e.loss = st->loss;
             e.kappa = ka;
@@ -255,7 +273,7 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
             if (st->best_f < 0 || fmin < st->best_f) {
                 better = 1;
                 st->best_f = fmin;
-                st->best_fcolor = __ldcg(P.fcolor + dstar);  // written above (the block synced since)
+                st->best_fcolor = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
                 st->best_feq = __ldcg(P.feq + dstar);
                 st->best_d = dstar;
                 st->best_t = t;
@@ -273,7 +291,7 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
             for (size_t e = threadIdx.x; e < (size_t)P.n * P.cmax; e += blockDim.x)
                 P.best_m[e] = P.cm[(size_t)s_dstar * P.n * P.cmax + e];
     }
-    if (threadIdx.x == 0) st->done_classes = 0u;
+    if (threadIdx.x == 0) st->done_gsum = 0u;
 }
 
 

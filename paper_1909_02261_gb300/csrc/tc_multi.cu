@@ -99,9 +99,10 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P, int 
     const int n = P.n, k = P.k, d = blockIdx.x, cmax = P.cmax;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = MC_THREADS / 32;
     const uint16_t* cmd = P.cm + (size_t)d * n * cmax;
+    uint32_t* rd = P.rec + (size_t)d * P.rec_stride;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         s_hist[j] = 0;
-        P.E[(size_t)d * k + j] = 0.0f;
+        tc_rec_E(rd, P.perm_stride, k)[j] = 0.0f;
     }
     extern __shared__ uint32_t mk[];  // masks: bit b of mk[j aw + w]: vertex 32 w + b has colour j
     const int aw = P.adj_words;
@@ -125,10 +126,11 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P, int 
         }
         s_off[k] = run;
         P.feq[d] = 0;
+        P.fcolor[d] = 0;  // k_gsum counts the conflicts over these class lists
     }
     __syncthreads();
-    int* od = P.off + (size_t)d * (k + 1);
-    uint32_t* pd = P.perm + (size_t)d * P.perm_stride;
+    int* od = tc_rec_off(rd, P.perm_stride);
+    uint32_t* pd = rd;
     for (int j = threadIdx.x; j <= k; j += blockDim.x) od[j] = s_off[j];
     // a warp per class, members in vertex order
     for (int j = warp; j < k; j += nwp) {
@@ -158,38 +160,6 @@ __global__ void __launch_bounds__(MC_THREADS) k_classes_multi(tc_kparams P, int 
             }
         }
         for (int q = pos + lane; q < s_off[j + 1]; q += 32) pd[q] = (uint32_t)n;  // padding entries
-    }
-    // f_color: the colours shared across edges, from the gamma matrix (each
-    // shared colour of an edge counted from both ends)
-    __shared__ long long s_g[MC_THREADS / 32];
-    long long g = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int c = P.dem[i];
-        for (int q = 0; q < c; ++q)
-            g += __ldcg(P.G16 + tc_gamma_index(d, i, cmd[(size_t)i * cmax + q], P.n_pad, k));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) s_g[warp] = g;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int w = 0; w < nwp; ++w) t += s_g[w];
-        P.fc_acc[d] = (int)(t / 2);
-    }
-    // completion ticket: the last block reduces the population before any
-    // weight of this iteration changes
-    __shared__ int s_last;
-    __shared__ __align__(16) unsigned char s_fin[TC_FINALIZE_SCRATCH];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&P.st->done_classes, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_population(P, s_fin);
     }
 }
 

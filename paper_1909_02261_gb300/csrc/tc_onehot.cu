@@ -343,12 +343,11 @@ __device__ T block_sum(T v, T* sh) {
 // k_classes: one individual per block.  Class sizes, equity (eq. 3, eq. 14)
 // and a stable counting sort of the vertices by colour into `perm` with every
 // class padded to a multiple of 4 entries (padding = vertex n, a zero row of
-// the pair matrix), the class order of k_gsum's slot walk; in the dense forms
-// the individual's conflicts from the gamma matrix.  The last block reduces
-// the population (finalize_population).  Dynamic shared memory: the
-// individual's colours, then the per-warp colour counts of the sort.
+// the pair matrix) and the class order of k_gsum's slot walk.  Dynamic
+// shared memory: the individual's colours, then the per-warp colour counts of
+// the sort.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks) {
+__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     // Launched once k_pairs has passed its own wait, so the colours of the
     // previous update (and the stop flag) are final: the class lists need
     // nothing from k_pairs and are built while it runs.  The wait for k_pairs
@@ -363,20 +362,13 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks
     __shared__ int s_scan[64];
     __shared__ int s_bk[64];
     __shared__ long long sh_ll[CLS_THREADS / 32];
-    __shared__ __align__(16) unsigned char s_fin[TC_FINALIZE_SCRATCH];  // the population reduction
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int n = P.n, k = P.k, d = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
     uint16_t* cs = reinterpret_cast<uint16_t*>(s_dyn);  // n colours
     int* wcnt = reinterpret_cast<int*>(s_dyn + ((n + 7) / 8) * 4);  // after the colours: nwp x k counts
-    // after the counts (masks = 1): per colour j a bitmask of its vertices, adj_words words
-    uint32_t* mk = reinterpret_cast<uint32_t*>(wcnt + nwp * k);
-    const int aw = P.adj_words;
-    const bool onehot = P.G16 == nullptr;  // the dense forms count conflicts from the gamma matrix
     const uint16_t* cd = P.c + (size_t)d * n;
     for (int j = threadIdx.x; j < k; j += blockDim.x) s_hist[j] = 0;
-    if (onehot && masks)
-        for (int e = threadIdx.x; e < k * aw; e += blockDim.x) mk[e] = 0u;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const uint16_t c = cd[i];
         cs[i] = c;
@@ -385,61 +377,12 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks
         if (P.csr_walk) P.c_snap[(size_t)d * n + i] = c;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        atomicAdd(&s_hist[cs[i]], 1);
-        if (onehot && masks) atomicOr(&mk[cs[i] * aw + (i >> 5)], 1u << (i & 31));
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[cs[i]], 1);
     for (int b = threadIdx.x; b < 64; b += blockDim.x) s_bk[b] = 0;
     __syncthreads();
-    // Step 2 (eq. 1), one-hot form: the individual's monochromatic edges,
-    // counted from both ends as the popcount of each vertex's adjacency row
-    // masked by its class (a warp per vertex, a lane per word); needs nothing
-    // from k_pairs, so it runs beside it
-    long long conf2 = 0;
-    if (onehot && masks) {
-        // 16-byte quads of the adjacency rows (rows are padded to 16 bytes);
-        // eight independent loads per thread in flight
-        const int wq = aw >> 2;
-        const uint4* adj4 = reinterpret_cast<const uint4*>(P.adj);
-        auto quad_conf = [&](uint4 a, int i, int q) {
-            const uint4 m = *reinterpret_cast<const uint4*>(mk + cs[i] * aw + 4 * q);
-            return __popc(a.x & m.x) + __popc(a.y & m.y) + __popc(a.z & m.z) + __popc(a.w & m.w);
-        };
-        if (wq <= 32) {  // 32 / wq vertices per warp step, a lane per quad
-            const int vpw = 32 / wq, sub = lane / wq, q = lane - sub * wq;
-            const bool act = sub < vpw;
-            const int step = nwp * vpw;
-            for (int i0 = warp * vpw + sub; i0 < n; i0 += 8 * step) {
-                uint4 a[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int i = i0 + u * step;
-                    a[u] = act && i < n ? __ldg(adj4 + (size_t)i * wq + q) : make_uint4(0u, 0u, 0u, 0u);
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int i = i0 + u * step;
-                    if (act && i < n) conf2 += quad_conf(a[u], i, q);
-                }
-            }
-        } else {  // long rows: a warp per vertex, eight quads per lane in flight
-            for (int i = warp; i < n; i += nwp)
-                for (int q0 = lane; q0 < wq; q0 += 8 * 32) {
-                    uint4 a[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int q = q0 + 32 * u;
-                        a[u] = q < wq ? __ldg(adj4 + (size_t)i * wq + q) : make_uint4(0u, 0u, 0u, 0u);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (q0 + 32 * u < wq) conf2 += quad_conf(a[u], i, q0 + 32 * u);
-                }
-        }
-    }
     // the class order of k_gsum's slot walk: classes by decreasing padded
-    // length (in 4-entry chunks; 63 chunks or more share the first bucket);
-    // the order within a bucket does not change any sum
+    // length (in 4-entry chunks; 63 chunks or more share the first bucket),
+    // by colour within a bucket (a stable, run-independent order)
     auto bucket = [&](int j) { return 63 - min((s_hist[j] + 3) >> 2, 63); };
     for (int j = threadIdx.x; j < k; j += blockDim.x) atomicAdd(&s_bk[bucket(j)], 1);
     __syncthreads();
@@ -455,9 +398,20 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks
         s_bk[2 * lane + 1] = incl - a1;
     }
     __syncthreads();
-    {
-        uint16_t* cod = P.cord + (size_t)d * P.cord_stride;
-        for (int j = threadIdx.x; j < k; j += blockDim.x) cod[atomicAdd(&s_bk[bucket(j)], 1)] = (uint16_t)j;
+    if (warp == 0) {  // stable scatter, 32 classes at a time (ranks among equal buckets by warp matching)
+        uint16_t* cod = tc_rec_cord(P.rec + (size_t)d * P.rec_stride, P.perm_stride, k);
+        for (int j0 = 0; j0 < k; j0 += 32) {
+            const int j = j0 + lane;
+            const unsigned valid = __ballot_sync(0xffffffffu, j < k);
+            if (j < k) {
+                const int b = bucket(j);
+                const unsigned peers = __match_any_sync(valid, b);
+                cod[s_bk[b] + __popc(peers & ((1u << lane) - 1u))] = (uint16_t)j;
+                __syncwarp(valid);
+                if ((__ffs(peers) - 1) == lane) s_bk[b] += __popc(peers);
+            }
+            __syncwarp();
+        }
     }
     // exclusive scan of the padded class sizes: contiguous chunks per thread,
     // warp shuffles, then the warp totals
@@ -484,8 +438,11 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks
     }
     __syncthreads();
     int run = (warp > 0 ? s_scan[32 + warp - 1] : 0) + incl - local;
-    int* od = P.off + (size_t)d * (k + 1);
-    uint32_t* pd = P.perm + (size_t)d * P.perm_stride;
+    uint32_t* rd = P.rec + (size_t)d * P.rec_stride;
+    int* od = tc_rec_off(rd, P.perm_stride);
+    uint32_t* pd = rd;
+    float* Ed = tc_rec_E(rd, P.perm_stride, k);
+    if (threadIdx.x < 4) tc_rec_zchunk(rd, P.perm_stride, k)[threadIdx.x] = (uint32_t)n;
     for (int j = j0; j < j1; ++j) {
         const int h = s_hist[j], ph = (h + 3) & ~3;
         od[j] = run;
@@ -505,10 +462,10 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks
         if (mscp) {
             const int z = __ldg(P.zcost + j);
             fe += (long long)h * z;
-            P.E[(size_t)d * k + j] = (float)z;
+            Ed[j] = (float)z;
         } else {
             fe += min(abs(h - c1), abs(h - c2));
-            P.E[(size_t)d * k + j] = h > c2 ? 1.0f : (h < c1 ? -1.0f : 0.0f);
+            Ed[j] = h > c2 ? 1.0f : (h < c1 ? -1.0f : 0.0f);
         }
     }
     fe = block_sum<long long>(fe, sh_ll);
@@ -554,49 +511,9 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P, int masks
         }
         __syncwarp();
     }
-    if (onehot) {
-        if (!masks) {
-            // the masks did not fit: walk each vertex's class list (vertex
-            // order) for its later members, both ends counted as above
-            __syncthreads();  // the class lists are written
-            const uint32_t* pdl = P.perm + (size_t)d * P.perm_stride;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int c = cs[i], b0 = s_cur[c], h = s_hist[c];
-                const uint32_t* arow = P.adj + (size_t)i * aw;
-                for (int q = h - 1; q >= 0; --q) {
-                    const int m = (int)__ldcg(pdl + b0 + q);
-                    if (m <= i) break;
-                    conf2 += 2 * ((__ldg(arow + (m >> 5)) >> (m & 31)) & 1u);
-                }
-            }
-        }
-        conf2 = block_sum<long long>(conf2, sh_ll);
-        if (threadIdx.x == 0) P.fc_acc[d] = (int)(conf2 / 2);
-    }
-    pdl_wait();  // k_pairs (and in the dense forms the GEMMs) complete
-    if (P.G16) {
-        // dense forms: gamma_d(i) = Gamma_d[i][c_d(i)] (eq. 1; the footnote
-        // to eq. 13), each monochromatic edge counted from both ends
-        long long g = 0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            g += __ldcg(P.G16 + tc_gamma_index(d, i, cs[i], P.n_pad, k));
-        g = block_sum<long long>(g, sh_ll);
-        if (threadIdx.x == 0) P.fc_acc[d] = (int)(g / 2);
-    }
-    // completion ticket: the last block reduces the population (Algorithm 1's
-    // stop test, the best-so-far copy, the loss of eq. 7) before any weight
-    // of this iteration changes
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&P.st->done_classes, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_population(P, s_fin);
-    }
+    // conflicts (eq. 1) are counted by k_gsum, which walks these class lists
+    if (threadIdx.x == 0) P.fcolor[d] = 0;
+    pdl_wait();
     pdl_trigger();
 }
 
@@ -640,19 +557,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps (up to `ns` nanoseconds) until it completes instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned parity, unsigned ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
 
-// Bounded wait: gives up after one second and reports TC_ERR_TIMEOUT.
+// Bounded wait: the thread sleeps in try_wait (20 us per attempt) until the
+// phase completes; gives up after one second and reports TC_ERR_TIMEOUT.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    for (unsigned it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 1023u) == 0 && global_ns() - t0 > 1000000000ull) break;
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (global_ns() - t0 > 1000000000ull) break;
     }
     atomicCAS(err, 0, TC_ERR_TIMEOUT);
     return false;
@@ -676,6 +607,13 @@ __device__ __forceinline__ void bulk_load_hint(void* smem_dst, const void* gsrc,
             "r"(smem_u32(smem_dst)),
         "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(smem_dst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void bulk_store_hint(void* gdst, const void* smem_src, unsigned bytes, uint64_t pol) {
@@ -832,11 +770,52 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
 // row n of B) instead of branching, and all four groups store their class
 // sums together at the end of the slot.
 // ---------------------------------------------------------------------------
+// One 4-entry chunk of a class walk, on 32-bit shared-memory addresses:
+// the chunk's vertex indices v0..v3 at `src`, and for each the 16 bytes
+// B[v][4 l8 .. 4 l8 + 3] at colb + 128 v (the lane's four rows of the
+// panel row v).  acc01 / acc23 hold the rows' running sums as packed pairs
+// (add.rn.f32x2, IEEE per element): acc += (b0 + b1) + (b2 + b3) per row.
+__device__ __forceinline__ void walk_chunk(uint32_t src, uint32_t colb, uint64_t& acc01, uint64_t& acc23) {
+    asm volatile(
+        "{\n"
+        " .reg .u32 v0, v1, v2, v3, a0, a1, a2, a3;\n"
+        " .reg .b64 p0, q0, p1, q1, p2, q2, p3, q3, s, t;\n"
+        " ld.shared.v4.u32 {v0, v1, v2, v3}, [%2];\n"
+        " mad.lo.u32 a0, v0, 128, %3;\n"
+        " mad.lo.u32 a1, v1, 128, %3;\n"
+        " mad.lo.u32 a2, v2, 128, %3;\n"
+        " mad.lo.u32 a3, v3, 128, %3;\n"
+        " ld.shared.v2.b64 {p0, q0}, [a0];\n"
+        " ld.shared.v2.b64 {p1, q1}, [a1];\n"
+        " ld.shared.v2.b64 {p2, q2}, [a2];\n"
+        " ld.shared.v2.b64 {p3, q3}, [a3];\n"
+        " add.rn.f32x2 s, p0, p1;\n"
+        " add.rn.f32x2 t, p2, p3;\n"
+        " add.rn.f32x2 s, s, t;\n"
+        " add.rn.f32x2 %0, %0, s;\n"
+        " add.rn.f32x2 s, q0, q1;\n"
+        " add.rn.f32x2 t, q2, q3;\n"
+        " add.rn.f32x2 s, s, t;\n"
+        " add.rn.f32x2 %1, %1, s;\n"
+        "}\n"
+        : "+l"(acc01), "+l"(acc23)
+        : "r"(src), "r"(colb)
+        : "memory");
+}
+
+// The four row sums of a class walk (the packed pairs) plus nu t E_dj.
+__device__ __forceinline__ float4 walk_result(uint64_t acc01, uint64_t acc23, float ex) {
+    float x, y, z, w;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(acc01));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(z), "=f"(w) : "l"(acc23));
+    return make_float4(x + ex, y + ex, z + ex, w + ex);
+}
+
 __device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
                                           const float* xs, const uint32_t* zchunk, float nut, const float* panel,
                                           int k, int h, int lane, float* gtile) {
     const int grp = lane >> 3, l8 = lane & 7;
-    const float* col = panel + 4 * l8;
+    const uint32_t colb = smem_u32(panel) + 16u * (uint32_t)l8, lists = smem_u32(list), zcs = smem_u32(zchunk);
     const int nslots = (k + 7) >> 3;
     for (int s = 0; s < nslots; ++s) {
         const int pos = 8 * s + 4 * h + grp;
@@ -845,25 +824,12 @@ __device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, c
         const int len = j >= 0 ? of[j + 1] - p0 : 0;
         int m = max(len, __shfl_xor_sync(0xffffffffu, len, 8));
         m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint64_t a01 = 0ull, a23 = 0ull;  // +0.0f pairs
+        const uint32_t srcb = lists + 4u * (uint32_t)p0;
 #pragma unroll 1
-        for (int c = 0; c < m; c += 4) {
-            const uint32_t* src = c < len ? list + p0 + c : zchunk;
-            const uint4 v = *reinterpret_cast<const uint4*>(src);
-            const float4 b0 = *reinterpret_cast<const float4*>(col + v.x * 32);
-            const float4 b1 = *reinterpret_cast<const float4*>(col + v.y * 32);
-            const float4 b2 = *reinterpret_cast<const float4*>(col + v.z * 32);
-            const float4 b3 = *reinterpret_cast<const float4*>(col + v.w * 32);
-            acc.x += (b0.x + b1.x) + (b2.x + b3.x);
-            acc.y += (b0.y + b1.y) + (b2.y + b3.y);
-            acc.z += (b0.z + b1.z) + (b2.z + b3.z);
-            acc.w += (b0.w + b1.w) + (b2.w + b3.w);
-        }
-        if (j >= 0) {
-            const float ex = nut * xs[j];
-            __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8),
-                   make_float4(acc.x + ex, acc.y + ex, acc.z + ex, acc.w + ex));
-        }
+        for (int c = 0; c < m; c += 4) walk_chunk(c < len ? srcb + 4u * (uint32_t)c : zcs, colb, a01, a23);
+        if (j >= 0)
+            __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8), walk_result(a01, a23, nut * xs[j]));
     }
 }
 
@@ -947,8 +913,7 @@ constexpr int GSUM_MAX_WARPS = 30;  // the staged class walk: 15 warp pairs (nam
 // share it; warp h of the pair sums the colours [h kh, min(k, (h+1) kh)),
 // kh = ceil(k / 2).
 __host__ __device__ inline int gsum_stage_words(int perm_stride, int k) {
-    // + the class order of the slot walk (k uint16) and its chunk of padding vertices
-    return perm_stride + ((k + 1 + 3) & ~3) + ((k + 3) & ~3) + (((k + 1) / 2 + 3) & ~3) + 4;
+    return tc_rec_words(perm_stride, k);  // one individual's record
 }
 
 // Items (32-vertex tile T, individual d) run tile-major; each tile's D
@@ -988,10 +953,11 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     const int unit = STG ? warp >> 1 : warp, nunits = STG ? nw >> 1 : nw, h = STG ? (warp & 1) : 0;
     uint32_t* ps = reinterpret_cast<uint32_t*>(sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) +
                                                (size_t)unit * gsum_stage_words(P.perm_stride, k));  // STG only
-    int* os = reinterpret_cast<int*>(ps + P.perm_stride);
-    float* xs = reinterpret_cast<float*>(os + ((k + 1 + 3) & ~3));
-    uint16_t* cs = reinterpret_cast<uint16_t*>(xs + ((k + 3) & ~3));  // the slot walk's class order
-    uint32_t* zc = reinterpret_cast<uint32_t*>(cs) + (((k + 1) / 2 + 3) & ~3);  // 4 padding vertices
+    // the staged record (STG): list, offsets, additive-term factors, class order, padding chunk
+    int* os = tc_rec_off(ps, P.perm_stride);
+    float* xs = tc_rec_E(ps, P.perm_stride, k);
+    uint16_t* cs = tc_rec_cord(ps, P.perm_stride, k);
+    uint32_t* zc = tc_rec_zchunk(ps, P.perm_stride, k);
     unsigned bphase = 0;
     if (BTS && threadIdx.x == 0) {
         mbar_init(&s_bbar, 1);
@@ -1020,12 +986,6 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     };
     if (BTS && threadIdx.x == 0 && q < qend) load_panel((int)(q / D));
     pdl_wait();  // the class lists (and equity terms) from k_classes
-    // k_classes reduced this iteration's population: a legal individual stops
-    // Algorithm 1 before Step 3 (no gradient, no weight change)
-    if (P.commit && *reinterpret_cast<volatile int*>(&st->stop)) {
-        if (BTS && threadIdx.x == 0 && q < qend) mbar_wait_bounded(&s_bbar, 0u, &st->err);  // the panel in flight
-        return;
-    }
     bool first = true;
     while (q < qend) {
         const int T = (int)(q / D);
@@ -1049,22 +1009,17 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         const int i0 = T * 32, rows = min(32, n - i0);
         for (long long qq = q + unit; qq < seg_end; qq += nunits) {
             const int d = (int)(qq - (long long)T * D);
-            const uint32_t* pm = P.perm + (size_t)d * P.perm_stride;
-            const int* of = P.off + (size_t)d * (k + 1);
-            const float* Ed = P.E + (size_t)d * k;
+            uint32_t* rd = P.rec + (size_t)d * P.rec_stride;
+            const uint32_t* pm = rd;
+            const int* of = tc_rec_off(rd, P.perm_stride);
+            const float* Ed = tc_rec_E(rd, P.perm_stride, k);
             if (STG) {
                 pair_sync(unit);  // the pair's reads of the previous item are done
                 // asynchronous copies (cp.async), all in flight at once
                 const uint4* src = reinterpret_cast<const uint4*>(pm);
                 const int t64 = h * 32 + lane;
-                for (int l = t64; l < P.perm_stride / 4; l += 64) cp_async_16(smem_u32(ps) + 16u * l, src + l);
-                for (int j = t64; j <= k; j += 64) cp_async_4(smem_u32(os + j), of + j);
-                for (int j = t64; j < k; j += 64) cp_async_4(smem_u32(xs + j), Ed + j);
-                if (GROUPED) {
-                    const uint32_t* co = reinterpret_cast<const uint32_t*>(P.cord + (size_t)d * P.cord_stride);
-                    for (int j = t64; j < (k + 1) / 2; j += 64) cp_async_4(smem_u32(cs) + 4u * j, co + j);
-                    if (t64 < 4) zc[t64] = (uint32_t)n;
-                }
+                // the whole record (a multiple of 16 bytes) in one pass
+                for (int l = t64; l < P.rec_stride / 4; l += 64) cp_async_16(smem_u32(ps) + 16u * l, src + l);
                 cp_async_wait_all();
                 pair_sync(unit);
             } else if (!CSR) {
@@ -1082,9 +1037,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             float* Gout = P.Gbuf + ((size_t)d * nT + T) * k * 32 + lane;
             const bool live = lane < rows;
             const int bstride = BTS ? 32 : P.ldb;
-            // per-vertex conflicts gamma_d(i) (eq. 1) are counted here only for the
-            // debug output; f_color comes from k_pairs or the gamma matrix
-            const bool counter = P.dbg_gamma && !CSR && h == (STG ? 1 : 0);
+            const bool counter = !CSR && h == (STG ? 1 : 0);  // the warp that counts the conflicts
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
             if (GROUPED) {
@@ -1129,9 +1082,29 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                     }
                 }
             }
-            if (conf >= 0 && P.dbg_gamma && live) P.dbg_gamma[(size_t)d * n + i0 + lane] = conf;
+            if (conf >= 0) {  // warp-uniform
+                if (P.dbg_gamma && live) P.dbg_gamma[(size_t)d * n + i0 + lane] = conf;
+                int sum = conf;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0 && sum) atomicAdd(P.fcolor + d, sum);  // twice the conflicts of the item's rows
+            }
         }
         q = seg_end;
+    }
+    // completion ticket: the last block reduces the population (Algorithm 1's
+    // stop test, the best-so-far copy, the loss of eq. 7) before k_update
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(&st->done_gsum, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_population(P, sm);  // the panel and staging areas are free now
     }
 }
 
@@ -1458,13 +1431,10 @@ cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
     if (P.cm) return tc_launch_classes_multi(P, s);  // multicolouring: a vertex in several classes
     const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // per-warp colour counts
-    const long long base = counts + 16ll * ((P.n + 7) / 8);    // + the individual's colours
-    const long long mask_bytes = 4ll * P.k * P.adj_words;       // + the class bitmasks (one-hot form)
-    const int masks = P.G16 == nullptr && mask_bytes <= 64 * 1024 && base + mask_bytes <= kSmemOptin ? 1 : 0;
-    const int smem = (int)(base + (masks ? mask_bytes : 0));
+    const int smem = (int)(counts + 16ll * ((P.n + 7) / 8));  // + the individual's colours
     cudaError_t e = cudaFuncSetAttribute(k_classes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return tc_launch_pdl(k_classes, dim3(P.D), dim3(CLS_THREADS), smem, s, P, masks);
+    return tc_launch_pdl(k_classes, dim3(P.D), dim3(CLS_THREADS), smem, s, P);
 }
 
 template <bool BTS, bool CSR, bool STG>

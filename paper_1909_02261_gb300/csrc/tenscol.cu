@@ -44,10 +44,7 @@ struct tc_ctx {
     uint16_t* d_cT = nullptr;
     float* d_B = nullptr;
     float* d_Gbuf = nullptr;  // grad_S L tiles between k_gsum and k_update
-    uint32_t* d_perm = nullptr;
-    int* d_off = nullptr;
-    uint16_t* d_cord = nullptr;  // classes by decreasing length (k_gsum's slot walk)
-    float* d_E = nullptr;
+    uint32_t* d_rec = nullptr;  // per-individual records: class lists, offsets, additive terms, class order
     int* d_z = nullptr;         // k colour costs (minimum sum colouring), z_j = j + 1 unless set
     // multicolouring (tc_set_demands; dense forms): demands, colour sets
     int cmax = 0;                // largest demand; 0: one colour per vertex
@@ -59,7 +56,6 @@ struct tc_ctx {
     tc_trace_entry* d_trace = nullptr;
     int trace_cap = 0, trace_every = 1;
     int* d_fcolor = nullptr;
-    int* d_fc_acc = nullptr;  // conflicts being counted (cleared by the population reduction)
     int* d_feq = nullptr;
     float* d_loss_part = nullptr;
     float* d_lut = nullptr;  // 4 x (D + 1): lutA, lutB, powA, powB
@@ -193,13 +189,9 @@ void free_population(tc_ctx* c) {
     dfree(c->d_cT);
     dfree(c->d_B);
     dfree(c->d_Gbuf);
-    dfree(c->d_perm);
-    dfree(c->d_off);
-    dfree(c->d_cord);
-    dfree(c->d_E);
+    dfree(c->d_rec);
     dfree(c->d_z);
     dfree(c->d_fcolor);
-    dfree(c->d_fc_acc);
     dfree(c->d_feq);
     dfree(c->d_loss_part);
     dfree(c->d_lut);
@@ -246,6 +238,9 @@ int perm_stride_for(int n, int k, int cmax, long long dem_sum) {
 }
 int mt_max_for(int D, int cmax) { return D * (cmax > 0 ? cmax : 1); }
 int perm_stride(const tc_ctx* c) { return perm_stride_for(c->n, c->k, c->cmax, c->dem_sum); }
+int rec_stride_for(int n, int k, int cmax, long long dem_sum) {
+    return tc_rec_words(perm_stride_for(n, k, cmax, dem_sum), k);
+}
 int mt_max(const tc_ctx* c) { return mt_max_for(c->D, c->cmax); }
 
 tc_kparams make_kparams(tc_ctx* c, int commit) {
@@ -280,15 +275,11 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.B = c->d_B;
     P.Gbuf = c->d_Gbuf;
     P.ldb = c->ldb;
-    P.perm = c->d_perm;
+    P.rec = c->d_rec;
     P.perm_stride = perm_stride(c);
-    P.off = c->d_off;
-    P.cord = c->d_cord;
-    P.cord_stride = (c->k + 7) & ~7;
-    P.E = c->d_E;
+    P.rec_stride = tc_rec_words(P.perm_stride, c->k);
     P.zcost = c->d_z;
     P.fcolor = c->d_fcolor;
-    P.fc_acc = c->d_fc_acc;
     P.feq = c->d_feq;
     P.loss_part = c->d_loss_part;
     P.n_pair_blocks = c->n_tiles;
@@ -1161,9 +1152,7 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     if ((rc = dalloc(&c->d_W, Wtiled)) || (rc = dalloc(&c->d_c, (size_t)D * n)) || (rc = dalloc(&c->d_csnap, (size_t)D * n)) ||
         (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
         (rc = dalloc(&c->d_Gbuf, (size_t)D * ((n + 31) / 32) * 32 * k)) ||
-        (rc = dalloc(&c->d_perm, (size_t)D * ((n + 3 * k + 7) & ~7))) || (rc = dalloc(&c->d_off, (size_t)D * (k + 1))) ||
-        (rc = dalloc(&c->d_cord, (size_t)D * ((k + 7) & ~7))) ||
-        (rc = dalloc(&c->d_E, (size_t)D * k)) || (rc = dalloc(&c->d_z, (size_t)k)) || (rc = dalloc(&c->d_fcolor, D)) || (rc = dalloc(&c->d_fc_acc, D)) ||
+        (rc = dalloc(&c->d_rec, (size_t)D * rec_stride_for(n, k, 0, 0))) || (rc = dalloc(&c->d_z, (size_t)k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
         (rc = dalloc(&c->d_lut, 4 * (size_t)(D + 1))) || (rc = dalloc(&c->d_st, 1)) ||
         (rc = dalloc(&c->d_best, n))) {
@@ -1191,7 +1180,6 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     if (e == cudaSuccess)  // row n of B is the zero row the padded classes point at
         e = cudaMemsetAsync(c->d_B, 0, sizeof(float) * (size_t)(n + 1) * ((n + 3) & ~3), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fcolor, 0, sizeof(int) * D, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fc_acc, 0, sizeof(int) * D, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_best, 0, sizeof(uint16_t) * n, c->stream);
     std::vector<int> zdef(k);
     for (int j = 0; j < k; ++j) zdef[j] = j + 1;  // colours numbered 1..k
@@ -1371,7 +1359,6 @@ static int set_state_common(tc_ctx* c, const float* W, const int64_t* t, cudaMem
         TC_CHECK(cudaMemcpyAsync(&c->d_st->t, &tv, sizeof(tv), cudaMemcpyHostToDevice, c->stream));
     }
     TC_CHECK(cudaMemsetAsync(&c->d_st->stop, 0, sizeof(int), c->stream));
-    TC_CHECK(cudaMemsetAsync(c->d_fc_acc, 0, sizeof(int) * c->D, c->stream));
     TC_CHECK(tc_launch_assign(make_kparams(c, 0), c->stream));
     c->launches += 1;
     TC_CHECK(rebuild_onehot(c));
@@ -1428,11 +1415,10 @@ int tc_evaluate(tc_ctx* c, int32_t* colors, int32_t* gamma_own, int32_t* f_color
     if (e == cudaSuccess) e = tc_launch_pairs(P, c->stream);
     if (e == cudaSuccess && dense && launch_dense_gemms(c, 1, c->stream)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = tc_launch_classes(P, c->stream);
-    // k_classes reduced the population (conflicts from k_pairs or the gamma
-    // matrix); k_gsum counts per-vertex conflicts only for gamma_own, and
-    // k_update copies grad_S L out (debug mode 1) when G is wanted
-    if (e == cudaSuccess && G) e = launch_grad_update(c, P, 1);
-    else if (e == cudaSuccess && gamma_own) e = tc_launch_gsum(P, c->tmB, c->num_sms, c->stream);
+    // k_gsum counts the conflicts and reduces the population; k_update only
+    // copies grad_S L out (debug mode 1) when G is wanted
+    if (e == cudaSuccess)
+        e = G ? launch_grad_update(c, P, 1) : tc_launch_gsum(P, c->tmB, c->num_sms, c->stream);
     c->launches += 2;
     std::vector<uint16_t> hc;
     tc_dev_state h;
@@ -1678,28 +1664,28 @@ int tc_set_demands(tc_ctx* c, const int32_t* demand, int n) {
     const int new_cmax = cmax > 1 ? cmax : 0;  // all demands 1: one colour per vertex
     const long long new_sum = cmax > 1 ? sum : 0;
     // new buffers first: a failed allocation leaves the context as it was
-    uint32_t* perm = nullptr;
+    uint32_t* rec = nullptr;
     float* lut = nullptr;
     int* dem = nullptr;
     uint16_t *cm = nullptr, *best_m = nullptr;
     int rc;
-    if ((rc = dalloc(&perm, (size_t)c->D * perm_stride_for(c->n, c->k, new_cmax, new_sum))) ||
+    if ((rc = dalloc(&rec, (size_t)c->D * rec_stride_for(c->n, c->k, new_cmax, new_sum))) ||
         (rc = dalloc(&lut, 4 * (size_t)(mt_max_for(c->D, new_cmax) + 1))) ||
         (new_cmax > 0 && ((rc = dalloc(&dem, (size_t)n)) || (rc = dalloc(&cm, (size_t)c->D * n * new_cmax)) ||
                           (rc = dalloc(&best_m, (size_t)n * new_cmax))))) {
-        dfree(perm);
+        dfree(rec);
         dfree(lut);
         dfree(dem);
         dfree(cm);
         dfree(best_m);
         return rc;
     }
-    dfree(c->d_perm);
+    dfree(c->d_rec);
     dfree(c->d_lut);
     dfree(c->d_dem);
     dfree(c->d_cm);
     dfree(c->d_best_m);
-    c->d_perm = perm;
+    c->d_rec = rec;
     c->d_lut = lut;
     c->d_dem = dem;
     c->d_cm = cm;
