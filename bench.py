@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-baseline-iters", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations' lines")
     ap.add_argument("--dense-plan", default=None,
                     help="pin the FP8 form's GEMM plan after tuning (reproducible profiles): seven integers "
                          "gamma_rows,gamma_cols,gamma_cluster,mtilde_rows,mtilde_cols,mtilde_cluster,mtilde_splits "
@@ -229,6 +230,142 @@ def run_reference(args):
     }), flush=True)
 
 
+CONFIG_WORKLOADS = (
+    # name, parameters (Table 2 and Section 5.2), timed steps: the workload of
+    # each other configuration, benchmarked on its own graph
+    ("gnp125_k18_D20", {}, 2000),
+    ("ecp_gnp1000p01_k25_D128", {"problem": 1, "mu": 0.0, "nu": 1e-5}, 500),
+    ("ecp_gnp1000p09_k230_D128", {"problem": 1, "mu": 0.0, "nu": 1e-5, "alpha": 1.5}, 500),
+)
+
+
+def stage_roofline(n, k, D, stage_ms, peaks):
+    """The gradient + update stage (k_gsum + k_update) against HBM: the
+    algorithmic bytes of one launch of the stage over its event-timed
+    duration."""
+    alg = algorithmic_update_bytes(n, k, D)
+    ach = alg / (stage_ms * 1e-3) / 1e9
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "kernel": "k_gsum+k_update", "algorithmic_bytes_per_launch": alg, "avg_launch_ms": stage_ms,
+            "peak_source": "measured" if peaks else "fallback"}
+
+
+def bench_configs(T, torch, dev, flush, peaks, with_oracle):
+    """The other configurations of the path on their own graphs, each timed as
+    the headline (CUDA events on the library's stream, L2 flushed between
+    steps, stop_on_legal off) with a per-kernel pass and the roofline of its
+    gradient + update stage; the batched workload as one CUDA-graph launch
+    of all instances per chunk of iterations."""
+    from paper_1909_02261_gb300 import inputs
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    for name, kw, steps in CONFIG_WORKLOADS:
+        w = inputs.WORKLOADS[name]
+        rp, ci, _ = inputs.workload_graph(name)
+        n, k, D = w["n"], w["k"], w["D"]
+        p = T.params(int(kw.get("problem", 0)), stop_on_legal=0,
+                     **{a: v for a, v in kw.items() if a != "problem"})
+        with T.TensCol(0) as ctx:
+            ctx.tc_init_graph(n, rp, ci)
+            ctx.tc_init_population(w["w_seed"], D, k, p)
+            ctx.tc_set_stream(stream.cuda_stream)
+
+            def timed(nsteps, kernel_timing):
+                with torch.cuda.stream(stream):
+                    for _ in range(5):
+                        ctx.tc_step_async(1)
+                        flush.zero_()
+                    stream.synchronize()
+                    ctx.tc_set_timing(kernel_timing)
+                    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                           for _ in range(nsteps)]
+                    for a, b in evs:
+                        a.record(stream)
+                        ctx.tc_step_async(1)
+                        b.record(stream)
+                        flush.zero_()
+                    stream.synchronize()
+                    kms, kcnt = ctx.tc_kernel_times()
+                    ctx.tc_set_timing(False)
+                return float(sum(a.elapsed_time(b) for a, b in evs)), kms, kcnt
+
+            ms, _, _ = timed(steps, False)
+            _, kms, kcnt = timed(min(steps, 200), True)
+            kus = {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * kms[q] / max(1, kcnt[q])
+                   for q in range(len(kms)) if kcnt[q] > 0}
+            stage_ms = (kms[T.TC_KID_GSUM] + kms[T.TC_KID_UPDATE]) / max(1, kcnt[T.TC_KID_UPDATE])
+            rec = {"value": D * steps / (ms / 1e3), "unit": "individual-steps/s", "ms_per_step": ms / steps,
+                   "steps": steps, "graph": f"G({n},{w['p']}) seed {w['graph_seed']}", "n": n, "k": k, "D": D,
+                   "edges": int(len(ci) // 2), "kernels_us": kus,
+                   "roofline": stage_roofline(n, k, D, stage_ms, peaks)}
+            if name.startswith("ecp_gnp1000p01"):
+                # the adjacency-list walk of the sparse ECP: D 2|E| additions
+                adds = float(D) * len(ci)
+                rec["gsum_adjacency_walk"] = {"work_per_launch": adds, "unit": "Gadd/s",
+                                              "achieved": adds / (kus["k_gsum"] * 1e-6) / 1e9}
+            out[name] = rec
+        if name == "gnp125_k18_D20" and with_oracle:
+            # the oracle over the configuration's full 2000 iterations (one core)
+            from oracle import oracle as O
+            W0 = inputs.init_weights(D, n, k, 0.01, seed=w["w_seed"])
+            po = O.make_params(rho=100.0)
+            t0 = time.perf_counter()
+            r = O.run(rp, ci, W0, po, 0, steps, stop_on_legal=False)
+            dt = time.perf_counter() - t0
+            out[name]["cpu_baseline"] = {"value": D * r["iters"] / dt, "unit": "individual-steps/s", "cores": 1,
+                                         "kind": "oracle",
+                                         "sample": f"all {r['iters']} oracle iterations of {name} ({dt:.1f} s)"}
+    # the batched workload: G(4000, 0.5) k = 290 D = 100 and eight uneven
+    # instances, one graph launch per chunk of iterations (host wall clock
+    # around the synchronising tc_batch_step; the ~0.6 GB working set is
+    # larger than L2); then each instance alone with per-kernel events
+    insts = inputs.batched_instances()
+    ctxs = []
+    try:
+        for q, w in enumerate(insts):
+            rp, ci = inputs.gnp(w["n"], w["p"], w["graph_seed"])
+            c = T.TensCol(0)
+            c.tc_init_graph(w["n"], rp, ci)
+            c.tc_init_population(w["w_seed"], w["D"], w["k"], T.params(T.TC_KCOL, stop_on_legal=0))
+            ctxs.append((c, w))
+        with T.TensColBatch(0) as b:
+            for c, _ in ctxs:
+                b.add(c)
+            chunk, iters = 10, 60
+            b.step(2 * chunk, chunk)  # capture + warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.step(iters, chunk)
+            dt = time.perf_counter() - t0
+        total_ind = sum(w["D"] for _, w in ctxs)
+        alg = sum(algorithmic_update_bytes(w["n"], w["k"], w["D"]) for _, w in ctxs)
+        per = []
+        stage_total = 0.0
+        for c, w in ctxs:
+            c.tc_set_timing(True)
+            c.tc_step(5)
+            kms, kcnt = c.tc_kernel_times()
+            c.tc_set_timing(False)
+            kus = {T.KERNEL_NAMES.get(q, f"kid{q}"): 1e3 * kms[q] / max(1, kcnt[q])
+                   for q in range(len(kms)) if kcnt[q] > 0}
+            stage_total += (kms[T.TC_KID_GSUM] + kms[T.TC_KID_UPDATE]) / max(1, kcnt[T.TC_KID_UPDATE])
+            per.append({"n": w["n"], "p": w["p"], "k": w["k"], "D": w["D"], "kernels_us": kus})
+        ms_step = 1e3 * dt / iters
+        out["batched_9"] = {"value": total_ind * iters / dt, "unit": "individual-steps/s", "ms_per_step": ms_step,
+                            "steps": iters, "graph_chunk": chunk, "instances": per,
+                            "roofline": dict(stage_roofline(1, 1, 1, ms_step, peaks), algorithmic_bytes_per_launch=alg,
+                                             achieved=alg / (ms_step * 1e-3) / 1e9,
+                                             frac=alg / (ms_step * 1e-3) / 1e9 / (peaks["hbm_gbs"] if peaks else 6800.0),
+                                             kernel="whole batched step (all instances)",
+                                             avg_launch_ms=ms_step),
+                            "sum_of_instance_stage_ms": stage_total}
+    finally:
+        for c, _ in ctxs:
+            c.close()
+    return out
+
+
 def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1 or args.gpus != 1:
@@ -400,6 +537,10 @@ def run_ours(args):
                     ctx.tc_set_demands(np.ones(n, np.int32))
         ctx.tc_set_params(p)
 
+    configs = None
+    if not args.no_configs:
+        configs = bench_configs(T, torch, dev, flush, measured_peaks(), not args.no_cpu_baseline)
+
     # roofline of the dominant stage: the gradient + update stage (k_update,
     # preceded by k_gsum when the gradient tiles are computed separately)
     kid = int(np.argmax(kms))
@@ -457,6 +598,7 @@ def run_ours(args):
         "roofline_gsum": gsum_roof,
         "forms": forms,
         "variants": variants,
+        "configs": configs,
         "kernels": kernels,
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -251,6 +251,22 @@ int tc_relaxed_dev(tc_ctx *ctx, const float *W_dev, float tau, int64_t t, float 
 int tc_pair_terms_noalloc(int n, int D, const uint16_t *colors_dev, const uint8_t *adj_dev, float alpha,
                           float beta, int bonus_diag, float *out_dev, void *stream);
 
+/* Limit of every bounded device wait of the context's one-hot kernels (a
+ * TMA or record copy that never lands, an arrival that never comes), in
+ * nanoseconds; 0 restores the default of one second.  A wait that runs out
+ * records TC_ERR_TIMEOUT, which the next tc_step / tc_evaluate returns; the
+ * kernel returns without touching memory outside its buffers, and the
+ * context stays usable after tc_init_population.  Fault injection for tests
+ * (environment, host side): TC_FAULT=alloc | copy | launch makes the next
+ * allocation, host-device copy or iteration launch fail with
+ * TC_ERR_INJECTED; TC_FAULT=wait makes k_gsum wait for an arrival that never
+ * comes (the limit then decides when it gives up); with the device index
+ * checks of libtenscol_bounds.so (a build with TC_BOUNDS=1), TC_FAULT=index
+ * plants a vertex index past n in the first individual's class list, which
+ * the checks report as TC_ERR_DEVICE_BOUNDS.  TC_ERR_ARG for a NULL context
+ * or ns outside [0, 6e10]. */
+int tc_set_wait_limit(tc_ctx *ctx, int64_t ns);
+
 /* Number of device kernel launches issued by this context since creation
  * (for launch accounting in benchmarks). */
 int tc_launch_count(tc_ctx *ctx, int64_t *count);

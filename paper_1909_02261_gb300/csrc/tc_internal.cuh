@@ -104,6 +104,12 @@ struct tc_kparams {
     float* dbg_G;             // optional D x n x k grad_S L output
     float* Gbuf;              // D x nT x k x 32 grad_S L tiles of the split update
     int* dbg_gamma;           // optional D x n conflicting-neighbour counts
+    // failure handling: the limit of every bounded device wait (ns), and the
+    // host-side fault injections that reach the device (TC_FAULT=wait: k_gsum
+    // waits for an arrival that never comes; TC_FAULT=index, TC_BOUNDS builds
+    // only: k_classes plants a vertex index past n that the checks must catch)
+    unsigned long long wait_ns;
+    int dbg_withhold, dbg_plant;
 };
 
 // Layout of an individual's record (words): the colour-sorted list

@@ -27,6 +27,10 @@
 
 #include "tc_internal.cuh"
 
+#ifndef TC_BOUNDS
+#define TC_BOUNDS 0  // 1: device-side index checks of the class walk (libtenscol_bounds.so)
+#endif
+
 namespace {
 
 constexpr int PT = 32;              // pair tile edge
@@ -513,6 +517,10 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     }
     // conflicts (eq. 1) are counted by k_gsum, which walks these class lists
     if (threadIdx.x == 0) P.fcolor[d] = 0;
+#if TC_BOUNDS
+    __syncthreads();  // the sort's entries are written
+    if (P.dbg_plant && d == 0 && threadIdx.x == 0) pd[0] = (uint32_t)(n + 1);  // TC_FAULT=index
+#endif
     pdl_wait();
     pdl_trigger();
 }
@@ -576,14 +584,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait: the thread sleeps in try_wait (20 us per attempt) until the
-// phase completes; gives up after one second and reports TC_ERR_TIMEOUT.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+// Bounded wait: the thread sleeps in try_wait (up to 20 us per attempt) until
+// the phase completes; gives up after `limit_ns` (the context's wait limit,
+// one second by default) and reports TC_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err,
+                                                  unsigned long long limit_ns = 1000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
+    const unsigned hint = limit_ns < 20000ull ? (unsigned)limit_ns : 20000u;
     for (;;) {
-        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-        if (global_ns() - t0 > 1000000000ull) break;
+        if (mbar_try_wait_sleep(bar, parity, hint)) return true;
+        if (global_ns() - t0 > limit_ns) break;
     }
     atomicCAS(err, 0, TC_ERR_TIMEOUT);
     return false;
@@ -811,23 +822,48 @@ __device__ __forceinline__ float4 walk_result(uint64_t acc01, uint64_t acc23, fl
     return make_float4(x + ex, y + ex, z + ex, w + ex);
 }
 
+// TC_BOUNDS builds check the record the walk reads (class order, offsets,
+// vertex indices <= n) and replace what is out of range, recording
+// TC_ERR_DEVICE_BOUNDS in *err instead of reading outside the record or panel.
 __device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
                                           const float* xs, const uint32_t* zchunk, float nut, const float* panel,
-                                          int k, int h, int lane, float* gtile) {
+                                          int k, int h, int lane, float* gtile, int nmax, int plen, int* err) {
     const int grp = lane >> 3, l8 = lane & 7;
     const uint32_t colb = smem_u32(panel) + 16u * (uint32_t)l8, lists = smem_u32(list), zcs = smem_u32(zchunk);
     const int nslots = (k + 7) >> 3;
     for (int s = 0; s < nslots; ++s) {
         const int pos = 8 * s + 4 * h + grp;
-        const int j = pos < k ? (int)cord[pos] : -1;
-        const int p0 = j >= 0 ? of[j] : 0;
-        const int len = j >= 0 ? of[j + 1] - p0 : 0;
+        int j = pos < k ? (int)cord[pos] : -1;
+        int p0 = j >= 0 ? of[j] : 0;
+        int len = j >= 0 ? of[j + 1] - p0 : 0;
+#if TC_BOUNDS
+        if (j >= k || p0 < 0 || len < 0 || p0 + len > plen || (len & 3)) {
+            atomicCAS(err, 0, TC_ERR_DEVICE_BOUNDS);
+            j = -1;
+            p0 = 0;
+            len = 0;
+        }
+#else
+        (void)nmax;
+        (void)plen;
+        (void)err;
+#endif
         int m = max(len, __shfl_xor_sync(0xffffffffu, len, 8));
         m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
         uint64_t a01 = 0ull, a23 = 0ull;  // +0.0f pairs
         const uint32_t srcb = lists + 4u * (uint32_t)p0;
 #pragma unroll 1
-        for (int c = 0; c < m; c += 4) walk_chunk(c < len ? srcb + 4u * (uint32_t)c : zcs, colb, a01, a23);
+        for (int c = 0; c < m; c += 4) {
+#if TC_BOUNDS
+            // the chunk's vertex indices must name a panel row (0 .. n)
+            const uint4 v = *reinterpret_cast<const uint4*>(c < len ? list + p0 + c : zchunk);
+            if (v.x > (uint32_t)nmax || v.y > (uint32_t)nmax || v.z > (uint32_t)nmax || v.w > (uint32_t)nmax) {
+                atomicCAS(err, 0, TC_ERR_DEVICE_BOUNDS);
+                continue;
+            }
+#endif
+            walk_chunk(c < len ? srcb + 4u * (uint32_t)c : zcs, colb, a01, a23);
+        }
         if (j >= 0)
             __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8), walk_result(a01, a23, nut * xs[j]));
     }
@@ -930,7 +966,9 @@ __host__ __device__ inline long long gsum_chunk_item(long long c, int cpt, int D
 // may be present; without it their code is compiled out of the one-hot walk.
 template <bool BTS, bool CSR, bool STG, bool DN>
 __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
-    k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB) {
+    k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int dbuf) {
+    // dbuf (STG): two record buffers per warp pair, the next item's record
+    // arriving by one bulk copy while the pair walks the current one
     pdl_trigger();
     // k_classes lets this kernel start only after its own predecessors (k_pairs
     // and, in the dense forms, the GEMMs) are complete: the stop flag of the
@@ -945,22 +983,34 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     constexpr bool GROUPED = STG && BTS && !DN && !CSR;
     extern __shared__ __align__(1024) float sm[];
     __shared__ __align__(8) uint64_t s_bbar;
+    __shared__ __align__(8) uint64_t s_rbar[GSUM_MAX_WARPS / 2][2];  // dbuf: the record buffers' barriers
+    __shared__ __align__(8) uint64_t s_never;  // TC_FAULT=wait: a barrier nothing arrives at
     const int n = P.n, D = P.D, k = P.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
     float* Bt = sm;
     float* Gw = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * 32 * k;  // CSR only
     const int unit = STG ? warp >> 1 : warp, nunits = STG ? nw >> 1 : nw, h = STG ? (warp & 1) : 0;
-    uint32_t* ps = reinterpret_cast<uint32_t*>(sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) +
-                                               (size_t)unit * gsum_stage_words(P.perm_stride, k));  // STG only
-    // the staged record (STG): list, offsets, additive-term factors, class order, padding chunk
-    int* os = tc_rec_off(ps, P.perm_stride);
-    float* xs = tc_rec_E(ps, P.perm_stride, k);
-    uint16_t* cs = tc_rec_cord(ps, P.perm_stride, k);
-    uint32_t* zc = tc_rec_zchunk(ps, P.perm_stride, k);
+    const int sw = gsum_stage_words(P.perm_stride, k);
+    uint32_t* const psb = reinterpret_cast<uint32_t*>(sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0)) +
+                          (size_t)unit * (dbuf ? 2 : 1) * sw;  // STG only
+    const unsigned rec_bytes = 4u * (unsigned)P.rec_stride;
     unsigned bphase = 0;
-    if (BTS && threadIdx.x == 0) {
-        mbar_init(&s_bbar, 1);
+    if (P.dbg_withhold && threadIdx.x == 0) {
+        // injected failure: a device wait whose arrival is withheld, before
+        // any copy is in flight; it runs out after the context's wait limit
+        // and records TC_ERR_TIMEOUT, and the kernel then goes on as usual
+        mbar_init(&s_never, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait_bounded(&s_never, 0u, &st->err, P.wait_ns);
+    }
+    if (threadIdx.x == 0 && (BTS || dbuf)) {
+        if (BTS) mbar_init(&s_bbar, 1);
+        if (dbuf)
+            for (int u = 0; u < nunits; ++u) {
+                mbar_init(&s_rbar[u][0], 1);
+                mbar_init(&s_rbar[u][1], 1);
+            }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -985,7 +1035,30 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 : "memory");
     };
     if (BTS && threadIdx.x == 0 && q < qend) load_panel((int)(q / D));
+    // this pair's item after qq (tile T), across tile segments; qend: none
+    auto unit_next = [&](long long qq, int T) -> long long {
+        long long a = (long long)(T + 1) * D;  // the next segment's start
+        if (qq + nunits < min(qend, a)) return qq + nunits;
+        while (a < qend) {
+            const long long se = min(qend, a + D);
+            if (a + unit < se) return a + unit;
+            a = se;
+        }
+        return qend;
+    };
+    const bool leader = STG && h == 0 && lane == 0;
     pdl_wait();  // the class lists (and equity terms) from k_classes
+    if (STG && dbuf && leader && q < qend) {  // the pair's first record
+        long long q1 = q + unit;
+        const int T0 = (int)(q / D);
+        if (q1 >= min(qend, (long long)(T0 + 1) * D)) q1 = unit_next(q1 - nunits, T0);
+        if (q1 < qend) {
+            const int d1 = (int)(q1 - (q1 / D) * D);
+            mbar_expect_tx(&s_rbar[unit][0], rec_bytes);
+            bulk_load(psb, P.rec + (size_t)d1 * P.rec_stride, rec_bytes, &s_rbar[unit][0]);
+        }
+    }
+    int it = 0;  // items this pair has started (dbuf: buffer it & 1, phase (it >> 1) & 1)
     bool first = true;
     while (q < qend) {
         const int T = (int)(q / D);
@@ -1013,7 +1086,28 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const uint32_t* pm = rd;
             const int* of = tc_rec_off(rd, P.perm_stride);
             const float* Ed = tc_rec_E(rd, P.perm_stride, k);
-            if (STG) {
+            // the staged record (STG): list, offsets, additive-term factors,
+            // class order, padding chunk
+            uint32_t* ps = psb + (dbuf ? (size_t)(it & 1) * sw : 0);
+            int* os = tc_rec_off(ps, P.perm_stride);
+            float* xs = tc_rec_E(ps, P.perm_stride, k);
+            uint16_t* cs = tc_rec_cord(ps, P.perm_stride, k);
+            uint32_t* zc = tc_rec_zchunk(ps, P.perm_stride, k);
+            if (STG && dbuf) {
+                pair_sync(unit);  // the pair's reads of the previous item (the other buffer) are done
+                if (leader) {
+                    const long long nx = unit_next(qq, T);
+                    if (nx < qend) {
+                        const int dn = (int)(nx - (nx / D) * D);
+                        uint64_t* bar = &s_rbar[unit][(it + 1) & 1];
+                        fence_proxy_async();
+                        mbar_expect_tx(bar, rec_bytes);
+                        bulk_load(psb + (size_t)((it + 1) & 1) * sw, P.rec + (size_t)dn * P.rec_stride, rec_bytes,
+                                  bar);
+                    }
+                }
+                mbar_wait_bounded(&s_rbar[unit][it & 1], (unsigned)(it >> 1) & 1u, &st->err, P.wait_ns);
+            } else if (STG) {
                 pair_sync(unit);  // the pair's reads of the previous item are done
                 // asynchronous copies (cp.async), all in flight at once
                 const uint4* src = reinterpret_cast<const uint4*>(pm);
@@ -1026,7 +1120,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
             }
             if (BTS && panel_pending) {
-                mbar_wait_bounded(&s_bbar, seg_phase, &st->err);
+                mbar_wait_bounded(&s_bbar, seg_phase, &st->err, P.wait_ns);
                 panel_pending = false;
             }
             const float* Bl = BTS ? (Bt + lane) : (P.B + min(i0 + lane, n - 1));
@@ -1041,7 +1135,8 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
             if (GROUPED) {
-                slot_walk(ps, os, cs, xs, zc, nut, Bt, k, h, lane, P.Gbuf + ((size_t)d * nT + T) * k * 32);
+                slot_walk(ps, os, cs, xs, zc, nut, Bt, k, h, lane, P.Gbuf + ((size_t)d * nT + T) * k * 32, n,
+                          P.perm_stride, &st->err);
                 if (counter) {
                     conf = 0;
                     if (live) conf = own_class_conflicts<true>(ps, os, ci, Bt + lane, 32, gs);
@@ -1089,6 +1184,7 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
                 if (lane == 0 && sum) atomicAdd(P.fcolor + d, sum);  // twice the conflicts of the item's rows
             }
+            ++it;
         }
         q = seg_end;
     }
@@ -1308,7 +1404,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
         if (warp == 0 && lane == 0) {  // no copy may still be landing when the block exits
             for (int r = 0; r < pre; ++r)
                 bulk_load_hint(stages + (size_t)r * 64 * k, P.Gbuf + tile_of(r), bytes, full + r, spol);
-            for (int r = 0; r < pre; ++r) mbar_wait_bounded(full + r, 0u, &st->err);
+            for (int r = 0; r < pre; ++r) mbar_wait_bounded(full + r, 0u, &st->err, P.wait_ns);
         }
         return;
     }
@@ -1322,7 +1418,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
                     bulk_load_hint(Gs, P.Gbuf + tile, bytes, full + s, spol);
                     continue;
                 }
-                if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
+                if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err, P.wait_ns);
                 mbar_expect_tx(full + s, debug_only == 1 ? bytes : 2 * bytes);
                 bulk_load_hint(Gs, P.Gbuf + tile, bytes, full + s, spol);
                 if (debug_only != 1) bulk_load_hint(Gs + 32 * k, P.W + tile, bytes, full + s, spol);
@@ -1351,8 +1447,8 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
             // of use u - 1 were issued, since this group's previous item,
             // loaded later, was; their bytes may not have landed): wait for
             // that use to be released first, then for use u's bytes.
-            if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err);
-            mbar_wait_bounded(full + s, (unsigned)u & 1u, &st->err);
+            if (u > 0) mbar_wait_bounded(done + s, (unsigned)(u - 1) & 1u, &st->err, P.wait_ns);
+            mbar_wait_bounded(full + s, (unsigned)u & 1u, &st->err, P.wait_ns);
             float* Gs = stages + (size_t)s * 64 * k;
             update_item(P, Gs, Gs + 32 * k, xa, xb, grp, h, T, d, cur, smooth, debug_only, DN);
             // all the group's warps are past its last barrier of the item (their
@@ -1439,14 +1535,14 @@ cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {
 
 template <bool BTS, bool CSR, bool STG>
 static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, int warps, int smem,
-                                 cudaStream_t s) {
+                                 int dbuf, cudaStream_t s) {
     auto fn = (P.G16 || P.cm) ? k_gsum<BTS, CSR, STG, true> : k_gsum<BTS, CSR, STG, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int units = STG ? warps / 2 : warps;
     const long long chunks = (long long)((P.n + 31) / 32) * ((P.D + units - 1) / units);
     const int blocks = (int)std::max(1ll, std::min<long long>(num_sms, chunks));
-    return tc_launch_pdl(fn, dim3(blocks), dim3(warps * 32), smem, s, P, tmB);
+    return tc_launch_pdl(fn, dim3(blocks), dim3(warps * 32), smem, s, P, tmB, dbuf);
 }
 
 // grad_S L tiles (k_gsum) into P.Gbuf: the B panel in shared memory when it
@@ -1461,10 +1557,14 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
     const bool stg = !P.csr_walk && base + 4 * stage <= kSmemOptin;  // 4 pairs or more
     int warps = GSUM_MAX_WARPS;
     long long smem_ll = base;
-    if (stg) {  // one staging area per warp pair
-        const int pairs = (int)std::min<long long>(GSUM_MAX_WARPS / 2, (kSmemOptin - base) / stage);
+    // two record buffers per warp pair only when the most pairs still fit
+    // (at the benchmark shape 8 double-buffered pairs took 61.3 us against
+    // 55.4 us for 15 pairs with one buffer each)
+    const int dbuf = stg && (kSmemOptin - base) / (2 * stage) >= GSUM_MAX_WARPS / 2 ? 1 : 0;
+    if (stg) {  // one or two staging areas per warp pair
+        const int pairs = (int)std::min<long long>(GSUM_MAX_WARPS / 2, (kSmemOptin - base) / ((1 + dbuf) * stage));
         warps = 2 * pairs;
-        smem_ll += stage * pairs;
+        smem_ll += (1 + dbuf) * stage * pairs;
     } else if (per_warp > 0) {
         warps = (int)std::min<long long>(GSUM_MAX_WARPS, (kSmemOptin - base) / per_warp);
         smem_ll += per_warp * warps;
@@ -1472,13 +1572,13 @@ cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_
     if (warps < 1) return cudaErrorInvalidValue;
     const int smem = (int)std::max(smem_ll, 2048ll);  // the population reduction's scratch at least
     if (P.csr_walk)
-        return bts ? launch_gsum_t<true, true, false>(P, tmB, num_sms, warps, smem, s)
-                   : launch_gsum_t<false, true, false>(P, tmB, num_sms, warps, smem, s);
+        return bts ? launch_gsum_t<true, true, false>(P, tmB, num_sms, warps, smem, 0, s)
+                   : launch_gsum_t<false, true, false>(P, tmB, num_sms, warps, smem, 0, s);
     if (stg)
-        return bts ? launch_gsum_t<true, false, true>(P, tmB, num_sms, warps, smem, s)
-                   : launch_gsum_t<false, false, true>(P, tmB, num_sms, warps, smem, s);
-    return bts ? launch_gsum_t<true, false, false>(P, tmB, num_sms, warps, smem, s)
-               : launch_gsum_t<false, false, false>(P, tmB, num_sms, warps, smem, s);
+        return bts ? launch_gsum_t<true, false, true>(P, tmB, num_sms, warps, smem, dbuf, s)
+                   : launch_gsum_t<false, false, true>(P, tmB, num_sms, warps, smem, dbuf, s);
+    return bts ? launch_gsum_t<true, false, false>(P, tmB, num_sms, warps, smem, 0, s)
+               : launch_gsum_t<false, false, false>(P, tmB, num_sms, warps, smem, 0, s);
 }
 
 // k_update: as many stages as fit (at most 16), at most 5 consumer groups,

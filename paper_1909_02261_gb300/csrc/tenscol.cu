@@ -94,6 +94,7 @@ struct tc_ctx {
     cudaGraphExec_t gexec = nullptr;
     long long gen = 0;          // bumped whenever captured work would go stale
     tc_batch* batch = nullptr;  // the batch this context belongs to, if any
+    unsigned long long wait_ns = 1000000000ull;  // limit of every bounded device wait (tc_set_wait_limit)
     // per-kernel event timing
     int timing = 0;
     bool capturing = false;
@@ -292,6 +293,9 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.powB = c->d_lut + 3 * D1;
     P.st = c->d_st;
     P.best = c->d_best;
+    P.wait_ns = c->wait_ns;
+    P.dbg_withhold = fault("wait") ? 1 : 0;
+    P.dbg_plant = fault("index") ? 1 : 0;
     // with mu = 0 the pair matrix vanishes off the edges; below a density of
     // 1/8 walking the adjacency lists beats walking all n vertices per class
     P.csr_walk = c->p.mu == 0.0f && c->nnz * 8 < (long long)c->n * c->n && c->cmax == 0;
@@ -1540,6 +1544,14 @@ int tc_relaxed_dev(tc_ctx* c, const float* W_dev, float tau, int64_t t, float* l
     dfree(S); dfree(M); dfree(Bp); dfree(part);
     if (rc) return rc;
     TC_CHECK(e);
+    return TC_OK;
+}
+
+int tc_set_wait_limit(tc_ctx* c, int64_t ns) {
+    if (!c || ns < 0 || ns > 60000000000ll) return TC_ERR_ARG;
+    DeviceGuard g(c->device);
+    drop_graph_exec(c);
+    c->wait_ns = ns > 0 ? (unsigned long long)ns : 1000000000ull;
     return TC_OK;
 }
 

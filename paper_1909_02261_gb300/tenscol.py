@@ -65,13 +65,32 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"\b(tc_[a-z0-9_]+)\s*\(", src)))
 
 
+_lib_bounds = None
+
+
+def load_bounds(build_if_missing: bool = True):
+    """libtenscol_bounds.so: the same entry points with the device-side index
+    checks of the class walk (TC_BOUNDS=1), for failure tests."""
+    global _lib_bounds
+    if _lib_bounds is None:
+        if build_if_missing:
+            _build.build()
+        _lib_bounds = _declare(C.CDLL(_build.LIB_BOUNDS))
+    return _lib_bounds
+
+
 def load(build_if_missing: bool = True):
     """Load (building if needed) the shared library and declare signatures."""
     global _lib
     if _lib is not None:
         return _lib
     path = _build.build() if build_if_missing else _build.LIB
-    L = C.CDLL(path)
+    _lib = _declare(C.CDLL(path))
+    return _lib
+
+
+def _declare(L):
+    """Declares the argument and result types of the entry points on L."""
     vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
     P = C.POINTER
     sig = {
@@ -92,6 +111,7 @@ def load(build_if_missing: bool = True):
         "tc_evaluate": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "tc_launch_count": (C.c_int, [vp, P(i64)]),
         "tc_set_graph_chunk": (C.c_int, [vp, C.c_int]),
+        "tc_set_wait_limit": (C.c_int, [vp, i64]),
         "tc_step_async": (C.c_int, [vp, i64]),
         "tc_set_timing": (C.c_int, [vp, C.c_int]),
         "tc_kernel_times": (C.c_int, [vp, vp, vp]),
@@ -120,7 +140,6 @@ def load(build_if_missing: bool = True):
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
-    _lib = L
     return L
 
 
@@ -162,10 +181,11 @@ def params(problem: int = TC_KCOL, **kw) -> tc_params:
 
 
 class TensCol:
-    """One context: a graph and a population on one CUDA device."""
+    """One context: a graph and a population on one CUDA device (bounds: on
+    the library with device-side index checks)."""
 
-    def __init__(self, device: int = 0):
-        self._L = load()
+    def __init__(self, device: int = 0, bounds: bool = False):
+        self._L = load_bounds() if bounds else load()
         h = C.c_void_p()
         _ck(self._L.tc_create(C.byref(h), device), "tc_create")
         self.h = h
@@ -210,6 +230,10 @@ class TensCol:
 
     def tc_set_graph_chunk(self, chunk: int):
         _ck(self._L.tc_set_graph_chunk(self.h, chunk), "tc_set_graph_chunk")
+
+    def tc_set_wait_limit(self, ns: int):
+        """Limit (ns) of every bounded device wait; 0 restores one second."""
+        _ck(self._L.tc_set_wait_limit(self.h, ns), "tc_set_wait_limit")
 
     # --- iterate ------------------------------------------------------------
     def tc_step(self, n_iters: int) -> int:

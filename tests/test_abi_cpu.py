@@ -18,8 +18,10 @@ def test_library_exports_every_header_symbol():
     assert not missing, missing
 
 
-def test_exported_symbols_match_nm():
-    lib = T.load()._name
+@pytest.mark.parametrize("loader", [T.load, T.load_bounds])
+def test_exported_symbols_match_nm(loader):
+    # the main library and the build with device index checks export the same ABI
+    lib = loader()._name
     out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
     exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
     for nm in T.header_functions():
