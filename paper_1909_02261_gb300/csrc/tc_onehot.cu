@@ -638,18 +638,6 @@ __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-__device__ __forceinline__ void cp_async_16(uint32_t smem_dst, const void* gsrc) {  // both 16-byte aligned
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_dst), "l"(gsrc) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_4(uint32_t smem_dst, const void* gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_dst), "l"(gsrc) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {  // this thread's copies have landed
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 __device__ __forceinline__ void pair_sync(int pair) {  // warps 2 pair, 2 pair + 1 (named barrier pair + 1)
     asm volatile("bar.sync %0, 64;" ::"r"(pair + 1) : "memory");
 }
@@ -1004,9 +992,9 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         mbar_wait_bounded(&s_never, 0u, &st->err, P.wait_ns);
     }
-    if (threadIdx.x == 0 && (BTS || dbuf)) {
+    if (threadIdx.x == 0 && (BTS || STG)) {
         if (BTS) mbar_init(&s_bbar, 1);
-        if (dbuf)
+        if (STG)  // the record buffers' barriers (one used per pair without dbuf)
             for (int u = 0; u < nunits; ++u) {
                 mbar_init(&s_rbar[u][0], 1);
                 mbar_init(&s_rbar[u][1], 1);
@@ -1109,13 +1097,15 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                 mbar_wait_bounded(&s_rbar[unit][it & 1], (unsigned)(it >> 1) & 1u, &st->err, P.wait_ns);
             } else if (STG) {
                 pair_sync(unit);  // the pair's reads of the previous item are done
-                // asynchronous copies (cp.async), all in flight at once
-                const uint4* src = reinterpret_cast<const uint4*>(pm);
-                const int t64 = h * 32 + lane;
-                // the whole record (a multiple of 16 bytes) in one pass
-                for (int l = t64; l < P.rec_stride / 4; l += 64) cp_async_16(smem_u32(ps) + 16u * l, src + l);
-                cp_async_wait_all();
-                pair_sync(unit);
+                // the whole record (a multiple of 16 bytes) by one bulk copy:
+                // the copy engine writes shared memory without load/store
+                // instructions of the pair (the class walk's own pipe)
+                if (leader) {
+                    fence_proxy_async();
+                    mbar_expect_tx(&s_rbar[unit][0], rec_bytes);
+                    bulk_load(ps, pm, rec_bytes, &s_rbar[unit][0]);
+                }
+                mbar_wait_bounded(&s_rbar[unit][0], (unsigned)it & 1u, &st->err, P.wait_ns);
             } else if (!CSR) {
                 prefetch_item(pm, P.perm_stride, of, k, Ed, lane);
             }
