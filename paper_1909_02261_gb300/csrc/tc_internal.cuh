@@ -22,10 +22,11 @@ struct tc_dev_state {
     int best_d;
     int last_fmin;
     int last_dstar;
-    unsigned int done_gsum;     // completion tickets (last-block patterns): k_gsum blocks
-    unsigned int done_update;
+    unsigned int done_gsum;     // completion ticket (last-block pattern) of k_gsum's blocks
+    unsigned int done_spare;
     float loss, kappa, varpi;
-    int pad;
+    int best_pending;     // 1: the last evaluation improved the best-so-far, whose colours
+                          // (individual last_dstar) k_update copies before it overwrites them
     long long trace_n;    // trace records written so far
 };
 
@@ -181,25 +182,40 @@ cudaError_t tc_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
 // Population reduction of one iteration, run by the last block of k_gsum
 // once every individual's conflicts (counted twice, over both ends of each
 // edge) and additive term are in: min_d f(S_d) with the lowest d on ties (Algorithm 1 stop test),
-// the best-so-far copy, the loss of eq. 7, the stop flag and the trace.
+// the best-so-far record, the loss of eq. 7, the stop flag and the trace.
+// It sits between the last walk and k_update on the iteration's critical
+// path, so every load it needs is issued at once (one memory round trip);
+// the colours of an improved best are copied by k_update, which reads each
+// row's colour before overwriting it (best_pending), except in the
+// multicolouring, whose colour sets change in another kernel.  t is the
+// iteration's counter, which the block read at its start.
 // `scratch`: TC_FINALIZE_SCRATCH bytes of shared memory, 8-byte aligned; any
 // block size up to 1024 threads (fixed-order sums: deterministic for a given
 // block size).
-constexpr int TC_FINALIZE_SCRATCH = 1152;
-__device__ __forceinline__ void finalize_population(const tc_kparams& P, void* scratch) {
-    // one pass: per-thread partials, warp trees, then thread 0 over the warps
+constexpr int TC_FINALIZE_SCRATCH = 1296;
+__device__ __forceinline__ void finalize_population(const tc_kparams& P, void* scratch, long long t) {
+    // one pass: per-thread partials, warp trees, then warp 0 over the warps
     // (fixed order: deterministic for a given block size, at most 1024)
     long long* sh_fc = reinterpret_cast<long long*>(scratch);
     long long* sh_fe = sh_fc + 32;
     unsigned long long* sh_key = reinterpret_cast<unsigned long long*>(sh_fe + 32);
-    float* sh_ka = reinterpret_cast<float*>(sh_key + 32);
+    unsigned long long* sh_ab = sh_key + 32;  // f_color, additive term of the key's individual
+    float* sh_ka = reinterpret_cast<float*>(sh_ab + 32);
     float* sh_va = sh_ka + 32;
     int& s_dstar = *reinterpret_cast<int*>(sh_va + 32);
     int& s_better = *(reinterpret_cast<int*>(sh_va + 32) + 1);
     tc_dev_state* st = P.st;
     const int D = P.D, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    // the state thread 0 needs below, loaded with the per-individual values
+    int prev_best = 0;
+    long long trace_n = 0, evaluated = 0;
+    if (threadIdx.x == 0) {
+        prev_best = __ldcg(&st->best_f);
+        trace_n = __ldcg(&st->trace_n);
+        evaluated = __ldcg(&st->evaluated);
+    }
     long long fc = 0, fe = 0;
-    unsigned long long key = ~0ull;
+    unsigned long long key = ~0ull, ab = 0ull;
     float ka = 0.f, va = 0.f;
     const bool part = tc_is_partition(P.problem), with_eq = tc_has_additive(P.problem);
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
@@ -214,7 +230,10 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
         const long long fobj = part ? P.n_edges - a : (long long)a;
         const unsigned long long f = (unsigned long long)(fobj + (with_eq ? b : 0));
         const unsigned long long kk = (f << 32) | (unsigned)d;
-        key = kk < key ? kk : key;
+        if (kk < key) {
+            key = kk;
+            ab = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+        }
     }
     for (int b = threadIdx.x; b < P.n_pair_blocks; b += blockDim.x) {
         ka += __ldcg(P.loss_part + 2 * b);
@@ -225,7 +244,11 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
         fc += __shfl_xor_sync(0xffffffffu, fc, o);
         fe += __shfl_xor_sync(0xffffffffu, fe, o);
         const unsigned long long u = __shfl_xor_sync(0xffffffffu, key, o);
-        key = u < key ? u : key;
+        const unsigned long long uab = __shfl_xor_sync(0xffffffffu, ab, o);
+        if (u < key) {  // keys are distinct (they hold d)
+            key = u;
+            ab = uab;
+        }
         ka += __shfl_xor_sync(0xffffffffu, ka, o);
         va += __shfl_xor_sync(0xffffffffu, va, o);
     }
@@ -233,23 +256,36 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
         sh_fc[warp] = fc;
         sh_fe[warp] = fe;
         sh_key[warp] = key;
+        sh_ab[warp] = ab;
         sh_ka[warp] = ka;
         sh_va[warp] = va;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        fc = fe = 0;
-        key = ~0ull;
-        ka = va = 0.f;
-        for (int w = 0; w < nw; ++w) {
-            fc += sh_fc[w];
-            fe += sh_fe[w];
-            key = sh_key[w] < key ? sh_key[w] : key;
-            ka += sh_ka[w];
-            va += sh_va[w];
+    if (warp == 0) {  // the warps' partials, by the same butterfly
+        const bool in = lane < nw;
+        fc = in ? sh_fc[lane] : 0;
+        fe = in ? sh_fe[lane] : 0;
+        key = in ? sh_key[lane] : ~0ull;
+        ab = in ? sh_ab[lane] : 0ull;
+        ka = in ? sh_ka[lane] : 0.f;
+        va = in ? sh_va[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fc += __shfl_xor_sync(0xffffffffu, fc, o);
+            fe += __shfl_xor_sync(0xffffffffu, fe, o);
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, key, o);
+            const unsigned long long uab = __shfl_xor_sync(0xffffffffu, ab, o);
+            if (u < key) {
+                key = u;
+                ab = uab;
+            }
+            ka += __shfl_xor_sync(0xffffffffu, ka, o);
+            va += __shfl_xor_sync(0xffffffffu, va, o);
         }
+    }
+    if (threadIdx.x == 0) {
         const int fmin = (int)(key >> 32), dstar = (int)(key & 0xffffffffu);
-        const long long t = st->t;
+        const int fcol_star = (int)(ab >> 32), fadd_star = (int)(unsigned)(ab & 0xffffffffu);
         const double tt = (double)t;
         const long long fsum = part ? (long long)D * P.n_edges - fc : fc;  // the fitness term of eq. 7
         st->loss = (float)fsum + (float)((double)P.nu * tt) * (float)fe +
@@ -264,36 +300,43 @@ __device__ __forceinline__ void finalize_population(const tc_kparams& P, void* s
             e.t = t;
             e.f_min = fmin;
             e.individual = dstar;
-            e.f_color = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
-            e.f_add = __ldcg(P.feq + dstar);
+            e.f_color = fcol_star;
+            e.f_add = fadd_star;
             e.loss = st->loss;
             e.kappa = ka;
             e.varpi = va;
             e.pad = 0;
-            P.trace[st->trace_n % P.trace_cap] = e;
-            st->trace_n += 1;
+            P.trace[trace_n % P.trace_cap] = e;
+            st->trace_n = trace_n + 1;
         }
         int better = 0;
         if (P.commit) {
-            st->evaluated += 1;
-            if (st->best_f < 0 || fmin < st->best_f) {
+            st->evaluated = evaluated + 1;
+            if (prev_best < 0 || fmin < prev_best) {
                 better = 1;
                 st->best_f = fmin;
-                st->best_fcolor = __ldcg(P.fcolor + dstar);  // halved above (the block synced since)
-                st->best_feq = __ldcg(P.feq + dstar);
+                st->best_fcolor = fcol_star;
+                st->best_feq = fadd_star;
                 st->best_d = dstar;
                 st->best_t = t;
             }
-            if (P.stop_on_legal && fmin == 0) st->stop = 1;
+            // the iteration ends here unless it stops before Step 3; its update
+            // (k_update) reads the new counter
+            if (P.stop_on_legal && fmin == 0)
+                st->stop = 1;
+            else
+                st->t = t + 1;
         }
+        // k_update copies the colours (one colour per vertex)
+        st->best_pending = better && !P.cm;
         s_dstar = dstar;
-        s_better = better;
+        s_better = better && P.cm;
     }
     __syncthreads();
-    if (s_better) {
+    if (s_better) {  // multicolouring: the colours and the colour sets here
         for (int i = threadIdx.x; i < P.n; i += blockDim.x)
             P.best[i] = P.c[(size_t)s_dstar * P.n + i];
-        if (P.cm)  // multicolouring: the colour sets too
+        if (P.cm)
             for (size_t e = threadIdx.x; e < (size_t)P.n * P.cmax; e += blockDim.x)
                 P.best_m[e] = P.cm[(size_t)s_dstar * P.n * P.cmax + e];
     }

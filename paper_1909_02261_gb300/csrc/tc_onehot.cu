@@ -1179,19 +1179,19 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         q = seg_end;
     }
     // completion ticket: the last block reduces the population (Algorithm 1's
-    // stop test, the best-so-far copy, the loss of eq. 7) before k_update
+    // stop test, the best-so-far record, the loss of eq. 7) before k_update.
+    // The ticket is an acquire-release atomic taken after the block barrier:
+    // it releases the block's conflict counts and, for the last block,
+    // acquires every other block's (the barrier below passes both on)
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned ticket = atomicAdd(&st->done_gsum, 1u);
+        unsigned ticket;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(ticket) : "l"(&st->done_gsum) : "memory");
         s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_population(P, sm);  // the panel and staging areas are free now
-    }
+    if (s_last) finalize_population(P, sm, t);  // the panel and staging areas are free now
 }
 
 // ---------------------------------------------------------------------------
@@ -1369,8 +1369,6 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
         fence_proxy_async();
     }
     __syncthreads();
-    const long long t = st->t;
-    const bool smooth = ((t + 1) % P.nb_iter) == 0;
     const int nT = (n + 31) / 32;
     const long long Q = (long long)nT * D;
     const long long q0 = (long long)blockIdx.x * items_per_block;
@@ -1390,12 +1388,21 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
             bulk_load_hint(stages + (size_t)r * 64 * k + 32 * k, P.W + tile_of(r), bytes, full + r, spol);
         }
     pdl_wait();  // the grad_S tiles and the stop flag from k_gsum
+    // an improved best-so-far (k_gsum's population reduction): its colours
+    // are copied here, each row just before its update overwrites it
+    const int best_d = debug_only == 0 && __ldcg(&st->best_pending) ? __ldcg(&st->last_dstar) : -1;
+    // Step 4-iv after the update of iteration t: the population reduction of
+    // a committed iteration that goes on has already set the counter to t + 1
+    const long long tc = __ldcg(&st->t);
+    const bool smooth = ((debug_only ? tc + 1 : tc) % P.nb_iter) == 0;
     if (!debug_only && st->stop) {
         if (warp == 0 && lane == 0) {  // no copy may still be landing when the block exits
             for (int r = 0; r < pre; ++r)
                 bulk_load_hint(stages + (size_t)r * 64 * k, P.Gbuf + tile_of(r), bytes, full + r, spol);
             for (int r = 0; r < pre; ++r) mbar_wait_bounded(full + r, 0u, &st->err, P.wait_ns);
         }
+        if (best_d >= 0 && blockIdx.x == 0)  // no update: the colours are the evaluated ones
+            for (int i = threadIdx.x; i < n; i += blockDim.x) P.best[i] = P.c[(size_t)best_d * n + i];
         return;
     }
     if (warp == 0) {
@@ -1432,6 +1439,7 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
             const int s = r % S, u = r / S;
             const int cur = cur_next;
             if (r + ngroups < R) cur_next = colour_of(r + ngroups);
+            if (d == best_d && h == 0 && T * 32 + lane < n) P.best[T * 32 + lane] = (uint16_t)cur;
             // A parity wait is only sound within one phase of the barrier.
             // Another group may still hold use u - 1 of this stage (the loads
             // of use u - 1 were issued, since this group's previous item,
@@ -1453,18 +1461,6 @@ __global__ void __launch_bounds__(UPD_MAX_WARPS * 32, 1)
             }
         }
         if (h == 0 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
-    }
-    if (!debug_only) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned ticket = atomicAdd(&st->done_update, 1u);
-            if (ticket == gridDim.x - 1) {
-                st->done_update = 0u;
-                st->t = t + 1;
-                __threadfence();
-            }
-        }
     }
 }
 
