@@ -160,6 +160,45 @@ def fp8_library_tflops(dev, N=8192):
         return {"tflops": None, "error": f"{type(e).__name__}: {e}"[:200]}
 
 
+def step3ii_tensor_core_probe(dev, flush, n, k, D):
+    """The tensor-core form of Step 3-ii, timed with the vendor library at
+    this shape: grad_S L's class sums are P = B' S_cat (n x n times n x D k,
+    S_cat one-hot), which FP16 tensor cores reach to FP32 accuracy only in
+    two passes (B' split into FP16 high and low parts: K = 2 n).  cuBLAS
+    (torch.mm) on FP16 operands with an FP16 result stands for it; the
+    real product also needs an FP32 result, the additive term and the
+    conflicts, so these times are lower bounds.  Median of 10 launches, L2
+    flushed before each, CUDA events."""
+    import torch
+    try:
+        m = (n + 127) // 128 * 128
+        g = torch.Generator(device=dev).manual_seed(0)
+        a2 = torch.randn(m, 2 * m, device=dev, generator=g).to(torch.float16)
+        s2 = (torch.rand(2 * m, D * k, device=dev, generator=g) < 1.0 / k).to(torch.float16)
+        out = {}
+        for name, a, b in (("two_pass", a2, s2), ("one_pass", a2[:, :m], s2[:m])):
+            for _ in range(3):
+                torch.mm(a, b)
+            ts = []
+            for _ in range(10):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.mm(a, b)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = sorted(ts)[len(ts) // 2]
+            flop = 2.0 * a.shape[0] * a.shape[1] * b.shape[1]
+            out[name] = {"us": 1e3 * ms, "tflops": flop / (ms * 1e-3) / 1e12, "shape": list(a.shape) + [b.shape[1]]}
+        del a2, s2
+        out["how"] = ("torch.mm (cuBLAS) FP16 x FP16 -> FP16, B' split in two FP16 parts (two_pass, K = 2 n_pad) "
+                      "or one part (one_pass, short of FP32 accuracy): lower bounds of the tensor-core Step 3-ii")
+        return out
+    except Exception as e:
+        return {"error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -589,6 +628,12 @@ def run_ours(args):
                      "unit": "Gadd/s", "frac": ach / peak_lds, "work_per_launch": adds,
                      "peak_source": f"{sms} SMs x 32 shared-memory loads per clock x {mhz:.0f} MHz"}
 
+    # the tensor-core alternative of Step 3-ii at this shape (vendor library)
+    tc3 = None
+    if not args.no_forms and kcnt[T.TC_KID_GSUM] > 0:
+        tc3 = step3ii_tensor_core_probe(dev, flush, n, k, D)
+        tc3["k_gsum_us"] = 1e3 * kms[T.TC_KID_GSUM] / kcnt[T.TC_KID_GSUM]
+
     line = {
         "metric": METRIC, "value": value, "unit": "individual-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -603,6 +648,7 @@ def run_ours(args):
         "roofline": roof,
         "roofline_tensor": tensor_roof,
         "roofline_gsum": gsum_roof,
+        "step3ii_tensor_core": tc3,
         "forms": forms,
         "variants": variants,
         "configs": configs,
