@@ -193,6 +193,7 @@ int tc_step_async(tc_ctx *ctx, int64_t n_iters);
 #define TC_KID_GEMM_G 4  /* dense forms: Gamma = A S GEMM                    */
 #define TC_KID_GSUM 5    /* grad_S L tiles (class sums of the pair matrix)   */
 #define TC_KID_GEMM_F 6  /* dense FP8 form: M~ and Gamma in one launch       */
+#define TC_KID_FRONT 7   /* one-hot form: classes and pair terms, one launch */
 #define TC_NUM_KID 8
 
 /* Per-kernel device timing with CUDA events recorded around every launch

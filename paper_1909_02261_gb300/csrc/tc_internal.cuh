@@ -350,6 +350,8 @@ cudaError_t tc_launch_init_weights(float* W, int D, int n, int k, unsigned long 
 cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s);
+// The class blocks and the pair blocks in one launch (one-hot form, one colour per vertex).
+cudaError_t tc_launch_front(const tc_kparams& P, cudaStream_t s);
 cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s);
 cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, int debug_only);
 // Tiled 2-D tensor map (TMA) over a row-major matrix: `inner` elements per

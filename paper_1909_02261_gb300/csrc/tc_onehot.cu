@@ -162,14 +162,16 @@ __global__ void k_assign(tc_kparams P) {
 // cancel in x, so no lane of x has its top bit set, x & 0x7f.. is x and the
 // mark is ~(x + 0x7f..) & 0x80.. (one operation fewer per word).
 // ---------------------------------------------------------------------------
-template <int CB, bool C7, bool DN>  // DN: M~ comes from the dense forms' GEMM
-__global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
+// FRONT: a pair block of k_front (the class blocks run in the same launch):
+// it lets k_gsum start once its pair coefficients are written and fenced.
+template <int CB, bool C7, bool DN, bool FRONT>  // DN: M~ comes from the dense forms' GEMM
+__device__ __forceinline__ void pairs_block(const tc_kparams& P, int blk) {
     static_assert(!C7 || CB == 1, "7-bit colours are packed in bytes");
     pdl_wait();  // colours from the previous k_update (dense forms: M~ from the GEMM)
     // k_classes reads the colours before its own wait: it may start only
     // once this kernel's predecessors are complete
-    pdl_trigger();
-    const int2 tile = P.pair_tiles[blockIdx.x];
+    if (!FRONT) pdl_trigger();
+    const int2 tile = P.pair_tiles[blk];
     if (P.commit && P.st->stop) {
         // the dense forms' M~ accumulates by reduce-adds: every block leaves
         // its entries zero for the next GEMM, also when it has nothing to do
@@ -320,9 +322,19 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
             ka += s_red[0][q];
             va += s_red[1][q];
         }
-        P.loss_part[2 * blockIdx.x] = ka;
-        P.loss_part[2 * blockIdx.x + 1] = va;
+        P.loss_part[2 * blk] = ka;
+        P.loss_part[2 * blk + 1] = va;
     }
+    if (FRONT) {  // k_gsum reads B before its own wait
+        __threadfence();
+        __syncthreads();
+        pdl_trigger();
+    }
+}
+
+template <int CB, bool C7, bool DN>
+__global__ void __launch_bounds__(PAIR_THREADS) k_pairs(tc_kparams P) {
+    pairs_block<CB, C7, DN, false>(P, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,14 +363,22 @@ __device__ T block_sum(T v, T* sh) {
 // shared memory: the individual's colours, then the per-warp colour counts of
 // the sort.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
+// FRONT: a class block of k_front, launched with the pair blocks: it waits
+// for the previous k_update at its start and does not hold k_gsum back
+// (k_gsum reads the class lists only after its own wait).
+template <bool FRONT>
+__device__ __forceinline__ void classes_block(const tc_kparams& P, int d) {
     // Launched once k_pairs has passed its own wait, so the colours of the
     // previous update (and the stop flag) are final: the class lists need
     // nothing from k_pairs and are built while it runs.  The wait for k_pairs
     // comes at the end, before this kernel lets k_gsum start (k_gsum reads
     // the pair matrix of k_pairs before its own wait).
-    if (P.commit && P.st->stop) {
+    if (FRONT) {
         pdl_wait();
+        pdl_trigger();
+    }
+    if (P.commit && P.st->stop) {
+        if (!FRONT) pdl_wait();
         return;
     }
     __shared__ int s_hist[TC_MAX_K];
@@ -367,7 +387,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     __shared__ int s_bk[64];
     __shared__ long long sh_ll[CLS_THREADS / 32];
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    const int n = P.n, k = P.k, d = blockIdx.x;
+    const int n = P.n, k = P.k;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwp = CLS_THREADS / 32;
     uint16_t* cs = reinterpret_cast<uint16_t*>(s_dyn);  // n colours
     int* wcnt = reinterpret_cast<int*>(s_dyn + ((n + 7) / 8) * 4);  // after the colours: nwp x k counts
@@ -521,8 +541,27 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) {
     __syncthreads();  // the sort's entries are written
     if (P.dbg_plant && d == 0 && threadIdx.x == 0) pd[0] = (uint32_t)(n + 1);  // TC_FAULT=index
 #endif
-    pdl_wait();
-    pdl_trigger();
+    if (!FRONT) {
+        pdl_wait();
+        pdl_trigger();
+    }
+}
+
+__global__ void __launch_bounds__(CLS_THREADS) k_classes(tc_kparams P) { classes_block<false>(P, blockIdx.x); }
+
+// k_front (one-hot form): the colour classes (the first D blocks,
+// classes_block) and Step 3-i with the pair coefficients (the n_pair_blocks
+// after them, pairs_block) in one launch.  The class blocks are short and
+// latency-bound, the pair blocks long and ALU-bound: dispatched first, the
+// class blocks' warps are the older ones an SM's schedulers favour, so their
+// chain of barriers runs in the pair blocks' shadow instead of after them.
+template <int CB, bool C7>
+__global__ void __launch_bounds__(PAIR_THREADS) k_front(tc_kparams P) {
+    static_assert(PAIR_THREADS == CLS_THREADS, "one block size for both roles");
+    if ((int)blockIdx.x < P.D)
+        classes_block<true>(P, (int)blockIdx.x);
+    else
+        pairs_block<CB, C7, false, true>(P, (int)blockIdx.x - P.D);
 }
 
 
@@ -1508,6 +1547,15 @@ cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {
                           : tc_launch_pdl(k_pairs<1, false, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s,
                                           P);
     return tc_launch_pdl(k_pairs<2, false, false>, dim3(P.n_pair_blocks), dim3(PAIR_THREADS), 0, s, P);
+}
+
+cudaError_t tc_launch_front(const tc_kparams& P, cudaStream_t s) {
+    const long long counts = 4ll * (CLS_THREADS / 32) * P.k;  // the class blocks' per-warp colour counts
+    const int smem = (int)(counts + 16ll * ((P.n + 7) / 8));  // + the individual's colours
+    auto fn = P.ct_bytes == 1 ? (P.k <= 128 ? k_front<1, true> : k_front<1, false>) : k_front<2, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return tc_launch_pdl(fn, dim3(P.D + P.n_pair_blocks), dim3(PAIR_THREADS), smem, s, P);
 }
 
 cudaError_t tc_launch_classes(const tc_kparams& P, cudaStream_t s) {

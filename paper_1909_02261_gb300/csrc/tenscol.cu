@@ -805,15 +805,20 @@ int launch_iteration(tc_ctx* c) {
     // k_pairs and k_classes share no data: k_classes builds its class lists
     // while k_pairs runs (it is launched once k_pairs has passed its wait)
     // and waits for k_pairs only before it lets k_gsum start
-    if (dense && (rc = launch_dense_gemms(c, 0, c->stream))) return rc;
-    TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
-    if (dense && (rc = launch_dense_gemms(c, 1, c->stream))) return rc;
-    TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
+    if (!dense && !P.cm) {  // one-hot form: the class and pair blocks in one launch
+        TC_CHECK(timed(c, TC_KID_FRONT, [&] { return tc_launch_front(P, c->stream); }));
+    } else {
+        if (dense && (rc = launch_dense_gemms(c, 0, c->stream))) return rc;
+        TC_CHECK(timed(c, TC_KID_PAIRS, [&] { return tc_launch_pairs(P, c->stream); }));
+        if (dense && (rc = launch_dense_gemms(c, 1, c->stream))) return rc;
+        TC_CHECK(timed(c, TC_KID_CLASSES, [&] { return tc_launch_classes(P, c->stream); }));
+    }
     TC_CHECK(launch_grad_update(c, P, 0));
     return TC_OK;
 }
 
 int launches_per_iteration(const tc_ctx* c) {
+    if (c->p.form == TC_FORM_ONEHOT && c->cmax == 0) return 3;  // k_front, k_gsum, k_update
     const int gemms = c->p.form == TC_FORM_ONEHOT ? 0 : (c->fused ? 1 : 2);
     return 4 + gemms + (c->cmax > 0 ? 1 : 0);
 }

@@ -18,10 +18,11 @@ from . import build as _build
 TC_OK = 0
 TC_KCOL, TC_ECP, TC_KPART, TC_KPART_BAL, TC_MSCP = 0, 1, 2, 3, 4  # problems (tenscol.h)
 TC_FORM_ONEHOT, TC_FORM_DENSE_FP8, TC_FORM_DENSE_FP32 = 0, 1, 2
-TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE, TC_KID_GEMM_M, TC_KID_GEMM_G, TC_KID_GSUM, TC_KID_GEMM_F = range(7)
+TC_KID_PAIRS, TC_KID_CLASSES, TC_KID_UPDATE, TC_KID_GEMM_M, TC_KID_GEMM_G, TC_KID_GSUM, TC_KID_GEMM_F, \
+    TC_KID_FRONT = range(8)
 KERNEL_NAMES = {TC_KID_PAIRS: "k_pairs", TC_KID_CLASSES: "k_classes", TC_KID_UPDATE: "k_update",
                 TC_KID_GEMM_M: "gemm_mtilde", TC_KID_GEMM_G: "gemm_gamma", TC_KID_GSUM: "k_gsum",
-                TC_KID_GEMM_F: "gemm_fused"}
+                TC_KID_GEMM_F: "gemm_fused", TC_KID_FRONT: "k_front"}
 HEADER = os.path.join(_build.INCLUDE, "tenscol.h")
 
 
