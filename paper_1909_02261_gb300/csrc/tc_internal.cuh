@@ -55,6 +55,10 @@ struct tc_kparams {
     uint16_t* c;              // D x n colours
     uint16_t* c_snap;         // D x n colours of the iteration, for the adjacency walk
     uint16_t* cT;             // n x Dp colours (vertex-major, ct_bytes each), pads all-ones
+    uint32_t* planes;         // k <= 128, one colour per vertex: n x png x 8 bit-plane words, word
+                              // p of group g of vertex i holding bit p of c_d(i) at bit d - 32 g
+                              // (d in 32 g .. 32 g + 31; plane 7 and absent individuals 0)
+    int png;                  // groups of 32 individuals, ceil(D / 32)
     const uint32_t* adj;      // n x adj_words adjacency bitmask
     const int* rowptr;        // CSR
     const int* colidx;

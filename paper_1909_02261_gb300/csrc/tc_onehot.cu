@@ -126,7 +126,14 @@ __global__ void k_w_layout(const float* src, float* dst, int D, int n, int k, bo
 
 // Step 1 (Section 3.4) for a fresh W: c_d(i) = lowest j with maximal w.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_colour(const tc_kparams& P, int d, int i, int c) {
+// old: the colour being replaced (the bit planes change by its difference)
+__device__ __forceinline__ void store_colour(const tc_kparams& P, int d, int i, int old, int c) {
+    if (P.planes && old != c) {
+        const unsigned x = (unsigned)(old ^ c), bit = 1u << (d & 31);
+        uint32_t* w = P.planes + ((size_t)i * P.png + (d >> 5)) * 8;
+        for (int p = 0; p < 7; ++p)
+            if ((x >> p) & 1u) atomicXor(w + p, bit);
+    }
     P.c[(size_t)d * P.n + i] = (uint16_t)c;
     if (P.ct_bytes == 1)
         reinterpret_cast<uint8_t*>(P.cT)[(size_t)i * P.Dp + d] = (uint8_t)c;
@@ -148,7 +155,7 @@ __global__ void k_assign(tc_kparams P) {
             best = j;
         }
     }
-    store_colour(P, d, i, best);
+    store_colour(P, d, i, best, best);  // (the planes are rebuilt after the assignment)
 }
 
 // ---------------------------------------------------------------------------
@@ -185,8 +192,10 @@ __device__ __forceinline__ void pairs_block(const tc_kparams& P, int blk) {
             }
         return;
     }
-    __shared__ uint32_t s_a[PT][PAIR_CW + 1];
-    __shared__ uint32_t s_b[PT][PAIR_CW + 1];
+    // colour words of the tile's rows (odd stride: the column reads are free
+    // of bank conflicts), or their bit planes at a 68-word stride (16-byte rows)
+    __shared__ __align__(16) uint32_t s_a[PT][PAIR_CW + 5];
+    __shared__ __align__(16) uint32_t s_b[PT][PAIR_CW + 5];
     __shared__ float s_red[2][PAIR_THREADS / 32];
     constexpr uint32_t LOW = CB == 1 ? 0x7F7F7F7Fu : 0x7FFF7FFFu;
     constexpr uint32_t HIGH = CB == 1 ? 0x80808080u : 0x80008000u;
@@ -198,12 +207,62 @@ __device__ __forceinline__ void pairs_block(const tc_kparams& P, int blk) {
     const uint32_t* cTw = reinterpret_cast<const uint32_t*>(P.cT);
 
     uint32_t wide[PP][PP];
+    int mis[PP][PP];  // bit-plane path: individuals whose colours differ
 #pragma unroll
     for (int a = 0; a < PP; ++a)
 #pragma unroll
-        for (int b = 0; b < PP; ++b) wide[a][b] = 0u;
+        for (int b = 0; b < PP; ++b) {
+            wide[a][b] = 0u;
+            mis[a][b] = 0;
+        }
     constexpr bool from_gemm = DN;  // dense form: M~ came from a GEMM
-    for (int w0 = 0; w0 < (from_gemm ? 0 : Dw); w0 += PAIR_CW) {
+    const bool planes = C7 && !from_gemm && P.planes != nullptr;
+    if (planes) {
+        // 32 individuals at a time: the colours of i and m agree in individual
+        // d exactly when no bit plane differs at bit d, so the OR of the seven
+        // planes' XORs marks the individuals that differ (absent individuals
+        // have all planes 0 for every vertex: they never differ)
+        constexpr int PLS = 68;
+        uint32_t* pa = &s_a[0][0];
+        uint32_t* pb = &s_b[0][0];
+        const int ng = P.png;
+        for (int g0 = 0; g0 < ng; g0 += 8) {
+            const int gc = min(8, ng - g0);
+            __syncthreads();
+            for (int e = tid; e < PT * gc * 2; e += PAIR_THREADS) {
+                const int r = e / (gc * 2), q = e - r * (gc * 2);
+                const int ii = I * PT + r, mm = M * PT + r;
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                reinterpret_cast<uint4*>(pa + r * PLS)[q] =
+                    ii < n ? __ldg(reinterpret_cast<const uint4*>(P.planes + ((size_t)ii * ng + g0) * 8) + q) : z;
+                reinterpret_cast<uint4*>(pb + r * PLS)[q] =
+                    mm < n ? __ldg(reinterpret_cast<const uint4*>(P.planes + ((size_t)mm * ng + g0) * 8) + q) : z;
+            }
+            __syncthreads();
+            for (int g = 0; g < gc; ++g) {
+                uint4 a0[PP], a1[PP], b0[PP], b1[PP];
+#pragma unroll
+                for (int r = 0; r < PP; ++r) {
+                    const uint4* ar = reinterpret_cast<const uint4*>(pa + (ty + 16 * r) * PLS + 8 * g);
+                    const uint4* br = reinterpret_cast<const uint4*>(pb + (tx + 16 * r) * PLS + 8 * g);
+                    a0[r] = ar[0];
+                    a1[r] = ar[1];
+                    b0[r] = br[0];
+                    b1[r] = br[1];
+                }
+#pragma unroll
+                for (int a = 0; a < PP; ++a)
+#pragma unroll
+                    for (int b = 0; b < PP; ++b) {
+                        const uint32_t x = (a0[a].x ^ b0[b].x) | (a0[a].y ^ b0[b].y) | (a0[a].z ^ b0[b].z) |
+                                           (a0[a].w ^ b0[b].w) | (a1[a].x ^ b1[b].x) | (a1[a].y ^ b1[b].y) |
+                                           (a1[a].z ^ b1[b].z);
+                        mis[a][b] += __popc(x);
+                    }
+            }
+        }
+    }
+    for (int w0 = 0; w0 < (from_gemm || planes ? 0 : Dw); w0 += PAIR_CW) {
         const int cw = min(PAIR_CW, Dw - w0);
         __syncthreads();
         for (int e = tid; e < PT * cw; e += PAIR_THREADS) {
@@ -270,7 +329,7 @@ __device__ __forceinline__ void pairs_block(const tc_kparams& P, int blk) {
                     mt = mg[a][b];
                     P.M32[(size_t)i * P.ldm + m] = 0.f;
                 } else {
-                    mt = (int)(wide[a][b] >> 7) - pad;
+                    mt = planes ? D - mis[a][b] : (int)(wide[a][b] >> 7) - pad;
                 }
                 // a count of shared colours: the tables hold mt_max + 1 entries
                 mt = min(max(mt, 0), P.mt_max);
@@ -1378,7 +1437,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
             P.S8T[co * P.n_pad + i] = 0;
             P.S8T[cn * P.n_pad + i] = 0x38;
         }
-        store_colour(P, d, i, newc);
+        store_colour(P, d, i, cur, newc);
     }
 }
 
@@ -1533,10 +1592,33 @@ cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k
     return cudaGetLastError();
 }
 
+// The bit planes from the colours: one warp per (vertex, group of 32
+// individuals), a ballot per bit.
+__global__ void k_planes(tc_kparams P) {
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (long long)P.n * P.png) return;
+    const int i = (int)(wid / P.png), g = (int)(wid % P.png), d = 32 * g + lane;
+    const unsigned c = d < P.D ? P.c[(size_t)d * P.n + i] : 0u;
+    unsigned mine = 0u;
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+        const unsigned b = __ballot_sync(0xffffffffu, (c >> p) & 1u);
+        if (lane == p) mine = b;
+    }
+    if (lane < 8) P.planes[((size_t)i * P.png + g) * 8 + lane] = mine;  // plane 7: 0
+}
+
 cudaError_t tc_launch_assign(const tc_kparams& P, cudaStream_t s) {
     const long long rows = (long long)P.D * P.n;
     k_assign<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(P);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && P.planes) {
+        const long long warps = (long long)P.n * P.png;
+        k_planes<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(P);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t tc_launch_pairs(const tc_kparams& P, cudaStream_t s) {

@@ -41,6 +41,7 @@ struct tc_ctx {
     float* d_W = nullptr;
     uint16_t* d_c = nullptr;
     uint16_t* d_csnap = nullptr;
+    uint32_t* d_planes = nullptr;  // bit planes of the colours (k <= 128; k_pairs' compares)
     uint16_t* d_cT = nullptr;
     float* d_B = nullptr;
     float* d_Gbuf = nullptr;  // grad_S L tiles between k_gsum and k_update
@@ -187,6 +188,7 @@ void free_population(tc_ctx* c) {
     dfree(c->d_W);
     dfree(c->d_c);
     dfree(c->d_csnap);
+    dfree(c->d_planes);
     dfree(c->d_cT);
     dfree(c->d_B);
     dfree(c->d_Gbuf);
@@ -270,6 +272,10 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     P.c = c->d_c;
     P.c_snap = c->d_csnap;
     P.cT = c->d_cT;
+    // the bit planes are kept with every colour store while k <= 128 and one
+    // colour per vertex; the colour assignment rebuilds them
+    P.png = (c->D + 31) / 32;
+    P.planes = c->k <= 128 && c->cmax == 0 ? c->d_planes : nullptr;
     P.adj = c->d_adj;
     P.rowptr = c->d_rowptr;
     P.colidx = c->d_colidx;
@@ -1159,7 +1165,7 @@ int tc_init_population(tc_ctx* c, uint64_t seed, int D, int k, const tc_params* 
     const int Dp = (D + 3) & ~3;
     const size_t Wtiled = (size_t)D * ((n + TC_WT - 1) / TC_WT) * TC_WT * k;
     if ((rc = dalloc(&c->d_W, Wtiled)) || (rc = dalloc(&c->d_c, (size_t)D * n)) || (rc = dalloc(&c->d_csnap, (size_t)D * n)) ||
-        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
+        (rc = dalloc(&c->d_cT, (size_t)n * Dp)) || (rc = dalloc(&c->d_planes, (size_t)n * ((D + 31) / 32) * 8)) || (rc = dalloc(&c->d_B, (size_t)(n + 1) * ((n + 3) & ~3))) ||
         (rc = dalloc(&c->d_Gbuf, (size_t)D * ((n + 31) / 32) * 32 * k)) ||
         (rc = dalloc(&c->d_rec, (size_t)D * rec_stride_for(n, k, 0, 0))) || (rc = dalloc(&c->d_z, (size_t)k)) || (rc = dalloc(&c->d_fcolor, D)) ||
         (rc = dalloc(&c->d_feq, D)) || (rc = dalloc(&c->d_loss_part, 2 * (size_t)c->n_tiles)) ||
