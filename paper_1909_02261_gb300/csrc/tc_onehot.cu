@@ -1704,8 +1704,11 @@ cudaError_t tc_launch_update(const tc_kparams& P, int num_sms, cudaStream_t s, i
     int S = (int)std::min<long long>(UPD_MAX_STAGES, (kSmemOptin - 1024ll) / per_stage);
     if (S < 1) return cudaErrorInvalidValue;
     // groups of UPD_GW warps, three stages loading ahead of them (at the
-    // benchmark shape 9 stages: 3, 4, 5 groups measured 50.9, 43.5, 42.6 us)
-    int pairs = S >= 4 ? std::min(UPD_MAX_GROUPS, S - 3) : 1;
+    // benchmark shape 9 stages: 3, 4, 5 groups measured 50.9, 43.5, 42.6 us);
+    // with fewer than four stages (k above ~220) one stage loads ahead of
+    // S - 1 groups (k = 230: 3 stages, 2 groups 78.9 us against 137.5 us for
+    // one group)
+    int pairs = S >= 4 ? std::min(UPD_MAX_GROUPS, S - 3) : std::max(1, S - 1);
     while (S > 1 && upd_smem_bytes(P.k, S, pairs) > kSmemOptin) --S;
     if (upd_smem_bytes(P.k, S, pairs) > kSmemOptin) return cudaErrorInvalidValue;
     const int smem = (int)upd_smem_bytes(P.k, S, pairs);
