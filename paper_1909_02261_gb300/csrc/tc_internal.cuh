@@ -50,6 +50,7 @@ struct tc_kparams {
     int problem, nb_iter, bonus_diag, stop_on_legal, commit;
     long long n_edges;  // |E| (the partitioning fitness is |E| - f_color)
     int csr_walk;     // grad_S L by adjacency lists (mu = 0, sparse graph)
+    int max_degree;   // largest vertex degree (the staged adjacency walk's [degree][32] tiles)
     float eta, rho, lambda_, mu, nu, alpha, beta;
     float* W;                 // weights, tile-transposed (tc_w_index)
     uint16_t* c;              // D x n colours

@@ -1024,11 +1024,50 @@ __device__ __forceinline__ void prefetch_item(const uint32_t* pm, int plen, cons
     }
 }
 
+// The same sums on shared-memory copies: the tile's adjacency entries, entry
+// t of row r at t * 32 + r (col: neighbour, bv: pair coefficient; staged
+// once per tile for all its items, so the 32 lanes read one contiguous line
+// per step), and the individual's colours (cw, staged once per item); vertex
+// i0 + lane walks its own deg entries, the warp to the tile's largest degree.
+__device__ __forceinline__ int neighbour_sums_staged(const uint16_t* col, const float* bv, const uint16_t* cw,
+                                                     int deg, int tmax, const float* Ed, const uint16_t* grow,
+                                                     float gs, int gstride, float nut, int k, float* Gs, int i0,
+                                                     int lane, bool valid) {
+    for (int j = 0; j < k; ++j) {
+        float g0 = nut * __ldg(Ed + j);
+        if (grow) g0 += gs * (float)__ldg(grow + (size_t)j * gstride);
+        Gs[j * 32] = g0;
+    }
+    const int ci = valid ? cw[i0 + lane] : -1;
+    int conf = 0;
+    for (int t = 0; t < tmax; t += 4) {  // four entries' loads ahead of their additions
+        int c[4];
+        float b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            c[u] = -1;
+            b[u] = 0.f;
+            if (t + u < deg) {
+                c[u] = cw[col[(t + u) * 32 + lane]];
+                b[u] = bv[(t + u) * 32 + lane];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (c[u] >= 0) {
+                Gs[c[u] * 32] += b[u];
+                conf += c[u] == ci;
+            }
+    }
+    return valid ? conf : 0;
+}
+
 // ---------------------------------------------------------------------------
 // k_gsum: one block per SM, 16 warps (the adjacency walk keeps a shared
 // 32 x k accumulator per warp and runs fewer).
 // ---------------------------------------------------------------------------
 constexpr int GSUM_MAX_WARPS = 30;  // the staged class walk: 15 warp pairs (named barriers 1..15)
+constexpr int GSUM_CSR_WARPS = 32;  // the adjacency walk: one warp per item, no named barriers
 
 // Staging (STG): the item's colour-sorted vertices, class offsets and equity
 // terms, copied to shared memory once per item by the PAIR of warps that
@@ -1051,7 +1090,7 @@ __host__ __device__ inline long long gsum_chunk_item(long long c, int cpt, int D
 // DN: the dense forms' gamma matrix (and the multicolouring's colour sets)
 // may be present; without it their code is compiled out of the one-hot walk.
 template <bool BTS, bool CSR, bool STG, bool DN>
-__global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
+__global__ void __launch_bounds__((CSR ? GSUM_CSR_WARPS : GSUM_MAX_WARPS) * 32, 1)
     k_gsum(tc_kparams P, const __grid_constant__ CUtensorMap tmB, int dbuf) {
     // dbuf (STG): two record buffers per warp pair, the next item's record
     // arriving by one bulk copy while the pair walks the current one
@@ -1075,7 +1114,18 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nbox = (n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS;  // rows 0..n, row n zero
     float* Bt = sm;
-    float* Gw = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + (size_t)warp * 32 * k;  // CSR only
+    // CSR: the per-warp grad_S tiles; staged (dbuf = 1): after the tile's
+    // adjacency entries (neighbours, pair coefficients), and each warp's
+    // tile followed by its copy of the individual's colours
+    const bool cstaged = CSR && dbuf;
+    const int ce_words = cstaged ? 16 * P.max_degree + 32 * P.max_degree : 0;  // [deg][32] uint16, then FP32
+    const int cw_words = cstaged ? ((n + 7) / 8) * 4 : 0;
+    uint16_t* s_col = reinterpret_cast<uint16_t*>(sm);
+    float* s_bv = sm + 16 * P.max_degree;
+    float* Gw = sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0) + ce_words +
+                (size_t)warp * (32 * k + cw_words);  // CSR only
+    uint16_t* cw = reinterpret_cast<uint16_t*>(Gw + 32 * k);
+    __shared__ int s_rp[33];
     const int unit = STG ? warp >> 1 : warp, nunits = STG ? nw >> 1 : nw, h = STG ? (warp & 1) : 0;
     const int sw = gsum_stage_words(P.perm_stride, k);
     uint32_t* const psb = reinterpret_cast<uint32_t*>(sm + (BTS ? (size_t)nbox * TC_BT_BOX_ROWS * 32 : 0)) +
@@ -1155,6 +1205,25 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
         // previous panel before the barrier below lets the next one start.
         bool panel_pending = false;
         unsigned seg_phase = 0;
+        if (cstaged) {  // the tile's adjacency entries: lane = row, warp w takes the steps t = w, w + nw, ...
+            const int i = T * 32 + lane;
+            __syncthreads();  // every warp is done with the previous tile's entries
+            const int a = i < n ? __ldg(P.rowptr + i) : 0, deg = i < n ? __ldg(P.rowptr + i + 1) - a : 0;
+            int tmax = deg;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            if (warp == 0) {
+                s_rp[lane] = deg;
+                if (lane == 0) s_rp[32] = tmax;
+            }
+            for (int t = warp; t < tmax; t += nw)
+                if (t < deg) {
+                    const int m = __ldg(P.colidx + a + t);
+                    s_col[t * 32 + lane] = (uint16_t)m;
+                    s_bv[t * 32 + lane] = __ldg(P.B + (size_t)i * P.ldb + m);
+                }
+            __syncthreads();
+        }
         if (BTS) {
             if (!first) {
                 __syncthreads();  // every pair is done with the previous panel
@@ -1230,8 +1299,22 @@ __global__ void __launch_bounds__(GSUM_MAX_WARPS * 32, 1)
                     if (live) conf = own_class_conflicts<true>(ps, os, ci, Bt + lane, 32, gs);
                 }
             } else if (CSR) {
-                conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, gs, gstride, Bl,
-                                      bstride, nut, k, Gw + lane, i0 + lane, live);
+                if (cstaged) {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(P.c_snap + (size_t)d * n);
+                    uint32_t* dst = reinterpret_cast<uint32_t*>(cw);
+                    if ((((size_t)d * n) & 1) == 0)  // 4-byte aligned row
+                        for (int x = lane; x < n / 2; x += 32) dst[x] = __ldg(src + x);
+                    else
+                        for (int x = lane; x < n / 2; x += 32)
+                            cw[2 * x] = P.c_snap[(size_t)d * n + 2 * x], cw[2 * x + 1] = P.c_snap[(size_t)d * n + 2 * x + 1];
+                    if ((n & 1) && lane == 0) cw[n - 1] = P.c_snap[(size_t)d * n + n - 1];
+                    __syncwarp();
+                    conf = neighbour_sums_staged(s_col, s_bv, cw, s_rp[lane], s_rp[32], Ed, grow, gs, gstride, nut, k,
+                                                 Gw + lane, i0, lane, live);
+                } else {
+                    conf = neighbour_sums(P.rowptr, P.colidx, P.c_snap + (size_t)d * n, Ed, grow, gs, gstride, Bl,
+                                          bstride, nut, k, Gw + lane, i0 + lane, live);
+                }
                 __syncwarp();
                 for (int j = 0; j < k; ++j) Gout[j * 32] = Gw[j * 32 + lane];
                 __syncwarp();
@@ -1667,6 +1750,21 @@ static cudaError_t launch_gsum_t(const tc_kparams& P, const CUtensorMap& tmB, in
 cudaError_t tc_launch_gsum(const tc_kparams& P, const CUtensorMap& tmB, int num_sms, cudaStream_t s) {
     const long long bt = 4ll * 32 * ((P.n + TC_BT_BOX_ROWS) / TC_BT_BOX_ROWS) * TC_BT_BOX_ROWS;
     const long long stage = 4ll * gsum_stage_words(P.perm_stride, P.k);
+    if (P.csr_walk && P.n < 65536) {
+        // the staged adjacency walk: the tile's entries ([degree][32] uint16
+        // neighbours and FP32 pair coefficients) once per tile, then per warp
+        // its grad_S tile and the individual's colours (G(1000, 0.1), k = 25,
+        // D = 128: 64.2 -> 35.0 us; entries read from global memory before)
+        const long long ce = 4ll * 48 * P.max_degree;  // [max degree][32] uint16 + FP32
+        const long long pw = 4ll * (32ll * P.k + ((P.n + 7) / 8) * 4);
+        // 32 warps: D = 128 items per tile make 4 chunks of 32, one round per
+        // block (30 warps made 5 chunks of ~26 and two rounds for some blocks)
+        const long long w = std::min<long long>(GSUM_CSR_WARPS, (kSmemOptin - ce) / pw);
+        if (w >= 8) {
+            const int smem = (int)std::max(ce + w * pw, 2048ll);
+            return launch_gsum_t<false, true, false>(P, tmB, num_sms, (int)w, smem, 1, s);
+        }
+    }
     long long per_warp = P.csr_walk ? 4ll * 32 * P.k : 0;
     const bool bts = bt + per_warp <= kSmemOptin;
     const long long base = bts ? bt : 0;

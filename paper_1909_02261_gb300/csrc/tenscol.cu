@@ -28,6 +28,7 @@ struct tc_ctx {
     // graph
     int n = 0;
     long long nnz = 0;
+    int max_degree = 0;      // largest vertex degree
     int* d_rowptr = nullptr;
     int* d_colidx = nullptr;
     uint32_t* d_adj = nullptr;
@@ -305,6 +306,7 @@ tc_kparams make_kparams(tc_ctx* c, int commit) {
     // with mu = 0 the pair matrix vanishes off the edges; below a density of
     // 1/8 walking the adjacency lists beats walking all n vertices per class
     P.csr_walk = c->p.mu == 0.0f && c->nnz * 8 < (long long)c->n * c->n && c->cmax == 0;
+    P.max_degree = c->max_degree;
     if (c->trace_cap > 0) {
         P.trace = c->d_trace;
         P.trace_cap = c->trace_cap;
@@ -1141,6 +1143,8 @@ int tc_init_graph(tc_ctx* c, int n, const int32_t* rowptr, const int32_t* colidx
     }
     c->n = n;
     c->nnz = (long long)ci.size();
+    c->max_degree = 0;
+    for (int i = 0; i < n; ++i) c->max_degree = std::max(c->max_degree, rp[i + 1] - rp[i]);
     c->adj_words = aw;
     c->h_rowptr = rp;
     c->h_colidx = ci;
