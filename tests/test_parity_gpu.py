@@ -94,7 +94,7 @@ def test_ecp_step(n, k):
 @pytest.mark.parametrize("n,p_edge,problem", [
     (1700, 0.3, TC_KCOL),   # B columns of a tile in shared memory, class lists read from global memory
     (2000, 0.3, TC_KCOL),   # B read from global memory (the panel no longer fits), class lists staged
-    (2000, 0.01, TC_ECP),   # mu = 0 on a sparse graph: adjacency-list walk, B from global memory
+    (2000, 0.01, TC_ECP),   # mu = 0 on a sparse graph: the adjacency walk on shared-memory tiles
 ])
 def test_large_n_gradient_paths(n, p_edge, problem):
     """k_gsum's variants past the shared-memory sizes of the benchmark."""
