@@ -797,7 +797,12 @@ __device__ __forceinline__ void class_sums(const uint32_t* pm, const int* of, co
             a2 += Bl[(int)v.z * bs];
             a3 += Bl[(int)v.w * bs];
         }
-        Gout[j * 32] = ((a0 + a1) + (a2 + a3)) + extra;
+        // (B from global memory: the grad_S tiles stream past L2, which then
+        // keeps more of B's columns)
+        if (BS == 0)
+            __stcs(Gout + j * 32, ((a0 + a1) + (a2 + a3)) + extra);
+        else
+            Gout[j * 32] = ((a0 + a1) + (a2 + a3)) + extra;
         s = e;
         e = e_next;
     }
