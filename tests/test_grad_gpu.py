@@ -30,7 +30,7 @@ def ctx_for(rp, ci, D, k, p):
     return c
 
 
-@pytest.mark.parametrize("n,D,k,form", [(125, 20, 18, 0), (300, 9, 130, 0), (125, 20, 18, TC_FORM_DENSE_FP8)])
+@pytest.mark.parametrize("n,D,k,form", [(125, 20, 18, 0), (300, 9, 130, 0), (100, 6, 240, 0), (125, 20, 18, TC_FORM_DENSE_FP8)])
 def test_straight_through_backward_is_the_step(n, D, k, form):
     rp, ci = inputs.gnp(n, 0.5, seed=3)
     W = inputs.init_weights(D, n, k, 0.02, seed=4)
