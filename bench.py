@@ -626,7 +626,9 @@ def run_ours(args):
         peak_lds = sms * 32 * mhz * 1e6 / 1e9
         gsum_roof = {"bound": "alu", "kernel": "k_gsum", "achieved": ach, "peak": peak_lds,
                      "unit": "Gadd/s", "frac": ach / peak_lds, "work_per_launch": adds,
-                     "peak_source": f"{sms} SMs x 32 shared-memory loads per clock x {mhz:.0f} MHz"}
+                     "peak_source": f"{sms} SMs x 32 shared-memory loads per clock x {mhz:.0f} MHz: the ceiling "
+                                    "of the gather schedule (one 4-byte shared load per addition), not of the "
+                                    "method; the FP32 pipe (128 lanes per SM) would allow 4 x that"}
 
     # the tensor-core alternative of Step 3-ii at this shape (vendor library)
     tc3 = None

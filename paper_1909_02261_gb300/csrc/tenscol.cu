@@ -17,6 +17,10 @@
 
 #include "tc_internal.cuh"
 
+// NVTX ranges (header-only; inert unless a profiler is attached): one per
+// iteration and one per kernel launch, named as the kernel timing names them
+#include <nvtx3/nvToolsExt.h>
+
 struct tc_batch;
 
 struct tc_ctx {
@@ -713,7 +717,14 @@ cudaEvent_t take_event(tc_ctx* c) {
     return e;
 }
 
-// Launches one kernel through `fn`, bracketed by timing events when enabled.
+const char* kernel_name(int kid) {
+    static const char* names[TC_NUM_KID] = {"k_pairs", "k_classes", "k_update", "gemm_mtilde",
+                                            "gemm_gamma", "k_gsum", "gemm_fused", "k_front"};
+    return kid >= 0 && kid < TC_NUM_KID && names[kid] ? names[kid] : "kernel";
+}
+
+// Launches one kernel through `fn`, bracketed by timing events when enabled
+// and by an NVTX range.
 template <typename F>
 cudaError_t timed(tc_ctx* c, int kid, F fn, cudaStream_t s = nullptr) {
     if (!s) s = c->stream;
@@ -721,7 +732,9 @@ cudaError_t timed(tc_ctx* c, int kid, F fn, cudaStream_t s = nullptr) {
     cudaEvent_t a = on ? take_event(c) : nullptr;
     cudaEvent_t b = on ? take_event(c) : nullptr;
     if (a && b) cudaEventRecord(a, s);
+    nvtxRangePushA(kernel_name(kid));
     cudaError_t e = fn();
+    nvtxRangePop();
     if (a && b) {
         cudaEventRecord(b, s);
         c->pending.push_back({kid, a, b});
@@ -805,8 +818,17 @@ cudaError_t launch_grad_update(tc_ctx* c, const tc_kparams& P, int debug_only) {
     return e;
 }
 
+int launch_iteration_body(tc_ctx* c);
+
 int launch_iteration(tc_ctx* c) {
     if (fault("launch")) return TC_ERR_INJECTED;
+    nvtxRangePushA("tc_iteration");
+    const int rc = launch_iteration_body(c);
+    nvtxRangePop();
+    return rc;
+}
+
+int launch_iteration_body(tc_ctx* c) {
     tc_kparams P = make_kparams(c, 1);
     const bool dense = P.M32 != nullptr;
     int rc;
