@@ -913,48 +913,122 @@ __device__ __forceinline__ float4 walk_result(uint64_t acc01, uint64_t acc23, fl
     return make_float4(x + ex, y + ex, z + ex, w + ex);
 }
 
+// The chunks c = 0, 4, ... < m of entries c0 + c of the class at p0 of the
+// list (entries at or past len: the padding chunk); m is the same in the
+// whole warp, so the groups run in lockstep.  TC_BOUNDS builds check every
+// vertex index against the panel (rows 0 .. n) and skip a chunk that names
+// another row, recording TC_ERR_DEVICE_BOUNDS in *err.
+__device__ __forceinline__ void walk_chunks(const uint32_t* list, const uint32_t* zchunk, uint32_t lists,
+                                            uint32_t zcs, uint32_t colb, int p0, int c0, int len, int m, int nmax,
+                                            int* err, uint64_t& a01, uint64_t& a23) {
+    const uint32_t srcb = lists + 4u * (uint32_t)(p0 + c0);
+#pragma unroll 1
+    for (int c = 0; c < m; c += 4) {
+        const bool in = c0 + c < len;
+#if TC_BOUNDS
+        const uint4 v = *reinterpret_cast<const uint4*>(in ? list + p0 + c0 + c : zchunk);
+        if (v.x > (uint32_t)nmax || v.y > (uint32_t)nmax || v.z > (uint32_t)nmax || v.w > (uint32_t)nmax) {
+            atomicCAS(err, 0, TC_ERR_DEVICE_BOUNDS);
+            continue;
+        }
+#else
+        (void)list;
+        (void)zchunk;
+        (void)nmax;
+        (void)err;
+#endif
+        walk_chunk(in ? srcb + 4u * (uint32_t)c : zcs, colb, a01, a23);
+    }
+}
+
+// Classes of at least SW_LONG entries lead the class order.  Side by side
+// with short classes they would leave three groups of their warp walking
+// padding: after the smoothing of Step 4-iv the weights are a hundredth of
+// their size, the next update moves about one colour in seven, and a few
+// classes of hundreds of vertices follow (the iteration after it took 13 us
+// longer in the walk at the benchmark shape).  Each such class is walked by
+// the four groups of one warp, a quarter of its chunks each, and their sums
+// combined by two shuffles in a fixed order; it goes to the warp of the pair
+// with fewer chunks so far (warp 0 on ties), the same choice in both warps.
+constexpr int SW_LONG = 32;
+
 // TC_BOUNDS builds check the record the walk reads (class order, offsets,
 // vertex indices <= n) and replace what is out of range, recording
 // TC_ERR_DEVICE_BOUNDS in *err instead of reading outside the record or panel.
+__device__ __forceinline__ bool class_ok(int j, int p0, int len, int k, int plen, int* err) {
+#if TC_BOUNDS
+    if (j < 0 || j >= k || p0 < 0 || len < 0 || p0 + len > plen || (len & 3)) {
+        atomicCAS(err, 0, TC_ERR_DEVICE_BOUNDS);
+        return false;
+    }
+#else
+    (void)j;
+    (void)p0;
+    (void)len;
+    (void)k;
+    (void)plen;
+    (void)err;
+#endif
+    return true;
+}
+
 __device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
                                           const float* xs, const uint32_t* zchunk, float nut, const float* panel,
                                           int k, int h, int lane, float* gtile, int nmax, int plen, int* err) {
     const int grp = lane >> 3, l8 = lane & 7;
     const uint32_t colb = smem_u32(panel) + 16u * (uint32_t)l8, lists = smem_u32(list), zcs = smem_u32(zchunk);
-    const int nslots = (k + 7) >> 3;
+    int nlong = 0;
+    while (nlong < k) {
+        const int j = cord[nlong];
+#if TC_BOUNDS
+        if (j >= k) break;  // reported by the slots below
+#endif
+        if (of[j + 1] - of[j] < SW_LONG) break;
+        ++nlong;
+    }
+    int w0 = 0, w1 = 0;  // chunks per group given to each warp
+    for (int i = 0; i < nlong; ++i) {
+        const int j = cord[i], p0 = of[j], len = of[j + 1] - p0;
+        if (!class_ok(j, p0, len, k, plen, err)) continue;
+        const int per = 4 * (((len >> 2) + 3) >> 2);  // entries per group
+        const int w = w1 < w0 ? 1 : 0;
+        if (w)
+            w1 += per;
+        else
+            w0 += per;
+        if (w != h) continue;
+        uint64_t a01 = 0ull, a23 = 0ull;
+        walk_chunks(list, zchunk, lists, zcs, colb, p0, grp * per, len, per, nmax, err, a01, a23);
+        float4 r = walk_result(a01, a23, -0.0f);  // (x + -0 = x)
+        r.x += __shfl_xor_sync(0xffffffffu, r.x, 8);
+        r.y += __shfl_xor_sync(0xffffffffu, r.y, 8);
+        r.z += __shfl_xor_sync(0xffffffffu, r.z, 8);
+        r.w += __shfl_xor_sync(0xffffffffu, r.w, 8);
+        r.x += __shfl_xor_sync(0xffffffffu, r.x, 16);
+        r.y += __shfl_xor_sync(0xffffffffu, r.y, 16);
+        r.z += __shfl_xor_sync(0xffffffffu, r.z, 16);
+        r.w += __shfl_xor_sync(0xffffffffu, r.w, 16);
+        if (grp == 0) {
+            const float ex = nut * xs[j];
+            __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8),
+                   make_float4(r.x + ex, r.y + ex, r.z + ex, r.w + ex));
+        }
+    }
+    const int nslots = (k - nlong + 7) >> 3;
     for (int s = 0; s < nslots; ++s) {
-        const int pos = 8 * s + 4 * h + grp;
+        const int pos = nlong + 8 * s + 4 * h + grp;
         int j = pos < k ? (int)cord[pos] : -1;
         int p0 = j >= 0 ? of[j] : 0;
         int len = j >= 0 ? of[j + 1] - p0 : 0;
-#if TC_BOUNDS
-        if (j >= k || p0 < 0 || len < 0 || p0 + len > plen || (len & 3)) {
-            atomicCAS(err, 0, TC_ERR_DEVICE_BOUNDS);
+        if (j >= 0 && !class_ok(j, p0, len, k, plen, err)) {
             j = -1;
             p0 = 0;
             len = 0;
         }
-#else
-        (void)nmax;
-        (void)plen;
-        (void)err;
-#endif
         int m = max(len, __shfl_xor_sync(0xffffffffu, len, 8));
         m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
         uint64_t a01 = 0ull, a23 = 0ull;  // +0.0f pairs
-        const uint32_t srcb = lists + 4u * (uint32_t)p0;
-#pragma unroll 1
-        for (int c = 0; c < m; c += 4) {
-#if TC_BOUNDS
-            // the chunk's vertex indices must name a panel row (0 .. n)
-            const uint4 v = *reinterpret_cast<const uint4*>(c < len ? list + p0 + c : zchunk);
-            if (v.x > (uint32_t)nmax || v.y > (uint32_t)nmax || v.z > (uint32_t)nmax || v.w > (uint32_t)nmax) {
-                atomicCAS(err, 0, TC_ERR_DEVICE_BOUNDS);
-                continue;
-            }
-#endif
-            walk_chunk(c < len ? srcb + 4u * (uint32_t)c : zcs, colb, a01, a23);
-        }
+        walk_chunks(list, zchunk, lists, zcs, colb, p0, 0, len, m, nmax, err, a01, a23);
         if (j >= 0)
             __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8), walk_result(a01, a23, nut * xs[j]));
     }
@@ -1476,6 +1550,10 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
     const float num = (xa[32 + lane] + xa[96 + lane]) + (xa[160 + lane] + xa[224 + lane]);
     const float invZ = 1.0f / Z;
     const float dot = num * invZ;  // (S^ (.) grad_S L) . J of eq. 12
+    // Step 4-iv: W / rho as a product with the rounded reciprocal (within
+    // one rounding of the quotient; the IEEE division cost 7.7 us in every
+    // smoothing iteration at the benchmark shape)
+    const float rrho = 1.0f / P.rho;
     float bestv = -INFINITY;
     int newc = jb;
     if (live) {
@@ -1491,7 +1569,7 @@ __device__ __forceinline__ void update_item(const tc_kparams& P, float* Gs, floa
                 continue;
             }
             float wn = __fsub_rn(w, __fmul_rn(P.eta, gw));
-            if (smooth) wn = __fdiv_rn(wn, P.rho);
+            if (smooth) wn = __fmul_rn(wn, rrho);
             wr[j * 32] = wn;
             if (wn > bestv) {  // first maximum wins
                 bestv = wn;
