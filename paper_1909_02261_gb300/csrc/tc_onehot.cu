@@ -864,13 +864,16 @@ __device__ __forceinline__ void class_sums_shared(uint32_t pm, const int* of, co
 // 4 l8 .. 4 l8 + 3, so one 16-byte load of panel row m brings
 // B[m][4 l8 .. 4 l8 + 3] = B[i][m] for its four rows (B is symmetric) and a
 // group's 8 loads of one vertex are one 128-byte line.  k_classes lists each
-// individual's classes by decreasing padded length (cord); in slot s the
-// group g (0..3) of warp h of the pair sums the class at position
-// 8 s + 4 h + g of that list, so the four classes a warp walks side by side
+// individual's classes by decreasing padded length (cord).  Classes of at
+// least SW_LONG entries (they come first) are walked one at a time by the
+// four groups of a warp; the others form quads, consecutive in that order,
+// whose four classes the four groups of a warp walk side by side, so they
 // have nearly equal lengths.  The warp loops to the longest of the four; a
 // group whose class is shorter reads a chunk of padding vertices (the zero
 // row n of B) instead of branching, and all four groups store their class
-// sums together at the end of the slot.
+// sums together at the end of the quad.  Each long class goes to the warp of
+// the pair with fewer long-class entries so far; the quads alternate between
+// the two warps.
 // ---------------------------------------------------------------------------
 // One 4-entry chunk of a class walk, on 32-bit shared-memory addresses:
 // the chunk's vertex indices v0..v3 at `src`, and for each the 16 bytes
@@ -1014,6 +1017,11 @@ __device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, c
                    make_float4(r.x + ex, r.y + ex, r.z + ex, r.w + ex));
         }
     }
+    // the other classes four side by side: in slot s, group g of warp h
+    // walks the class at position nlong + 8 s + 4 h + g (quads of nearly
+    // equal lengths, alternating between the warps: handing each quad to
+    // the warp with fewer entries so far took 57.1 against 53.2 us at the
+    // benchmark shape, the extra per-quad work outweighing the balance)
     const int nslots = (k - nlong + 7) >> 3;
     for (int s = 0; s < nslots; ++s) {
         const int pos = nlong + 8 * s + 4 * h + grp;

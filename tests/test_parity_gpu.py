@@ -62,6 +62,31 @@ def test_ragged_and_degenerate_shapes(n, p_edge, D, k):
         check_iteration(ctx, rp, ci, p, 9)
 
 
+@pytest.mark.parametrize("sizes,t", [
+    ([75, 75, 75, 75], 3),                       # every class long: whole-warp walks only
+    ([212] + [4] * 22, 4),                       # one class of 212 beside short ones (smoothing step)
+    ([32, 31, 33, 28, 36, 64, 1, 2, 3, 30], 3),  # lengths around the 32-entry threshold
+    ([200, 40, 40, 40, 40, 40] + [7] * 12, 9),   # long classes split unevenly between the two warps
+])
+def test_long_classes_in_the_class_walk(sizes, t):
+    """Designed colour classes: the class walk hands classes of 32 entries or
+    more to the four lane groups of one warp and the rest four side by side;
+    both must give the oracle's gradient rows and W step."""
+    n, k, D = sum(sizes), len(sizes), 6
+    rp, ci = inputs.gnp(n, 0.5, seed=n + k)
+    rng = np.random.default_rng(k)
+    W = rng.normal(0.0, 0.01, (D, n, k)).astype(np.float32)
+    for d in range(D):  # individual d: the classes' sizes in a permuted order of colours
+        cols = np.repeat(rng.permutation(k), np.array(sizes)[np.arange(k)])[rng.permutation(n)]
+        W[d, np.arange(n), cols] += 1.0
+    p = params(TC_KCOL, stop_on_legal=0, lambda_=1e-3, mu=1e-3)
+    with make_ctx(rp, ci, D, k, p, W, t) as ctx:
+        ev = ctx.tc_evaluate(want_G=False, want_M=False)
+        for d in range(D):
+            assert sorted(np.bincount(ev["colors"][d], minlength=k).tolist()) == sorted(sizes)
+        check_iteration(ctx, rp, ci, p, t)
+
+
 def test_ties_take_lowest_colour():
     rp, ci = inputs.gnp(50, 0.4, seed=2)
     rng = np.random.default_rng(0)
