@@ -159,6 +159,10 @@ __host__ __device__ inline size_t tc_gamma_index(int d, int i, int j, int n_pad,
 // src (standard D x n x k) -> dst (tiled) when to_tiled, else back.
 cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k, bool to_tiled,
                                cudaStream_t s);
+// The same conversion by (individual, 32-row tile) blocks, whole lines on both
+// sides (for host memory the device reads or writes directly);
+// cudaErrorInvalidValue when a tile does not fit 48 KB of shared memory.
+cudaError_t tc_launch_w_tiles(const float* src, float* dst, int D, int n, int k, bool to_tiled, cudaStream_t s);
 
 // Programmatic dependent launch: a kernel launched with tc_launch_pdl may be
 // scheduled while the previous kernel on the stream still runs; pdl_wait()

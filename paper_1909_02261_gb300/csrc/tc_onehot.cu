@@ -124,6 +124,42 @@ __global__ void k_w_layout(const float* src, float* dst, int D, int n, int k, bo
         dst[e] = src[t];
 }
 
+// The same conversion one (individual, 32-row tile) per block: the tile's
+// rows are one contiguous block of 32 k weights in either layout, so both
+// sides are read and written in whole lines (host memory reached over the
+// chip-to-chip link included), the transpose going through shared memory
+// (32 x (k + 1) floats: an odd row stride for even k, so neither phase has
+// bank conflicts worth counting).
+__global__ void k_w_tiles(const float* src, float* dst, int n, int k, bool to_tiled) {
+    extern __shared__ float tl[];
+    const int nT = (n + TC_WT - 1) / TC_WT;
+    const long long b = blockIdx.x;  // d nT + T
+    const int d = (int)(b / nT), T = (int)(b - (long long)d * nT);
+    const int rows = min(TC_WT, n - T * TC_WT), ld = k + 1;
+    const size_t s0 = ((size_t)d * n + (size_t)T * TC_WT) * k, t0 = (size_t)b * k * TC_WT;
+    if (to_tiled) {
+        for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
+            const int r = e / k;
+            tl[r * ld + (e - r * k)] = src[s0 + e];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < TC_WT * k; e += blockDim.x) {
+            const int j = e / TC_WT, r = e - j * TC_WT;
+            dst[t0 + e] = r < rows ? tl[r * ld + j] : 0.f;
+        }
+    } else {
+        for (int e = threadIdx.x; e < TC_WT * k; e += blockDim.x) {
+            const int j = e / TC_WT, r = e - j * TC_WT;
+            tl[r * ld + j] = src[t0 + e];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
+            const int r = e / k;
+            dst[s0 + e] = tl[r * ld + (e - r * k)];
+        }
+    }
+}
+
 // Step 1 (Section 3.4) for a fresh W: c_d(i) = lowest j with maximal w.
 // ---------------------------------------------------------------------------
 // old: the colour being replaced (the bit planes change by its difference)
@@ -1763,6 +1799,14 @@ cudaError_t tc_launch_w_layout(const float* src, float* dst, int D, int n, int k
                                cudaStream_t s) {
     const long long total = (long long)D * ((n + TC_WT - 1) / TC_WT) * k * TC_WT;
     k_w_layout<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, dst, D, n, k, to_tiled);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_w_tiles(const float* src, float* dst, int D, int n, int k, bool to_tiled, cudaStream_t s) {
+    const size_t smem = sizeof(float) * TC_WT * ((size_t)k + 1);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;  // (k > 374: the element-wise conversion)
+    const long long blocks = (long long)D * ((n + TC_WT - 1) / TC_WT);
+    k_w_tiles<<<(unsigned)blocks, 256, smem, s>>>(src, dst, n, k, to_tiled);
     return cudaGetLastError();
 }
 

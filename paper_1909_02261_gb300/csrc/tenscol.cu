@@ -1358,17 +1358,36 @@ int tc_best(tc_ctx* c, int32_t* coloring, int64_t* conflicts, int64_t* equity, i
     return TC_OK;
 }
 
+// Device address of a page-locked host buffer (cudaHostAlloc or
+// cudaHostRegister memory, torch's pin_memory included), or null for
+// pageable memory: the weight conversions read and write page-locked
+// buffers directly, in whole lines, instead of staging them with a copy.
+static void* pinned_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int tc_get_state(tc_ctx* c, float* W, int64_t* t) {
     if (!c) return TC_ERR_ARG;
     if (!c->pop) return TC_ERR_STATE;
     DeviceGuard g(c->device);
     if (W) {
         if (fault("copy")) return TC_ERR_INJECTED;
-        // untile into the grad_S buffer (free between iterations), then copy
-        TC_CHECK(tc_launch_w_layout(c->d_W, c->d_Gbuf, c->D, c->n, c->k, false, c->stream));
-        c->launches += 1;
-        TC_CHECK(cudaMemcpyAsync(W, c->d_Gbuf, sizeof(float) * (size_t)c->D * c->n * c->k,
-                                 cudaMemcpyDeviceToHost, c->stream));
+        float* Wd = static_cast<float*>(pinned_device_ptr(W));
+        if (Wd && tc_launch_w_tiles(c->d_W, Wd, c->D, c->n, c->k, false, c->stream) == cudaSuccess) {
+            c->launches += 1;  // untiled straight into the page-locked buffer
+        } else {
+            (void)cudaGetLastError();
+            // untile into the grad_S buffer (free between iterations), then copy
+            TC_CHECK(tc_launch_w_layout(c->d_W, c->d_Gbuf, c->D, c->n, c->k, false, c->stream));
+            c->launches += 1;
+            TC_CHECK(cudaMemcpyAsync(W, c->d_Gbuf, sizeof(float) * (size_t)c->D * c->n * c->k,
+                                     cudaMemcpyDeviceToHost, c->stream));
+        }
     }
     if (t) {
         long long tv = 0;
@@ -1388,12 +1407,18 @@ static int set_state_common(tc_ctx* c, const float* W, const int64_t* t, cudaMem
     if (W) {
         if (fault("copy")) return TC_ERR_INJECTED;
         const float* src = W;
-        if (kind == cudaMemcpyHostToDevice) {  // through the grad_S buffer
-            TC_CHECK(cudaMemcpyAsync(c->d_Gbuf, W, sizeof(float) * (size_t)c->D * c->n * c->k, kind, c->stream));
-            src = c->d_Gbuf;
+        const float* Wd = kind == cudaMemcpyHostToDevice ? static_cast<const float*>(pinned_device_ptr(W)) : nullptr;
+        if (Wd && tc_launch_w_tiles(Wd, c->d_W, c->D, c->n, c->k, true, c->stream) == cudaSuccess) {
+            c->launches += 1;  // tiled straight from the page-locked buffer
+        } else {
+            (void)cudaGetLastError();
+            if (kind == cudaMemcpyHostToDevice) {  // through the grad_S buffer
+                TC_CHECK(cudaMemcpyAsync(c->d_Gbuf, W, sizeof(float) * (size_t)c->D * c->n * c->k, kind, c->stream));
+                src = c->d_Gbuf;
+            }
+            TC_CHECK(tc_launch_w_layout(src, c->d_W, c->D, c->n, c->k, true, c->stream));
+            c->launches += 1;
         }
-        TC_CHECK(tc_launch_w_layout(src, c->d_W, c->D, c->n, c->k, true, c->stream));
-        c->launches += 1;
     }
     if (t) {
         const long long tv = *t;

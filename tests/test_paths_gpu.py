@@ -19,7 +19,8 @@ def make_ctx(rp, ci, D, k, p, W, t):
     ctx = TensCol(0)
     ctx.tc_init_graph(len(rp) - 1, rp, ci)
     ctx.tc_init_population(1, D, k, p)
-    ctx.tc_set_state(W, t)
+    if W is not None:
+        ctx.tc_set_state(W, t)
     return ctx
 
 
@@ -84,3 +85,32 @@ def test_adjacency_walk_shapes(case):
     p = params(TC_ECP, stop_on_legal=0, nu=1e-3)
     with make_ctx(rp, ci, D, k, p, W, 17) as ctx:
         check_iteration(ctx, rp, ci, p, 17)
+
+
+@pytest.mark.parametrize("n,D,k", [(125, 20, 18), (1000, 7, 90), (97, 3, 33), (40, 2, 375), (33, 5, 1)])
+def test_state_round_trip_through_page_locked_buffers(n, D, k):
+    """tc_set_state / tc_get_state read and write page-locked host buffers
+    directly (one block per 32-row tile), pageable ones through a copy and
+    the element-wise conversion (also k = 375, whose tile does not fit the
+    block's shared memory): both must give back the weights bit for bit,
+    ragged last tiles included, and the same colours."""
+    torch = pytest.importorskip("torch")
+    rp, ci = inputs.gnp(n, 0.5, seed=n + k)
+    W = inputs.init_weights(D, n, k, 0.05, seed=D + k)
+    p = params(TC_KCOL, stop_on_legal=0)
+    Wp = torch.empty((D, n, k), dtype=torch.float32, pin_memory=True).numpy()
+    Wp[...] = W
+    with make_ctx(rp, ci, D, k, p, W, 3) as a, make_ctx(rp, ci, D, k, p, None, 0) as b:
+        b.tc_set_state(Wp, 3)
+        out = torch.empty((D, n, k), dtype=torch.float32, pin_memory=True).numpy()
+        out[...] = np.nan
+        b.tc_get_state(out)
+        assert np.array_equal(out, W)
+        back, t = a.tc_get_state()
+        assert t == 3 and np.array_equal(back, W)
+        assert np.array_equal(a.tc_evaluate(want_G=False, want_M=False)["colors"],
+                              b.tc_evaluate(want_G=False, want_M=False)["colors"])
+        # one step from either state gives the same weights
+        assert a.tc_step(1) == 1 and b.tc_step(1) == 1
+        b.tc_get_state(out)
+        assert np.array_equal(out, a.tc_get_state()[0])
