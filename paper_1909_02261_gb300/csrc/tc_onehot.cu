@@ -1011,7 +1011,8 @@ __device__ __forceinline__ bool class_ok(int j, int p0, int len, int k, int plen
     return true;
 }
 
-__device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
+// Returns the number of long classes.
+__device__ __forceinline__ int slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
                                           const float* xs, const uint32_t* zchunk, float nut, const float* panel,
                                           int k, int h, int lane, float* gtile, int nmax, int plen, int* err) {
     const int grp = lane >> 3, l8 = lane & 7;
@@ -1076,6 +1077,7 @@ __device__ __forceinline__ void slot_walk(const uint32_t* list, const int* of, c
         if (j >= 0)
             __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8), walk_result(a01, a23, nut * xs[j]));
     }
+    return nlong;
 }
 
 // Sparse form of the same sums, used when B vanishes off the edges (mu = 0:
@@ -1121,10 +1123,18 @@ __device__ __forceinline__ int neighbour_sums(const int* rowptr, const int* coli
 // tells them apart exactly: sg B_im >= 1 on edges (1 + lambda t (...) >= 1)
 // and sg B_im <= 0 off them (-mu t (...) <= 0, the diagonal, the padding
 // row), sg = -1 for the partitioning problems (whose B is negated), else 1.
+// half: 0 the whole class, 1 / 2 its first / second half (in 4-wide chunks).
 template <bool STG>
 __device__ __forceinline__ int own_class_conflicts(const uint32_t* pm, const int* of, int ci, const float* Bl,
-                                                   int bstride, float sg) {
-    const int s = STG ? of[ci] : __ldg(of + ci), e = STG ? of[ci + 1] : __ldg(of + ci + 1);
+                                                   int bstride, float sg, int half = 0) {
+    int s = STG ? of[ci] : __ldg(of + ci), e = STG ? of[ci + 1] : __ldg(of + ci + 1);
+    if (half) {
+        const int mid = s + 4 * ((e - s) >> 3);
+        if (half == 1)
+            e = mid;
+        else
+            s = mid;
+    }
     int conf = 0;
     for (int p = s; p < e; p += 4) {  // padded class: whole 4-wide chunks
         const uint4 v = STG ? *reinterpret_cast<const uint4*>(pm + p) : __ldg(reinterpret_cast<const uint4*>(pm + p));
@@ -1415,11 +1425,21 @@ __global__ void __launch_bounds__((CSR ? GSUM_CSR_WARPS : GSUM_MAX_WARPS) * 32, 
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
             if (GROUPED) {
-                slot_walk(ps, os, cs, xs, zc, nut, Bt, k, h, lane, P.Gbuf + ((size_t)d * nT + T) * k * 32, n,
-                          P.perm_stride, &st->err);
-                if (counter) {
+                const int nlong = slot_walk(ps, os, cs, xs, zc, nut, Bt, k, h, lane,
+                                            P.Gbuf + ((size_t)d * nT + T) * k * 32, n, P.perm_stride, &st->err);
+                // with classes of 32 entries or more the rows' own classes are
+                // mostly long as well: both warps count half of each (the
+                // partitioning problems keep most vertices in a few classes,
+                // where warp 1 counting whole classes took about as long as the
+                // walk itself); tc_evaluate's per-vertex counts come whole
+                // from warp 1
+                const bool split = nlong > 0 && P.dbg_gamma == nullptr;
+                if (counter || split) {
                     conf = 0;
-                    if (live) conf = own_class_conflicts<true>(ps, os, ci, Bt + lane, 32, gs);
+                    if (live) {
+                        const int cc = counter ? ci : (int)__ldg(P.c + (size_t)d * n + i0 + lane);
+                        conf = own_class_conflicts<true>(ps, os, cc, Bt + lane, 32, gs, split ? 1 + h : 0);
+                    }
                 }
             } else if (CSR) {
                 if (cstaged) {
