@@ -1011,10 +1011,30 @@ __device__ __forceinline__ bool class_ok(int j, int p0, int len, int k, int plen
     return true;
 }
 
-// Returns the number of long classes.
+// The class sum of the four rows plus nu t E_dj, plus in the dense forms
+// gs times the gamma-matrix entries of the four rows (gam: colour j of rows
+// 4 l8 .. 4 l8 + 3 at gam + j gstride + 4 l8, four uint16).
+template <bool GM>
+__device__ __forceinline__ float4 class_result(float4 r, float ex, const uint16_t* gam, int gstride, float gs, int j,
+                                               int l8) {
+    r = make_float4(r.x + ex, r.y + ex, r.z + ex, r.w + ex);
+    if (GM) {
+        const uint2 g = __ldg(reinterpret_cast<const uint2*>(gam + (size_t)j * gstride + 4 * l8));
+        r.x += gs * (float)(g.x & 0xffffu);
+        r.y += gs * (float)(g.x >> 16);
+        r.z += gs * (float)(g.y & 0xffffu);
+        r.w += gs * (float)(g.y >> 16);
+    }
+    return r;
+}
+
+// Returns the number of long classes.  GM: the dense forms, whose pair
+// matrix leaves out the A.S term; it is added from the gamma matrix (gam).
+template <bool GM>
 __device__ __forceinline__ int slot_walk(const uint32_t* list, const int* of, const uint16_t* cord,
                                           const float* xs, const uint32_t* zchunk, float nut, const float* panel,
-                                          int k, int h, int lane, float* gtile, int nmax, int plen, int* err) {
+                                          int k, int h, int lane, float* gtile, int nmax, int plen, int* err,
+                                          const uint16_t* gam, int gstride, float gs) {
     const int grp = lane >> 3, l8 = lane & 7;
     const uint32_t colb = smem_u32(panel) + 16u * (uint32_t)l8, lists = smem_u32(list), zcs = smem_u32(zchunk);
     int nlong = 0;
@@ -1048,11 +1068,9 @@ __device__ __forceinline__ int slot_walk(const uint32_t* list, const int* of, co
         r.y += __shfl_xor_sync(0xffffffffu, r.y, 16);
         r.z += __shfl_xor_sync(0xffffffffu, r.z, 16);
         r.w += __shfl_xor_sync(0xffffffffu, r.w, 16);
-        if (grp == 0) {
-            const float ex = nut * xs[j];
+        if (grp == 0)
             __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8),
-                   make_float4(r.x + ex, r.y + ex, r.z + ex, r.w + ex));
-        }
+                   class_result<GM>(r, nut * xs[j], gam, gstride, gs, j, l8));
     }
     // the other classes four side by side: in slot s, group g of warp h
     // walks the class at position nlong + 8 s + 4 h + g (quads of nearly
@@ -1075,7 +1093,8 @@ __device__ __forceinline__ int slot_walk(const uint32_t* list, const int* of, co
         uint64_t a01 = 0ull, a23 = 0ull;  // +0.0f pairs
         walk_chunks(list, zchunk, lists, zcs, colb, p0, 0, len, m, nmax, err, a01, a23);
         if (j >= 0)
-            __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8), walk_result(a01, a23, nut * xs[j]));
+            __stcg(reinterpret_cast<float4*>(gtile + j * 32 + 4 * l8),
+                   class_result<GM>(walk_result(a01, a23, -0.0f), nut * xs[j], gam, gstride, gs, j, l8));
     }
     return nlong;
 }
@@ -1237,8 +1256,10 @@ __global__ void __launch_bounds__((CSR ? GSUM_CSR_WARPS : GSUM_MAX_WARPS) * 32, 
         pdl_wait();
         return;
     }
-    // the grouped walk: staged lists, the B panel in shared memory, the one-hot form
-    constexpr bool GROUPED = STG && BTS && !DN && !CSR;
+    // the grouped walk: staged lists, the B panel in shared memory, one
+    // colour per vertex (the multicolouring keeps the per-warp class loop)
+    constexpr bool GROUPED_OK = STG && BTS && !CSR;
+    const bool GROUPED = GROUPED_OK && !(DN && P.cm);
     extern __shared__ __align__(1024) float sm[];
     __shared__ __align__(8) uint64_t s_bbar;
     __shared__ __align__(8) uint64_t s_rbar[GSUM_MAX_WARPS / 2][2];  // dbuf: the record buffers' barriers
@@ -1424,9 +1445,19 @@ __global__ void __launch_bounds__((CSR ? GSUM_CSR_WARPS : GSUM_MAX_WARPS) * 32, 
             const bool counter = !CSR && h == (STG ? 1 : 0);  // the warp that counts the conflicts
             const int ci = counter && live ? (int)__ldg(P.c + (size_t)d * n + i0 + lane) : 0;  // ahead of use
             int conf = -1;  // gamma_d(i0 + lane), counted by one warp of the item
-            if (GROUPED) {
-                const int nlong = slot_walk(ps, os, cs, xs, zc, nut, Bt, k, h, lane,
-                                            P.Gbuf + ((size_t)d * nT + T) * k * 32, n, P.perm_stride, &st->err);
+            if (GROUPED_OK && GROUPED) {
+                int nlong;
+                if (DN && P.G16) {  // the dense forms: A.S and gamma_d(i) from the gamma matrix
+                    nlong = slot_walk<true>(ps, os, cs, xs, zc, nut, Bt, k, h, lane,
+                                            P.Gbuf + ((size_t)d * nT + T) * k * 32, n, P.perm_stride, &st->err,
+                                            P.G16 + tc_gamma_index(d, i0, 0, P.n_pad, k), P.n_pad, gs);
+                    if (counter) conf = live ? (int)__ldg(grow + (size_t)ci * gstride) : 0;
+                    nlong = 0;  // (no own-class walks to share)
+                } else {
+                    nlong = slot_walk<false>(ps, os, cs, xs, zc, nut, Bt, k, h, lane,
+                                             P.Gbuf + ((size_t)d * nT + T) * k * 32, n, P.perm_stride, &st->err,
+                                             nullptr, 0, gs);
+                }
                 // with classes of 32 entries or more the rows' own classes are
                 // mostly long as well: both warps count half of each (the
                 // partitioning problems keep most vertices in a few classes,
@@ -1434,7 +1465,7 @@ __global__ void __launch_bounds__((CSR ? GSUM_CSR_WARPS : GSUM_MAX_WARPS) * 32, 
                 // walk itself); tc_evaluate's per-vertex counts come whole
                 // from warp 1
                 const bool split = nlong > 0 && P.dbg_gamma == nullptr;
-                if (counter || split) {
+                if (!(DN && P.G16) && (counter || split)) {
                     conf = 0;
                     if (live) {
                         const int cc = counter ? ci : (int)__ldg(P.c + (size_t)d * n + i0 + lane);
