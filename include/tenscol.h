@@ -156,9 +156,13 @@ int tc_step(tc_ctx *ctx, int64_t n_iters, int64_t *iters_done);
 int tc_best(tc_ctx *ctx, int32_t *coloring, int64_t *conflicts, int64_t *equity,
             int32_t *individual, int64_t *iteration);
 
-/* Copies W (D*n*k floats) and the iteration counter t out / in.  Setting
- * the state also recomputes the assignment S (Step 1) and clears the stop
- * flag; the best-so-far is kept.  Either pointer may be NULL to skip it. */
+/* Copies W (D*n*k floats, host memory, [d][i][j] order) and the iteration
+ * counter t out / in.  Setting the state also recomputes the assignment S
+ * (Step 1) and clears the stop flag; the best-so-far is kept.  Either
+ * pointer may be NULL to skip it.  Page-locked W buffers (cudaHostAlloc,
+ * cudaHostRegister) are read or written by the device directly, one block
+ * per 32-row tile; pageable ones go through a staging copy.  Both return
+ * once the transfer is complete. */
 int tc_get_state(tc_ctx *ctx, float *W, int64_t *t);
 int tc_set_state(tc_ctx *ctx, const float *W, const int64_t *t);
 
