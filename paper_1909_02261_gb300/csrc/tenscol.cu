@@ -1378,10 +1378,11 @@ int tc_get_state(tc_ctx* c, float* W, int64_t* t) {
     if (W) {
         if (fault("copy")) return TC_ERR_INJECTED;
         float* Wd = static_cast<float*>(pinned_device_ptr(W));
+        // (a null address, a tile beyond 48 KB or a failed launch: the staged path;
+        // the launcher has taken the error of its launch)
         if (Wd && tc_launch_w_tiles(c->d_W, Wd, c->D, c->n, c->k, false, c->stream) == cudaSuccess) {
             c->launches += 1;  // untiled straight into the page-locked buffer
         } else {
-            (void)cudaGetLastError();
             // untile into the grad_S buffer (free between iterations), then copy
             TC_CHECK(tc_launch_w_layout(c->d_W, c->d_Gbuf, c->D, c->n, c->k, false, c->stream));
             c->launches += 1;
@@ -1411,7 +1412,6 @@ static int set_state_common(tc_ctx* c, const float* W, const int64_t* t, cudaMem
         if (Wd && tc_launch_w_tiles(Wd, c->d_W, c->D, c->n, c->k, true, c->stream) == cudaSuccess) {
             c->launches += 1;  // tiled straight from the page-locked buffer
         } else {
-            (void)cudaGetLastError();
             if (kind == cudaMemcpyHostToDevice) {  // through the grad_S buffer
                 TC_CHECK(cudaMemcpyAsync(c->d_Gbuf, W, sizeof(float) * (size_t)c->D * c->n * c->k, kind, c->stream));
                 src = c->d_Gbuf;
