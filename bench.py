@@ -466,9 +466,19 @@ def run_ours(args):
             launches = ctx.tc_launch_count() - launches0
             kms, kcnt = ctx.tc_kernel_times()
             ctx.tc_set_timing(False)
+        time_steps.last_step_ms = step_ms
         return float(sum(step_ms)), kms, kcnt, launches, wall, clocks
 
     total_ms, _, _, launches, wall, clocks = time_steps(args.steps, args.warmup, True, False)
+    # the timed steps by their phase in the smoothing cycle (Step 4-iv divides
+    # W by rho after the update of every iteration t with t + 1 = 0 mod
+    # nb_iter; the next update then moves many colours at once): step i of
+    # the timed region is iteration t = warmup + i
+    nb = int(p.nb_iter)
+    phase_ms = {}
+    for i, ms in enumerate(time_steps.last_step_ms):
+        phase_ms.setdefault((args.warmup + i) % nb, []).append(ms)
+    phases = {f"t mod {nb} = {q}": round(1e3 * sum(v) / len(v), 2) for q, v in sorted(phase_ms.items())}
     # per-kernel CUDA-event times on the library's stream, same workload
     ksteps = min(args.steps, 1000)
     kernel_pass_ms, kms, kcnt, _, _, _ = time_steps(ksteps, 3, False, True)
@@ -655,6 +665,7 @@ def run_ours(args):
         "variants": variants,
         "configs": configs,
         "kernels": kernels,
+        "us_per_step_by_phase": phases,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "individual-steps/s", "h2d_bytes_per_step": h2d,
