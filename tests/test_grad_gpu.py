@@ -1,4 +1,4 @@
-"""The hand-written backward (the benchmark spec (b)) on the GPU.
+"""The hand-written backward of the loss (eq. 7) on the GPU.
 
 * Straight-through path (eq. 12-13 at the one-hot S): the backward equals the
   update the fused step applies, bit for bit (W_next = W - eta gW with one
